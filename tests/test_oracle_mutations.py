@@ -1,0 +1,115 @@
+"""Planted mistakes in the oracle (CPU only): each must make a pin fail.
+
+A plausible slip -- a dropped term, a wrong sign or index, a transposed
+operand -- is patched into the oracle for the duration of one test, and the
+pin that should catch it is run and expected to fail.
+"""
+import inspect
+
+import numpy as np
+import pytest
+
+import oracle.minres as om
+import oracle.operator as oo
+import oracle.recycle as orc
+from tests import test_oracle_minres as tm
+from tests import test_oracle_operator as to
+from tests import test_oracle_recycle as tr
+
+
+def _expect_fail(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_wrong_sign_in_gradient_adjoint_is_caught(monkeypatch):
+    good = oo.Operator.grad_adjoint
+    monkeypatch.setattr(oo.Operator, "grad_adjoint", lambda self, q: -good(self, q))
+    _expect_fail(to.test_gradient_and_adjoint_match_dense, (7, 11))
+
+
+def test_wrong_boundary_in_blur_is_caught(monkeypatch):
+    def periodic(x, taps, axis):
+        r = (len(taps) - 1) // 2
+        return sum(taps[a + r] * np.roll(x, -a, axis=axis) for a in range(-r, r + 1))
+    monkeypatch.setattr(oo, "_toeplitz_apply", periodic)
+    _expect_fail(to.test_blur_and_adjoint_match_dense_kronecker, (7, 11), 2)
+
+
+def test_untransposed_blur_adjoint_is_caught(monkeypatch):
+    monkeypatch.setattr(oo.Operator, "blur_adjoint", lambda self, y: self.blur(y))
+    _expect_fail(to.test_blur_adjoint_is_the_transpose_for_asymmetric_taps)
+
+
+def test_dropped_weight_in_E_is_caught(monkeypatch):
+    monkeypatch.setattr(oo.Operator, "apply_E", lambda self, x, w: self.grad_adjoint(self.grad(x)))
+    _expect_fail(to.test_shifted_operator_matches_dense_and_is_spd, (8, 8))
+
+
+def _mutated_minres(old, new):
+    """recycled_minres with one line of its recurrence replaced."""
+    src = inspect.getsource(om.recycled_minres)
+    assert old in src
+    ns = dict(vars(om))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    return ns["recycled_minres"]
+
+
+@pytest.mark.parametrize("old,new", [
+    ("eps = sn2 * beta", "eps = sn1 * beta"),                     # wrong rotation index
+    ("delta = cs1 * dbar + sn1 * alpha", "delta = cs1 * dbar - sn1 * alpha"),   # wrong sign
+    ("d = (v - delta * d1 - eps * d2) / gamma", "d = (v - delta * d1) / gamma"),  # dropped term
+])
+def test_planted_minres_recurrence_mistakes_are_caught(monkeypatch, old, new):
+    monkeypatch.setattr(tm, "recycled_minres", _mutated_minres(old, new))
+    _expect_fail(tm.test_plain_minres_matches_scipy_iterates, 12)
+
+
+def test_dropped_recycle_coupling_is_caught(monkeypatch):
+    real = om.recycled_minres
+
+    def no_coupling(op_apply, r, K, tol_abs, maxit, keep=0, reorth=False):
+        res = real(op_apply, r, K, tol_abs, maxit, keep, reorth)
+        if K is not None:
+            res.z = K.T @ r          # forgets - K^T Op V_m y
+        return res
+    monkeypatch.setattr(tm, "recycled_minres", no_coupling)
+    _expect_fail(tm.test_recycled_minres_is_least_squares_over_U_and_Krylov, 3, 6)
+
+
+def test_dropped_quadratic_term_in_orthupdate_is_caught(monkeypatch):
+    real_eye = np.eye
+
+    def guesses_without_N(Ut, AU, EU, b, gammas, gamma_star):
+        B = AU + gamma_star * EU
+        K, R = np.linalg.qr(B)
+        EUi = np.linalg.solve(R.T, EU.T).T
+        Mm = K.T @ EUi
+        C = np.zeros((Ut.shape[1], len(gammas)))
+        X0 = np.zeros((len(gammas), Ut.shape[0]))
+        R0 = np.zeros_like(X0)
+        for l, gl in enumerate(gammas):
+            dl = gl - gamma_star
+            Sm = real_eye(Ut.shape[1]) + dl * (Mm + Mm.T)          # no d^2 N
+            q = np.linalg.solve(Sm, K.T @ b + dl * EUi.T @ b)
+            c = np.linalg.solve(R, q)
+            C[:, l], X0[l] = c, Ut @ c
+            R0[l] = b - (AU @ c + gl * (EU @ c))
+        return C, X0, R0
+    monkeypatch.setattr(tr, "principal_guesses", guesses_without_N)
+    _expect_fail(tr.test_principal_guess_is_the_least_squares_minimiser_over_the_principal_space)
+
+
+def test_largest_instead_of_smallest_ritz_vectors_is_caught(monkeypatch):
+    def largest(Ah, Eh, gamma, nJ):
+        H = Ah + gamma * Eh
+        _, Wt = np.linalg.eigh(0.5 * (H + H.T))
+        return Wt[:, ::-1][:, :nJ]
+    monkeypatch.setattr(tr, "interior_ritz", largest)
+    _expect_fail(tr.test_interior_ritz_on_the_full_space_gives_the_smallest_eigenvectors)
+
+
+def test_stabilize_without_threshold_is_caught(monkeypatch):
+    real = orc.stabilize
+    monkeypatch.setattr(tr, "stabilize", lambda Ut, p_max, ratio=1e10: real(Ut, p_max, ratio=1e300))
+    _expect_fail(tr.test_stabilize_drops_near_dependent_columns_at_ratio_1e10)
