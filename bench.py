@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the recycled shifted solves on GB300.
+
+Workload (one step): the 512 x 512 image of the single-image workload
+(sigma 2.5, radius 8, 2 % noise), 16 shifts log-spaced over 1e-5..1, 5 outer
+reweighting steps (k = 0: principal space from two MINRES solves; k >= 1:
+update by Eq. delta; the IRN weights from the L-curve corner), principal
+recycle dimension 40, 8 local Ritz vectors, every system solved to a true
+relative residual of 1e-8. All of it runs through librecyc's C ABI.
+
+Metric: shifted solves per second (and matvecs per second) over the whole job,
+inputs resident in HBM; `e2e` repeats it with the data image copied in from
+pinned host memory and every step's solutions copied back. `roofline` is the
+dominant kernel's achieved rate from CUDA events around its launches in the
+timed region; `cpu_baseline` is the FP64 oracle on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "shifted solves/sec & matvecs/sec at rel. residual 1e-8; HBM GB/s vs roofline"
+FP64_PEAK_GFLOPS = 152 * 2070e6 * 4 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2070 MHz (nominal 1.25 TF)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--workload", default="C2")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(wl, precision):
+    return {
+        "workload": f"{wl.height}x{wl.width} image, sigma {wl.sigma}, radius {wl.radius}, "
+                    f"{int(wl.eta * 100)}% noise; {wl.M} shifts 1e{int(wl.log_lo)}..1e{int(wl.log_hi)}; "
+                    f"{wl.K} outer IRN steps; p={wl.p}, |J|={wl.n_ritz_local}; tol {wl.tol:g}",
+        "n": wl.n, "shifts": wl.M, "outer_steps": wl.K, "p": wl.p, "local_ritz": wl.n_ritz_local,
+        "precision": precision,
+        "l2": "flushed between timed steps (256 MB write); one step's working set is 0.3-0.6 GB",
+        "parallelism": "replicas (one independent workload per GPU)",
+    }
+
+
+def oracle_counts(name):
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_counts_{name}.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def oracle_matvec_rate(wl, seconds):
+    """FP64 oracle matvecs per second on this workload's operator (host cores)."""
+    import numpy as np
+
+    import synth
+    from oracle.operator import Operator, make_data
+    op = Operator(wl.height, wl.width, wl.sigma, wl.radius)
+    x = synth.piecewise_constant_image(wl.height, wl.width, wl.seed)
+    z = synth.noise_direction(wl.height, wl.width, wl.seed)
+    d, b = make_data(op, x, z, wl.eta)
+    w = synth.random_weights(wl.n, 1, lo=1.0, hi=1000.0)
+    v = b.copy()
+    count = 0
+    t0 = time.perf_counter()
+    while True:
+        v = op.apply(v, 1e-3, w)
+        v /= np.linalg.norm(v)
+        count += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return count / el, count, el
+
+
+def cpu_baseline(wl, name, seconds):
+    rate, count, el = oracle_matvec_rate(wl, seconds)
+    oc = oracle_counts(name)
+    solves_per_s = rate * oc["total_solves"] / oc["total_matvecs"]
+    return {
+        "value": solves_per_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        "matvecs_per_s": rate,
+        "sample": (f"FP64 NumPy oracle: {count} matvecs of this workload's operator in {el:.1f} s "
+                   f"(1 thread), scaled by the oracle's own count for the whole workload "
+                   f"({oc['total_matvecs']} matvecs for {oc['total_solves']} solves, "
+                   f"tests/golden/oracle_counts_{name}.json)"),
+    }, oc
+
+
+def clocks_start(dev_index):
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    os.close(fd)
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
+                              "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except (FileNotFoundError, OSError):
+        return None, path
+    return p, path
+
+
+def clocks_stop(p, path):
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [s.strip() for s in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, val in zip(names, parts[5:9]):
+            if val.lower().startswith("active"):
+                reasons.add(nm)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Runner:
+    """One replica of the workload on one GPU, through the C ABI."""
+
+    def __init__(self, wl, precision, dev):
+        import numpy as np
+        import torch
+
+        import synth
+        from paper_2306_15049_gb300 import recyc
+        from paper_2306_15049_gb300.workloads import desc_for
+        self.torch, self.recyc, self.wl, self.dev = torch, recyc, wl, dev
+        self.desc = desc_for(wl, precision=recyc.RS_MIXED if precision == "mixed" else recyc.RS_FP64)
+        x = synth.piecewise_constant_image(wl.height, wl.width, wl.seed).reshape(-1)
+        z = synth.noise_direction(wl.height, wl.width, wl.seed).reshape(-1)
+        xt = torch.tensor(x, dtype=torch.float64, device=dev)
+        zt = torch.tensor(z, dtype=torch.float64, device=dev)
+        self.d = torch.empty_like(xt)
+        scratch = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+        recyc.rs_synthesize_data(self.desc[0], xt, zt, wl.eta, self.d, scratch)
+        self.workspace = torch.empty(recyc.rs_workspace_bytes(self.desc[0]), dtype=torch.uint8, device=dev)
+        self.X = torch.empty(wl.M, wl.n, dtype=torch.float64, device=dev)
+        self.w = torch.ones(2 * wl.n, dtype=torch.float64, device=dev)
+        self.w_next = torch.empty_like(self.w)
+        self.d_host = self.d.cpu().pin_memory()
+        self.w0_host = torch.ones(2 * wl.n, dtype=torch.float64).pin_memory()
+        self.X_host = torch.empty(wl.M, wl.n, dtype=torch.float64).pin_memory()
+        self.timing = {"launches": [0, 0], "ms": [0.0, 0.0], "pixels": [0, 0]}
+        self.last = None
+        self.np = np
+
+    def step(self, timing=False, e2e=False):
+        """The whole workload: K outer steps of all M shifts. Returns work counts."""
+        torch, recyc, wl = self.torch, self.recyc, self.wl
+        if e2e:
+            self.d.copy_(self.d_host, non_blocking=True)
+            self.w.copy_(self.w0_host, non_blocking=True)
+        else:
+            self.w.fill_(1.0)
+        P = recyc.Problem(self.desc, self.d, workspace=self.workspace)
+        if timing:
+            P.rs_set_timing(True)
+        solves, worst, iters = 0, 0.0, 0
+        for k in range(wl.K):
+            P.rs_set_weights(self.w)
+            P.rs_update_recycle(recyc.RS_INIT if k == 0 else recyc.RS_UPDATE)
+            stats = P.rs_solve_shifts(self.X)
+            if e2e:
+                self.X_host.copy_(self.X, non_blocking=True)
+            solves += wl.M
+            worst = max(worst, max(s["relres_true"] for s in stats))
+            iters += sum(s["iters"] for s in stats)
+            if k + 1 < wl.K:
+                _, _, ls = P.rs_lcurve(self.X, wl.M)
+                P.rs_irn_weights(self.X[ls], wl.beta, self.w_next)
+                self.w, self.w_next = self.w_next, self.w
+        info = P.rs_get_info()
+        if timing:
+            t = P.rs_get_timing()
+            for c in range(2):
+                self.timing["launches"][c] += t["launches"][c]
+                self.timing["ms"][c] += t["ms"][c]
+                self.timing["pixels"][c] += t["pixels"][c]
+        P.close()
+        self.last = {"solves": solves, "matvecs": info["matvecs_total"], "worst_relres": worst,
+                     "iters": iters, "nc": info["nc"], "kernel_launches": info["kernel_launches"]}
+        return self.last
+
+
+def timed(runner, steps, flush, timing=False, e2e=False):
+    """Run `steps` steps; each bracketed by CUDA events; L2 flushed in between."""
+    torch = runner.torch
+    stream = torch.cuda.current_stream(runner.dev)
+    tot_ms, solves, mvs = 0.0, 0, 0
+    launches0 = None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(runner.dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = runner.step(timing=timing, e2e=e2e)
+        b.record(stream)
+        torch.cuda.synchronize(runner.dev)
+        tot_ms += a.elapsed_time(b)
+        solves += r["solves"]
+        mvs += r["matvecs"]
+        if launches0 is None:
+            launches0 = r["kernel_launches"]
+    return tot_ms, solves, mvs
+
+
+def main():
+    args = parse()
+    import synth
+    wl = synth.WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = workload_config(wl, args.precision)
+
+    if args.impl == "reference":
+        # the FP64 oracle on the host cores; under torchrun only rank 0 works
+        if rank != 0:
+            return
+        rate_w, _, _ = oracle_matvec_rate(wl, 1.0) if args.warmup > 0 else (0, 0, 0)
+        for _ in range(max(0, args.warmup - 1)):
+            oracle_matvec_rate(wl, 0.5)
+        oc = oracle_counts(args.workload)
+        per = max(2.0, min(20.0, 90.0 / max(1, args.steps)))
+        rates = []
+        samples = 0
+        for _ in range(args.steps):
+            r, c, el = oracle_matvec_rate(wl, per)
+            rates.append(r)
+            samples += c
+        rate = sum(rates) / len(rates)
+        value = rate * oc["total_solves"] / oc["total_matvecs"]
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * oc["total_matvecs"] / rate, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(config, precision="fp64 (oracle)"),
+            "matvecs_per_s": rate,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} samples of {per:.0f} s of oracle FP64 matvecs "
+                                       f"({samples} matvecs, 1 thread) scaled by the oracle's own "
+                                       f"{oc['total_matvecs']} matvecs for {oc['total_solves']} solves; "
+                                       "ms_per_step is that extrapolation"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    runner = Runner(wl, args.precision, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(3, args.warmup)):
+        runner.step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    props = torch.cuda.get_device_properties(dev)
+    smi_id = str(getattr(props, "uuid", local))
+    if smi_id and not smi_id.startswith("GPU-") and len(smi_id) > 8:
+        smi_id = "GPU-" + smi_id
+    launches_before = runner.last["kernel_launches"]
+    clk_p, clk_path = clocks_start(smi_id)
+    ms, solves, mvs = timed(runner, args.steps, flush, timing=True)
+    clocks = clocks_stop(clk_p, clk_path)
+    launches_timed = runner.last["kernel_launches"] - launches_before
+    run_stats = dict(runner.last)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        cnt = torch.tensor([solves, mvs], dtype=torch.float64, device=dev)
+        dist.all_reduce(cnt)
+        solves, mvs = int(cnt[0].item()), int(cnt[1].item())
+    ms_per_step = ms / args.steps
+    value = solves / (ms / 1000.0)
+
+    # end to end: host data in, every step's solutions out
+    runner.step(e2e=True)
+    e_ms, e_solves, _ = timed(runner, args.steps, flush, e2e=True)
+    if dist:
+        t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+        e_solves *= world
+    e2e = {"value": e_solves / (e_ms / 1000.0), "unit": "solves/s",
+           "h2d_bytes_per_step": 8 * (wl.n + 2 * wl.n),
+           "d2h_bytes_per_step": 8 * wl.K * wl.M * wl.n}
+
+    # roofline of the dominant kernel (live CUDA-event times from the timed region)
+    peaks, peak_kind = measured_peaks()
+    tm = runner.timing
+    cat = 0 if tm["ms"][0] >= tm["ms"][1] else 1
+    launches = max(1, tm["launches"][cat])
+    avg_s = tm["ms"][cat] / 1000.0 / launches
+    pix = tm["pixels"][cat] / launches
+    fp32_krylov = (cat == 0 and args.precision == "mixed")
+    if fp32_krylov:
+        bytes_per = 16.0 * pix                      # read x (4n) + w (8n), write y (4n)
+        achieved = bytes_per / avg_s / 1e9
+        roof = {"kernel": "k_op_apply<float> (Krylov matvec)", "bound": "hbm", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": bytes_per}
+    else:
+        flops_per = (8.0 * (2 * wl.radius + 1) + 10.0) * pix
+        achieved = flops_per / avg_s / 1e9
+        name = "k_op_apply<double> (FP64 residual matvec)" if cat == 1 else "k_op_apply<double> (Krylov matvec)"
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2070 MHz",
+                "algorithmic_flops_per_launch": flops_per}
+    roof["launches"] = tm["launches"][cat]
+    roof["avg_launch_us"] = avg_s * 1e6
+    roof["kernel_time_share_of_step"] = tm["ms"][cat] / ms if ms > 0 else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 Krylov + f64 refinement" if args.precision == "mixed" else "f64",
+        "data": "synthetic", "config": config,
+        "matvecs_per_s": mvs / (ms / 1000.0),
+        "run": {"matvecs_per_step": run_stats["matvecs"], "iters_per_step": run_stats["iters"],
+                "worst_true_relres": run_stats["worst_relres"], "n_c": run_stats["nc"]},
+        # kernels the library launched inside the timed region (its own counter)
+        "gpu_launches": int(launches_timed), "clocks": clocks, "roofline": roof, "e2e": e2e,
+    }
+
+    if not args.no_fp64_compare and args.precision == "mixed":
+        r64 = Runner(wl, "fp64", dev)
+        r64.step()
+        f_ms, f_solves, f_mvs = timed(r64, 1, flush)
+        line["fp64_gpu"] = {"value": f_solves / (f_ms / 1000.0), "unit": "solves/s",
+                            "ms_per_step": f_ms, "matvecs_per_s": f_mvs / (f_ms / 1000.0),
+                            "worst_true_relres": r64.last["worst_relres"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(wl, args.workload, args.cpu_seconds)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

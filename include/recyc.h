@@ -1,0 +1,211 @@
+/*
+ * recyc.h -- C ABI of the GB300 library for recycled Krylov solves of the
+ * shifted systems  (A + gamma_l E_k) x^(k,l) = b,  l = 1..M,  k = 0..K
+ * (Kilmer & de Sturler, "Subspace Recycling for Sequences of Shifted Systems
+ * with Applications in Image Recovery", Section 1 Eq. seqsys, Section 4
+ * Eq. shift).
+ *
+ *   A   = H^T H, H a zero-boundary separable Gaussian blur of one image
+ *         (Section 2.1 Eq. blkeqn; the symmetric Gaussian blur of Section 8.2);
+ *   E_k = L^T W_k L, L = [D_x; D_y] forward differences with a zero last
+ *         column / row, W_k = diag(w), w of length 2n ordered [w_x; w_y];
+ *   b   = H^T d for a data image d.
+ *
+ * Conventions (all entry points):
+ *  - Images are row-major, x[i * width + j], n = height * width.
+ *  - Every pointer named *_dev is a device pointer on the current CUDA device;
+ *    *_host pointers are host memory. The caller owns every buffer, the
+ *    workspace and the stream, and keeps them valid until the call returns
+ *    (device buffers: until the work queued on the stream has finished).
+ *  - The library never allocates device memory: all device state lives in
+ *    the caller's workspace of rs_workspace_bytes() bytes.
+ *  - Work is queued on the problem's stream. Calls that report results to
+ *    the host (stats, counts) synchronise that stream.
+ *  - A problem is not thread-safe; use one problem per stream.
+ *  - Every call returns an rs_status; on failure rs_last_error() describes it.
+ *    Inputs are validated before any work is queued (RS_EINVAL).
+ */
+#ifndef RECYC_H
+#define RECYC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rs_problem rs_problem;   /* opaque, owned by the library */
+
+typedef enum {
+  RS_OK = 0,
+  RS_EINVAL = 1,       /* invalid argument or size */
+  RS_ENOCONV = 2,      /* a shift hit maxit; its best x and stats are still written */
+  RS_EBREAKDOWN = 3,   /* a small dense factorisation failed (not SPD / singular) */
+  RS_ENOTREADY = 4,    /* called out of order (e.g. solve before update_recycle) */
+  RS_ECUDA = 5,        /* a CUDA runtime error */
+  RS_ENOMEM = 6        /* workspace too small */
+} rs_status;
+
+typedef enum {
+  RS_FP64 = 0,         /* all vectors, matvecs and reductions in FP64 */
+  RS_MIXED = 1         /* FP32 vectors/matvecs/Krylov, FP64 Gram, small solves and
+                          iterative-refinement residuals; X is FP64 */
+} rs_precision;
+
+typedef enum { RS_INIT = 0, RS_UPDATE = 1 } rs_recycle_mode;
+
+/* Problem description. Index fields are 1-based like the paper's index table
+ * (Section 5.5): I_split (the left/right shift groups, Section 5.4), i1, i2
+ * (the two systems seeding the principal space, Section 5.1), i_star (gamma_*
+ * of Eq. establishU), l_c (the correction system of Eq. delta), J_L, J_R
+ * (the shifts whose Ritz vectors seed the local spaces, Algorithm
+ * updatelocalV2). */
+typedef struct {
+  int height, width;       /* image size, n = height * width >= 1 */
+  double sigma;            /* Gaussian blur standard deviation (> 0) */
+  int radius;              /* blur half-width r, 0 <= r <= 16 */
+  int M;                   /* number of shifts, 1 <= M <= 256 */
+  const double* gammas_host; /* M shifts, strictly increasing, > 0 (copied) */
+  double tol;              /* relative residual tolerance ||b - Op x|| / ||b|| */
+  int maxit;               /* MINRES step cap per solve (> 0) */
+  int p_max;               /* principal recycle dimension cap n_c <= p_max <= 110 */
+  int a_ritz;              /* Lanczos vectors kept from the gamma_i1 solve (all -> V_i1) */
+  int b_ritz;              /* Ritz vectors kept from the gamma_i2 solve (smallest) */
+  int n_ritz_local;        /* |J|, Ritz vectors per local space, 0 <= |J| <= 14 */
+  int vnew_cap;            /* MINRES steps for V^(new) (Section 5.2; <= 100) */
+  int I_split, i1, i2, i_star, l_c, J_L, J_R;
+  int precision;           /* rs_precision */
+  int batched_local;       /* 0: paper's chain g^(k,l-1); 1: g^(k-1,l-1) instead */
+} rs_problem_desc;
+
+/* Per-shift results of rs_solve_shifts. */
+typedef struct {
+  int iters;               /* recycled MINRES steps (all refinement sweeps) */
+  int matvecs;             /* operator applications for this shift */
+  int local_dim;           /* columns of K_l after drops */
+  int sweeps;              /* FP64 refinement sweeps (RS_MIXED), else 1 */
+  double relres0;          /* ||r0|| / ||b|| of the principal initial guess */
+  double relres_est;       /* MINRES least-squares residual / ||b|| */
+  double relres_true;      /* ||b - (A + gamma E) x|| / ||b||, recomputed in FP64 */
+  int status;              /* rs_status of this shift */
+} rs_solve_stats;
+
+/* Per-problem information (rs_get_info). */
+typedef struct {
+  int n;                   /* pixels */
+  int k;                   /* current outer step (-1 before the first set_weights) */
+  int nc;                  /* principal recycle dimension n_c after stabilize */
+  long long matvecs_total; /* all operator applications so far */
+  long long matvecs_overhead; /* principal-space construction and images */
+  int ld;                  /* leading dimension of device blocks (elements) */
+  long long kernel_launches; /* CUDA kernels launched by the library in this process */
+} rs_info;
+
+/* Per-kernel device time, gathered with CUDA events around every launch of
+ * the two matvec kernels while timing is on (rs_set_timing). Index 0: the
+ * Krylov matvec (A + gamma E) v in the working precision; index 1: the FP64
+ * matvec of the true / refinement residual. Launches of a solve that had
+ * already stopped (no-ops) are not counted. */
+typedef struct {
+  long long launches[2];
+  double ms[2];
+  long long pixels[2];     /* pixels processed by the counted launches */
+} rs_timing;
+
+/* Bytes of device workspace a problem with this description needs. Returns 0
+ * for an invalid description. */
+size_t rs_workspace_bytes(const rs_problem_desc* desc);
+
+/* Create a problem. d_dev (n doubles) is the data image; b = H^T d is formed
+ * on the device. workspace_dev must be 256-byte aligned and at least
+ * rs_workspace_bytes(desc) bytes; stream is a cudaStream_t (NULL: default).
+ * On success *out receives the problem (free it with rs_destroy). */
+rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev,
+                            void* workspace_dev, size_t workspace_bytes, void* stream,
+                            rs_problem** out);
+
+/* Start the next outer step k with weights w (2n doubles, finite, > 0):
+ * E_k = L^T diag(w) L (Section 2.1). The previous weights are kept for the
+ * right-hand side of Eq. delta. */
+rs_status rs_set_weights(rs_problem* prob, const double* w_dev);
+
+/* Build the principal recycle space of the current step (Algorithm "Shifted
+ * Recycling Algorithm", steps 2-13): RS_INIT (k = 0, Section 5.1, Eq.
+ * widetildeU: two MINRES solves with kept, reorthogonalized Lanczos vectors and
+ * their Ritz vectors) or RS_UPDATE (k >= 1, Section 5.2, Eqs. delta and
+ * tildeUupdate), then Algorithm "Stabilized U", the images A U~ and E_k U~,
+ * (A + gamma_* E_k) U~ = K R (Eq. establishU), the small matrices of
+ * Eq. orthupdate and A^ = U~^T A U~, E^ = U~^T E_k U~ (Eq. hq). */
+rs_status rs_update_recycle(rs_problem* prob, int mode);
+
+/* Same as rs_update_recycle but with a caller-given basis U~ (ncols columns
+ * of n doubles each, column j at U_dev + j * n); it is stabilized like the
+ * paper's own basis. */
+rs_status rs_set_recycle_basis(rs_problem* prob, const double* U_dev, int ncols);
+
+/* Solve all M shifted systems of the current step in order l = 1..M
+ * (Section 4: initial guesses by Eq. orthupdate, local spaces by
+ * Algorithms interior / updatelocalV2, recycled MINRES by Eq. minShift,
+ * solutions by Eq. xFinal / upest). X_dev receives M x n doubles (shift l in
+ * row l). stats_host (M entries) may be NULL. iters_override_host (M ints)
+ * may be NULL; if given, shift l runs exactly that many MINRES steps and the
+ * tolerance is ignored (for comparing iterates). Returns RS_ENOCONV if any
+ * shift reached maxit. */
+rs_status rs_solve_shifts(rs_problem* prob, double* X_dev, rs_solve_stats* stats_host,
+                          const int* iters_override_host);
+
+/* Initial guesses of Eq. orthupdate for all shifts (after update_recycle):
+ * X0_dev and R0_dev receive M x n doubles each (x0 and r0 = b - Op x0). */
+rs_status rs_initial_guesses(rs_problem* prob, double* X0_dev, double* R0_dev);
+
+/* Copy the stabilized principal basis U~ (n x n_c, column-major, FP64) into
+ * U_dev (room for p_max columns of n doubles). *nc_host receives n_c. */
+rs_status rs_get_principal_basis(rs_problem* prob, double* U_dev, int* nc_host);
+
+/* y = (A + gamma E_k) x  (mode 0), or y = A x and y2 = E_k x (mode 1), or
+ * y = E_k x (mode 2), or y = H x (mode 3). x, y, y2: n doubles on the device,
+ * computed in the problem's working precision for modes 0-2 when
+ * use_working_precision is 1, else in FP64. Counts as one matvec (modes 0-2). */
+rs_status rs_apply_operator(rs_problem* prob, double gamma, const double* x_dev,
+                            double* y_dev, double* y2_dev, int mode,
+                            int use_working_precision);
+
+/* Edge-preserving weights w = ((L x)^2 + beta^2)^(-1/2) (2n doubles) of the
+ * solution x (n doubles): the IRN / smoothed-TV reweighting of Section 2.1. */
+rs_status rs_irn_weights(rs_problem* prob, const double* x_dev, double beta, double* w_dev);
+
+/* L-curve of Section 2.2 for count solutions X (count x n doubles): writes
+ * rho[l] = ||H x_l - d|| and eta[l] = ||w_k^(1/2) .* L x_l|| (host arrays of
+ * count doubles) and returns in *l_star_host the 0-based index of the corner
+ * (maximum signed Menger curvature of the log-log points; ties: smaller l). */
+rs_status rs_lcurve(rs_problem* prob, const double* X_dev, int count, double* rho_host,
+                    double* eta_host, int* l_star_host);
+
+/* Synthetic data: d = H x + eta ||H x|| / ||z|| z (Section 2.1, Eq. forward)
+ * for an image x and a noise direction z (n doubles each, device). Uses only
+ * the description's image size and blur; needs no problem. */
+rs_status rs_synthesize_data(const rs_problem_desc* desc, const double* x_dev,
+                             const double* z_dev, double eta, double* d_out_dev,
+                             void* workspace_dev, size_t workspace_bytes, void* stream);
+
+rs_status rs_get_info(const rs_problem* prob, rs_info* info_host);
+
+/* Turn per-kernel event timing on (1) or off (0); either call resets the
+ * accumulated times. Timing adds two event records per matvec launch. */
+rs_status rs_set_timing(rs_problem* prob, int on);
+
+/* Accumulated per-kernel times since the last rs_set_timing (host struct). */
+rs_status rs_get_timing(const rs_problem* prob, rs_timing* timing_host);
+
+/* Message of the last failed call on this problem (never NULL). With a NULL
+ * problem: the last failure of a call that had no problem yet. */
+const char* rs_last_error(const rs_problem* prob);
+
+/* Release the host-side problem object (the workspace stays the caller's). */
+void rs_destroy(rs_problem* prob);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECYC_H */

@@ -1,0 +1,1142 @@
+// Host orchestration and the C ABI of librecyc (include/recyc.h).
+//
+// One outer step k of the paper's "Shifted Recycling Algorithm" (Section 5.5)
+// is driven from here; every vector and small-matrix operation is one of the
+// kernels of matvec.cu, blas.cu, dense.cu, minres.cu and cgs.cu, queued on
+// the problem's stream. Host code only sequences launches, carves the
+// caller's workspace, and reads back the few integers that decide what to
+// launch next (n_c after stabilize, convergence flags, skip decisions).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "recyc.h"
+
+using namespace rk;
+
+namespace {
+
+char g_err[512] = "no error";
+
+constexpr double kStabilizeRatio = 1e10;   // Algorithm "Stabilized U"
+constexpr double kStabDrop = 1e-12;        // numerically dependent candidate (CGS2)
+constexpr double kLocalDrop = 1e-10;       // local column drop rule
+constexpr double kAngleCos = 0.99;         // footnote of Section 5.3
+constexpr int kPoll = 8;                   // MINRES steps between stop-flag polls
+constexpr int kMaxSweeps = 12;             // FP64 refinement sweeps (mixed precision)
+constexpr double kInnerRho = 1e-4;         // inner relative reduction per sweep (mixed)
+constexpr int kDotStride = kMaxLocal + 1;
+
+long round_up(long x, long a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// small helper kernels (setup only)
+// ---------------------------------------------------------------------------
+__global__ void k_coef_neg(const double* C, const double* gammas, int nc, int M, double* CA,
+                           double* CE) {
+  for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < nc * M; idx += blockDim.x * gridDim.x) {
+    const int l = idx / nc;
+    CA[idx] = -C[idx];
+    CE[idx] = -gammas[l] * C[idx];
+  }
+}
+
+// H = sym(Ah) + gamma sym(Eh)
+__global__ void k_form_h(const double* Ah, const double* Eh, int nc, double gamma, double* Hs) {
+  for (int idx = threadIdx.x; idx < nc * nc; idx += blockDim.x) {
+    const int i = idx % nc, j = idx / nc;
+    Hs[idx] = 0.5 * (Ah[i + j * nc] + Ah[j + i * nc]) + gamma * 0.5 * (Eh[i + j * nc] + Eh[j + i * nc]);
+  }
+}
+
+// dense tridiagonal T_m from recorded alpha_j, beta_{j+1}
+__global__ void k_form_tridiag(const double* alphas, const double* betas, int m, double* T) {
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    double v = 0.0;
+    if (i == j) v = alphas[i];
+    else if (i == j + 1) v = betas[j];
+    else if (j == i + 1) v = betas[i];
+    T[idx] = v;
+  }
+}
+
+// XT (ncand x nk) = Rfull(0:nk, 0:ncand)^T, Rfull column-major with ld ldrf
+__global__ void k_transpose_r(const double* Rfull, int ldrf, int nk, int ncand, double* XT) {
+  for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < nk * ncand; idx += blockDim.x * gridDim.x) {
+    const int i = idx % ncand, j = idx / ncand;   // XT[i + j*ncand] = Rfull[j + i*ldrf]
+    XT[idx] = Rfull[j + (long)i * ldrf];
+  }
+}
+
+// cos of the angle between two vectors from (a.b, a.a, b.b)
+__global__ void k_cosine(const double* dots, double* out) {
+  if (threadIdx.x == 0) {
+    const double den = sqrt(dots[1] * dots[2]);
+    out[0] = den > 0.0 ? fabs(dots[0]) / den : 0.0;
+  }
+}
+
+// d += eta * sqrt(num2 / den2) * z
+__global__ void k_add_scaled(const double* z, const double* num2, const double* den2, double eta,
+                             double* d, long n) {
+  const double sc = (*den2 > 0.0) ? eta * sqrt(*num2 / *den2) : 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    d[i] += sc * z[i];
+}
+
+// L-curve corner: max signed Menger curvature of (log rho, log eta); ties -> smaller l
+__global__ void k_lcurve_corner(const double* rho2, const double* eta2, int M, int* lstar) {
+  if (threadIdx.x != 0) return;
+  if (M < 3) { *lstar = 0; return; }
+  double best = -INFINITY;
+  int bl = 1;
+  for (int l = 1; l < M - 1; ++l) {
+    const double x0 = 0.5 * log(rho2[l - 1]), x1 = 0.5 * log(rho2[l]), x2 = 0.5 * log(rho2[l + 1]);
+    const double y0 = 0.5 * log(eta2[l - 1]), y1 = 0.5 * log(eta2[l]), y2 = 0.5 * log(eta2[l + 1]);
+    const double ax = x1 - x0, ay = y1 - y0, bx = x2 - x1, by = y2 - y1, cx = x2 - x0, cy = y2 - y0;
+    const double cross = ax * by - ay * bx;
+    const double den = sqrt((ax * ax + ay * ay) * (bx * bx + by * by) * (cx * cx + cy * cy));
+    const double kap = den > 0.0 ? 2.0 * cross / den : 0.0;
+    if (kap > best) { best = kap; bl = l; }
+  }
+  *lstar = bl;
+}
+
+Taps make_taps(double sigma, int r) {
+  Taps tp{};
+  tp.r = r;
+  double sum = 0.0;
+  for (int a = -r; a <= r; ++a) {
+    tp.g[a + r] = std::exp(-(double)(a * a) / (2.0 * sigma * sigma));
+    sum += tp.g[a + r];
+  }
+  for (int k = 0; k <= 2 * r; ++k) tp.g[k] /= sum;
+  return tp;
+}
+
+// ---------------------------------------------------------------------------
+// workspace carving
+// ---------------------------------------------------------------------------
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (size_t)round_up((long)off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct Dims {
+  long n, ld, ld2;
+  int M, p, J, a, bq, cap, cmax, keep, smax, G, psz;
+};
+
+bool valid_desc(const rs_problem_desc* d, std::string* why) {
+  auto fail = [&](const char* m) { if (why) *why = m; return false; };
+  if (!d) return fail("desc is NULL");
+  if (d->height < 1 || d->width < 1) return fail("height and width must be >= 1");
+  if (!(d->sigma > 0.0) || !std::isfinite(d->sigma)) return fail("sigma must be > 0");
+  if (d->radius < 0 || d->radius > 16) return fail("radius must be in [0, 16]");
+  if (d->M < 1 || d->M > 256) return fail("M must be in [1, 256]");
+  if (!d->gammas_host) return fail("gammas_host is NULL");
+  for (int l = 0; l < d->M; ++l) {
+    if (!(d->gammas_host[l] > 0.0) || !std::isfinite(d->gammas_host[l])) return fail("shifts must be finite and > 0");
+    if (l && !(d->gammas_host[l] > d->gammas_host[l - 1])) return fail("shifts must increase strictly");
+  }
+  if (!(d->tol >= 0.0)) return fail("tol must be >= 0");
+  if (d->maxit < 1) return fail("maxit must be >= 1");
+  if (d->p_max < 1 || d->p_max > kMaxP) return fail("p_max must be in [1, 110]");
+  if (d->a_ritz < 0 || d->b_ritz < 0 || d->a_ritz > 200 || d->b_ritz > d->a_ritz + 200) return fail("bad Ritz counts");
+  if (d->n_ritz_local < 0 || d->n_ritz_local > kMaxLocal - 2) return fail("n_ritz_local must be in [0, 14]");
+  if (d->vnew_cap < 1 || d->vnew_cap > 100) return fail("vnew_cap must be in [1, 100]");
+  auto idx_ok = [&](int v) { return v >= 1 && v <= d->M; };
+  if (!idx_ok(d->I_split) || !idx_ok(d->i1) || !idx_ok(d->i2) || !idx_ok(d->i_star) ||
+      !idx_ok(d->l_c) || !idx_ok(d->J_L) || !idx_ok(d->J_R))
+    return fail("index fields must be in [1, M]");
+  if (d->precision != RS_FP64 && d->precision != RS_MIXED) return fail("precision must be RS_FP64 or RS_MIXED");
+  const long n = (long)d->height * d->width;
+  if (n > (1L << 28)) return fail("image too large");
+  const int cmax = std::max(2 + d->a_ritz + d->b_ritz, d->a_ritz + 1 + d->vnew_cap + d->M);
+  if (cmax > 240) return fail("pre-stabilize width (a + 1 + vnew_cap + M) exceeds 240");
+  return true;
+}
+
+Dims dims_of(const rs_problem_desc* d) {
+  Dims z{};
+  z.n = (long)d->height * d->width;
+  z.ld = round_up(z.n, 64);
+  z.ld2 = round_up(2 * z.n, 64);
+  z.M = d->M;
+  z.p = d->p_max;
+  z.J = d->n_ritz_local;
+  z.a = d->a_ritz;
+  z.bq = d->b_ritz;
+  z.cap = d->vnew_cap;
+  z.cmax = std::max({2 + z.a + z.bq, z.a + 1 + z.cap + z.M, z.p});
+  z.keep = std::max(z.a, z.cap);
+  z.smax = z.J + 2;
+  z.G = red_grid(z.n);
+  z.psz = (long)z.G * (z.cmax + 8) + 152L * 8192;
+  return z;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the problem object
+// ---------------------------------------------------------------------------
+struct rs_problem {
+  rs_problem_desc d{};
+  std::vector<double> gammas;
+  cudaStream_t s = nullptr;
+  Dims z{};
+  Taps tp{};
+  bool mixed = false;
+  int k = -1;
+  int nc = 0;
+  int nk_stab = 0;
+  bool have_recycle = false;
+  bool have_prev = false;
+  long long mv_total = 0, mv_over = 0;
+  double bnorm = 0.0;
+  std::string err = "no error";
+  std::vector<char> gprev_nz, gcur_nz;
+  int kept_init = 0;    // columns of V_i1
+
+  // FP64 buffers
+  double *b = nullptr, *dimg = nullptr, *r64 = nullptr, *y64 = nullptr, *t64 = nullptr;
+  double *w64 = nullptr, *wprev64 = nullptr, *dw64 = nullptr;
+  double *Xprev = nullptr, *Ut_raw = nullptr, *Vi1 = nullptr;
+  // working-precision buffers (float or double)
+  void *bT = nullptr, *wT = nullptr, *Ut = nullptr, *AU = nullptr, *EU = nullptr, *Kp = nullptr;
+  void *WL = nullptr, *WR = nullptr, *AWL = nullptr, *EWL = nullptr, *AWR = nullptr, *EWR = nullptr;
+  void *Bc = nullptr, *Kl = nullptr, *Gcur = nullptr, *Gprev = nullptr, *Vkeep = nullptr;
+  void *vring[3] = {nullptr, nullptr, nullptr}, *dring[3] = {nullptr, nullptr, nullptr};
+  void *vzero = nullptr, *u = nullptr, *y = nullptr, *xm = nullptr, *rT = nullptr;
+  // small device arrays
+  double *partials = nullptr, *gam = nullptr, *C = nullptr, *CA = nullptr, *CE = nullptr;
+  double *Rp = nullptr, *Mm = nullptr, *Nm = nullptr, *T1 = nullptr, *G_KE = nullptr, *G_EE = nullptr;
+  double *G_Eb = nullptr, *Ktb = nullptr, *UtEb = nullptr, *Ah = nullptr, *Eh = nullptr, *Hs = nullptr;
+  double *eigw = nullptr, *lam = nullptr, *Qe = nullptr, *WtL = nullptr, *WtR = nullptr;
+  double *Rfull = nullptr, *XT = nullptr, *Vsv = nullptr, *sig = nullptr, *hdots = nullptr;
+  double *coef = nullptr, *scal = nullptr, *Ktr = nullptr, *Rk = nullptr, *zc = nullptr;
+  double *arec = nullptr, *brec = nullptr, *lc = nullptr;
+  int *cnt = nullptr, *flag = nullptr, *kept = nullptr, *perm = nullptr, *status = nullptr;
+  int *poll = nullptr, *ok = nullptr, *lstar = nullptr;
+  MinresState* st = nullptr;
+  size_t need = 0;
+
+  // per-kernel event timing (rs_set_timing)
+  struct TimedLaunch {
+    int cat;
+    int iter;          // MINRES step of the launch, or -1 (always executed)
+    long long pixels;
+  };
+  bool timing = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<TimedLaunch> pending;
+  size_t pending_used = 0;
+  long long t_launches[2] = {0, 0}, t_pixels[2] = {0, 0};
+  double t_ms[2] = {0.0, 0.0};
+
+  ~rs_problem() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+  }
+
+  int set_err(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+};
+
+namespace {
+
+void carve(rs_problem* P, Carver& cv) {
+  const Dims& z = P->z;
+  const size_t vt = P->mixed ? sizeof(float) : sizeof(double);
+  auto vec = [&](long count) -> void* { return cv.take<char>((size_t)count * vt); };
+  P->b = cv.take<double>(z.ld);
+  P->dimg = cv.take<double>(z.ld);
+  P->r64 = cv.take<double>(z.ld);
+  P->y64 = cv.take<double>(z.ld);
+  P->t64 = cv.take<double>(z.ld);
+  P->w64 = cv.take<double>(z.ld2);
+  P->wprev64 = cv.take<double>(z.ld2);
+  P->dw64 = cv.take<double>(z.ld2);
+  P->Xprev = cv.take<double>((size_t)z.M * z.ld);
+  P->Ut_raw = cv.take<double>((size_t)z.cmax * z.ld);
+  P->Vi1 = cv.take<double>((size_t)std::max(z.a, 1) * z.ld);
+  if (P->mixed) {
+    P->bT = vec(z.ld);
+    P->wT = vec(z.ld2);
+  }
+  P->Ut = vec((long)z.p * z.ld);
+  P->AU = vec((long)z.p * z.ld);
+  P->EU = vec((long)z.p * z.ld);
+  P->Kp = vec((long)z.p * z.ld);
+  const long jn = (long)std::max(z.J, 1) * z.ld;
+  P->WL = vec(jn); P->WR = vec(jn); P->AWL = vec(jn); P->EWL = vec(jn); P->AWR = vec(jn); P->EWR = vec(jn);
+  P->Bc = vec((long)z.smax * z.ld);
+  P->Kl = vec((long)z.smax * z.ld);
+  P->Gcur = vec((long)z.M * z.ld);
+  P->Gprev = vec((long)z.M * z.ld);
+  P->Vkeep = vec((long)std::max(z.keep, 1) * z.ld);
+  for (int i = 0; i < 3; ++i) P->vring[i] = vec(z.ld);
+  for (int i = 0; i < 3; ++i) P->dring[i] = vec(z.ld);
+  P->vzero = vec(z.ld);
+  P->u = vec(z.ld);
+  P->y = vec(z.ld);
+  P->xm = vec(z.ld);
+  P->rT = vec(z.ld);
+  P->partials = cv.take<double>(z.psz);
+  P->gam = cv.take<double>(z.M);
+  P->C = cv.take<double>((size_t)z.p * z.M);
+  P->CA = cv.take<double>((size_t)z.p * z.M);
+  P->CE = cv.take<double>((size_t)z.p * z.M);
+  const size_t pp = (size_t)z.p * z.p;
+  P->Rp = cv.take<double>(pp); P->Mm = cv.take<double>(pp); P->Nm = cv.take<double>(pp);
+  P->T1 = cv.take<double>(pp); P->G_KE = cv.take<double>(pp); P->G_EE = cv.take<double>(pp);
+  P->G_Eb = cv.take<double>(z.p); P->Ktb = cv.take<double>(z.p); P->UtEb = cv.take<double>(z.p);
+  P->Ah = cv.take<double>(pp); P->Eh = cv.take<double>(pp);
+  const int em = std::max(z.p, z.keep);
+  P->Hs = cv.take<double>((size_t)em * em);
+  P->eigw = cv.take<double>(2 * (size_t)em * em + em);
+  P->lam = cv.take<double>(em);
+  P->Qe = cv.take<double>((size_t)em * em);
+  P->WtL = cv.take<double>((size_t)z.p * std::max(z.J, 1));
+  P->WtR = cv.take<double>((size_t)z.p * std::max(z.J, 1));
+  P->Rfull = cv.take<double>((size_t)z.cmax * z.cmax);
+  P->XT = cv.take<double>((size_t)z.cmax * z.cmax);
+  P->Vsv = cv.take<double>((size_t)z.cmax * z.cmax);
+  P->sig = cv.take<double>(z.cmax);
+  P->hdots = cv.take<double>(kMaxDots);
+  P->coef = cv.take<double>(2 * (size_t)z.cmax + 2 * kMaxDots);
+  P->scal = cv.take<double>(16);
+  P->Ktr = cv.take<double>(kMaxLocal);
+  P->Rk = cv.take<double>((size_t)std::max(z.p, kMaxLocal) * std::max(z.p, kMaxLocal));
+  P->zc = cv.take<double>(kMaxLocal);
+  P->arec = cv.take<double>(std::max(z.keep, 1));
+  P->brec = cv.take<double>(std::max(z.keep, 1));
+  P->lc = cv.take<double>(2 * (size_t)z.M + 2);
+  P->cnt = cv.take<int>(4);
+  P->flag = cv.take<int>(4);
+  P->kept = cv.take<int>(z.cmax + kMaxLocal);
+  P->perm = cv.take<int>(z.cmax + 4);
+  P->status = cv.take<int>(z.M);
+  P->poll = cv.take<int>(4);
+  P->ok = cv.take<int>(4);
+  P->lstar = cv.take<int>(4);
+  P->st = cv.take<MinresState>(1);
+}
+
+#define CU(...)                                                                         \
+  do {                                                                                  \
+    cudaError_t _e = (__VA_ARGS__);                                                            \
+    if (_e != cudaSuccess)                                                              \
+      return (rs_status)P->set_err(RS_ECUDA, "CUDA error %s at %s:%d",                 \
+                                   cudaGetErrorString(_e), __FILE__, __LINE__);         \
+  } while (0)
+#define RS(...)                     \
+  do {                              \
+    int _r = (__VA_ARGS__);                \
+    if (_r != RS_OK) return _r;     \
+  } while (0)
+
+template <typename T> T* vp(void* p) { return reinterpret_cast<T*>(p); }
+template <typename T> T* col(void* p, long j, long ld) { return reinterpret_cast<T*>(p) + j * ld; }
+
+int read_back(rs_problem* P, void* host, const void* dev, size_t bytes) {
+  CU(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, P->s));
+  CU(cudaStreamSynchronize(P->s));
+  return RS_OK;
+}
+
+// Event pair around one timed launch; returns the slot or -1 when timing is off.
+int timed_begin(rs_problem* P) {
+  if (!P->timing) return -1;
+  if (P->pending_used == P->pending.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
+    P->events.push_back(a);
+    P->events.push_back(b);
+    P->pending.push_back({0, -1, 0});
+  }
+  const int i = (int)P->pending_used++;
+  cudaEventRecord(P->events[2 * i], P->s);
+  return i;
+}
+
+void timed_end(rs_problem* P, int i, int cat, int iter, long long pixels) {
+  if (i < 0) return;
+  cudaEventRecord(P->events[2 * i + 1], P->s);
+  P->pending[i] = {cat, iter, pixels};
+}
+
+// After a stream synchronisation: add up the recorded pairs. Launches of a
+// MINRES step beyond valid_iter were no-ops of a stopped solve and are skipped.
+void timed_flush(rs_problem* P, int valid_iter) {
+  for (size_t i = 0; i < P->pending_used; ++i) {
+    const auto& r = P->pending[i];
+    if (r.iter >= 0 && r.iter > valid_iter) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P->events[2 * i], P->events[2 * i + 1]) != cudaSuccess) continue;
+    P->t_ms[r.cat] += ms;
+    P->t_launches[r.cat] += 1;
+    P->t_pixels[r.cat] += r.pixels;
+  }
+  P->pending_used = 0;
+}
+
+// ||x||^2 of a working-precision vector into dst (device)
+template <typename T>
+int norm2_to(rs_problem* P, const T* x, double* dst) {
+  CU(norm2_partials<T>(x, P->z.n, P->partials, P->s));
+  CU(reduce_partials(P->partials, P->z.G, 1, 1, dst, P->s, nullptr, 0, nullptr));
+  return RS_OK;
+}
+
+// FP64 true residual: r64 = b - (A + gamma E) x64; returns ||r|| / ||b|| on the host.
+int true_residual(rs_problem* P, double gamma, const double* x64, double* relres) {
+  const int slot = timed_begin(P);
+  CU(op_apply<double>(x64, P->z.ld, 1, P->w64, P->y64, nullptr, P->z.ld, P->d.height, P->d.width,
+                      P->tp, gamma, 0, P->s));
+  timed_end(P, slot, 1, -1, P->z.n);
+  CU(residual64(P->b, P->y64, P->r64, P->z.n, P->partials, P->s));
+  CU(reduce_partials(P->partials, P->z.G, 1, 1, P->scal + 8, P->s, nullptr, 0, nullptr));
+  double r2 = 0.0;
+  RS(read_back(P, &r2, P->scal + 8, sizeof r2));
+  timed_flush(P, 0);
+  *relres = std::sqrt(r2) / P->bnorm;
+  P->mv_total += 1;
+  return RS_OK;
+}
+
+// Recycled MINRES on (A + gamma E) g = r (Section 2.3 / Eq. minShift) with the
+// local space (Kl, count on the device, may be 0) and optional kept Lanczos
+// vectors (keep, reorth). On exit xm holds V_m y and st->z the coupling part.
+template <typename T>
+int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_abs, int maxit,
+               int keep, bool reorth, int* iters_out, double* eta_out, int* breakdown_out) {
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  cudaStream_t s = P->s;
+  T* Kl = vp<T>(P->Kl);
+  const int* cntK = P->cnt;   // local count lives in cnt[0] (CGS context)
+  T* u = vp<T>(P->u);
+  T* y = vp<T>(P->y);
+  T* xm = vp<T>(P->xm);
+  T* Vk = vp<T>(P->Vkeep);
+  // zero-count device int for solves without a local space
+  const int* cnt_use = use_K ? cntK : P->cnt + 2;
+  if (!use_K) CU(cudaMemsetAsync(P->cnt + 2, 0, sizeof(int), s));
+  // u = (I - K K^T) r, Ktr = K^T r, xi^2 = ||u||^2
+  CU(multidot<T>(Kl, ld, cnt_use, 0, nullptr, r, n, P->partials, kDotStride, s, nullptr));
+  CU(reduce_partials(P->partials, z.G, kMaxLocal, kDotStride, P->Ktr, s, cnt_use, 0, nullptr));
+  CU(cudaMemcpyAsync(u, r, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CU(multi_axpy<T>(Kl, ld, cnt_use, 0, P->Ktr, -1.0, u, n, P->partials, s, nullptr));
+  CU(reduce_partials(P->partials, z.G, 1, 1, P->scal + 0, s, nullptr, 0, nullptr));
+  CU(minres_init(P->st, P->scal + 0, P->Ktr, cnt_use, tol_abs, maxit, s));
+  CU(cudaMemsetAsync(xm, 0, n * sizeof(T), s));
+  CU(cudaMemsetAsync(P->vzero, 0, n * sizeof(T), s));
+  for (int i = 0; i < 3; ++i) CU(cudaMemsetAsync(P->dring[i], 0, n * sizeof(T), s));
+  auto vptr = [&](int j) -> T* {
+    if (j <= 0) return vp<T>(P->vzero);
+    if (j <= keep) return Vk + (long)(j - 1) * ld;
+    return vp<T>(P->vring[j % 3]);
+  };
+  auto dptr = [&](int j) -> T* { return vp<T>(P->dring[((j % 3) + 3) % 3]); };
+  // v_1 = u / xi
+  CU(scale_dev<T>(u, vptr(1), n, &P->st->inv_beta_next, 0, nullptr, s));
+  const int* stop = &P->st->stop;
+  int hpoll[2] = {0, 0};
+  int j = 1;
+  for (; j <= maxit; ++j) {
+    T* vj = vptr(j);
+    const int slot = timed_begin(P);
+    CU(op_apply<T>(vj, ld, 1, vp<T>(P->mixed ? P->wT : (void*)P->w64), y, nullptr, ld, P->d.height,
+                   P->d.width, P->tp, gamma, 0, s, stop));
+    timed_end(P, slot, 0, j, n);
+    CU(multidot<T>(Kl, ld, cnt_use, 0, vj, y, n, P->partials, kDotStride, s, stop));
+    CU(reduce_partials(P->partials, z.G, kMaxLocal + 1, kDotStride, P->hdots, s, cnt_use, 1, stop));
+    CU(lanczos_update<T>(P->st, Kl, ld, P->hdots, y, vj, vptr(j - 1), u, n, P->partials, s));
+    if (reorth && j < keep) {
+      for (int pass = 0; pass < 2; ++pass) {
+        CU(multidot<T>(Vk, ld, nullptr, j, nullptr, u, n, P->partials + (long)z.G * 4, z.cmax + 2, s, stop));
+        CU(reduce_partials(P->partials + (long)z.G * 4, z.G, j, z.cmax + 2, P->coef, s, nullptr, 0, stop));
+        CU(multi_axpy<T>(Vk, ld, nullptr, j, P->coef, -1.0, u, n, pass == 1 ? P->partials : nullptr, s, stop));
+      }
+    }
+    CU(minres_step(P->st, P->hdots, P->partials, z.G, P->arec, P->brec, keep, s));
+    CU(minres_direction<T>(P->st, u, vptr(j + 1), vj, dptr(j - 1), dptr(j - 2), dptr(j), xm, n, s));
+    if (j % kPoll == 0 || j == maxit) {
+      CU(minres_poll(P->st, P->poll, s));
+      RS(read_back(P, hpoll, P->poll, sizeof hpoll));
+      timed_flush(P, hpoll[1]);
+      if (hpoll[0]) break;
+    }
+  }
+  MinresState hs;
+  RS(read_back(P, &hs, P->st, sizeof hs));
+  timed_flush(P, hs.iters);
+  *iters_out = hs.iters;
+  *eta_out = std::fabs(hs.eta);
+  if (breakdown_out) *breakdown_out = hs.breakdown;
+  P->mv_total += hs.iters;
+  return RS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// principal space
+// ---------------------------------------------------------------------------
+CgsCtx cgs_ctx(rs_problem* P, int ldr, double* Rk, double* Rfull, int ldrf, double drop) {
+  CgsCtx c{};
+  c.count = P->cnt;
+  c.flag = P->flag;
+  c.Rk = Rk;
+  c.ldr = ldr;
+  c.Rfull = Rfull;
+  c.ldrf = ldrf;
+  c.kept_idx = P->kept;
+  c.coef = P->coef;
+  c.partials = P->partials;
+  c.scal = P->scal;
+  c.drop_rel = drop;
+  return c;
+}
+
+// Algorithm "Stabilized U" on the ncand columns of Ut_raw (FP64), then the
+// images, K, R, the matrices of Eq. orthupdate and Eq. hq, and the Ritz
+// vectors of Algorithm "interior" at gamma_{J_L}, gamma_{J_R}.
+template <typename T>
+int finish_principal(rs_problem* P, int ncand) {
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  cudaStream_t s = P->s;
+  // stabilize: CGS2 (in place, normalised R per candidate), SVD of R
+  CgsCtx c = cgs_ctx(P, z.cmax, nullptr, P->Rfull, z.cmax, kStabDrop);
+  CU(cgs_reset(c, s));
+  for (int j = 0; j < ncand; ++j)
+    CU(cgs2_column<double>(c, P->Ut_raw, ld, P->Ut_raw + (long)j * ld, j, n, s));
+  int nk = 0;
+  RS(read_back(P, &nk, P->cnt, sizeof nk));
+  int ncn = 0;
+  if (nk > 0) {
+    k_transpose_r<<<32, 256, 0, s>>>(P->Rfull, z.cmax, nk, ncand, P->XT);
+    CU(launched());
+    CU(jacobi_svd(P->XT, ncand, nk, ncand, P->Vsv, P->sig, P->perm, s));
+    std::vector<double> sg(nk);
+    RS(read_back(P, sg.data(), P->sig, nk * sizeof(double)));
+    for (int i = 0; i < nk; ++i)
+      if (sg[0] > 0.0 && sg[i] > 0.0 && sg[0] / sg[i] < kStabilizeRatio) ++ncn;
+    ncn = std::min(ncn, z.p);
+  }
+  P->nc = ncn;
+  P->nk_stab = nk;
+  if (ncn == 0) return P->set_err(RS_EBREAKDOWN, "principal recycle space is empty");
+  T* Ut = vp<T>(P->Ut);
+  T* AU = vp<T>(P->AU);
+  T* EU = vp<T>(P->EU);
+  T* Kp = vp<T>(P->Kp);
+  CU(gemm_ts<double, T>(P->Ut_raw, ld, nk, P->Vsv, nk, ncn, 0.0, Ut, ld, n, s));
+  // images A U~, E U~ (n_c matvecs)
+  T* wT = vp<T>(P->mixed ? P->wT : (void*)P->w64);
+  CU(op_apply<T>(Ut, ld, ncn, wT, AU, EU, ld, P->d.height, P->d.width, P->tp, 0.0, 1, s));
+  P->mv_total += ncn;
+  P->mv_over += ncn;
+  // (A + g* E) U~ = K R
+  const double gstar = P->gammas[P->d.i_star - 1];
+  CU(cudaMemcpyAsync(Kp, AU, (size_t)ncn * ld * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CU(axpby<T, T>(EU, gstar, Kp, 1.0, (long)ncn * ld, s));
+  CgsCtx ck = cgs_ctx(P, ncn, P->Rp, nullptr, 0, 0.0);   // R with leading dimension n_c
+  CU(cgs_reset(ck, s));
+  for (int j = 0; j < ncn; ++j) CU(cgs2_column<T>(ck, Kp, ld, Kp + (long)j * ld, j, n, s));
+  int nkk = 0;
+  RS(read_back(P, &nkk, P->cnt, sizeof nkk));
+  if (nkk != ncn) return P->set_err(RS_EBREAKDOWN, "(A + gamma_* E) U~ is rank deficient (%d of %d)", nkk, ncn);
+  // Gram blocks
+  const T* bT = vp<T>(P->mixed ? P->bT : (void*)P->b);
+  CU(gram<T>(Kp, ld, ncn, EU, ld, ncn, n, P->partials, P->G_KE, s));
+  CU(gram<T>(EU, ld, ncn, EU, ld, ncn, n, P->partials, P->G_EE, s));
+  CU(gram<T>(EU, ld, ncn, bT, ld, 1, n, P->partials, P->G_Eb, s));
+  CU(gram<T>(Kp, ld, ncn, bT, ld, 1, n, P->partials, P->Ktb, s));
+  CU(gram<T>(Ut, ld, ncn, AU, ld, ncn, n, P->partials, P->Ah, s));
+  CU(gram<T>(Ut, ld, ncn, EU, ld, ncn, n, P->partials, P->Eh, s));
+  PrincipalSmall ps{P->Rp, P->G_KE, P->G_EE, P->G_Eb, P->Mm, P->Nm, P->UtEb};
+  CU(principal_small(ps, ncn, P->T1, s));
+  CU(principal_solves(P->Mm, P->Nm, P->Ktb, P->UtEb, P->Rp, ncn, P->gam, gstar, z.M, P->C, P->status, s));
+  k_coef_neg<<<8, 256, 0, s>>>(P->C, P->gam, ncn, z.M, P->CA, P->CE);
+  CU(launched());
+  std::vector<int> stt(z.M);
+  RS(read_back(P, stt.data(), P->status, z.M * sizeof(int)));
+  for (int l = 0; l < z.M; ++l)
+    if (stt[l]) return P->set_err(RS_EBREAKDOWN, "orthupdate matrix of shift %d is not SPD", l + 1);
+  // Ritz vectors of the projected systems (Algorithm interior)
+  const int J = std::min(z.J, ncn);
+  for (int grp = 0; grp < 2; ++grp) {
+    const int jidx = grp == 0 ? P->d.J_L : P->d.J_R;
+    double* Wt = grp == 0 ? P->WtL : P->WtR;
+    T* Wv = vp<T>(grp == 0 ? P->WL : P->WR);
+    T* AW = vp<T>(grp == 0 ? P->AWL : P->AWR);
+    T* EW = vp<T>(grp == 0 ? P->EWL : P->EWR);
+    if (J == 0) continue;
+    k_form_h<<<1, 256, 0, s>>>(P->Ah, P->Eh, ncn, P->gammas[jidx - 1], P->Hs);
+    CU(launched());
+    CU(spd_eig(P->Hs, ncn, P->lam, P->Qe, P->eigw, P->perm, s));
+    CU(cudaMemcpyAsync(Wt, P->Qe, (size_t)ncn * J * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(gemm_ts<T, T>(Ut, ld, ncn, Wt, ncn, J, 0.0, Wv, ld, n, s));
+    CU(gemm_ts<T, T>(AU, ld, ncn, Wt, ncn, J, 0.0, AW, ld, n, s));
+    CU(gemm_ts<T, T>(EU, ld, ncn, Wt, ncn, J, 0.0, EW, ld, n, s));
+  }
+  P->have_recycle = true;
+  return RS_OK;
+}
+
+// Section 5.1: two MINRES solves with kept, reorthogonalized Lanczos vectors.
+template <typename T>
+int init_principal(rs_problem* P) {
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  cudaStream_t s = P->s;
+  int col_out = 2;
+  for (int which = 0; which < 2; ++which) {
+    const int idx = which == 0 ? P->d.i1 : P->d.i2;
+    const double g = P->gammas[idx - 1];
+    double* x64 = P->Ut_raw + (long)which * ld;   // x^(0,i) goes to column 0 / 1
+    CU(cudaMemsetAsync(x64, 0, n * sizeof(double), s));
+    // sweep 0 from r = b with kept vectors; mixed precision refines in FP64
+    CU(convert<double, T>(P->b, vp<T>(P->rT), n, s));
+    int it = 0, bd = 0;
+    double eta = 0.0;
+    const double tol_abs = P->d.tol * P->bnorm;
+    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * P->bnorm) : tol_abs;
+    RS(run_minres<T>(P, g, vp<T>(P->rT), false, inner_tol, P->d.maxit, z.a, true, &it, &eta, &bd));
+    P->mv_over += it;
+    const int m = std::min(it, z.a);
+    CU(axpby<T, double>(vp<T>(P->xm), 1.0, x64, 1.0, n, s));
+    if (P->mixed) {
+      double rel = 0.0;
+      for (int sw = 1; sw < kMaxSweeps; ++sw) {
+        RS(true_residual(P, g, x64, &rel));
+        P->mv_over += 1;
+        if (rel <= P->d.tol) break;
+        CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
+        const double rn = rel * P->bnorm;
+        RS(run_minres<T>(P, g, vp<T>(P->rT), false, std::max(0.5 * tol_abs, kInnerRho * rn), P->d.maxit, 0, false, &it, &eta, &bd));
+        P->mv_over += it;
+        CU(axpby<T, double>(vp<T>(P->xm), 1.0, x64, 1.0, n, s));
+      }
+    }
+    // Ritz vectors from T_m
+    if (m > 0) {
+      k_form_tridiag<<<1, 256, 0, s>>>(P->arec, P->brec, m, P->Hs);
+      CU(launched());
+      CU(spd_eig(P->Hs, m, P->lam, P->Qe, P->eigw, P->perm, s));
+      const int take = which == 0 ? m : std::min(m, z.bq);
+      CU(gemm_ts<T, double>(vp<T>(P->Vkeep), ld, m, P->Qe, m, take, 0.0, P->Ut_raw + (long)col_out * ld, ld, n, s));
+      if (which == 0) {
+        CU(cudaMemcpyAsync(P->Vi1, P->Ut_raw + (long)col_out * ld, (size_t)take * ld * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+        P->kept_init = take;
+      }
+      col_out += take;
+    } else if (which == 0) {
+      P->kept_init = 0;
+    }
+  }
+  return finish_principal<T>(P, col_out);
+}
+
+// Section 5.2: V^(new) from at most vnew_cap MINRES steps on Eq. delta, then
+// U~ = [V_i1, V^(new), x^(k-1, 1..M)] (Eq. tildeUupdate).
+template <typename T>
+int update_principal(rs_problem* P) {
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  cudaStream_t s = P->s;
+  const int lc = P->d.l_c - 1;
+  const double g = P->gammas[lc];
+  // rhs = gamma_lc (E_k - E_{k-1}) x^(k-1, l_c)
+  CU(axpby<double, double>(P->w64, 1.0, P->dw64, 0.0, 2 * n, s));
+  CU(axpby<double, double>(P->wprev64, -1.0, P->dw64, 1.0, 2 * n, s));
+  CU(op_apply<double>(P->Xprev + (long)lc * ld, ld, 1, P->dw64, P->t64, nullptr, ld, P->d.height,
+                      P->d.width, P->tp, 0.0, 2, s));
+  P->mv_total += 1;
+  P->mv_over += 1;
+  CU(convert<double, T>(P->t64, vp<T>(P->rT), n, s));
+  CU(axpby<T, T>(vp<T>(P->rT), g, vp<T>(P->rT), 0.0, n, s));
+  double r2 = 0.0;
+  RS(norm2_to<T>(P, vp<T>(P->rT), P->scal + 9));
+  RS(read_back(P, &r2, P->scal + 9, sizeof r2));
+  int it = 0, bd = 0;
+  double eta = 0.0;
+  RS(run_minres<T>(P, g, vp<T>(P->rT), false, P->d.tol * std::sqrt(r2), z.cap, z.cap, false, &it, &eta, &bd));
+  P->mv_over += it;
+  const int m = std::min(it, z.cap);
+  int c = 0;
+  double* U = P->Ut_raw;
+  if (P->kept_init > 0) {
+    CU(cudaMemcpyAsync(U, P->Vi1, (size_t)P->kept_init * ld * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    c += P->kept_init;
+  }
+  CU(convert<T, double>(vp<T>(P->xm), U + (long)c * ld, n, s));
+  c += 1;
+  for (int j = 0; j < m; ++j) {
+    CU(convert<T, double>(vp<T>(P->Vkeep) + (long)j * ld, U + (long)c * ld, n, s));
+    c += 1;
+  }
+  CU(cudaMemcpyAsync(U + (long)c * ld, P->Xprev, (size_t)z.M * ld * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  c += z.M;
+  return finish_principal<T>(P, c);
+}
+
+// ---------------------------------------------------------------------------
+// the shifted solves of one outer step
+// ---------------------------------------------------------------------------
+template <typename T>
+int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) {
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  cudaStream_t s = P->s;
+  const int nc = P->nc;
+  const int J = std::min(z.J, nc);
+  T* Ut = vp<T>(P->Ut);
+  T* Bc = vp<T>(P->Bc);
+  T* Kl = vp<T>(P->Kl);
+  T* wT = vp<T>(P->mixed ? P->wT : (void*)P->w64);
+  const double tol_abs = P->d.tol * P->bnorm;
+  int any_noconv = 0;
+  std::vector<char> gnz(z.M, 0);
+  for (int l = 0; l < z.M; ++l) {
+    const double gl = P->gammas[l];
+    rs_solve_stats sl{};
+    sl.sweeps = 0;
+    double* x = X + (long)l * n;    // caller's X is dense M x n
+    // initial guess x0 = U~ c_l and r0 = b - A U~ c_l - gamma_l E U~ c_l
+    CU(gemm_ts<T, double>(Ut, ld, nc, P->C + (long)l * nc, nc, 1, 0.0, x, n, n, s));
+    CU(cudaMemcpyAsync(P->r64, P->b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(gemm_ts<T, double>(vp<T>(P->AU), ld, nc, P->CA + (long)l * nc, nc, 1, 1.0, P->r64, ld, n, s));
+    CU(gemm_ts<T, double>(vp<T>(P->EU), ld, nc, P->CE + (long)l * nc, nc, 1, 1.0, P->r64, ld, n, s));
+    CU(norm2_partials<double>(P->r64, n, P->partials, s));
+    CU(reduce_partials(P->partials, z.G, 1, 1, P->scal + 10, s, nullptr, 0, nullptr));
+    double r02 = 0.0;
+    RS(read_back(P, &r02, P->scal + 10, sizeof r02));
+    sl.relres0 = std::sqrt(r02) / P->bnorm;
+    const int forced = over ? over[l] : -1;
+    T* gl_buf = vp<T>(P->Gcur) + (long)l * ld;
+    if (forced < 0 && sl.relres0 <= P->d.tol) {
+      CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
+      sl.relres_est = sl.relres0;
+      RS(true_residual(P, gl, x, &sl.relres_true));
+      sl.matvecs = 1;
+      sl.sweeps = 0;
+      if (stats) stats[l] = sl;
+      continue;
+    }
+    // local space [W, g^(k-1,l), g^(k,l-1)] and its image
+    const bool left = (l + 1) <= P->d.I_split;
+    T* Wv = vp<T>(left ? P->WL : P->WR);
+    PtrList cand{};
+    int ncand = 0;
+    if (J > 0) {
+      CU(cudaMemcpyAsync(Bc, left ? P->AWL : P->AWR, (size_t)J * ld * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      CU(axpby<T, T>(vp<T>(left ? P->EWL : P->EWR), gl, Bc, 1.0, (long)J * ld, s));
+      for (int j = 0; j < J; ++j) cand.p[ncand++] = Wv + (long)j * ld;
+    }
+    const T* gold = nullptr;
+    const T* gnew = nullptr;
+    if (P->have_prev && P->gprev_nz[l]) gold = vp<T>(P->Gprev) + (long)l * ld;
+    if (P->d.batched_local) {
+      if (P->have_prev && l >= 1 && P->gprev_nz[l - 1]) gnew = vp<T>(P->Gprev) + (long)(l - 1) * ld;
+    } else {
+      if (l >= 1 && gnz[l - 1]) gnew = vp<T>(P->Gcur) + (long)(l - 1) * ld;
+    }
+    if (gold && gnew) {
+      // angle rule: keep only g^(k,l-1) when |cos| > 0.99
+      CU(multidot<T>(gold, 0, nullptr, 1, nullptr, gnew, n, P->partials, 3, s, nullptr));
+      CU(multidot<T>(gold, 0, nullptr, 1, nullptr, gold, n, P->partials + 1, 3, s, nullptr));
+      CU(multidot<T>(gnew, 0, nullptr, 1, nullptr, gnew, n, P->partials + 2, 3, s, nullptr));
+      CU(reduce_partials(P->partials, z.G, 3, 3, P->scal + 11, s, nullptr, 0, nullptr));
+      k_cosine<<<1, 32, 0, s>>>(P->scal + 11, P->scal + 14);
+      CU(launched());
+      double cs = 0.0;
+      RS(read_back(P, &cs, P->scal + 14, sizeof cs));
+      if (cs > kAngleCos) gold = nullptr;
+    }
+    for (const T* gv : {gold, gnew}) {
+      if (!gv) continue;
+      CU(op_apply<T>(gv, ld, 1, wT, Bc + (long)(ncand - 0) * ld, nullptr, ld, P->d.height, P->d.width,
+                     P->tp, gl, 0, s));
+      cand.p[ncand++] = gv;
+      sl.matvecs += 1;
+      P->mv_total += 1;
+    }
+    CgsCtx c = cgs_ctx(P, kMaxLocal, P->Rk, nullptr, 0, kLocalDrop);
+    CU(cgs_reset(c, s));
+    for (int j = 0; j < ncand; ++j) {
+      // candidate j's image is in Bc[:, j]; kept columns are compacted into Kl
+      CU(cudaMemcpyAsync(P->u, Bc + (long)j * ld, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      CU(cgs2_column<T>(c, Kl, ld, vp<T>(P->u), j, n, s));
+    }
+    int sdim = 0;
+    RS(read_back(P, &sdim, P->cnt, sizeof sdim));
+    sl.local_dim = sdim;
+    // sweeps: sweep 0 from r0; in mixed precision further sweeps from the FP64 residual
+    CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
+    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * std::sqrt(r02)) : tol_abs;
+    const int max_sw = P->mixed ? kMaxSweeps : 1;
+    for (int sw = 0; sw < max_sw; ++sw) {
+      int it = 0, bd = 0;
+      double eta = 0.0;
+      const int mi = forced >= 0 ? forced : P->d.maxit;
+      RS(run_minres<T>(P, gl, vp<T>(P->rT), sdim > 0, forced >= 0 ? 0.0 : inner_tol, mi, 0, false, &it, &eta, &bd));
+      sl.iters += it;
+      sl.matvecs += it;
+      sl.relres_est = eta / P->bnorm;
+      sl.sweeps = sw + 1;
+      if (sdim > 0) {
+        CU(tri_solve_upper(P->Rk, kMaxLocal, P->cnt, P->st->z, P->zc, s));
+        CU(gather_axpy<T>(cand, P->kept, P->cnt, P->zc, vp<T>(P->xm), n, s));
+      }
+      CU(axpby<T, double>(vp<T>(P->xm), 1.0, x, 1.0, n, s));
+      if (sw == 0) CU(cudaMemcpyAsync(gl_buf, P->xm, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      else CU(axpby<T, T>(vp<T>(P->xm), 1.0, gl_buf, 1.0, n, s));
+      RS(true_residual(P, gl, x, &sl.relres_true));
+      sl.matvecs += 1;
+      if (!P->mixed || sl.relres_true <= P->d.tol || forced >= 0) break;
+      CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
+      inner_tol = std::max(0.5 * tol_abs, kInnerRho * sl.relres_true * P->bnorm);
+      if (sw + 1 == max_sw) break;
+    }
+    gnz[l] = 1;
+    sl.status = (forced < 0 && sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) && sl.iters >= P->d.maxit)
+                    ? RS_ENOCONV : RS_OK;
+    if (sl.status == RS_ENOCONV) any_noconv = 1;
+    if (stats) stats[l] = sl;
+  }
+  // hand over to the next outer step
+  CU(cudaMemcpy2DAsync(P->Xprev, ld * sizeof(double), X, n * sizeof(double), n * sizeof(double), z.M,
+                       cudaMemcpyDeviceToDevice, s));
+  std::swap(P->Gcur, P->Gprev);
+  P->gprev_nz = gnz;
+  P->have_prev = true;
+  return any_noconv ? P->set_err(RS_ENOCONV, "a shift reached maxit") : RS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+size_t rs_workspace_bytes(const rs_problem_desc* desc) {
+  std::string why;
+  if (!valid_desc(desc, &why)) return 0;
+  rs_problem tmp;
+  tmp.d = *desc;
+  tmp.mixed = desc->precision == RS_MIXED;
+  tmp.z = dims_of(desc);
+  Carver cv{nullptr};
+  carve(&tmp, cv);
+  return cv.off + 256;
+}
+
+rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* stream, rs_problem** out) {
+  std::string why;
+  if (!out) { snprintf(g_err, sizeof g_err, "out is NULL"); return RS_EINVAL; }
+  *out = nullptr;
+  if (!valid_desc(desc, &why)) { snprintf(g_err, sizeof g_err, "%s", why.c_str()); return RS_EINVAL; }
+  if (!d_dev || !workspace_dev) { snprintf(g_err, sizeof g_err, "d_dev / workspace_dev is NULL"); return RS_EINVAL; }
+  if (((uintptr_t)workspace_dev) % 256) { snprintf(g_err, sizeof g_err, "workspace must be 256-byte aligned"); return RS_EINVAL; }
+  const size_t need = rs_workspace_bytes(desc);
+  if (workspace_bytes < need) {
+    snprintf(g_err, sizeof g_err, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+    return RS_ENOMEM;
+  }
+  rs_problem* P = new rs_problem();
+  P->d = *desc;
+  P->gammas.assign(desc->gammas_host, desc->gammas_host + desc->M);
+  P->d.gammas_host = P->gammas.data();
+  P->s = (cudaStream_t)stream;
+  P->mixed = desc->precision == RS_MIXED;
+  P->z = dims_of(desc);
+  P->tp = make_taps(desc->sigma, desc->radius);
+  P->need = need;
+  P->gprev_nz.assign(desc->M, 0);
+  Carver cv{(char*)workspace_dev};
+  carve(P, cv);
+  const long n = P->z.n;
+  auto fail = [&](cudaError_t e) {
+    snprintf(g_err, sizeof g_err, "CUDA error %s in rs_create_problem", cudaGetErrorString(e));
+    delete P;
+    return RS_ECUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(P->gam, P->gammas.data(), desc->M * sizeof(double), cudaMemcpyHostToDevice, P->s))) return fail(e);
+  if ((e = cudaMemcpyAsync(P->dimg, d_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, P->s))) return fail(e);
+  if ((e = check_finite(P->dimg, n, 0, P->ok, P->s))) return fail(e);
+  int okh = 0;
+  if ((e = cudaMemcpyAsync(&okh, P->ok, sizeof(int), cudaMemcpyDeviceToHost, P->s))) return fail(e);
+  if ((e = cudaStreamSynchronize(P->s))) return fail(e);
+  if (!okh) { snprintf(g_err, sizeof g_err, "d contains NaN or Inf"); delete P; return RS_EINVAL; }
+  if ((e = blur_apply(P->dimg, P->b, desc->height, desc->width, P->tp, 1, P->s))) return fail(e);
+  if ((e = norm2_partials<double>(P->b, n, P->partials, P->s))) return fail(e);
+  if ((e = reduce_partials(P->partials, P->z.G, 1, 1, P->scal + 15, P->s, nullptr, 0, nullptr))) return fail(e);
+  double b2 = 0.0;
+  if ((e = cudaMemcpyAsync(&b2, P->scal + 15, sizeof b2, cudaMemcpyDeviceToHost, P->s))) return fail(e);
+  if ((e = cudaStreamSynchronize(P->s))) return fail(e);
+  P->bnorm = std::sqrt(b2);
+  if (!(P->bnorm > 0.0)) { snprintf(g_err, sizeof g_err, "b = H^T d is zero"); delete P; return RS_EINVAL; }
+  if (P->mixed) {
+    if ((e = convert<double, float>(P->b, (float*)P->bT, n, P->s))) return fail(e);
+  }
+  *out = P;
+  return RS_OK;
+}
+
+rs_status rs_set_weights(rs_problem* P, const double* w_dev) {
+  if (!P) return RS_EINVAL;
+  if (!w_dev) return (rs_status)P->set_err(RS_EINVAL, "w_dev is NULL");
+  const long n = P->z.n;
+  CU(check_finite(w_dev, 2 * n, 1, P->ok, P->s));
+  int okh = 0;
+  if (read_back(P, &okh, P->ok, sizeof okh)) return RS_ECUDA;
+  if (!okh) return (rs_status)P->set_err(RS_EINVAL, "weights must be finite and > 0");
+  if (P->k >= 0) CU(cudaMemcpyAsync(P->wprev64, P->w64, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
+  CU(cudaMemcpyAsync(P->w64, w_dev, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
+  if (P->mixed) CU((convert<double, float>(P->w64, (float*)P->wT, 2 * n, P->s)));
+  P->k += 1;
+  P->have_recycle = false;
+  return RS_OK;
+}
+
+rs_status rs_update_recycle(rs_problem* P, int mode) {
+  if (!P) return RS_EINVAL;
+  if (P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  if (mode == RS_INIT) {
+    if (P->mixed) return (rs_status)init_principal<float>(P);
+    return (rs_status)init_principal<double>(P);
+  }
+  if (mode == RS_UPDATE) {
+    if (!P->have_prev || P->k < 1)
+      return (rs_status)P->set_err(RS_ENOTREADY, "RS_UPDATE needs the solutions of a previous step");
+    if (P->mixed) return (rs_status)update_principal<float>(P);
+    return (rs_status)update_principal<double>(P);
+  }
+  return (rs_status)P->set_err(RS_EINVAL, "mode must be RS_INIT or RS_UPDATE");
+}
+
+rs_status rs_set_recycle_basis(rs_problem* P, const double* U_dev, int ncols) {
+  if (!P) return RS_EINVAL;
+  if (P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  if (!U_dev || ncols < 1 || ncols > P->z.cmax)
+    return (rs_status)P->set_err(RS_EINVAL, "need 1 <= ncols <= %d and a non-NULL U", P->z.cmax);
+  CU(cudaMemcpy2DAsync(P->Ut_raw, P->z.ld * sizeof(double), U_dev, P->z.n * sizeof(double),
+                       P->z.n * sizeof(double), ncols, cudaMemcpyDeviceToDevice, P->s));
+  if (P->mixed) return (rs_status)finish_principal<float>(P, ncols);
+  return (rs_status)finish_principal<double>(P, ncols);
+}
+
+rs_status rs_solve_shifts(rs_problem* P, double* X_dev, rs_solve_stats* stats_host,
+                          const int* iters_override_host) {
+  if (!P) return RS_EINVAL;
+  if (!P->have_recycle) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_update_recycle first");
+  if (!X_dev) return (rs_status)P->set_err(RS_EINVAL, "X_dev is NULL");
+  if (iters_override_host)
+    for (int l = 0; l < P->z.M; ++l)
+      if (iters_override_host[l] < 0) return (rs_status)P->set_err(RS_EINVAL, "negative iteration override");
+  if (P->mixed) return (rs_status)solve_all<float>(P, X_dev, stats_host, iters_override_host);
+  return (rs_status)solve_all<double>(P, X_dev, stats_host, iters_override_host);
+}
+
+rs_status rs_initial_guesses(rs_problem* P, double* X0_dev, double* R0_dev) {
+  if (!P) return RS_EINVAL;
+  if (!P->have_recycle) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_update_recycle first");
+  if (!X0_dev || !R0_dev) return (rs_status)P->set_err(RS_EINVAL, "NULL output");
+  const long n = P->z.n, ld = P->z.ld;
+  const int nc = P->nc, M = P->z.M;
+  for (int l = 0; l < M; ++l) CU(cudaMemcpyAsync(R0_dev + (long)l * n, P->b, n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
+  if (P->mixed) {
+    CU((gemm_ts<float, double>((float*)P->Ut, ld, nc, P->C, nc, M, 0.0, X0_dev, n, n, P->s)));
+    CU((gemm_ts<float, double>((float*)P->AU, ld, nc, P->CA, nc, M, 1.0, R0_dev, n, n, P->s)));
+    CU((gemm_ts<float, double>((float*)P->EU, ld, nc, P->CE, nc, M, 1.0, R0_dev, n, n, P->s)));
+  } else {
+    CU((gemm_ts<double, double>((double*)P->Ut, ld, nc, P->C, nc, M, 0.0, X0_dev, n, n, P->s)));
+    CU((gemm_ts<double, double>((double*)P->AU, ld, nc, P->CA, nc, M, 1.0, R0_dev, n, n, P->s)));
+    CU((gemm_ts<double, double>((double*)P->EU, ld, nc, P->CE, nc, M, 1.0, R0_dev, n, n, P->s)));
+  }
+  CU(cudaStreamSynchronize(P->s));
+  return RS_OK;
+}
+
+rs_status rs_get_principal_basis(rs_problem* P, double* U_dev, int* nc_host) {
+  if (!P) return RS_EINVAL;
+  if (!P->have_recycle) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_update_recycle first");
+  if (!U_dev || !nc_host) return (rs_status)P->set_err(RS_EINVAL, "NULL output");
+  const long n = P->z.n, ld = P->z.ld;
+  for (int j = 0; j < P->nc; ++j) {
+    if (P->mixed) CU((convert<float, double>((float*)P->Ut + (long)j * ld, U_dev + (long)j * n, n, P->s)));
+    else CU(cudaMemcpyAsync(U_dev + (long)j * n, (double*)P->Ut + (long)j * ld, n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
+  }
+  CU(cudaStreamSynchronize(P->s));
+  *nc_host = P->nc;
+  return RS_OK;
+}
+
+rs_status rs_apply_operator(rs_problem* P, double gamma, const double* x_dev, double* y_dev,
+                            double* y2_dev, int mode, int use_working_precision) {
+  if (!P) return RS_EINVAL;
+  if (!x_dev || !y_dev || (mode == 1 && !y2_dev)) return (rs_status)P->set_err(RS_EINVAL, "NULL vector");
+  if (mode < 0 || mode > 3) return (rs_status)P->set_err(RS_EINVAL, "mode must be 0..3");
+  if (mode != 3 && P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  const long n = P->z.n, ld = P->z.ld;
+  const int H = P->d.height, W = P->d.width;
+  if (mode == 3) {
+    CU(blur_apply(x_dev, y_dev, H, W, P->tp, 0, P->s));
+  } else if (P->mixed && use_working_precision) {
+    float* xf = (float*)P->u;
+    float* yf = (float*)P->y;
+    float* y2f = (float*)P->xm;
+    CU((convert<double, float>(x_dev, xf, n, P->s)));
+    CU(op_apply<float>(xf, ld, 1, (float*)P->wT, yf, y2f, ld, H, W, P->tp, gamma, mode, P->s));
+    CU((convert<float, double>(yf, y_dev, n, P->s)));
+    if (mode == 1) CU((convert<float, double>(y2f, y2_dev, n, P->s)));
+    P->mv_total += 1;
+  } else {
+    CU(op_apply<double>(x_dev, n, 1, P->w64, y_dev, y2_dev, n, H, W, P->tp, gamma, mode, P->s));
+    P->mv_total += 1;
+  }
+  CU(cudaStreamSynchronize(P->s));
+  return RS_OK;
+}
+
+rs_status rs_irn_weights(rs_problem* P, const double* x_dev, double beta, double* w_dev) {
+  if (!P) return RS_EINVAL;
+  if (!x_dev || !w_dev || !(beta > 0.0)) return (rs_status)P->set_err(RS_EINVAL, "need x, w and beta > 0");
+  CU(irn_weights(x_dev, beta, w_dev, P->d.height, P->d.width, P->s));
+  CU(cudaStreamSynchronize(P->s));
+  return RS_OK;
+}
+
+rs_status rs_lcurve(rs_problem* P, const double* X_dev, int count, double* rho_host,
+                    double* eta_host, int* l_star_host) {
+  if (!P) return RS_EINVAL;
+  if (!X_dev || count < 1 || count > P->z.M || !rho_host || !eta_host || !l_star_host)
+    return (rs_status)P->set_err(RS_EINVAL, "bad L-curve arguments");
+  if (P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  const long n = P->z.n;
+  for (int l = 0; l < count; ++l) {
+    const double* x = X_dev + (long)l * n;
+    CU(blur_apply(x, P->t64, P->d.height, P->d.width, P->tp, 0, P->s));
+    CU(residual64(P->dimg, P->t64, nullptr, n, P->partials, P->s));
+    CU(reduce_partials(P->partials, P->z.G, 1, 1, P->lc + l, P->s, nullptr, 0, nullptr));
+    CU(wgrad_norm2_partials(x, P->w64, P->d.height, P->d.width, P->partials, P->z.G, P->s));
+    CU(reduce_partials(P->partials, P->z.G, 1, 1, P->lc + P->z.M + l, P->s, nullptr, 0, nullptr));
+  }
+  k_lcurve_corner<<<1, 32, 0, P->s>>>(P->lc, P->lc + P->z.M, count, P->lstar);
+  CU(launched());
+  std::vector<double> h(2 * P->z.M);
+  if (read_back(P, h.data(), P->lc, 2 * P->z.M * sizeof(double))) return RS_ECUDA;
+  if (read_back(P, l_star_host, P->lstar, sizeof(int))) return RS_ECUDA;
+  for (int l = 0; l < count; ++l) {
+    rho_host[l] = std::sqrt(h[l]);
+    eta_host[l] = std::sqrt(h[P->z.M + l]);
+  }
+  return RS_OK;
+}
+
+rs_status rs_synthesize_data(const rs_problem_desc* desc, const double* x_dev, const double* z_dev,
+                             double eta, double* d_out_dev, void* workspace_dev, size_t workspace_bytes,
+                             void* stream) {
+  if (!desc || desc->height < 1 || desc->width < 1 || !(desc->sigma > 0.0) || desc->radius < 0 ||
+      desc->radius > 16) {
+    snprintf(g_err, sizeof g_err, "bad description");
+    return RS_EINVAL;
+  }
+  if (!x_dev || !z_dev || !d_out_dev || !workspace_dev) {
+    snprintf(g_err, sizeof g_err, "NULL pointer");
+    return RS_EINVAL;
+  }
+  const long n = (long)desc->height * desc->width;
+  const int G = red_grid(n);
+  if (workspace_bytes < (size_t)(G + 8) * sizeof(double)) {
+    snprintf(g_err, sizeof g_err, "workspace too small");
+    return RS_ENOMEM;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* part = (double*)workspace_dev;
+  double* sc = part + G;
+  const Taps tp = make_taps(desc->sigma, desc->radius);
+  cudaError_t e;
+  if ((e = blur_apply(x_dev, d_out_dev, desc->height, desc->width, tp, 0, s)) ||
+      (e = norm2_partials<double>(d_out_dev, n, part, s)) ||
+      (e = reduce_partials(part, G, 1, 1, sc, s, nullptr, 0, nullptr)) ||
+      (e = norm2_partials<double>(z_dev, n, part, s)) ||
+      (e = reduce_partials(part, G, 1, 1, sc + 1, s, nullptr, 0, nullptr))) {
+    snprintf(g_err, sizeof g_err, "CUDA error %s", cudaGetErrorString(e));
+    return RS_ECUDA;
+  }
+  k_add_scaled<<<64, 256, 0, s>>>(z_dev, sc, sc + 1, eta, d_out_dev, n);
+  if ((e = launched()) || (e = cudaStreamSynchronize(s))) {
+    snprintf(g_err, sizeof g_err, "CUDA error %s", cudaGetErrorString(e));
+    return RS_ECUDA;
+  }
+  return RS_OK;
+}
+
+rs_status rs_get_info(const rs_problem* P, rs_info* info) {
+  if (!P || !info) return RS_EINVAL;
+  info->n = (int)P->z.n;
+  info->k = P->k;
+  info->nc = P->nc;
+  info->matvecs_total = P->mv_total;
+  info->matvecs_overhead = P->mv_over;
+  info->ld = (int)P->z.ld;
+  info->kernel_launches = launch_count();
+  return RS_OK;
+}
+
+rs_status rs_set_timing(rs_problem* P, int on) {
+  if (!P) return RS_EINVAL;
+  CU(cudaStreamSynchronize(P->s));
+  timed_flush(P, 1 << 30);
+  P->timing = on != 0;
+  for (int c = 0; c < 2; ++c) {
+    P->t_launches[c] = 0;
+    P->t_pixels[c] = 0;
+    P->t_ms[c] = 0.0;
+  }
+  return RS_OK;
+}
+
+rs_status rs_get_timing(const rs_problem* P, rs_timing* t) {
+  if (!P || !t) return RS_EINVAL;
+  for (int c = 0; c < 2; ++c) {
+    t->launches[c] = P->t_launches[c];
+    t->ms[c] = P->t_ms[c];
+    t->pixels[c] = P->t_pixels[c];
+  }
+  return RS_OK;
+}
+
+const char* rs_last_error(const rs_problem* P) { return P ? P->err.c_str() : g_err; }
+
+void rs_destroy(rs_problem* P) { delete P; }
+
+}  // extern "C"

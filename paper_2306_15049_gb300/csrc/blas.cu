@@ -1,0 +1,393 @@
+// Vector kernels of the solver: multi-dots, fused updates, tall-skinny
+// products and Gram matrices. Every reduction is two-stage and deterministic:
+// a fixed grid writes one partial per CTA, and a second kernel adds the
+// partials in a fixed order, so FP64 results repeat bit for bit.
+// Products of FP32 vectors are accumulated in FP32 over runs of 8 elements
+// and then in FP64.
+#include "internal.cuh"
+
+namespace rk {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of one value per thread; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+  }
+  return t;
+}
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double a = 0.0;
+  __device__ void add(double x, double y) { a = fma(x, y, a); }
+  __device__ double get() const { return a; }
+};
+template <>
+struct Acc<float> {
+  double a = 0.0;
+  float part = 0.f;
+  int cnt = 0;
+  __device__ void add(float x, float y) {
+    part = fmaf(x, y, part);
+    if (++cnt == 8) {
+      a += (double)part;
+      part = 0.f;
+      cnt = 0;
+    }
+  }
+  __device__ double get() const { return a + (double)part; }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_multidot(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host,
+           const T* __restrict__ extra, const T* __restrict__ y, long n, double* partials,
+           int stride, const int* stop) {
+  if (stop && *stop) return;
+  __shared__ double sh[kThreads / 32];
+  const int cnt = cnt_dev ? *cnt_dev : cnt_host;
+  const int nd = cnt + (extra ? 1 : 0);
+  for (int k = 0; k < nd; ++k) {
+    const T* xk = (k < cnt) ? X + (long)k * ldx : extra;
+    Acc<T> acc;
+    for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads)
+      acc.add(xk[i], y[i]);
+    const double t = block_sum(acc.get(), sh);
+    if (threadIdx.x == 0) partials[(long)blockIdx.x * stride + k] = t;
+  }
+}
+
+// One warp per output; lanes add partials g = lane, lane + 32, ... then a
+// fixed shuffle tree.
+__global__ void k_reduce(const double* __restrict__ partials, int G, int nd, int stride,
+                         const int* cnt_dev, int extra, double* out, const int* stop) {
+  if (stop && *stop) return;
+  const int ndd = cnt_dev ? (*cnt_dev + extra) : nd;
+  const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= ndd) return;
+  double t = 0.0;
+  for (int g = lane; g < G; g += 32) t += partials[(long)g * stride + warp];
+  t = warp_sum(t);
+  if (lane == 0) out[warp] = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_multi_axpy(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host,
+             const double* __restrict__ c, double sign, T* __restrict__ y, long n,
+             double* norm_partials, const int* stop) {
+  if (stop && *stop) return;
+  __shared__ double sh[kThreads / 32];
+  __shared__ T sc[kMaxDots];
+  const int cnt = cnt_dev ? *cnt_dev : cnt_host;
+  for (int k = threadIdx.x; k < cnt; k += kThreads) sc[k] = T(sign * c[k]);
+  __syncthreads();
+  Acc<T> acc;
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
+    T v = y[i];
+    for (int k = 0; k < cnt; ++k) v += sc[k] * X[(long)k * ldx + i];
+    y[i] = v;
+    acc.add(v, v);
+  }
+  if (norm_partials) {
+    const double t = block_sum(acc.get(), sh);
+    if (threadIdx.x == 0) norm_partials[blockIdx.x] = t;
+  }
+}
+
+template <typename TX, typename TY>
+__global__ void __launch_bounds__(kThreads)
+k_gemm_ts(const TX* __restrict__ X, long ldx, int nx, const double* __restrict__ C, int ldc,
+          int ny, double beta, TY* __restrict__ Y, long ldy, long n) {
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
+    for (int l = 0; l < ny; ++l) {
+      double acc = 0.0;
+      const double* cl = C + (long)l * ldc;
+      for (int j = 0; j < nx; ++j) acc = fma((double)X[(long)j * ldx + i], cl[j], acc);
+      TY* yp = Y + (long)l * ldy + i;
+      *yp = (beta == 0.0) ? TY(acc) : TY(beta * (double)(*yp) + acc);
+    }
+  }
+}
+
+constexpr int kGramRows = 16;
+constexpr int kGramAcc = 32;   // outputs per thread: nx * ny <= kThreads * kGramAcc
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gram(const T* __restrict__ X, long ldx, int nx, const T* __restrict__ Y, long ldy, int ny, long n,
+       long rows_per_cta, double* partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Xs = reinterpret_cast<double*>(smem_raw);
+  double* Ys = Xs + kGramRows * nx;
+  const int nout = nx * ny;
+  double acc[kGramAcc];
+#pragma unroll
+  for (int q = 0; q < kGramAcc; ++q) acc[q] = 0.0;
+  const long r0 = blockIdx.x * rows_per_cta;
+  const long r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
+  for (long rb = r0; rb < r1; rb += kGramRows) {
+    for (int idx = threadIdx.x; idx < kGramRows * nx; idx += kThreads) {
+      const int k = idx / kGramRows, rr = idx - k * kGramRows;
+      const long row = rb + rr;
+      Xs[rr * nx + k] = (row < r1) ? (double)X[(long)k * ldx + row] : 0.0;
+    }
+    for (int idx = threadIdx.x; idx < kGramRows * ny; idx += kThreads) {
+      const int k = idx / kGramRows, rr = idx - k * kGramRows;
+      const long row = rb + rr;
+      Ys[rr * ny + k] = (row < r1) ? (double)Y[(long)k * ldy + row] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kGramAcc; ++q) {
+      const int o = threadIdx.x + q * kThreads;
+      if (o < nout) {
+        const int i = o % nx, j = o / nx;
+        double a = acc[q];
+#pragma unroll
+        for (int rr = 0; rr < kGramRows; ++rr) a = fma(Xs[rr * nx + i], Ys[rr * ny + j], a);
+        acc[q] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kGramAcc; ++q) {
+    const int o = threadIdx.x + q * kThreads;
+    if (o < nout) partials[(long)blockIdx.x * nout + o] = acc[q];
+  }
+}
+
+template <typename TX, typename TY>
+__global__ void k_axpby(const TX* __restrict__ x, double a, TY* __restrict__ y, double b, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] = TY(a * (double)x[i] + (b == 0.0 ? 0.0 : b * (double)y[i]));
+}
+
+template <typename T>
+__global__ void k_scale_dev(const T* __restrict__ x, T* __restrict__ y, long n,
+                            const double* scale, int invert, const int* flag) {
+  if (flag && *flag == 0) return;
+  const double sv = invert ? 1.0 / *scale : *scale;
+  const T sc = T(sv);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] = x[i] * sc;
+}
+
+template <typename TX, typename TY>
+__global__ void k_convert(const TX* __restrict__ x, TY* __restrict__ y, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] = TY(x[i]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_norm2(const T* __restrict__ x, long n, double* partials) {
+  __shared__ double sh[kThreads / 32];
+  Acc<T> acc;
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads)
+    acc.add(x[i], x[i]);
+  const double t = block_sum(acc.get(), sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_residual64(const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r,
+             long n, double* partials) {
+  __shared__ double sh[kThreads / 32];
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
+    const double v = b[i] - y[i];
+    if (r) r[i] = v;
+    acc = fma(v, v, acc);
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void k_check_finite(const double* __restrict__ x, long n, int positive_only, int* ok) {
+  int bad = 0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    if (!isfinite(v) || (positive_only && !(v > 0.0))) bad = 1;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicAnd(ok, 0);
+}
+
+int ew_grid(long n) {
+  long g = (n + kThreads - 1) / kThreads;
+  if (g > 8 * 152) g = 8 * 152;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t multidot(const T* X, long ldx, const int* cnt_dev, int cnt_host, const T* extra,
+                     const T* y, long n, double* partials, int stride, cudaStream_t s,
+                     const int* stop) {
+  k_multidot<T><<<red_grid(n), kThreads, 0, s>>>(X, ldx, cnt_dev, cnt_host, extra, y, n, partials,
+                                                 stride, stop);
+  return launched();
+}
+
+cudaError_t reduce_partials(const double* partials, int G, int nd, int stride, double* out,
+                            cudaStream_t s, const int* cnt_dev, int extra, const int* stop) {
+  if (nd <= 0) return cudaSuccess;
+  const int warps = 8;
+  k_reduce<<<(nd + warps - 1) / warps, warps * 32, 0, s>>>(partials, G, nd, stride, cnt_dev, extra,
+                                                            out, stop);
+  return launched();
+}
+
+template <typename T>
+cudaError_t multi_axpy(const T* X, long ldx, const int* cnt_dev, int cnt_host, const double* c,
+                       double sign, T* y, long n, double* norm_partials, cudaStream_t s,
+                       const int* stop) {
+  k_multi_axpy<T><<<red_grid(n), kThreads, 0, s>>>(X, ldx, cnt_dev, cnt_host, c, sign, y, n,
+                                                   norm_partials, stop);
+  return launched();
+}
+
+template <typename TX, typename TY>
+cudaError_t gemm_ts(const TX* X, long ldx, int nx, const double* C, int ldc, int ny, double beta,
+                    TY* Y, long ldy, long n, cudaStream_t s) {
+  if (ny <= 0) return cudaSuccess;
+  k_gemm_ts<TX, TY><<<ew_grid(n), kThreads, 0, s>>>(X, ldx, nx, C, ldc, ny, beta, Y, ldy, n);
+  return launched();
+}
+
+template <typename T>
+cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,
+                 double* partials, double* out, cudaStream_t s) {
+  // out (nx x ny, column-major) = X^T Y; Y is split into column chunks so that
+  // one CTA holds at most kThreads * kGramAcc outputs.
+  if (nx <= 0 || ny <= 0) return cudaSuccess;
+  if (nx > kThreads * kGramAcc) return cudaErrorInvalidValue;
+  const int G = 152;
+  const long rows = (n + G - 1) / G;
+  int chunk = (kThreads * kGramAcc) / nx;
+  if (chunk > 1500 - nx) chunk = 1500 - nx;   // shared memory: 16 (nx + chunk) doubles <= 192 KB
+  for (int j0 = 0; j0 < ny; j0 += chunk) {
+    const int nyc = (ny - j0 < chunk) ? ny - j0 : chunk;
+    const size_t smem = (size_t)kGramRows * (nx + nyc) * sizeof(double);
+    RK_TRY(cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gram<T><<<G, kThreads, smem, s>>>(X, ldx, nx, Y + (long)j0 * ldy, ldy, nyc, n, rows, partials);
+    RK_TRY(launched());
+    RK_TRY(reduce_partials(partials, G, nx * nyc, nx * nyc, out + (long)j0 * nx, s, nullptr, 0,
+                           nullptr));
+  }
+  return cudaSuccess;
+}
+
+template <typename TX, typename TY>
+cudaError_t axpby(const TX* x, double a, TY* y, double b, long n, cudaStream_t s) {
+  k_axpby<TX, TY><<<ew_grid(n), kThreads, 0, s>>>(x, a, y, b, n);
+  return launched();
+}
+
+template <typename T>
+cudaError_t scale_dev(const T* x, T* y, long n, const double* scale, int invert, const int* flag,
+                      cudaStream_t s) {
+  k_scale_dev<T><<<ew_grid(n), kThreads, 0, s>>>(x, y, n, scale, invert, flag);
+  return launched();
+}
+
+template <typename TX, typename TY>
+cudaError_t convert(const TX* x, TY* y, long n, cudaStream_t s) {
+  k_convert<TX, TY><<<ew_grid(n), kThreads, 0, s>>>(x, y, n);
+  return launched();
+}
+
+template <typename T>
+cudaError_t norm2_partials(const T* x, long n, double* partials, cudaStream_t s) {
+  k_norm2<T><<<red_grid(n), kThreads, 0, s>>>(x, n, partials);
+  return launched();
+}
+
+cudaError_t residual64(const double* b, const double* y, double* r, long n, double* partials,
+                       cudaStream_t s) {
+  k_residual64<<<red_grid(n), kThreads, 0, s>>>(b, y, r, n, partials);
+  return launched();
+}
+
+cudaError_t check_finite(const double* x, long n, int positive_only, int* ok_dev, cudaStream_t s) {
+  const int one = 1;
+  RK_TRY(cudaMemcpyAsync(ok_dev, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+  k_check_finite<<<ew_grid(n), kThreads, 0, s>>>(x, n, positive_only, ok_dev);
+  return launched();
+}
+
+#define RK_INST_T(T)                                                                              \
+  template cudaError_t multidot<T>(const T*, long, const int*, int, const T*, const T*, long,     \
+                                   double*, int, cudaStream_t, const int*);                       \
+  template cudaError_t multi_axpy<T>(const T*, long, const int*, int, const double*, double, T*, \
+                                     long, double*, cudaStream_t, const int*);                   \
+  template cudaError_t gram<T>(const T*, long, int, const T*, long, int, long, double*, double*,  \
+                               cudaStream_t);                                                     \
+  template cudaError_t scale_dev<T>(const T*, T*, long, const double*, int, const int*,           \
+                                    cudaStream_t);                                                \
+  template cudaError_t norm2_partials<T>(const T*, long, double*, cudaStream_t);
+RK_INST_T(float)
+RK_INST_T(double)
+#define RK_INST_2(TX, TY)                                                                         \
+  template cudaError_t gemm_ts<TX, TY>(const TX*, long, int, const double*, int, int, double, TY*, \
+                                       long, long, cudaStream_t);                                 \
+  template cudaError_t axpby<TX, TY>(const TX*, double, TY*, double, long, cudaStream_t);        \
+  template cudaError_t convert<TX, TY>(const TX*, TY*, long, cudaStream_t);
+RK_INST_2(float, float)
+RK_INST_2(double, double)
+RK_INST_2(float, double)
+RK_INST_2(double, float)
+
+}  // namespace rk
+
+namespace rk {
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gather_axpy(PtrList cand, const int* __restrict__ kept_idx, const int* __restrict__ cnt_dev,
+              const double* __restrict__ coef, T* __restrict__ y, long n) {
+  __shared__ const T* cols[kMaxLocal];
+  __shared__ T sc[kMaxLocal];
+  const int cnt = *cnt_dev;
+  if (threadIdx.x < cnt) {
+    cols[threadIdx.x] = reinterpret_cast<const T*>(cand.p[kept_idx[threadIdx.x]]);
+    sc[threadIdx.x] = T(coef[threadIdx.x]);
+  }
+  __syncthreads();
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
+    T v = y[i];
+    for (int k = 0; k < cnt; ++k) v += sc[k] * cols[k][i];
+    y[i] = v;
+  }
+}
+}  // namespace
+
+template <typename T>
+cudaError_t gather_axpy(const PtrList& cand, const int* kept_idx, const int* cnt_dev,
+                        const double* coef, T* y, long n, cudaStream_t s) {
+  k_gather_axpy<T><<<red_grid(n), kThreads, 0, s>>>(cand, kept_idx, cnt_dev, coef, y, n);
+  return launched();
+}
+template cudaError_t gather_axpy<float>(const PtrList&, const int*, const int*, const double*,
+                                        float*, long, cudaStream_t);
+template cudaError_t gather_axpy<double>(const PtrList&, const int*, const int*, const double*,
+                                         double*, long, cudaStream_t);
+}  // namespace rk

@@ -1,0 +1,300 @@
+// Small dense FP64 linear algebra on the device (one CTA per problem):
+//  * one-sided Jacobi (Hestenes) for the SVD used by Algorithm "Stabilized U"
+//    and for the eigenvectors of the small SPD matrices of Algorithm
+//    "interior" (A^ + gamma E^) and of the Lanczos matrix T_a (Section 5.1);
+//  * the n_c x n_c matrices of Eq. orthupdate from the Gram blocks and R;
+//  * the per-shift Cholesky solves of Eq. orthupdate (one CTA per shift);
+//  * back-substitution with the small R_l of Eq. localU.
+#include "internal.cuh"
+
+namespace rk {
+namespace {
+
+constexpr int kDenseThreads = 256;
+constexpr int kWarps = kDenseThreads / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One-sided Jacobi on the columns of X (m x nc, column-major, ld ldx), in
+// global memory (small: L1/L2 resident). Round-robin ordering: every round
+// rotates nc/2 disjoint column pairs in parallel, one warp per pair.
+// On exit X_out = X_in V, the columns of X_out are mutually orthogonal,
+// sig[j] = ||X_out[:, j]||, and the columns are sorted by descending sig.
+__global__ void __launch_bounds__(kDenseThreads)
+k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws) {
+  __shared__ int changed;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int N = nc + (nc & 1);                 // even number of slots (slot nc is a dummy)
+  int* perm = perm_ws;                         // N entries
+  for (int i = threadIdx.x; i < nc * nc; i += kDenseThreads) V[i] = ((i % nc) == (i / nc)) ? 1.0 : 0.0;
+  for (int i = threadIdx.x; i < N; i += kDenseThreads) perm[i] = i;
+  __syncthreads();
+  const double tol = 1e-15;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) changed = 0;
+    __syncthreads();
+    for (int round = 0; round < N - 1; ++round) {
+      for (int pr = warp; pr < N / 2; pr += kWarps) {
+        int p = perm[2 * pr], q = perm[2 * pr + 1];
+        if (p >= nc || q >= nc) continue;
+        if (p > q) { const int t = p; p = q; q = t; }
+        double* xp = X + (long)p * ldx;
+        double* xq = X + (long)q * ldx;
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          const double u = xp[i], v = xq[i];
+          a = fma(u, u, a);
+          b = fma(v, v, b);
+          c = fma(u, v, c);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        if (c != 0.0 && fabs(c) > tol * sqrt(a * b)) {
+          const double zeta = (b - a) / (2.0 * c);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int i = lane; i < m; i += 32) {
+            const double u = xp[i], v = xq[i];
+            xp[i] = cs * u - sn * v;
+            xq[i] = sn * u + cs * v;
+          }
+          double* vp = V + (long)p * nc;
+          double* vq = V + (long)q * nc;
+          for (int i = lane; i < nc; i += 32) {
+            const double u = vp[i], v = vq[i];
+            vp[i] = cs * u - sn * v;
+            vq[i] = sn * u + cs * v;
+          }
+          if (lane == 0) changed = 1;
+        }
+      }
+      __syncthreads();
+      // rotate the slots 1..N-1 (slot 0 fixed)
+      if (threadIdx.x == 0) {
+        const int last = perm[N - 1];
+        for (int i = N - 1; i > 1; --i) perm[i] = perm[i - 1];
+        perm[1] = last;
+      }
+      __syncthreads();
+    }
+    if (!changed) break;
+    __syncthreads();
+  }
+  // singular values and a stable descending sort (selection, swapping columns)
+  for (int j = warp; j < nc; j += kWarps) {
+    double a = 0.0;
+    for (int i = lane; i < m; i += 32) a = fma(X[(long)j * ldx + i], X[(long)j * ldx + i], a);
+    a = warp_sum(a);
+    if (lane == 0) sig[j] = sqrt(a);
+  }
+  __syncthreads();
+  __shared__ int best;
+  for (int j = 0; j < nc; ++j) {
+    if (threadIdx.x == 0) {
+      int bi = j;
+      for (int k = j + 1; k < nc; ++k)
+        if (sig[k] > sig[bi]) bi = k;
+      best = bi;
+    }
+    __syncthreads();
+    const int bi = best;
+    if (bi != j) {
+      for (int i = threadIdx.x; i < m; i += kDenseThreads) {
+        const double t = X[(long)j * ldx + i];
+        X[(long)j * ldx + i] = X[(long)bi * ldx + i];
+        X[(long)bi * ldx + i] = t;
+      }
+      for (int i = threadIdx.x; i < nc; i += kDenseThreads) {
+        const double t = V[(long)j * nc + i];
+        V[(long)j * nc + i] = V[(long)bi * nc + i];
+        V[(long)bi * nc + i] = t;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double t = sig[j];
+        sig[j] = sig[bi];
+        sig[bi] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Copy S into work, run one-sided Jacobi (for SPD S the right singular vectors
+// are the eigenvectors and the singular values the eigenvalues), and return
+// ascending eigenvalues with their eigenvectors.
+__global__ void k_copy_reverse_cols(const double* src, int rows, int cols, double* dst,
+                                    const double* sig, double* lam) {
+  for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+    const int j = idx / rows, i = idx - j * rows;
+    dst[(long)j * rows + i] = src[(long)(cols - 1 - j) * rows + i];
+  }
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) lam[j] = sig[cols - 1 - j];
+}
+
+__global__ void k_copy(const double* src, double* dst, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+}
+
+// Mm = G_KE R^{-1}, N = R^{-T} G_EE R^{-1}, UtEb = R^{-T} G_Eb. One CTA.
+__global__ void __launch_bounds__(kDenseThreads)
+k_principal_small(PrincipalSmall ps, int nc, double* T1) {
+  const double* R = ps.R;
+  // rows of X R = G  ->  X = G R^{-1}: x_j = (g_j - sum_{k<j} x_k R_kj) / R_jj
+  for (int i = threadIdx.x; i < nc; i += kDenseThreads) {
+    for (int j = 0; j < nc; ++j) {
+      double s = ps.G_KE[i + j * nc];
+      double t = ps.G_EE[i + j * nc];
+      for (int k = 0; k < j; ++k) {
+        s -= ps.Mm[i + k * nc] * R[k + j * nc];
+        t -= T1[i + k * nc] * R[k + j * nc];
+      }
+      ps.Mm[i + j * nc] = s / R[j + j * nc];
+      T1[i + j * nc] = t / R[j + j * nc];
+    }
+  }
+  __syncthreads();
+  // R^T N = T1 column by column: N_i,j = (T1_i,j - sum_{k<i} R_k,i N_k,j) / R_i,i
+  for (int j = threadIdx.x; j < nc; j += kDenseThreads) {
+    for (int i = 0; i < nc; ++i) {
+      double s = T1[i + j * nc];
+      for (int k = 0; k < i; ++k) s -= R[k + i * nc] * ps.N[k + j * nc];
+      ps.N[i + j * nc] = s / R[i + i * nc];
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nc; ++i) {
+      double s = ps.G_Eb[i];
+      for (int k = 0; k < i; ++k) s -= R[k + i * nc] * ps.UtEb[k];
+      ps.UtEb[i] = s / R[i + i * nc];
+    }
+  }
+}
+
+// One CTA per shift: S = I + d (M + M^T) + d^2 N (symmetrised), Cholesky in
+// shared memory, q = S^{-1} (Ktb + d UtEb), c = R^{-1} q.
+__global__ void __launch_bounds__(kDenseThreads)
+k_principal_solves(const double* __restrict__ Mm, const double* __restrict__ N,
+                   const double* __restrict__ Ktb, const double* __restrict__ UtEb,
+                   const double* __restrict__ R, int nc, const double* __restrict__ gammas,
+                   double gstar, double* C, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* S = reinterpret_cast<double*>(smem_raw);   // nc x nc
+  double* q = S + nc * nc;                           // nc
+  __shared__ int bad;
+  const int l = blockIdx.x;
+  const double d = gammas[l] - gstar;
+  for (int idx = threadIdx.x; idx < nc * nc; idx += kDenseThreads) {
+    const int i = idx % nc, j = idx / nc;
+    const double mij = Mm[i + j * nc] + Mm[j + i * nc];
+    const double nij = 0.5 * (N[i + j * nc] + N[j + i * nc]);
+    S[idx] = (i == j ? 1.0 : 0.0) + d * mij + d * d * nij;
+  }
+  for (int i = threadIdx.x; i < nc; i += kDenseThreads) q[i] = Ktb[i] + d * UtEb[i];
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  // right-looking Cholesky, lower factor stored in the lower triangle of S
+  for (int k = 0; k < nc; ++k) {
+    if (threadIdx.x == 0) {
+      const double piv = S[k + k * nc];
+      if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
+      S[k + k * nc] = sqrt(piv > 0.0 ? piv : 1.0);
+    }
+    __syncthreads();
+    const double lkk = S[k + k * nc];
+    for (int i = k + 1 + threadIdx.x; i < nc; i += kDenseThreads) S[i + k * nc] /= lkk;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (nc - k - 1) * (nc - k - 1); idx += kDenseThreads) {
+      const int i = k + 1 + idx % (nc - k - 1), j = k + 1 + idx / (nc - k - 1);
+      if (j <= i) S[i + j * nc] -= S[i + k * nc] * S[j + k * nc];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // L y = rhs, L^T q = y
+    for (int i = 0; i < nc; ++i) {
+      double s = q[i];
+      for (int k = 0; k < i; ++k) s -= S[i + k * nc] * q[k];
+      q[i] = s / S[i + i * nc];
+    }
+    for (int i = nc - 1; i >= 0; --i) {
+      double s = q[i];
+      for (int k = i + 1; k < nc; ++k) s -= S[k + i * nc] * q[k];
+      q[i] = s / S[i + i * nc];
+    }
+    // c = R^{-1} q (back substitution)
+    double* c = C + (long)l * nc;
+    for (int i = nc - 1; i >= 0; --i) {
+      double s = q[i];
+      for (int k = i + 1; k < nc; ++k) s -= R[i + k * nc] * c[k];
+      c[i] = s / R[i + i * nc];
+    }
+    status[l] = bad;
+  }
+}
+
+__global__ void k_tri_solve_upper(const double* R, int ldr, const int* cnt_dev, const double* z,
+                                  double* out) {
+  if (threadIdx.x != 0) return;
+  const int s = *cnt_dev;
+  for (int i = s - 1; i >= 0; --i) {
+    double v = z[i];
+    for (int k = i + 1; k < s; ++k) v -= R[i + k * ldr] * out[k];
+    out[i] = v / R[i + i * ldr];
+  }
+}
+
+}  // namespace
+
+cudaError_t jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws,
+                       cudaStream_t s) {
+  if (nc <= 0) return cudaSuccess;
+  k_jacobi_svd<<<1, kDenseThreads, 0, s>>>(X, m, nc, ldx, V, sig, perm_ws);
+  return launched();
+}
+
+cudaError_t spd_eig(const double* S, int n, double* lam, double* Q, double* work, int* perm_ws,
+                    cudaStream_t s) {
+  // work: n*n (copy of S) + n*n (V) + n (sig)
+  if (n <= 0) return cudaSuccess;
+  double* X = work;
+  double* V = work + (long)n * n;
+  double* sig = V + (long)n * n;
+  k_copy<<<1, kDenseThreads, 0, s>>>(S, X, n * n);
+  RK_TRY(launched());
+  k_jacobi_svd<<<1, kDenseThreads, 0, s>>>(X, n, n, n, V, sig, perm_ws);
+  RK_TRY(launched());
+  k_copy_reverse_cols<<<1, kDenseThreads, 0, s>>>(V, n, n, Q, sig, lam);
+  return launched();
+}
+
+cudaError_t principal_small(const PrincipalSmall& ps, int nc, double* T1, cudaStream_t s) {
+  if (nc <= 0) return cudaSuccess;
+  k_principal_small<<<1, kDenseThreads, 0, s>>>(ps, nc, T1);
+  return launched();
+}
+
+cudaError_t principal_solves(const double* Mm, const double* N, const double* Ktb,
+                             const double* UtEb, const double* R, int nc, const double* gammas,
+                             double gstar, int M, double* C, int* status, cudaStream_t s) {
+  if (nc <= 0 || M <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(nc * nc + nc) * sizeof(double);
+  RK_TRY(cudaFuncSetAttribute(k_principal_solves, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
+  k_principal_solves<<<M, kDenseThreads, smem, s>>>(Mm, N, Ktb, UtEb, R, nc, gammas, gstar, C,
+                                                    status);
+  return launched();
+}
+
+cudaError_t tri_solve_upper(const double* R, int ldr, const int* cnt_dev, const double* z,
+                            double* out, cudaStream_t s) {
+  k_tri_solve_upper<<<1, 32, 0, s>>>(R, ldr, cnt_dev, z, out);
+  return launched();
+}
+
+}  // namespace rk

@@ -1,0 +1,182 @@
+// Internal interface between the CUDA translation units of librecyc.
+// Not part of the public C ABI (include/recyc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rk {
+
+constexpr int kThreads = 256;        // threads per CTA of the vector kernels
+constexpr int kMaxTaps = 33;         // blur half-width r <= 16
+constexpr int kMaxLocal = 16;        // columns of a local recycle space K_l
+constexpr int kMaxDots = 256;        // dots reduced by one k_reduce launch
+constexpr int kMaxP = 110;           // principal recycle dimension cap
+
+struct Taps {
+  double g[kMaxTaps];
+  int r;
+};
+
+// Every kernel launch of the library goes through launched(): it returns the
+// launch status and counts the launch (process-wide, for the benchmark).
+cudaError_t launched();
+long long launch_count();
+
+// Number of CTAs of every grid-stride reduction over n elements. Fixed per n so
+// that partial sums are combined in the same order on every call.
+int red_grid(long n);
+
+// ---------------------------------------------------------------- matvec.cu
+// Shifted operator on ncols columns (column c at x + c*ldx, y + c*ldy):
+//   mode 0: y = A x + gamma E x;  mode 1: y = A x, y2 = E x;  mode 2: y = E x
+// with A = H^T H (zero-boundary separable blur) and E = L^T diag(w) L,
+// w = [w_x (n); w_y (n)] in the vector type.
+template <typename T>
+cudaError_t op_apply(const T* x, long ldx, int ncols, const T* w, T* y, T* y2, long ldy,
+                     int H, int W, const Taps& tp, double gamma, int mode, cudaStream_t s,
+                     const int* stop = nullptr);
+// y = H x (adjoint = 0) or y = H^T x (adjoint = 1), FP64.
+cudaError_t blur_apply(const double* x, double* y, int H, int W, const Taps& tp, int adjoint,
+                       cudaStream_t s);
+// w = ((L x)^2 + beta^2)^(-1/2) over 2n entries.
+cudaError_t irn_weights(const double* x, double beta, double* w, int H, int W, cudaStream_t s);
+// partials[g] = sum over CTA g of w .* (L x)^2 (for the L-curve seminorm).
+cudaError_t wgrad_norm2_partials(const double* x, const double* w, int H, int W, double* partials,
+                                 int G, cudaStream_t s);
+
+// ---------------------------------------------------------------- blas.cu
+// Kernels given a non-null `stop` do nothing when *stop != 0 (a finished
+// solve). Counts: cnt = cnt_dev ? *cnt_dev : cnt_host.
+// partials[g*stride + k] = CTA g's share of X_k . y for k < cnt (X_k = X + k*ldx);
+// if extra != nullptr also extra . y at index cnt.
+template <typename T>
+cudaError_t multidot(const T* X, long ldx, const int* cnt_dev, int cnt_host, const T* extra,
+                     const T* y, long n, double* partials, int stride, cudaStream_t s,
+                     const int* stop);
+// out[k] = sum_g partials[g*stride + k] in a fixed order, k < nd (or
+// k < *cnt_dev + extra when cnt_dev is given).
+cudaError_t reduce_partials(const double* partials, int G, int nd, int stride, double* out,
+                            cudaStream_t s, const int* cnt_dev, int extra, const int* stop);
+// y += sign * sum_{k < cnt} c[k] X_k (c on the device, cnt <= kMaxDots); with
+// norm_partials also the per-CTA partial sums of y^2.
+template <typename T>
+cudaError_t multi_axpy(const T* X, long ldx, const int* cnt_dev, int cnt_host, const double* c,
+                       double sign, T* y, long n, double* norm_partials, cudaStream_t s,
+                       const int* stop);
+// Y[:, l] = beta * Y[:, l] + sum_{j<nx} X[:, j] * C[j + l*ldc] for l < ny.
+template <typename TX, typename TY>
+cudaError_t gemm_ts(const TX* X, long ldx, int nx, const double* C, int ldc, int ny, double beta,
+                    TY* Y, long ldy, long n, cudaStream_t s);
+// out (nx x ny, column-major, FP64) = X^T Y; partials needs 152 * min(nx*ny, 8192) doubles.
+template <typename T>
+cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,
+                 double* partials, double* out, cudaStream_t s);
+// y = a*x + b*y (host scalars).
+template <typename TX, typename TY>
+cudaError_t axpby(const TX* x, double a, TY* y, double b, long n, cudaStream_t s);
+// y = x * (*scale) or x / (*scale) (invert); nothing when flag && *flag == 0.
+template <typename T>
+cudaError_t scale_dev(const T* x, T* y, long n, const double* scale, int invert, const int* flag,
+                      cudaStream_t s);
+template <typename TX, typename TY>
+cudaError_t convert(const TX* x, TY* y, long n, cudaStream_t s);
+template <typename T>
+cudaError_t norm2_partials(const T* x, long n, double* partials, cudaStream_t s);
+// r = b - y (r may be nullptr) and per-CTA partial sums of r^2.
+cudaError_t residual64(const double* b, const double* y, double* r, long n, double* partials,
+                       cudaStream_t s);
+// y += sum_{k < *cnt_dev} coef[k] * cand.p[kept_idx[k]] (columns given by pointers).
+struct PtrList {
+  const void* p[kMaxLocal];
+};
+template <typename T>
+cudaError_t gather_axpy(const PtrList& cand, const int* kept_idx, const int* cnt_dev,
+                        const double* coef, T* y, long n, cudaStream_t s);
+// *ok_dev = 1 if every entry is finite (and > 0 with positive_only), else 0.
+cudaError_t check_finite(const double* x, long n, int positive_only, int* ok_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- dense.cu
+// One-sided Jacobi on the columns of X (m x nc, ld ldx, in place):
+// X_out = X_in V with orthogonal columns sorted by descending norm sig.
+// V: nc x nc. perm_ws: nc + 1 ints. One CTA.
+cudaError_t jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws,
+                       cudaStream_t s);
+// Ascending eigenvalues lam and eigenvectors Q (n x n) of a small SPD S.
+// work: 2 n^2 + n doubles.
+cudaError_t spd_eig(const double* S, int n, double* lam, double* Q, double* work, int* perm_ws,
+                    cudaStream_t s);
+
+struct PrincipalSmall {
+  const double* R;       // nc x nc upper triangular, (A + g* E) U~ = K R
+  const double* G_KE;    // nc x nc: K^T (E U~)
+  const double* G_EE;    // nc x nc: (E U~)^T (E U~)
+  const double* G_Eb;    // nc: (E U~)^T b
+  double* Mm;            // out nc x nc: K^T E U = G_KE R^{-1}
+  double* N;             // out nc x nc: R^{-T} G_EE R^{-1}
+  double* UtEb;          // out nc: R^{-T} G_Eb = U^T E b
+};
+cudaError_t principal_small(const PrincipalSmall& ps, int nc, double* T1, cudaStream_t s);
+// One CTA per shift l: (I + d (M + M^T) + d^2 N) q = Ktb + d UtEb with
+// d = gammas[l] - gstar (Cholesky); C[:, l] = R^{-1} q; status[l] = 1 if not SPD.
+cudaError_t principal_solves(const double* Mm, const double* N, const double* Ktb,
+                             const double* UtEb, const double* R, int nc, const double* gammas,
+                             double gstar, int M, double* C, int* status, cudaStream_t s);
+// out = R^{-1} z for the leading cnt x cnt block of an upper-triangular R.
+cudaError_t tri_solve_upper(const double* R, int ldr, const int* cnt_dev, const double* z,
+                            double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- minres.cu
+// Device-resident scalars of one recycled MINRES solve.
+struct MinresState {
+  double beta;             // beta_j (coefficient of v_{j-1})
+  double cs1, sn1, cs2, sn2;
+  double eta;              // rotated right-hand side; |eta| = LSQ residual norm
+  double tol_abs;
+  double alpha, beta_next;
+  double inv_beta_next, delta, eps, inv_gamma, tau;   // this step's coefficients
+  double xi;
+  int iters, maxit, stop, performed, breakdown, s;
+  double h[kMaxLocal];     // K^T Op v_j
+  double h1[kMaxLocal], h2[kMaxLocal];
+  double z[kMaxLocal];     // K^T r - sum_j tau_j hhat_j
+};
+cudaError_t minres_init(MinresState* st, const double* xi2, const double* Ktr, const int* s_dev,
+                        double tol_abs, int maxit, cudaStream_t s);
+cudaError_t minres_step(MinresState* st, const double* hdots, const double* partials, int G,
+                        double* alphas_rec, double* betas_rec, int rec_cap, cudaStream_t s);
+template <typename T>
+cudaError_t lanczos_update(const MinresState* st, const T* K, long ldk, const double* hdots,
+                           const T* y, const T* v, const T* vprev, T* u, long n,
+                           double* norm_partials, cudaStream_t s);
+template <typename T>
+cudaError_t minres_direction(const MinresState* st, const T* u, T* vnext, const T* v,
+                             const T* d1, const T* d2, T* d, T* xm, long n, cudaStream_t s);
+cudaError_t minres_poll(const MinresState* st, int* out_dev2, cudaStream_t s);
+
+// ---------------------------------------------------------------- cgs.cu
+struct CgsCtx {
+  int* count;              // [0] kept columns s, [1] pending
+  int* flag;               // [0] last candidate kept
+  double* Rk;              // compact R (ldr x ldr) or nullptr
+  int ldr;                 // max kept columns (also the dot stride)
+  double* Rfull;           // per-candidate R columns (ldrf rows) or nullptr
+  int ldrf;
+  int* kept_idx;           // candidate index of every kept column
+  double* coef;            // scratch 2 * ldr
+  double* partials;        // scratch red_grid(n) * ldr
+  double* scal;            // scratch 4
+  double drop_rel;
+};
+cudaError_t cgs_reset(const CgsCtx& c, cudaStream_t s);
+template <typename T>
+cudaError_t cgs2_column(const CgsCtx& c, T* Q, long ldq, T* b, int cand_index, long n,
+                        cudaStream_t s);
+
+}  // namespace rk
+
+#define RK_TRY(expr)                          \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return _e;         \
+  } while (0)

@@ -1,0 +1,74 @@
+"""GPU parity of the fused shifted-operator kernel (matvec) against the FP64
+oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_util import Pair, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (height, width, sigma, radius): one tile, odd sizes, several tiles with a
+    # ragged tail, radius >= image/2, radius 0 and the workload radii
+    (8, 8, 1.0, 2), (37, 53, 1.5, 4), (64, 64, 1.5, 4), (130, 70, 2.5, 8),
+    (9, 7, 3.0, 12), (1, 40, 1.0, 3), (33, 1, 1.0, 3), (50, 45, 1.0, 0), (96, 100, 4.0, 12),
+]
+
+
+@pytest.mark.parametrize("h,w,sigma,r", CASES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_operator_modes_match_oracle(h, w, sigma, r, precision):
+    wl = synth.tiny(h, w, sigma=sigma, radius=r, M=4, p=4, n_ritz_local=1, seed=h * 7 + w)
+    # a random image: the piecewise-constant generator can be empty on 1-pixel-wide images
+    pr = Pair(wl, precision=precision, x_image=synth.random_vectors(h * w, 1, h + w)[:, 0])
+    n = h * w
+    wts = synth.random_weights(n, 3)
+    pr.P.rs_set_weights(pr.t(wts))
+    rng = np.random.default_rng(h + w)
+    x = rng.standard_normal(n)
+    xt = pr.t(x)
+    y = pr.torch.empty_like(xt)
+    y2 = pr.torch.empty_like(xt)
+    for wp in ([False, True] if precision == 1 else [False]):
+        tol = 1e-13 if not wp else 2e-6
+        for gamma in [1e-5, 0.3, 7.0]:
+            pr.P.rs_apply_operator(gamma, xt, y, mode=0, working_precision=wp)
+            assert rel(pr.n(y), pr.op.apply(x, gamma, wts)) < tol
+        pr.P.rs_apply_operator(0.0, xt, y, y2, mode=1, working_precision=wp)
+        assert rel(pr.n(y), pr.op.apply_A(x)) < tol
+        assert rel(pr.n(y2), pr.op.apply_E(x, wts)) < tol
+        pr.P.rs_apply_operator(0.0, xt, y, mode=2, working_precision=wp)
+        assert rel(pr.n(y), pr.op.apply_E(x, wts)) < tol
+    pr.P.rs_apply_operator(0.0, xt, y, mode=3)
+    assert rel(pr.n(y), pr.op.blur(x)) < 1e-13
+
+
+def test_synthesized_data_and_rhs_match_oracle():
+    wl = synth.tiny(40, 33, sigma=2.0, radius=6, M=4, p=4, n_ritz_local=1)
+    pr = Pair(wl)
+    assert rel(pr.n(pr.d_gpu), pr.d) < 1e-14
+
+
+def test_irn_weights_match_oracle():
+    from oracle.operator import irn_weights
+    wl = synth.tiny(29, 31, M=4, p=4, n_ritz_local=1)
+    pr = Pair(wl)
+    x = synth.piecewise_constant_image(29, 31, 5).reshape(-1) + 1e-3 * np.arange(29 * 31)
+    w = pr.torch.empty(2 * 29 * 31, dtype=pr.torch.float64, device=pr.dev)
+    pr.P.rs_irn_weights(pr.t(x), 1e-3, w)
+    assert rel(pr.n(w), irn_weights(pr.op, x, 1e-3)) < 1e-14
+
+
+def test_operator_at_full_workload_size():
+    """512 x 512, radius 8: every pixel against the oracle's matvec."""
+    wl = synth.C2
+    pr = Pair(wl)
+    n = wl.n
+    wts = synth.random_weights(n, 9, lo=1.0, hi=1000.0)
+    pr.P.rs_set_weights(pr.t(wts))
+    x = synth.piecewise_constant_image(wl.height, wl.width, 77).reshape(-1)
+    xt = pr.t(x)
+    y = pr.torch.empty_like(xt)
+    pr.P.rs_apply_operator(1e-3, xt, y)
+    assert rel(pr.n(y), pr.op.apply(x, 1e-3, wts)) < 1e-13

@@ -1,0 +1,236 @@
+"""GPU parity of the recycled shifted solves against the FP64 oracle, through
+the C ABI: principal space (Sections 5.1-5.2, Algorithm "Stabilized U"),
+initial guesses (Eq. orthupdate), local spaces and recycled MINRES
+(Eq. minShift, xFinal), FP64 and mixed precision, edge and error cases.
+
+Tolerances: FP64 solutions within 1e-6 relative of the oracle's (1e-8 when
+both run the same step counts on the same basis); mixed precision within 1e-4;
+every system's recomputed residual within the tolerance 1e-8 (a 1e-6 relative
+margin for the FP64 rounding of the residual itself)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.operator import irn_weights
+from oracle.outer import run as oracle_run
+from oracle.recycle import State, outer_step, principal_guesses
+from tests.gpu_util import Pair, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _proj_dist(A, B):
+    QA, _ = np.linalg.qr(A)
+    QB, _ = np.linalg.qr(B)
+    return np.linalg.norm(QA @ QA.T - QB @ QB.T, 2)
+
+
+@pytest.fixture(scope="module")
+def c1_oracle():
+    wl = synth.C1
+    pr = Pair(wl)
+    steps, lstars = oracle_run(pr.op, pr.b, pr.d, pr.gammas, pr.prm, wl.K, wl.beta)
+    weights = [np.ones(2 * wl.n)]
+    for k in range(wl.K - 1):
+        weights.append(irn_weights(pr.op, steps[k].X[lstars[k]], wl.beta))
+    return wl, steps, lstars, weights
+
+
+def _run_gpu(wl, weights, precision=0, batched_local=0):
+    pr = Pair(wl, precision=precision, batched_local=batched_local)
+    out = []
+    for k, w in enumerate(weights):
+        pr.P.rs_set_weights(pr.t(w))
+        pr.P.rs_update_recycle(0 if k == 0 else 1)
+        X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+        stats = pr.P.rs_solve_shifts(X)
+        info = pr.P.rs_get_info()
+        out.append((pr.n(X), stats, info))
+    return pr, out
+
+
+def test_c1_fp64_full_run_matches_oracle(c1_oracle):
+    wl, steps, lstars, weights = c1_oracle
+    pr, gpu = _run_gpu(wl, weights)
+    n_equal = n_total = 0
+    for k, (X, stats, info) in enumerate(gpu):
+        o = steps[k]
+        assert info["nc"] == o.nc, (k, info["nc"], o.nc)
+        for l in range(wl.M):
+            st = stats[l]
+            assert st["relres_true"] <= wl.tol * (1 + 1e-6), (k, l, st)
+            assert abs(st["iters"] - o.iters[l]) <= 2, (k, l, st["iters"], o.iters[l])
+            e = rel(X[l], o.X[l])
+            n_total += 1
+            if st["iters"] == o.iters[l]:
+                n_equal += 1
+                assert e <= 1e-6, (k, l, e)
+                assert st["matvecs"] == o.matvecs[l], (k, l, st["matvecs"], o.matvecs[l])
+            else:
+                assert e <= 1e-4, (k, l, e)
+    assert n_equal >= 0.75 * n_total
+
+
+def test_c1_principal_space_and_lcurve_match_oracle(c1_oracle):
+    wl, steps, lstars, weights = c1_oracle
+    pr = Pair(wl)
+    pr.P.rs_set_weights(pr.t(weights[0]))
+    pr.P.rs_update_recycle(0)
+    U = pr.torch.empty(wl.p, wl.n, dtype=pr.torch.float64, device=pr.dev)
+    nc = pr.P.rs_get_principal_basis(U)
+    Ug = pr.n(U)[:nc].T
+    assert nc == steps[0].nc
+    np.testing.assert_allclose(Ug.T @ Ug, np.eye(nc), atol=1e-12)
+    assert _proj_dist(Ug, steps[0].Ut) < 1e-6
+    X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+    pr.P.rs_solve_shifts(X)
+    rho, eta, ls = pr.P.rs_lcurve(X, wl.M)
+    np.testing.assert_allclose(rho, steps[0].extra["rho"], rtol=1e-6)
+    np.testing.assert_allclose(eta, steps[0].extra["eta"], rtol=1e-6)
+    assert ls == lstars[0]
+
+
+def test_initial_guesses_match_oracle_on_the_same_basis(c1_oracle):
+    wl, steps, lstars, weights = c1_oracle
+    pr = Pair(wl)
+    pr.P.rs_set_weights(pr.t(weights[1]))
+    Ut = steps[1].Ut
+    pr.P.rs_set_recycle_basis(pr.t(Ut.T), Ut.shape[1])
+    X0 = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+    R0 = pr.torch.empty_like(X0)
+    pr.P.rs_initial_guesses(X0, R0)
+    AU = np.stack([pr.op.apply_A(Ut[:, j]) for j in range(Ut.shape[1])], axis=1)
+    EU = np.stack([pr.op.apply_E(Ut[:, j], weights[1]) for j in range(Ut.shape[1])], axis=1)
+    C, X0o, R0o = principal_guesses(Ut, AU, EU, pr.b, pr.gammas, pr.gammas[wl.i_star - 1])
+    for l in range(wl.M):
+        assert rel(pr.n(X0)[l], X0o[l]) < 1e-8, l
+        assert rel(pr.n(R0)[l], R0o[l]) < 1e-8, l
+
+
+def test_forced_steps_on_the_same_basis_match_oracle_iterates(c1_oracle):
+    """Same principal basis, same MINRES step counts: the iterates agree to 1e-8."""
+    wl, steps, lstars, weights = c1_oracle
+    pr = Pair(wl)
+    Ut = steps[0].Ut
+    S = State()
+    forced = [max(3, int(i)) for i in steps[0].iters]
+    o = outer_step(pr.op, pr.b, pr.gammas, weights[0], S, pr.prm, Ut_given=Ut, iters_override=forced)
+    pr.P.rs_set_weights(pr.t(weights[0]))
+    pr.P.rs_set_recycle_basis(pr.t(Ut.T), Ut.shape[1])
+    X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+    stats = pr.P.rs_solve_shifts(X, iters_override=forced)
+    Xg = pr.n(X)
+    for l in range(wl.M):
+        assert stats[l]["iters"] == forced[l]
+        assert stats[l]["local_dim"] == o.local_dim[l]
+        assert rel(Xg[l], o.X[l]) < 1e-8, (l, rel(Xg[l], o.X[l]))
+
+
+def test_c1_mixed_precision_reaches_tolerance_and_oracle_accuracy(c1_oracle):
+    wl, steps, lstars, weights = c1_oracle
+    pr, gpu = _run_gpu(wl, weights, precision=1)
+    for k, (X, stats, info) in enumerate(gpu):
+        for l in range(wl.M):
+            assert stats[l]["relres_true"] <= wl.tol, (k, l, stats[l])
+            assert rel(X[l], steps[k].X[l]) <= 1e-4, (k, l, rel(X[l], steps[k].X[l]))
+            # the residual recomputed by the oracle's own operator
+            r = pr.b - pr.op.apply(X[l], pr.gammas[l], weights[k])
+            assert np.linalg.norm(r) / np.linalg.norm(pr.b) <= wl.tol * 1.001
+
+
+def test_batched_local_variant_matches_oracle():
+    wl = synth.tiny(24, 20, sigma=1.2, radius=3, M=6, p=8, n_ritz_local=3, seed=4, tol=1e-9)
+    pr = Pair(wl, batched_local=1)
+    S = State()
+    rng = np.random.default_rng(0)
+    ws = [np.ones(2 * wl.n), synth.random_weights(wl.n, 2)]
+    for k, w in enumerate(ws):
+        o = outer_step(pr.op, pr.b, pr.gammas, w, S, pr.prm)
+        pr.P.rs_set_weights(pr.t(w))
+        pr.P.rs_update_recycle(0 if k == 0 else 1)
+        X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+        stats = pr.P.rs_solve_shifts(X)
+        for l in range(wl.M):
+            assert stats[l]["relres_true"] <= wl.tol * (1 + 1e-6)
+            if stats[l]["iters"] == o.iters[l]:
+                assert rel(pr.n(X)[l], o.X[l]) < 1e-6
+
+
+@pytest.mark.parametrize("h,w,M,J,p", [(17, 23, 2, 0, 4), (33, 31, 3, 1, 5), (40, 40, 5, 2, 6)])
+def test_small_and_degenerate_configurations_converge(h, w, M, J, p):
+    wl = synth.tiny(h, w, sigma=1.0, radius=2, M=M, p=p, n_ritz_local=J, seed=h, tol=1e-9)
+    pr = Pair(wl)
+    S = State()
+    for k, wts in enumerate([np.ones(2 * wl.n), synth.random_weights(wl.n, 1)]):
+        o = outer_step(pr.op, pr.b, pr.gammas, wts, S, pr.prm)
+        pr.P.rs_set_weights(pr.t(wts))
+        pr.P.rs_update_recycle(0 if k == 0 else 1)
+        X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+        stats = pr.P.rs_solve_shifts(X)
+        assert pr.P.rs_get_info()["nc"] == o.nc
+        for l in range(wl.M):
+            assert stats[l]["relres_true"] <= wl.tol * (1 + 1e-6)
+            assert rel(pr.n(X)[l], o.X[l]) < 1e-5
+
+
+def test_errors_are_reported_not_raised_on_the_device():
+    from paper_2306_15049_gb300 import recyc
+    wl = synth.tiny(16, 16, M=4, p=4, n_ritz_local=1)
+    pr = Pair(wl)
+    X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+    with pytest.raises(recyc.RecycError) as e:
+        pr.P.rs_solve_shifts(X)
+    assert e.value.status == recyc.RS_ENOTREADY
+    bad = np.ones(2 * wl.n)
+    bad[5] = np.nan
+    with pytest.raises(recyc.RecycError) as e:
+        pr.P.rs_set_weights(pr.t(bad))
+    assert e.value.status == recyc.RS_EINVAL
+    bad[5] = -1.0
+    with pytest.raises(recyc.RecycError) as e:
+        pr.P.rs_set_weights(pr.t(bad))
+    assert e.value.status == recyc.RS_EINVAL
+    with pytest.raises(recyc.RecycError) as e:
+        pr.P.rs_update_recycle(0)
+    assert e.value.status == recyc.RS_ENOTREADY
+    pr.P.rs_set_weights(pr.t(np.ones(2 * wl.n)))
+    with pytest.raises(recyc.RecycError) as e:
+        pr.P.rs_update_recycle(1)          # no previous step yet
+    assert e.value.status == recyc.RS_ENOTREADY
+    # a workspace that is too small is refused before any work
+    import ctypes
+    lib = recyc.load()
+    h = ctypes.c_void_p()
+    st = lib.rs_create_problem(ctypes.byref(pr.desc[0]), int(pr.d_gpu.data_ptr()),
+                               int(pr.P.workspace.data_ptr()), 1024, None, ctypes.byref(h))
+    assert st == recyc.RS_ENOMEM
+
+
+def test_maxit_exhaustion_reports_noconv_with_stats():
+    from paper_2306_15049_gb300 import recyc
+    wl = synth.tiny(32, 32, sigma=1.5, radius=4, M=4, p=4, n_ritz_local=1, tol=1e-12)
+    pr = Pair(wl, maxit=3)
+    pr.P.rs_set_weights(pr.t(np.ones(2 * wl.n)))
+    pr.P.rs_update_recycle(0)
+    X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+    stats = pr.P.rs_solve_shifts(X, allow_noconv=True)
+    assert any(s["status"] == recyc.RS_ENOCONV for s in stats)
+    assert all(np.isfinite(s["relres_true"]) for s in stats)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c2_full_size_first_step_every_shift_meets_tolerance(precision):
+    """512 x 512, 16 shifts: each solution checked by the oracle's operator."""
+    wl = synth.C2
+    pr = Pair(wl, precision=precision)
+    w = np.ones(2 * wl.n)
+    pr.P.rs_set_weights(pr.t(w))
+    pr.P.rs_update_recycle(0)
+    X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+    stats = pr.P.rs_solve_shifts(X)
+    Xn = pr.n(X)
+    for l in range(wl.M):
+        r = pr.b - pr.op.apply(Xn[l], pr.gammas[l], w)
+        rr = np.linalg.norm(r) / np.linalg.norm(pr.b)
+        assert rr <= wl.tol * (1 + 1e-4), (l, rr, stats[l])
+        assert abs(rr - stats[l]["relres_true"]) <= 1e-3 * wl.tol
