@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the workload once (one step, no timing) for a profiler and exit")
     return ap.parse_args()
 
 
@@ -300,6 +302,11 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     runner = Runner(wl, args.precision, dev)
+    if args.profile_case:
+        r = runner.step()
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_case": wl.name, "precision": args.precision, **r}), flush=True)
+        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     for _ in range(max(3, args.warmup)):

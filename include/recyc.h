@@ -103,13 +103,16 @@ typedef struct {
 
 /* Per-kernel device time, gathered with CUDA events around every launch of
  * the two matvec kernels while timing is on (rs_set_timing). Index 0: the
- * Krylov matvec (A + gamma E) v in the working precision; index 1: the FP64
- * matvec of the true / refinement residual. Launches of a solve that had
- * already stopped (no-ops) are not counted. */
+ * fused MINRES step kernel (previous direction update, v_j = u / beta_j,
+ * (A + gamma E) v_j and the dots K^T y, v_j^T y) in the working precision;
+ * index 1: the FP64 matvec of the true / refinement residual. Launches of a
+ * solve that had already stopped (no-ops) are not counted. */
 typedef struct {
   long long launches[2];
   double ms[2];
   long long pixels[2];     /* pixels processed by the counted launches */
+  double bytes[2];         /* algorithmic bytes of the counted launches (no halo re-reads) */
+  double flops[2];         /* algorithmic flops of the counted launches */
 } rs_timing;
 
 /* Bytes of device workspace a problem with this description needs. Returns 0

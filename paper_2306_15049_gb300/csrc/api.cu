@@ -31,6 +31,7 @@ constexpr int kPoll = 8;                   // MINRES steps between stop-flag pol
 constexpr int kMaxSweeps = 12;             // FP64 refinement sweeps (mixed precision)
 constexpr double kInnerRho = 1e-4;         // inner relative reduction per sweep (mixed)
 constexpr int kDotStride = kMaxLocal + 1;
+constexpr int kChunk = 6;                  // MINRES steps per CUDA-graph replay (a multiple of 3)
 
 long round_up(long x, long a) { return (x + a - 1) / a * a; }
 
@@ -240,16 +241,28 @@ struct rs_problem {
     int cat;
     int iter;          // MINRES step of the launch, or -1 (always executed)
     long long pixels;
+    double bytes, flops;
   };
   bool timing = false;
   std::vector<cudaEvent_t> events;
   std::vector<TimedLaunch> pending;
   size_t pending_used = 0;
   long long t_launches[2] = {0, 0}, t_pixels[2] = {0, 0};
-  double t_ms[2] = {0.0, 0.0};
+  double t_ms[2] = {0.0, 0.0}, t_bytes[2] = {0.0, 0.0}, t_flops[2] = {0.0, 0.0};
+  // CUDA graph of kChunk fused MINRES steps (built on first use)
+  bool use_graph = true;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t gev[2 * kChunk] = {};
+  double* gcur = nullptr;
+  double* partials_a = nullptr;
 
   ~rs_problem() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaEvent_t e : gev)
+      if (e) cudaEventDestroy(e);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap) cudaStreamDestroy(cap);
   }
 
   int set_err(int code, const char* fmt, ...) {
@@ -341,6 +354,8 @@ void carve(rs_problem* P, Carver& cv) {
   P->ok = cv.take<int>(4);
   P->lstar = cv.take<int>(4);
   P->st = cv.take<MinresState>(1);
+  P->gcur = cv.take<double>(1);
+  P->partials_a = cv.take<double>((size_t)mr_matvec_blocks(P->d.height, P->d.width) * (kMaxLocal + 1));
 }
 
 #define CU(...)                                                                         \
@@ -374,17 +389,17 @@ int timed_begin(rs_problem* P) {
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
     P->events.push_back(a);
     P->events.push_back(b);
-    P->pending.push_back({0, -1, 0});
+    P->pending.push_back({0, -1, 0, 0.0, 0.0});
   }
   const int i = (int)P->pending_used++;
   cudaEventRecord(P->events[2 * i], P->s);
   return i;
 }
 
-void timed_end(rs_problem* P, int i, int cat, int iter, long long pixels) {
+void timed_end(rs_problem* P, int i, int cat, int iter, long long pixels, double bytes, double flops) {
   if (i < 0) return;
   cudaEventRecord(P->events[2 * i + 1], P->s);
-  P->pending[i] = {cat, iter, pixels};
+  P->pending[i] = {cat, iter, pixels, bytes, flops};
 }
 
 // After a stream synchronisation: add up the recorded pairs. Launches of a
@@ -398,6 +413,8 @@ void timed_flush(rs_problem* P, int valid_iter) {
     P->t_ms[r.cat] += ms;
     P->t_launches[r.cat] += 1;
     P->t_pixels[r.cat] += r.pixels;
+    P->t_bytes[r.cat] += r.bytes;
+    P->t_flops[r.cat] += r.flops;
   }
   P->pending_used = 0;
 }
@@ -415,7 +432,7 @@ int true_residual(rs_problem* P, double gamma, const double* x64, double* relres
   const int slot = timed_begin(P);
   CU(op_apply<double>(x64, P->z.ld, 1, P->w64, P->y64, nullptr, P->z.ld, P->d.height, P->d.width,
                       P->tp, gamma, 0, P->s));
-  timed_end(P, slot, 1, -1, P->z.n);
+  timed_end(P, slot, 1, -1, P->z.n, 32.0 * P->z.n, (8.0 * (2 * P->tp.r + 1) + 10.0) * P->z.n);
   CU(residual64(P->b, P->y64, P->r64, P->z.n, P->partials, P->s));
   CU(reduce_partials(P->partials, P->z.G, 1, 1, P->scal + 8, P->s, nullptr, 0, nullptr));
   double r2 = 0.0;
@@ -426,12 +443,55 @@ int true_residual(rs_problem* P, double gamma, const double* x64, double* relres
   return RS_OK;
 }
 
+// Capture kChunk fused steps (positions j = 2 .. kChunk+1; every chunk that
+// starts at j = 2 mod 3 has the same operands) into a graph, with an event
+// pair around every kernel A for the timing.
+template <typename T, typename FA, typename FB>
+int ensure_graph(rs_problem* P, FA mkA, FB mkB) {
+  if (P->gexec) return RS_OK;
+  if (!P->cap) CU(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+  for (int i = 0; i < 2 * kChunk; ++i)
+    if (!P->gev[i]) CU(cudaEventCreate(&P->gev[i]));
+  const long n = P->z.n;
+  CU(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < kChunk; ++i) {
+    const int j = 2 + i;
+    cudaEventRecordWithFlags(P->gev[2 * i], P->cap, cudaEventRecordExternal);
+    mr_matvec<T>(P->st, mkA(j), P->d.height, P->d.width, P->tp, P->cap);
+    cudaEventRecordWithFlags(P->gev[2 * i + 1], P->cap, cudaEventRecordExternal);
+    mr_lanczos<T>(P->st, mkB(j), n, nullptr, nullptr, 0, P->cap);
+  }
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamEndCapture(P->cap, &g));
+  cudaError_t e = cudaGraphInstantiate(&P->gexec, g, 0);
+  cudaGraphDestroy(g);
+  CU(e);
+  return RS_OK;
+}
+
+// Times of the kernel-A launches of the last graph replay (steps j0 ..
+// j0 + kChunk - 1); launches after the solve stopped were no-ops and are skipped.
+void graph_timing_flush(rs_problem* P, int j0, int iters_done, double bytes, double flops, long n) {
+  for (int i = 0; i < kChunk; ++i) {
+    if (j0 + i > iters_done) break;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P->gev[2 * i], P->gev[2 * i + 1]) != cudaSuccess) continue;
+    P->t_ms[0] += ms;
+    P->t_launches[0] += 1;
+    P->t_pixels[0] += n;
+    P->t_bytes[0] += bytes;
+    P->t_flops[0] += flops;
+  }
+}
+
 // Recycled MINRES on (A + gamma E) g = r (Section 2.3 / Eq. minShift) with the
 // local space (Kl, count on the device, may be 0) and optional kept Lanczos
 // vectors (keep, reorth). On exit xm holds V_m y and st->z the coupling part.
+// s_host is the local dimension (for the work accounting of the timing).
 template <typename T>
 int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_abs, int maxit,
-               int keep, bool reorth, int* iters_out, double* eta_out, int* breakdown_out) {
+               int keep, bool reorth, int* iters_out, double* eta_out, int* breakdown_out,
+               int s_host = 0) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
@@ -441,6 +501,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
   T* y = vp<T>(P->y);
   T* xm = vp<T>(P->xm);
   T* Vk = vp<T>(P->Vkeep);
+  T* wT = vp<T>(P->mixed ? P->wT : (void*)P->w64);
   // zero-count device int for solves without a local space
   const int* cnt_use = use_K ? cntK : P->cnt + 2;
   if (!use_K) CU(cudaMemsetAsync(P->cnt + 2, 0, sizeof(int), s));
@@ -460,36 +521,94 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     return vp<T>(P->vring[j % 3]);
   };
   auto dptr = [&](int j) -> T* { return vp<T>(P->dring[((j % 3) + 3) % 3]); };
-  // v_1 = u / xi
-  CU(scale_dev<T>(u, vptr(1), n, &P->st->inv_beta_next, 0, nullptr, s));
   const int* stop = &P->st->stop;
   int hpoll[2] = {0, 0};
-  int j = 1;
-  for (; j <= maxit; ++j) {
+  const int rr = P->tp.r;
+  const double a_bytes = (double)(11 + s_host) * n * sizeof(T);
+  const double a_flops = (8.0 * (2 * rr + 1) + 12.0 + 2.0 * s_host) * n;
+
+  CU(cudaMemcpyAsync(P->gcur, &gamma, sizeof(double), cudaMemcpyHostToDevice, s));
+  // Steps j < keep of a solve that keeps re-orthogonalized Lanczos vectors run
+  // unfused (op, dots, update, re-orthogonalization, scalar step, direction);
+  // all other steps run fused: two kernels per step, and chunks of kChunk steps
+  // replayed from a CUDA graph once the operands repeat (j = 2 mod 3, ring
+  // buffers only). Switching from unfused to fused needs nothing: the unfused
+  // step leaves v_{j+1} written and no direction update pending.
+  const int n_unfused = reorth ? std::min(keep - 1, maxit) : 0;
+  auto unfused = [&](int j) -> int {
     T* vj = vptr(j);
-    const int slot = timed_begin(P);
-    CU(op_apply<T>(vj, ld, 1, vp<T>(P->mixed ? P->wT : (void*)P->w64), y, nullptr, ld, P->d.height,
-                   P->d.width, P->tp, gamma, 0, s, stop));
-    timed_end(P, slot, 0, j, n);
+    CU(op_apply<T>(vj, ld, 1, wT, y, nullptr, ld, P->d.height, P->d.width, P->tp, gamma, 0, s, stop));
     CU(multidot<T>(Kl, ld, cnt_use, 0, vj, y, n, P->partials, kDotStride, s, stop));
     CU(reduce_partials(P->partials, z.G, kMaxLocal + 1, kDotStride, P->hdots, s, cnt_use, 1, stop));
     CU(lanczos_update<T>(P->st, Kl, ld, P->hdots, y, vj, vptr(j - 1), u, n, P->partials, s));
-    if (reorth && j < keep) {
-      for (int pass = 0; pass < 2; ++pass) {
-        CU(multidot<T>(Vk, ld, nullptr, j, nullptr, u, n, P->partials + (long)z.G * 4, z.cmax + 2, s, stop));
-        CU(reduce_partials(P->partials + (long)z.G * 4, z.G, j, z.cmax + 2, P->coef, s, nullptr, 0, stop));
-        CU(multi_axpy<T>(Vk, ld, nullptr, j, P->coef, -1.0, u, n, pass == 1 ? P->partials : nullptr, s, stop));
-      }
+    for (int pass = 0; pass < 2; ++pass) {
+      CU(multidot<T>(Vk, ld, nullptr, j, nullptr, u, n, P->partials + (long)z.G * 4, z.cmax + 2, s, stop));
+      CU(reduce_partials(P->partials + (long)z.G * 4, z.G, j, z.cmax + 2, P->coef, s, nullptr, 0, stop));
+      CU(multi_axpy<T>(Vk, ld, nullptr, j, P->coef, -1.0, u, n, pass == 1 ? P->partials : nullptr, s, stop));
     }
     CU(minres_step(P->st, P->hdots, P->partials, z.G, P->arec, P->brec, keep, s));
     CU(minres_direction<T>(P->st, u, vptr(j + 1), vj, dptr(j - 1), dptr(j - 2), dptr(j), xm, n, s));
-    if (j % kPoll == 0 || j == maxit) {
-      CU(minres_poll(P->st, P->poll, s));
-      RS(read_back(P, hpoll, P->poll, sizeof hpoll));
+    return RS_OK;
+  };
+  auto mkA = [&](int j) {
+    return MrA<T>{u, vptr(j), y, vptr(j - 1), dptr(j - 2), dptr(j - 3), dptr(j - 1), xm, Kl, ld,
+                  wT, P->gcur, P->partials_a, P->hdots};
+  };
+  auto mkB = [&](int j) { return MrB<T>{u, y, vptr(j), vptr(j - 1), Kl, ld, P->hdots, P->partials}; };
+  auto stepA = [&](int j, bool time_it) -> int {
+    const int slot = time_it ? timed_begin(P) : -1;
+    CU(mr_matvec<T>(P->st, mkA(j), P->d.height, P->d.width, P->tp, s));
+    timed_end(P, slot, 0, j, n, a_bytes, a_flops);
+    return RS_OK;
+  };
+  auto stepB = [&](int j) -> int {
+    CU(mr_lanczos<T>(P->st, mkB(j), n, keep ? P->arec : nullptr, keep ? P->brec : nullptr, keep, s));
+    return RS_OK;
+  };
+  auto poll = [&](bool graph_chunk, int j0) -> int {
+    CU(minres_poll(P->st, P->poll, s));
+    RS(read_back(P, hpoll, P->poll, sizeof hpoll));
+    if (graph_chunk) {
+      if (P->timing) graph_timing_flush(P, j0, hpoll[1], a_bytes, a_flops, n);
+    } else {
       timed_flush(P, hpoll[1]);
-      if (hpoll[0]) break;
+    }
+    return RS_OK;
+  };
+  if (n_unfused > 0) CU(scale_dev<T>(u, vptr(1), n, &P->st->inv_beta_next, 0, nullptr, s));
+  int j = 1;
+  int since_poll = 0;
+  bool stopped = false;
+  while (j <= maxit && !stopped) {
+    const bool graph_ok = P->use_graph && j > n_unfused && (j % 3) == 2 && j - 1 > keep &&
+                          j + kChunk - 1 <= maxit;
+    if (graph_ok) {
+      RS(ensure_graph<T>(P, mkA, mkB));
+      CU(cudaGraphLaunch(P->gexec, s));
+      add_launches(2 * kChunk);
+      const int j0 = j;
+      j += kChunk;
+      RS(poll(true, j0));
+      stopped = hpoll[0] != 0;
+      since_poll = 0;
+      continue;
+    }
+    if (j <= n_unfused) {
+      RS(unfused(j));
+    } else {
+      RS(stepA(j, true));
+      RS(stepB(j));
+    }
+    ++j;
+    if (++since_poll >= kChunk || j > maxit) {
+      RS(poll(false, 0));
+      stopped = hpoll[0] != 0;
+      since_poll = 0;
     }
   }
+  // a direction update of the last fused step may still be pending: kernel A
+  // with the stop flag set does only that (and nothing after an unfused step)
+  RS(stepA(j, false));
   MinresState hs;
   RS(read_back(P, &hs, P->st, sizeof hs));
   timed_flush(P, hs.iters);
@@ -803,7 +922,8 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
       int it = 0, bd = 0;
       double eta = 0.0;
       const int mi = forced >= 0 ? forced : P->d.maxit;
-      RS(run_minres<T>(P, gl, vp<T>(P->rT), sdim > 0, forced >= 0 ? 0.0 : inner_tol, mi, 0, false, &it, &eta, &bd));
+      RS(run_minres<T>(P, gl, vp<T>(P->rT), sdim > 0, forced >= 0 ? 0.0 : inner_tol, mi, 0, false, &it, &eta, &bd,
+                       sdim));
       sl.iters += it;
       sl.matvecs += it;
       sl.relres_est = eta / P->bnorm;
@@ -1120,6 +1240,8 @@ rs_status rs_set_timing(rs_problem* P, int on) {
   for (int c = 0; c < 2; ++c) {
     P->t_launches[c] = 0;
     P->t_pixels[c] = 0;
+    P->t_bytes[c] = 0.0;
+    P->t_flops[c] = 0.0;
     P->t_ms[c] = 0.0;
   }
   return RS_OK;
@@ -1131,6 +1253,8 @@ rs_status rs_get_timing(const rs_problem* P, rs_timing* t) {
     t->launches[c] = P->t_launches[c];
     t->ms[c] = P->t_ms[c];
     t->pixels[c] = P->t_pixels[c];
+    t->bytes[c] = P->t_bytes[c];
+    t->flops[c] = P->t_flops[c];
   }
   return RS_OK;
 }

@@ -39,7 +39,8 @@ k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* per
     __syncthreads();
     for (int round = 0; round < N - 1; ++round) {
       for (int pr = warp; pr < N / 2; pr += kWarps) {
-        int p = perm[2 * pr], q = perm[2 * pr + 1];
+        // circle method: slot i meets slot N-1-i; slot 0 stays, the rest rotate
+        int p = perm[pr], q = perm[N - 1 - pr];
         if (p >= nc || q >= nc) continue;
         if (p > q) { const int t = p; p = q; q = t; }
         double* xp = X + (long)p * ldx;

@@ -22,6 +22,7 @@ struct Taps {
 // launch status and counts the launch (process-wide, for the benchmark).
 cudaError_t launched();
 long long launch_count();
+void add_launches(long long k);   // kernels replayed from a CUDA graph
 
 // Number of CTAs of every grid-stride reduction over n elements. Fixed per n so
 // that partial sums are combined in the same order on every call.
@@ -137,6 +138,8 @@ struct MinresState {
   double inv_beta_next, delta, eps, inv_gamma, tau;   // this step's coefficients
   double xi;
   int iters, maxit, stop, performed, breakdown, s;
+  int dir_pending;         // fused path: the direction update of the last step is due
+  unsigned int cnt_a, cnt_b;   // last-CTA tickets of the fused kernels (0 between launches)
   double h[kMaxLocal];     // K^T Op v_j
   double h1[kMaxLocal], h2[kMaxLocal];
   double z[kMaxLocal];     // K^T r - sum_j tau_j hhat_j
@@ -153,6 +156,45 @@ template <typename T>
 cudaError_t minres_direction(const MinresState* st, const T* u, T* vnext, const T* v,
                              const T* d1, const T* d2, T* d, T* xm, long n, cudaStream_t s);
 cudaError_t minres_poll(const MinresState* st, int* out_dev2, cudaStream_t s);
+
+// ---------------------------------------------------------------- mrfused.cu
+// Operands of the fused step kernels (fixed per position j mod 3, so that a
+// chunk of steps can be captured in a CUDA graph).
+template <typename T>
+struct MrA {
+  const T* u;          // unnormalised Lanczos residual of step j-1 (v_j = u / beta_j)
+  T* vout;             // v_j
+  T* y;                // (A + gamma E) v_j
+  const T* vprev;      // v_{j-1}
+  const T* d1;         // d_{j-2}
+  const T* d2;         // d_{j-3}
+  T* dout;             // d_{j-1}
+  T* xm;               // V_m y accumulated
+  const T* K;          // local space, s columns (s from the state)
+  long ldk;
+  const T* w;          // weights [w_x; w_y]
+  const double* gamma; // the shift (device)
+  double* partials;    // blocks x (kMaxLocal + 1)
+  double* hdots;       // out: [K^T y; v_j^T y]
+};
+template <typename T>
+struct MrB {
+  T* u;
+  const T* y;
+  const T* v;
+  const T* vprev;
+  const T* K;
+  long ldk;
+  const double* hdots;
+  double* partials;    // red_grid(n)
+};
+template <typename T>
+cudaError_t mr_matvec(MinresState* st, const MrA<T>& a, int H, int W, const Taps& tp,
+                      cudaStream_t s);
+template <typename T>
+cudaError_t mr_lanczos(MinresState* st, const MrB<T>& b, long n, double* alphas_rec,
+                       double* betas_rec, int rec_cap, cudaStream_t s);
+int mr_matvec_blocks(int H, int W);
 
 // ---------------------------------------------------------------- cgs.cu
 struct CgsCtx {

@@ -10,12 +10,13 @@
 // intermediate H x being masked to zero outside the image (H maps the image
 // to itself). Columns of a block (A U~, E U~) run as grid.z.
 #include "internal.cuh"
+#include "optile.cuh"
 
 namespace rk {
 namespace {
 
-constexpr int TH = 32, TW = 32;
-constexpr int PPT = TH * TW / kThreads;   // output pixels per thread
+constexpr int TH = kTileH, TW = kTileW;
+constexpr int PPT = kPPT;
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -26,112 +27,30 @@ k_op_apply(const T* __restrict__ x, long ldx, const T* __restrict__ w, T* __rest
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T sg[kMaxTaps];
   const int r = tp.r;
-  const long n = (long)H * W;
   const long col = blockIdx.z;
   x += col * ldx;
   y += col * ldy;
   if (y2) y2 += col * ldy;
-  const T* wx = w;
-  const T* wy = w + n;
-  const int i0 = blockIdx.y * TH, j0 = blockIdx.x * TW;
-  const int AH = TH + 4 * r, AW = TW + 4 * r;
-  const int BW = TW + 2 * r, CH = TH + 2 * r;
   T* bufA = reinterpret_cast<T*>(smem_raw);
-  T* bufB = bufA + AH * AW;
-
+  T* bufB = bufA + (kTileH + 4 * r) * (kTileW + 4 * r);
   if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
-  for (int idx = threadIdx.x; idx < AH * AW; idx += kThreads) {
-    const int a = idx / AW, c = idx - a * AW;
-    const int gi = i0 - 2 * r + a, gj = j0 - 2 * r + c;
-    bufA[idx] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? x[(long)gi * W + gj] : T(0);
-  }
-  __syncthreads();
-
-  // E x = L^T (w .* L x) at the owned pixels
-  T ex[PPT];
+  T ax[kPPT], ex[kPPT], vc[kPPT];
+  op_tile<T>(x, T(1), w, H, W, sg, r, bufA, bufB, mode != 2, ax, ex, vc);
+  const int i0 = blockIdx.y * kTileH, j0 = blockIdx.x * kTileW;
 #pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    const int p = threadIdx.x + q * kThreads;
-    const int ti = p / TW, tj = p - ti * TW;
-    const int gi = i0 + ti, gj = j0 + tj;
-    T e = T(0);
-    if (gi < H && gj < W) {
-      const long gidx = (long)gi * W + gj;
-      if (r >= 1) {   // the staged halo (2r >= 2) holds the 4 neighbours
-        const T* s = bufA + (ti + 2 * r) * AW + (tj + 2 * r);
-        const T xc = s[0];
-        if (gj >= 1) e += wx[gidx - 1] * (xc - s[-1]);
-        if (gj < W - 1) e -= wx[gidx] * (s[1] - xc);
-        if (gi >= 1) e += wy[gidx - W] * (xc - s[-AW]);
-        if (gi < H - 1) e -= wy[gidx] * (s[AW] - xc);
-      } else {        // no halo: neighbours from global memory
-        const T xc = x[gidx];
-        if (gj >= 1) e += wx[gidx - 1] * (xc - x[gidx - 1]);
-        if (gj < W - 1) e -= wx[gidx] * (x[gidx + 1] - xc);
-        if (gi >= 1) e += wy[gidx - W] * (xc - x[gidx - W]);
-        if (gi < H - 1) e -= wy[gidx] * (x[gidx + W] - xc);
-      }
-    }
-    ex[q] = e;
-  }
-  if (mode == 2) {
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      const int p = threadIdx.x + q * kThreads;
-      const int ti = p / TW, tj = p - ti * TW;
-      const int gi = i0 + ti, gj = j0 + tj;
-      if (gi < H && gj < W) y[(long)gi * W + gj] = ex[q];
-    }
-    return;
-  }
-
-  // pass 1: T_w along rows; output column c is image column j0 - r + c
-  for (int idx = threadIdx.x; idx < AH * BW; idx += kThreads) {
-    const int a = idx / BW, c = idx - a * BW;
-    const T* s = bufA + a * AW + c;
-    T acc = T(0);
-    for (int k = 0; k <= 2 * r; ++k) acc += sg[k] * s[k];
-    bufB[idx] = acc;
-  }
-  __syncthreads();
-  // pass 2: T_h along columns -> u = H x on the tile plus a halo of r,
-  // zero outside the image; output row a is image row i0 - r + a
-  for (int idx = threadIdx.x; idx < CH * BW; idx += kThreads) {
-    const int a = idx / BW, c = idx - a * BW;
-    const int gi = i0 - r + a, gj = j0 - r + c;
-    T acc = T(0);
-    if (gi >= 0 && gi < H && gj >= 0 && gj < W) {
-      const T* s = bufB + a * BW + c;
-      for (int k = 0; k <= 2 * r; ++k) acc += sg[k] * s[k * BW];
-    }
-    bufA[idx] = acc;
-  }
-  __syncthreads();
-  // pass 3: T_w^T along rows (reversed taps); output column c is j0 + c
-  for (int idx = threadIdx.x; idx < CH * TW; idx += kThreads) {
-    const int a = idx / TW, c = idx - a * TW;
-    const T* s = bufA + a * BW + c;
-    T acc = T(0);
-    for (int k = 0; k <= 2 * r; ++k) acc += sg[2 * r - k] * s[k];
-    bufB[idx] = acc;
-  }
-  __syncthreads();
-  // pass 4: T_h^T along columns -> A x on the owned pixels
-#pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    const int p = threadIdx.x + q * kThreads;
-    const int ti = p / TW, tj = p - ti * TW;
+  for (int q = 0; q < kPPT; ++q) {
+    int ti, tj;
+    op_tile_pixel(q, ti, tj);
     const int gi = i0 + ti, gj = j0 + tj;
     if (gi < H && gj < W) {
-      const T* s = bufB + ti * TW + tj;
-      T acc = T(0);
-      for (int k = 0; k <= 2 * r; ++k) acc += sg[2 * r - k] * s[k * TW];
       const long gidx = (long)gi * W + gj;
       if (mode == 0) {
-        y[gidx] = acc + T(gamma) * ex[q];
-      } else {
-        y[gidx] = acc;
+        y[gidx] = ax[q] + T(gamma) * ex[q];
+      } else if (mode == 1) {
+        y[gidx] = ax[q];
         y2[gidx] = ex[q];
+      } else {
+        y[gidx] = ex[q];
       }
     }
   }
@@ -229,6 +148,8 @@ cudaError_t launched() {
   return cudaGetLastError();
 }
 
+void add_launches(long long k) { __atomic_fetch_add(&g_launches, k, __ATOMIC_RELAXED); }
+
 long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 int red_grid(long n) {
@@ -243,8 +164,9 @@ cudaError_t op_apply(const T* x, long ldx, int ncols, const T* w, T* y, T* y2, l
                      int W, const Taps& tp, double gamma, int mode, cudaStream_t s,
                      const int* stop) {
   if (ncols <= 0) return cudaSuccess;
-  const size_t smem = op_smem<T>(tp.r);
-  RK_TRY(cudaFuncSetAttribute(k_op_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = (size_t)op_tile_smem_elems(tp.r) * sizeof(T);
+  static int cached = 0;
+  RK_TRY(ensure_smem(k_op_apply<T>, smem, &cached));
   dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, ncols);
   k_op_apply<T><<<grid, kThreads, smem, s>>>(x, ldx, w, y, y2, ldy, H, W, tp, gamma, mode, stop);
   return launched();
@@ -254,7 +176,8 @@ cudaError_t blur_apply(const double* x, double* y, int H, int W, const Taps& tp,
                        cudaStream_t s) {
   const int AH = TH + 2 * tp.r, AW = TW + 2 * tp.r;
   const size_t smem = (size_t)(AH * AW + AH * TW) * sizeof(double);
-  RK_TRY(cudaFuncSetAttribute(k_blur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  static int cached = 0;
+  RK_TRY(ensure_smem(k_blur, smem, &cached));
   dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, 1);
   k_blur<<<grid, kThreads, smem, s>>>(x, y, H, W, tp, adjoint);
   return launched();

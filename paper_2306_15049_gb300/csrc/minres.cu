@@ -41,6 +41,9 @@ __global__ void k_minres_init(MinresState* st, const double* xi2, const double* 
   st->maxit = maxit;
   st->performed = 0;
   st->breakdown = 0;
+  st->dir_pending = 0;
+  st->cnt_a = 0;
+  st->cnt_b = 0;
   st->s = s;
   st->inv_beta_next = (xi > 0.0) ? 1.0 / xi : 0.0;
   st->stop = (!(xi > tol_abs) || maxit <= 0) ? 1 : 0;

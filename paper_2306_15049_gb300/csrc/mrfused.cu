@@ -1,0 +1,247 @@
+// One recycled-MINRES step in two kernels (Section 2.3 / 4.2, Eq. minShift).
+//
+// Kernel A (step j), one CTA per 32 x 32 tile:
+//   * the direction update of step j-1 on its tile:
+//       d_{j-1} = (v_{j-1} - delta d_{j-2} - eps d_{j-3}) / gamma,  x_m += tau d_{j-1};
+//   * v_j = u / beta_j, staged with a halo of 2r straight from the unnormalised
+//     Lanczos residual u, and written for its tile;
+//   * y = (A + gamma_l E) v_j on its tile (the fused operator of optile.cuh);
+//   * per-CTA partial dots [K^T y; v_j^T y]; the last CTA to finish adds the
+//     partials in a fixed order (deterministic) into hdots = [h_j; alpha_j].
+// Kernel B (step j), grid-stride over the image:
+//   * u = y - K h_j - alpha_j v_j - beta_j v_{j-1} and partial ||u||^2; the last
+//     CTA adds the partials in a fixed order and takes the scalar step: the
+//     Givens rotations, tau_j, eta_j, the hhat / z recurrences and the stop test.
+// "Last CTA" is decided by an atomic ticket after a __threadfence(); nothing
+// waits on anything, so no launch can hang.
+#include "internal.cuh"
+#include "optile.cuh"
+
+namespace rk {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kDots = kMaxLocal + 1;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_mr_matvec(MinresState* st, MrA<T> a, int H, int W, Taps tp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T sg[kMaxTaps];
+  __shared__ double red[kThreads / 32][kDots];
+  __shared__ int is_last;
+  const int pend = st->dir_pending;
+  const int stopped = st->stop;
+  const int i0 = blockIdx.y * kTileH, j0 = blockIdx.x * kTileW;
+  const int nblocks = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+
+  if (pend) {
+    const T de = T(st->delta), ep = T(st->eps), ig = T(st->inv_gamma), tau = T(st->tau);
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      int ti, tj;
+      op_tile_pixel(q, ti, tj);
+      const int gi = i0 + ti, gj = j0 + tj;
+      if (gi < H && gj < W) {
+        const long g = (long)gi * W + gj;
+        const T dv = (a.vprev[g] - de * a.d1[g] - ep * a.d2[g]) * ig;
+        a.dout[g] = dv;
+        a.xm[g] += tau * dv;
+      }
+    }
+  }
+  if (!stopped) {
+    const int r = tp.r;
+    const int s = st->s;
+    T* bufA = reinterpret_cast<T*>(smem_raw);
+    T* bufB = bufA + (kTileH + 4 * r) * (kTileW + 4 * r);
+    if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
+    T ax[kPPT], ex[kPPT], vc[kPPT];
+    op_tile<T>(a.u, T(st->inv_beta_next), a.w, H, W, sg, r, bufA, bufB, true, ax, ex, vc);
+    const T gam = T(*a.gamma);
+    T acc[kDots];
+#pragma unroll
+    for (int k = 0; k < kDots; ++k) acc[k] = T(0);
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      int ti, tj;
+      op_tile_pixel(q, ti, tj);
+      const int gi = i0 + ti, gj = j0 + tj;
+      if (gi < H && gj < W) {
+        const long g = (long)gi * W + gj;
+        const T yv = ax[q] + gam * ex[q];
+        a.y[g] = yv;
+        a.vout[g] = vc[q];
+#pragma unroll
+        for (int k = 0; k < kMaxLocal; ++k)
+          if (k < s) acc[k] += a.K[(long)k * a.ldk + g] * yv;
+        acc[kMaxLocal] += vc[q] * yv;
+      }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kDots; ++k) {
+      if (k < s || k == kMaxLocal) {
+        const double t = warp_sum((double)acc[k]);
+        if (lane == 0) red[warp][k] = t;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kDots) {
+      const int k = threadIdx.x;
+      if (k < s || k == kMaxLocal) {
+        double t = 0.0;
+        for (int wv = 0; wv < kThreads / 32; ++wv) t += red[wv][k];
+        a.partials[(long)bid * kDots + (k == kMaxLocal ? s : k)] = t;
+      }
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->cnt_a, 1u) == (unsigned)(nblocks - 1));
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if (!stopped) {
+    const int s = st->s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k <= s; k += kThreads / 32) {
+      double t = 0.0;
+      for (int g = lane; g < nblocks; g += 32) t += __ldcg(a.partials + (long)g * kDots + k);
+      t = warp_sum(t);
+      if (lane == 0) a.hdots[k] = t;
+    }
+  }
+  if (threadIdx.x == 0) {
+    st->cnt_a = 0;
+    st->dir_pending = 0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_mr_lanczos(MinresState* st, MrB<T> b, long n, double* alphas_rec, double* betas_rec,
+             int rec_cap) {
+  if (st->stop) return;
+  __shared__ T sh_h[kMaxLocal];
+  __shared__ double sh[kThreads / 32];
+  __shared__ int is_last;
+  const int s = st->s;
+  if (threadIdx.x < s) sh_h[threadIdx.x] = T(b.hdots[threadIdx.x]);
+  const T alpha = T(b.hdots[s]);
+  const T beta = T(st->beta);
+  __syncthreads();
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
+    T val = b.y[i] - alpha * b.v[i] - beta * b.vprev[i];
+    for (int k = 0; k < s; ++k) val -= sh_h[k] * b.K[(long)k * b.ldk + i];
+    b.u[i] = val;
+    acc += (double)val * (double)val;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+    b.partials[blockIdx.x] = t;
+    __threadfence();
+    is_last = (atomicAdd(&st->cnt_b, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // fixed-order sum of the norm partials
+  double t = 0.0;
+  for (int g = threadIdx.x; g < (int)gridDim.x; g += kThreads) t += __ldcg(b.partials + g);
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double unorm2 = 0.0;
+  for (int k = 0; k < kThreads / 32; ++k) unorm2 += sh[k];
+  st->cnt_b = 0;
+  const double alpha_d = b.hdots[s];
+  const double beta_d = st->beta;
+  const double beta_next = sqrt(unorm2);
+  const double eps = st->sn2 * beta_d;
+  const double dbar = st->cs2 * beta_d;
+  const double delta = st->cs1 * dbar + st->sn1 * alpha_d;
+  const double gbar = -st->sn1 * dbar + st->cs1 * alpha_d;
+  const double gamma = hypot(gbar, beta_next);
+  if (!(gamma > 0.0) || !isfinite(gamma)) {
+    st->breakdown = 1;
+    st->stop = 1;
+    return;
+  }
+  const double cs = gbar / gamma, sn = beta_next / gamma;
+  const double tau = cs * st->eta;
+  st->eta = -sn * st->eta;
+  const double ig = 1.0 / gamma;
+  for (int k = 0; k < s; ++k) {
+    const double hk = b.hdots[k];
+    const double hh = (hk - delta * st->h1[k] - eps * st->h2[k]) * ig;
+    st->z[k] -= tau * hh;
+    st->h2[k] = st->h1[k];
+    st->h1[k] = hh;
+  }
+  const int j = st->iters;
+  if (alphas_rec && j < rec_cap) {
+    alphas_rec[j] = alpha_d;
+    betas_rec[j] = beta_next;
+  }
+  st->delta = delta;
+  st->eps = eps;
+  st->inv_gamma = ig;
+  st->tau = tau;
+  st->inv_beta_next = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
+  st->cs2 = st->cs1;
+  st->sn2 = st->sn1;
+  st->cs1 = cs;
+  st->sn1 = sn;
+  st->iters = j + 1;
+  st->beta = beta_next;
+  st->dir_pending = 1;
+  if (fabs(st->eta) <= st->tol_abs || beta_next == 0.0 || st->iters >= st->maxit) st->stop = 1;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t mr_matvec(MinresState* st, const MrA<T>& a, int H, int W, const Taps& tp,
+                      cudaStream_t s) {
+  const size_t smem = (size_t)op_tile_smem_elems(tp.r) * sizeof(T);
+  static int cached = 0;
+  RK_TRY(ensure_smem(k_mr_matvec<T>, smem, &cached));
+  dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH, 1);
+  k_mr_matvec<T><<<grid, kThreads, smem, s>>>(st, a, H, W, tp);
+  return launched();
+}
+
+template <typename T>
+cudaError_t mr_lanczos(MinresState* st, const MrB<T>& b, long n, double* alphas_rec,
+                       double* betas_rec, int rec_cap, cudaStream_t s) {
+  k_mr_lanczos<T><<<red_grid(n), kThreads, 0, s>>>(st, b, n, alphas_rec, betas_rec, rec_cap);
+  return launched();
+}
+
+int mr_matvec_blocks(int H, int W) {
+  return ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+}
+
+template cudaError_t mr_matvec<float>(MinresState*, const MrA<float>&, int, int, const Taps&,
+                                      cudaStream_t);
+template cudaError_t mr_matvec<double>(MinresState*, const MrA<double>&, int, int, const Taps&,
+                                       cudaStream_t);
+template cudaError_t mr_lanczos<float>(MinresState*, const MrB<float>&, long, double*, double*,
+                                       int, cudaStream_t);
+template cudaError_t mr_lanczos<double>(MinresState*, const MrB<double>&, long, double*, double*,
+                                        int, cudaStream_t);
+
+}  // namespace rk

@@ -53,7 +53,8 @@ class rs_info(ctypes.Structure):
 
 class rs_timing(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong * 2), ("ms", ctypes.c_double * 2),
-                ("pixels", ctypes.c_longlong * 2)]
+                ("pixels", ctypes.c_longlong * 2), ("bytes", ctypes.c_double * 2),
+                ("flops", ctypes.c_double * 2)]
 
 
 _P = ctypes.c_void_p
@@ -231,7 +232,8 @@ class Problem:
     def rs_get_timing(self) -> dict:
         t = rs_timing()
         self._check(self.lib.rs_get_timing(self.h, ctypes.byref(t)))
-        return {"launches": list(t.launches), "ms": list(t.ms), "pixels": list(t.pixels)}
+        return {"launches": list(t.launches), "ms": list(t.ms), "pixels": list(t.pixels),
+                "bytes": list(t.bytes), "flops": list(t.flops)}
 
     def rs_get_info(self) -> dict:
         info = rs_info()
