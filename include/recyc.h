@@ -113,6 +113,11 @@ typedef struct {
   long long pixels[2];     /* pixels processed by the counted launches */
   double bytes[2];         /* algorithmic bytes of the counted launches (no halo re-reads) */
   double flops[2];         /* algorithmic flops of the counted launches */
+  /* wall time (ms, stream synchronised at each phase end) per phase:
+   * 0 INIT solves, 1 UPDATE (V^(new)), 2 stabilize + images + Grams + small
+   * solves + Ritz bases, 3 per-shift setup (initial guess, local space, QR),
+   * 4 per-shift recycled MINRES and assembly, 5 FP64 true / refinement residuals */
+  double phase_ms[6];
 } rs_timing;
 
 /* Bytes of device workspace a problem with this description needs. Returns 0

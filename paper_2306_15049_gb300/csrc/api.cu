@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <chrono>
 #include <vector>
 
 #include "internal.cuh"
@@ -249,6 +250,7 @@ struct rs_problem {
   size_t pending_used = 0;
   long long t_launches[2] = {0, 0}, t_pixels[2] = {0, 0};
   double t_ms[2] = {0.0, 0.0}, t_bytes[2] = {0.0, 0.0}, t_flops[2] = {0.0, 0.0};
+  double phase_ms[6] = {0, 0, 0, 0, 0, 0};
   // CUDA graph of kChunk fused MINRES steps (built on first use)
   bool use_graph = true;
   cudaStream_t cap = nullptr;
@@ -427,8 +429,25 @@ int norm2_to(rs_problem* P, const T* x, double* dst) {
   return RS_OK;
 }
 
+// Phase wall-clock accounting (timing mode only): the stream is synchronised at
+// both ends so that a phase is charged with its own device work.
+double phase_begin(rs_problem* P) {
+  if (!P->timing) return 0.0;
+  cudaStreamSynchronize(P->s);
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void phase_end(rs_problem* P, int ph, double t0) {
+  if (!P->timing) return;
+  cudaStreamSynchronize(P->s);
+  P->phase_ms[ph] += std::chrono::duration<double, std::milli>(
+                         std::chrono::steady_clock::now().time_since_epoch()).count() - t0;
+}
+
 // FP64 true residual: r64 = b - (A + gamma E) x64; returns ||r|| / ||b|| on the host.
 int true_residual(rs_problem* P, double gamma, const double* x64, double* relres) {
+  const double t0 = phase_begin(P);
   const int slot = timed_begin(P);
   CU(op_apply<double>(x64, P->z.ld, 1, P->w64, P->y64, nullptr, P->z.ld, P->d.height, P->d.width,
                       P->tp, gamma, 0, P->s));
@@ -438,6 +457,7 @@ int true_residual(rs_problem* P, double gamma, const double* x64, double* relres
   double r2 = 0.0;
   RS(read_back(P, &r2, P->scal + 8, sizeof r2));
   timed_flush(P, 0);
+  phase_end(P, 5, t0);
   *relres = std::sqrt(r2) / P->bnorm;
   P->mv_total += 1;
   return RS_OK;
@@ -642,7 +662,7 @@ CgsCtx cgs_ctx(rs_problem* P, int ldr, double* Rk, double* Rfull, int ldrf, doub
 // images, K, R, the matrices of Eq. orthupdate and Eq. hq, and the Ritz
 // vectors of Algorithm "interior" at gamma_{J_L}, gamma_{J_R}.
 template <typename T>
-int finish_principal(rs_problem* P, int ncand) {
+int finish_principal_body(rs_problem* P, int ncand) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
@@ -725,12 +745,21 @@ int finish_principal(rs_problem* P, int ncand) {
   return RS_OK;
 }
 
+template <typename T>
+int finish_principal(rs_problem* P, int ncand) {
+  const double t0 = phase_begin(P);
+  const int r = finish_principal_body<T>(P, ncand);
+  phase_end(P, 2, t0);
+  return r;
+}
+
 // Section 5.1: two MINRES solves with kept, reorthogonalized Lanczos vectors.
 template <typename T>
 int init_principal(rs_problem* P) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
+  const double t0 = phase_begin(P);
   int col_out = 2;
   for (int which = 0; which < 2; ++which) {
     const int idx = which == 0 ? P->d.i1 : P->d.i2;
@@ -777,6 +806,7 @@ int init_principal(rs_problem* P) {
       P->kept_init = 0;
     }
   }
+  phase_end(P, 0, t0);
   return finish_principal<T>(P, col_out);
 }
 
@@ -787,6 +817,7 @@ int update_principal(rs_problem* P) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
+  const double t0 = phase_begin(P);
   const int lc = P->d.l_c - 1;
   const double g = P->gammas[lc];
   // rhs = gamma_lc (E_k - E_{k-1}) x^(k-1, l_c)
@@ -820,6 +851,7 @@ int update_principal(rs_problem* P) {
   }
   CU(cudaMemcpyAsync(U + (long)c * ld, P->Xprev, (size_t)z.M * ld * sizeof(double), cudaMemcpyDeviceToDevice, s));
   c += z.M;
+  phase_end(P, 1, t0);
   return finish_principal<T>(P, c);
 }
 
@@ -842,6 +874,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
   std::vector<char> gnz(z.M, 0);
   for (int l = 0; l < z.M; ++l) {
     const double gl = P->gammas[l];
+    const double ph0 = phase_begin(P);
     rs_solve_stats sl{};
     sl.sweeps = 0;
     double* x = X + (long)l * n;    // caller's X is dense M x n
@@ -860,6 +893,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
     if (forced < 0 && sl.relres0 <= P->d.tol) {
       CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
       sl.relres_est = sl.relres0;
+      phase_end(P, 3, ph0);
       RS(true_residual(P, gl, x, &sl.relres_true));
       sl.matvecs = 1;
       sl.sweeps = 0;
@@ -914,6 +948,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
     int sdim = 0;
     RS(read_back(P, &sdim, P->cnt, sizeof sdim));
     sl.local_dim = sdim;
+    phase_end(P, 3, ph0);
     // sweeps: sweep 0 from r0; in mixed precision further sweeps from the FP64 residual
     CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
     double inner_tol = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * std::sqrt(r02)) : tol_abs;
@@ -922,6 +957,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
       int it = 0, bd = 0;
       double eta = 0.0;
       const int mi = forced >= 0 ? forced : P->d.maxit;
+      const double ph1 = phase_begin(P);
       RS(run_minres<T>(P, gl, vp<T>(P->rT), sdim > 0, forced >= 0 ? 0.0 : inner_tol, mi, 0, false, &it, &eta, &bd,
                        sdim));
       sl.iters += it;
@@ -935,6 +971,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
       CU(axpby<T, double>(vp<T>(P->xm), 1.0, x, 1.0, n, s));
       if (sw == 0) CU(cudaMemcpyAsync(gl_buf, P->xm, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
       else CU(axpby<T, T>(vp<T>(P->xm), 1.0, gl_buf, 1.0, n, s));
+      phase_end(P, 4, ph1);
       RS(true_residual(P, gl, x, &sl.relres_true));
       sl.matvecs += 1;
       if (!P->mixed || sl.relres_true <= P->d.tol || forced >= 0) break;
@@ -1244,6 +1281,7 @@ rs_status rs_set_timing(rs_problem* P, int on) {
     P->t_flops[c] = 0.0;
     P->t_ms[c] = 0.0;
   }
+  for (int ph = 0; ph < 6; ++ph) P->phase_ms[ph] = 0.0;
   return RS_OK;
 }
 
@@ -1255,6 +1293,9 @@ rs_status rs_get_timing(const rs_problem* P, rs_timing* t) {
     t->pixels[c] = P->t_pixels[c];
     t->bytes[c] = P->t_bytes[c];
     t->flops[c] = P->t_flops[c];
+  }
+  for (int ph = 0; ph < 6; ++ph) {
+    t->phase_ms[ph] = P->phase_ms[ph];
   }
   return RS_OK;
 }

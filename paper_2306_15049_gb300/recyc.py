@@ -54,7 +54,10 @@ class rs_info(ctypes.Structure):
 class rs_timing(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong * 2), ("ms", ctypes.c_double * 2),
                 ("pixels", ctypes.c_longlong * 2), ("bytes", ctypes.c_double * 2),
-                ("flops", ctypes.c_double * 2)]
+                ("flops", ctypes.c_double * 2), ("phase_ms", ctypes.c_double * 6)]
+
+PHASES = ("init_solves", "update_vnew", "principal_setup", "shift_setup", "shift_minres",
+          "fp64_residuals")
 
 
 _P = ctypes.c_void_p
@@ -233,7 +236,8 @@ class Problem:
         t = rs_timing()
         self._check(self.lib.rs_get_timing(self.h, ctypes.byref(t)))
         return {"launches": list(t.launches), "ms": list(t.ms), "pixels": list(t.pixels),
-                "bytes": list(t.bytes), "flops": list(t.flops)}
+                "bytes": list(t.bytes), "flops": list(t.flops),
+                "phase_ms": dict(zip(PHASES, list(t.phase_ms)))}
 
     def rs_get_info(self) -> dict:
         info = rs_info()
