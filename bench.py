@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="run the workload once (one step, no timing) for a profiler and exit")
+    ap.add_argument("--profile-case", nargs="?", const="full", choices=["full", "small"],
+                    help="run the workload once for a profiler and exit (small: every shift of "
+                         "the first outer step on a random principal basis, 24 MINRES steps each)")
     return ap.parse_args()
 
 
@@ -307,10 +308,23 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     runner = Runner(wl, args.precision, dev)
-    if args.profile_case:
+    if args.profile_case == "full":
         r = runner.step()
         torch.cuda.synchronize(dev)
         print(json.dumps({"profile_case": wl.name, "precision": args.precision, **r}), flush=True)
+        return
+    if args.profile_case == "small":
+        from paper_2306_15049_gb300 import recyc
+        P = recyc.Problem(runner.desc, runner.d, workspace=runner.workspace)
+        P.rs_set_weights(runner.w)
+        g = torch.Generator(device=dev).manual_seed(5)
+        U = torch.randn(wl.p, wl.n, dtype=torch.float64, device=dev, generator=g)
+        P.rs_set_recycle_basis(U, wl.p)
+        stats = P.rs_solve_shifts(runner.X, iters_override=[24] * wl.M)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_case": "small", "precision": args.precision,
+                          "iters": sum(s["iters"] for s in stats),
+                          "kernel_launches": P.rs_get_info()["kernel_launches"]}), flush=True)
         return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 

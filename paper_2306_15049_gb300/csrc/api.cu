@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <chrono>
@@ -575,6 +576,17 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
                   wT, P->gcur, P->partials_a, P->hdots};
   };
   auto mkB = [&](int j) { return MrB<T>{u, y, vptr(j), vptr(j - 1), Kl, ld, P->hdots, P->partials}; };
+  // The cached graph serves every later solve of the problem, so it is always
+  // captured with the ring-buffer operands (no kept Lanczos vectors); a solve
+  // replays it only for steps whose operands are ring buffers (j - 1 > keep).
+  auto vring_ptr = [&](int j) -> T* { return j <= 0 ? vp<T>(P->vzero) : vp<T>(P->vring[j % 3]); };
+  auto mkA_ring = [&](int j) {
+    return MrA<T>{u, vring_ptr(j), y, vring_ptr(j - 1), dptr(j - 2), dptr(j - 3), dptr(j - 1), xm, Kl,
+                  ld, wT, P->gcur, P->partials_a, P->hdots};
+  };
+  auto mkB_ring = [&](int j) {
+    return MrB<T>{u, y, vring_ptr(j), vring_ptr(j - 1), Kl, ld, P->hdots, P->partials};
+  };
   auto stepA = [&](int j, bool time_it) -> int {
     const int slot = time_it ? timed_begin(P) : -1;
     CU(mr_matvec<T>(P->st, mkA(j), P->d.height, P->d.width, P->tp, s));
@@ -603,7 +615,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     const bool graph_ok = P->use_graph && j > n_unfused && (j % 3) == 2 && j - 1 > keep &&
                           j + kChunk - 1 <= maxit;
     if (graph_ok) {
-      RS(ensure_graph<T>(P, mkA, mkB));
+      RS(ensure_graph<T>(P, mkA_ring, mkB_ring));
       CU(cudaGraphLaunch(P->gexec, s));
       add_launches(2 * kChunk);
       const int j0 = j;
@@ -1035,6 +1047,9 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   P->z = dims_of(desc);
   P->tp = make_taps(desc->sigma, desc->radius);
   P->need = need;
+  // RS_GRAPHS=0 launches the fused MINRES steps one by one instead of replaying
+  // them from a CUDA graph (the same kernels; for profilers that handle graphs poorly)
+  if (const char* g = std::getenv("RS_GRAPHS")) P->use_graph = std::strcmp(g, "0") != 0;
   P->gprev_nz.assign(desc->M, 0);
   Carver cv{(char*)workspace_dev};
   carve(P, cv);
@@ -1301,6 +1316,14 @@ rs_status rs_get_timing(const rs_problem* P, rs_timing* t) {
 }
 
 const char* rs_last_error(const rs_problem* P) { return P ? P->err.c_str() : g_err; }
+
+}  // extern "C"
+
+namespace rk {
+void set_null_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace rk
+
+extern "C" {
 
 void rs_destroy(rs_problem* P) { delete P; }
 

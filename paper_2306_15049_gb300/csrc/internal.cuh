@@ -23,6 +23,8 @@ struct Taps {
 cudaError_t launched();
 long long launch_count();
 void add_launches(long long k);   // kernels replayed from a CUDA graph
+// Message returned by rs_last_error(NULL) (failures of calls without a problem).
+void set_null_error(const char* msg);
 
 // Number of CTAs of every grid-stride reduction over n elements. Fixed per n so
 // that partial sums are combined in the same order on every call.

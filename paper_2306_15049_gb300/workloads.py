@@ -7,6 +7,6 @@ from .recyc import RS_FP64, make_desc
 def desc_for(wl, precision: int = RS_FP64, batched_local: int = 0, maxit=None):
     """rs_problem_desc (plus the shift array it points to) for a workload."""
     return make_desc(wl.height, wl.width, wl.sigma, wl.radius, list(wl.gammas()), wl.tol,
-                     int(maxit if maxit is not None else min(wl.maxit, 2_000_000)), wl.p,
+                     int(maxit if maxit is not None else min(wl.maxit, 100_000)), wl.p,
                      wl.a_ritz, wl.b_ritz, wl.n_ritz_local, wl.vnew_cap, wl.I_split, wl.i1,
                      wl.i2, wl.i_star, wl.l_c, wl.J_L, wl.J_R, precision, batched_local)

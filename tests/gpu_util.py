@@ -37,8 +37,9 @@ class Pair:
         self.x_true = x.reshape(-1)
         self.d, self.b = make_data(self.op, x, z, wl.eta)
         self.prm = Params.from_workload(wl, batched_local=bool(batched_local))
-        if maxit is not None:
-            self.prm.maxit = maxit
+        # every workload here converges in a few thousand steps; a cap keeps a
+        # regression from running for hours
+        self.prm.maxit = min(self.prm.maxit, 20000) if maxit is None else maxit
         self.gammas = wl.gammas()
         self.desc = desc_for(wl, precision=precision, batched_local=batched_local,
                              maxit=self.prm.maxit)
