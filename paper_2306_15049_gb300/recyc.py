@@ -78,6 +78,7 @@ _SIGS = {
     "rs_lcurve": (_I, [_P, _P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "rs_synthesize_data": (_I, [ctypes.POINTER(rs_problem_desc), _P, _P, _D, _P, _P,
                                 ctypes.c_size_t, _P]),
+    "rs_synthesize_data_noalloc": (_I, [ctypes.POINTER(rs_problem_desc), _P, _P, _D, _P, _P]),
     "rs_get_info": (_I, [_P, ctypes.POINTER(rs_info)]),
     "rs_set_timing": (_I, [_P, _I]),
     "rs_get_timing": (_I, [_P, ctypes.POINTER(rs_timing)]),
@@ -138,6 +139,15 @@ def rs_synthesize_data(desc, x_dev, z_dev, eta: float, d_out_dev, workspace, str
     st = lib.rs_synthesize_data(ctypes.byref(desc), _ptr(x_dev), _ptr(z_dev), float(eta),
                                 _ptr(d_out_dev), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                 stream)
+    if st != RS_OK:
+        raise RecycError(st, lib.rs_last_error(None).decode())
+
+
+def rs_synthesize_data_noalloc(desc, x_dev, z_dev, eta: float, d_out_dev, stream=None) -> None:
+    """rs_synthesize_data for callers that cannot allocate: no workspace argument."""
+    lib = load()
+    st = lib.rs_synthesize_data_noalloc(ctypes.byref(desc), _ptr(x_dev), _ptr(z_dev), float(eta),
+                                        _ptr(d_out_dev), stream)
     if st != RS_OK:
         raise RecycError(st, lib.rs_last_error(None).decode())
 
