@@ -14,30 +14,32 @@
 namespace rk {
 namespace {
 
+// One CTA: the keep decision and the R column(s) of one candidate, written by
+// all threads in parallel.
 __global__ void k_cgs_finalize(CgsCtx c, int cand, const double* coef1, const double* coef2,
                                const double* nb2, const double* np2) {
-  if (threadIdx.x != 0) return;
   const int s = c.count[0];
   const double nb = sqrt(*nb2), np = sqrt(*np2);
   const int keep = (nb > 0.0 && np > c.drop_rel * nb) ? 1 : 0;
   if (c.Rk && keep) {
-    for (int k = 0; k < s; ++k) c.Rk[k + (long)s * c.ldr] = coef1[k] + coef2[k];
-    for (int k = s + 1; k < c.ldr; ++k) c.Rk[k + (long)s * c.ldr] = 0.0;
-    c.Rk[s + (long)s * c.ldr] = np;
+    for (int k = threadIdx.x; k < c.ldr; k += blockDim.x)
+      c.Rk[k + (long)s * c.ldr] = (k < s) ? coef1[k] + coef2[k] : (k == s ? np : 0.0);
   }
   if (c.Rfull) {
     const double inv = nb > 0.0 ? 1.0 / nb : 0.0;
     double* col = c.Rfull + (long)cand * c.ldrf;
-    for (int k = 0; k < c.ldrf; ++k) col[k] = 0.0;
-    if (nb > 0.0) {
-      for (int k = 0; k < s; ++k) col[k] = (coef1[k] + coef2[k]) * inv;
-      if (keep) col[s] = np * inv;
+    for (int k = threadIdx.x; k < c.ldrf; k += blockDim.x) {
+      double v = 0.0;
+      if (nb > 0.0) v = (k < s) ? (coef1[k] + coef2[k]) * inv : ((k == s && keep) ? np * inv : 0.0);
+      col[k] = v;
     }
   }
-  if (keep) c.kept_idx[s] = cand;
-  c.scal[2] = keep ? 1.0 / np : 0.0;
-  c.flag[0] = keep;
-  c.count[1] = s + keep;
+  if (threadIdx.x == 0) {
+    if (keep) c.kept_idx[s] = cand;
+    c.scal[2] = keep ? 1.0 / np : 0.0;
+    c.flag[0] = keep;
+    c.count[1] = s + keep;
+  }
 }
 
 template <typename T>
@@ -79,7 +81,7 @@ cudaError_t cgs2_column(const CgsCtx& c, T* Q, long ldq, T* b, int cand, long n,
                          nullptr));
   }
   RK_TRY(reduce_partials(c.partials, G, 1, 1, c.scal + 1, s, nullptr, 0, nullptr));
-  k_cgs_finalize<<<1, 32, 0, s>>>(c, cand, c.coef, c.coef + c.ldr, c.scal + 0, c.scal + 1);
+  k_cgs_finalize<<<1, 256, 0, s>>>(c, cand, c.coef, c.coef + c.ldr, c.scal + 0, c.scal + 1);
   RK_TRY(launched());
   k_cgs_store<T><<<red_grid(n), kThreads, 0, s>>>(Q, ldq, c.count, b, c.scal + 2, c.flag, n);
   RK_TRY(launched());

@@ -19,27 +19,27 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One-sided Jacobi on the columns of X (m x nc, column-major, ld ldx), in
-// global memory (small: L1/L2 resident). Round-robin ordering: every round
-// rotates nc/2 disjoint column pairs in parallel, one warp per pair.
+constexpr int kJacThreads = 1024;
+constexpr int kJacWarps = kJacThreads / 32;
+
+// One-sided Jacobi (Hestenes) on the columns of X (m x nc, column-major, ld
+// ldx) with the rotations accumulated in V (nc x nc, ld ldv). Circle-method
+// ordering: every round rotates nc/2 disjoint column pairs in parallel, one
+// warp per pair; slot i meets slot N-1-i, slot 0 stays and the others rotate.
 // On exit X_out = X_in V, the columns of X_out are mutually orthogonal,
-// sig[j] = ||X_out[:, j]||, and the columns are sorted by descending sig.
-__global__ void __launch_bounds__(kDenseThreads)
-k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws) {
-  __shared__ int changed;
+// sig[j] = ||X_out[:, j]|| and the columns of X and V are sorted by descending sig.
+__device__ void jacobi_body(double* X, int ldx, double* V, int ldv, int m, int nc, double* sig,
+                            int* perm, int* changed, int* best) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int N = nc + (nc & 1);                 // even number of slots (slot nc is a dummy)
-  int* perm = perm_ws;                         // N entries
-  for (int i = threadIdx.x; i < nc * nc; i += kDenseThreads) V[i] = ((i % nc) == (i / nc)) ? 1.0 : 0.0;
-  for (int i = threadIdx.x; i < N; i += kDenseThreads) perm[i] = i;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) perm[i] = i;
   __syncthreads();
   const double tol = 1e-15;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    if (threadIdx.x == 0) changed = 0;
+    if (threadIdx.x == 0) *changed = 0;
     __syncthreads();
     for (int round = 0; round < N - 1; ++round) {
-      for (int pr = warp; pr < N / 2; pr += kWarps) {
-        // circle method: slot i meets slot N-1-i; slot 0 stays, the rest rotate
+      for (int pr = warp; pr < N / 2; pr += kJacWarps) {
         int p = perm[pr], q = perm[N - 1 - pr];
         if (p >= nc || q >= nc) continue;
         if (p > q) { const int t = p; p = q; q = t; }
@@ -58,24 +58,23 @@ k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* per
         if (c != 0.0 && fabs(c) > tol * sqrt(a * b)) {
           const double zeta = (b - a) / (2.0 * c);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          const double cs = rsqrt(1.0 + t * t), sn = cs * t;
           for (int i = lane; i < m; i += 32) {
             const double u = xp[i], v = xq[i];
             xp[i] = cs * u - sn * v;
             xq[i] = sn * u + cs * v;
           }
-          double* vp = V + (long)p * nc;
-          double* vq = V + (long)q * nc;
+          double* vp = V + (long)p * ldv;
+          double* vq = V + (long)q * ldv;
           for (int i = lane; i < nc; i += 32) {
             const double u = vp[i], v = vq[i];
             vp[i] = cs * u - sn * v;
             vq[i] = sn * u + cs * v;
           }
-          if (lane == 0) changed = 1;
+          if (lane == 0) *changed = 1;
         }
       }
       __syncthreads();
-      // rotate the slots 1..N-1 (slot 0 fixed)
       if (threadIdx.x == 0) {
         const int last = perm[N - 1];
         for (int i = N - 1; i > 1; --i) perm[i] = perm[i - 1];
@@ -83,37 +82,36 @@ k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* per
       }
       __syncthreads();
     }
-    if (!changed) break;
+    if (!*changed) break;
     __syncthreads();
   }
   // singular values and a stable descending sort (selection, swapping columns)
-  for (int j = warp; j < nc; j += kWarps) {
+  for (int j = warp; j < nc; j += kJacWarps) {
     double a = 0.0;
     for (int i = lane; i < m; i += 32) a = fma(X[(long)j * ldx + i], X[(long)j * ldx + i], a);
     a = warp_sum(a);
     if (lane == 0) sig[j] = sqrt(a);
   }
   __syncthreads();
-  __shared__ int best;
   for (int j = 0; j < nc; ++j) {
     if (threadIdx.x == 0) {
       int bi = j;
       for (int k = j + 1; k < nc; ++k)
         if (sig[k] > sig[bi]) bi = k;
-      best = bi;
+      *best = bi;
     }
     __syncthreads();
-    const int bi = best;
+    const int bi = *best;
     if (bi != j) {
-      for (int i = threadIdx.x; i < m; i += kDenseThreads) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const double t = X[(long)j * ldx + i];
         X[(long)j * ldx + i] = X[(long)bi * ldx + i];
         X[(long)bi * ldx + i] = t;
       }
-      for (int i = threadIdx.x; i < nc; i += kDenseThreads) {
-        const double t = V[(long)j * nc + i];
-        V[(long)j * nc + i] = V[(long)bi * nc + i];
-        V[(long)bi * nc + i] = t;
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        const double t = V[(long)j * ldv + i];
+        V[(long)j * ldv + i] = V[(long)bi * ldv + i];
+        V[(long)bi * ldv + i] = t;
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -123,6 +121,42 @@ k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* per
       }
     }
     __syncthreads();
+  }
+}
+
+// in_smem: X and V are copied into shared memory (m*nc + nc*nc doubles),
+// rotated there and copied back; otherwise they are rotated in place.
+__global__ void __launch_bounds__(kJacThreads)
+k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws, int in_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int changed, best;
+  __shared__ double sig_s[256];
+  __shared__ int perm_s[258];
+  double* Xw = X;
+  double* Vw = V;
+  int lx = ldx, lv = nc;
+  if (in_smem) {
+    Xw = reinterpret_cast<double*>(smem_raw);
+    Vw = Xw + (long)m * nc;
+    lx = m;
+    for (int idx = threadIdx.x; idx < m * nc; idx += blockDim.x) {
+      const int i = idx % m, j = idx / m;
+      Xw[idx] = X[i + (long)j * ldx];
+    }
+  }
+  for (int i = threadIdx.x; i < nc * nc; i += blockDim.x) Vw[i] = ((i % nc) == (i / nc)) ? 1.0 : 0.0;
+  __syncthreads();
+  const bool small = nc <= 256;
+  jacobi_body(Xw, lx, Vw, lv, m, nc, small ? sig_s : sig, small ? perm_s : perm_ws, &changed, &best);
+  __syncthreads();
+  if (small)
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) sig[j] = sig_s[j];
+  if (in_smem) {
+    for (int idx = threadIdx.x; idx < m * nc; idx += blockDim.x) {
+      const int i = idx % m, j = idx / m;
+      X[i + (long)j * ldx] = Xw[idx];
+    }
+    for (int i = threadIdx.x; i < nc * nc; i += blockDim.x) V[i] = Vw[i];
   }
 }
 
@@ -239,24 +273,49 @@ k_principal_solves(const double* __restrict__ Mm, const double* __restrict__ N,
   }
 }
 
+// Back substitution for a small R (cnt <= kMaxLocal): R and z are staged in
+// shared memory by all threads, then one thread solves.
 __global__ void k_tri_solve_upper(const double* R, int ldr, const int* cnt_dev, const double* z,
                                   double* out) {
-  if (threadIdx.x != 0) return;
+  __shared__ double Rs[kMaxLocal * kMaxLocal];
+  __shared__ double zs[kMaxLocal];
   const int s = *cnt_dev;
-  for (int i = s - 1; i >= 0; --i) {
-    double v = z[i];
-    for (int k = i + 1; k < s; ++k) v -= R[i + k * ldr] * out[k];
-    out[i] = v / R[i + i * ldr];
+  for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+    const int i = idx % s, k = idx / s;
+    Rs[i + k * kMaxLocal] = R[i + (long)k * ldr];
   }
+  for (int i = threadIdx.x; i < s; i += blockDim.x) zs[i] = z[i];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int i = s - 1; i >= 0; --i) {
+    double v = zs[i];
+    for (int k = i + 1; k < s; ++k) v -= Rs[i + k * kMaxLocal] * zs[k];
+    zs[i] = v / Rs[i + i * kMaxLocal];
+  }
+  for (int i = 0; i < s; ++i) out[i] = zs[i];
 }
 
+}  // namespace
+
+namespace {
+cudaError_t launch_jacobi(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws,
+                          cudaStream_t s) {
+  const size_t bytes = ((size_t)m * nc + (size_t)nc * nc) * sizeof(double);
+  const int in_smem = bytes <= 200 * 1024 ? 1 : 0;
+  static int cached = 0;
+  if (in_smem && (int)bytes > cached) {
+    RK_TRY(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cached = (int)bytes;
+  }
+  k_jacobi_svd<<<1, kJacThreads, in_smem ? bytes : 0, s>>>(X, m, nc, ldx, V, sig, perm_ws, in_smem);
+  return launched();
+}
 }  // namespace
 
 cudaError_t jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws,
                        cudaStream_t s) {
   if (nc <= 0) return cudaSuccess;
-  k_jacobi_svd<<<1, kDenseThreads, 0, s>>>(X, m, nc, ldx, V, sig, perm_ws);
-  return launched();
+  return launch_jacobi(X, m, nc, ldx, V, sig, perm_ws, s);
 }
 
 cudaError_t spd_eig(const double* S, int n, double* lam, double* Q, double* work, int* perm_ws,
@@ -268,8 +327,7 @@ cudaError_t spd_eig(const double* S, int n, double* lam, double* Q, double* work
   double* sig = V + (long)n * n;
   k_copy<<<1, kDenseThreads, 0, s>>>(S, X, n * n);
   RK_TRY(launched());
-  k_jacobi_svd<<<1, kDenseThreads, 0, s>>>(X, n, n, n, V, sig, perm_ws);
-  RK_TRY(launched());
+  RK_TRY(launch_jacobi(X, n, n, n, V, sig, perm_ws, s));
   k_copy_reverse_cols<<<1, kDenseThreads, 0, s>>>(V, n, n, Q, sig, lam);
   return launched();
 }
@@ -294,7 +352,7 @@ cudaError_t principal_solves(const double* Mm, const double* N, const double* Kt
 
 cudaError_t tri_solve_upper(const double* R, int ldr, const int* cnt_dev, const double* z,
                             double* out, cudaStream_t s) {
-  k_tri_solve_upper<<<1, 32, 0, s>>>(R, ldr, cnt_dev, z, out);
+  k_tri_solve_upper<<<1, 256, 0, s>>>(R, ldr, cnt_dev, z, out);
   return launched();
 }
 

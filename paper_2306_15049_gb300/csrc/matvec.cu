@@ -18,7 +18,7 @@ namespace {
 constexpr int TH = kTileH, TW = kTileW;
 constexpr int PPT = kPPT;
 
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(kThreads)
 k_op_apply(const T* __restrict__ x, long ldx, const T* __restrict__ w, T* __restrict__ y,
            T* __restrict__ y2, long ldy, int H, int W, Taps tp, double gamma, int mode,
@@ -33,9 +33,13 @@ k_op_apply(const T* __restrict__ x, long ldx, const T* __restrict__ w, T* __rest
   if (y2) y2 += col * ldy;
   T* bufA = reinterpret_cast<T*>(smem_raw);
   T* bufB = bufA + (kTileH + 4 * r) * (kTileW + 4 * r);
-  if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
   T ax[kPPT], ex[kPPT], vc[kPPT];
-  op_tile<T>(x, T(1), w, H, W, sg, r, bufA, bufB, mode != 2, ax, ex, vc);
+  if constexpr (R > 0) {
+    op_tile_fast<T, R>(x, T(1), w, H, W, tp.g, bufA, bufB, mode != 2, ax, ex, vc);
+  } else {
+    if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
+    op_tile<T>(x, T(1), w, H, W, sg, r, bufA, bufB, mode != 2, ax, ex, vc);
+  }
   const int i0 = blockIdx.y * kTileH, j0 = blockIdx.x * kTileW;
 #pragma unroll
   for (int q = 0; q < kPPT; ++q) {
@@ -165,11 +169,21 @@ cudaError_t op_apply(const T* x, long ldx, int ncols, const T* w, T* y, T* y2, l
                      const int* stop) {
   if (ncols <= 0) return cudaSuccess;
   const size_t smem = (size_t)op_tile_smem_elems(tp.r) * sizeof(T);
-  static int cached = 0;
-  RK_TRY(ensure_smem(k_op_apply<T>, smem, &cached));
   dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, ncols);
-  k_op_apply<T><<<grid, kThreads, smem, s>>>(x, ldx, w, y, y2, ldy, H, W, tp, gamma, mode, stop);
-  return launched();
+  auto go = [&](auto kernel, int* cached) -> cudaError_t {
+    RK_TRY(ensure_smem(kernel, smem, cached));
+    kernel<<<grid, kThreads, smem, s>>>(x, ldx, w, y, y2, ldy, H, W, tp, gamma, mode, stop);
+    return launched();
+  };
+  static int c0 = 0, c4 = 0, c6 = 0, c8 = 0, c10 = 0, c12 = 0;
+  switch (tp.r) {
+    case 4: return go(k_op_apply<T, 4>, &c4);
+    case 6: return go(k_op_apply<T, 6>, &c6);
+    case 8: return go(k_op_apply<T, 8>, &c8);
+    case 10: return go(k_op_apply<T, 10>, &c10);
+    case 12: return go(k_op_apply<T, 12>, &c12);
+    default: return go(k_op_apply<T, 0>, &c0);
+  }
 }
 
 cudaError_t blur_apply(const double* x, double* y, int H, int W, const Taps& tp, int adjoint,

@@ -28,7 +28,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int kDots = kMaxLocal + 1;
 
-template <typename T>
+// R > 0: compile-time radius (register-window tile); R == 0: any radius.
+template <typename T, int R>
 __global__ void __launch_bounds__(kThreads)
 k_mr_matvec(MinresState* st, MrA<T> a, int H, int W, Taps tp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -61,9 +62,13 @@ k_mr_matvec(MinresState* st, MrA<T> a, int H, int W, Taps tp) {
     const int s = st->s;
     T* bufA = reinterpret_cast<T*>(smem_raw);
     T* bufB = bufA + (kTileH + 4 * r) * (kTileW + 4 * r);
-    if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
     T ax[kPPT], ex[kPPT], vc[kPPT];
-    op_tile<T>(a.u, T(st->inv_beta_next), a.w, H, W, sg, r, bufA, bufB, true, ax, ex, vc);
+    if constexpr (R > 0) {
+      op_tile_fast<T, R>(a.u, T(st->inv_beta_next), a.w, H, W, tp.g, bufA, bufB, true, ax, ex, vc);
+    } else {
+      if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
+      op_tile<T>(a.u, T(st->inv_beta_next), a.w, H, W, sg, r, bufA, bufB, true, ax, ex, vc);
+    }
     const T gam = T(*a.gamma);
     T acc[kDots];
 #pragma unroll
@@ -163,52 +168,64 @@ k_mr_lanczos(MinresState* st, MrB<T> b, long n, double* alphas_rec, double* beta
   t = warp_sum(t);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double unorm2 = 0.0;
-  for (int k = 0; k < kThreads / 32; ++k) unorm2 += sh[k];
-  st->cnt_b = 0;
-  const double alpha_d = b.hdots[s];
-  const double beta_d = st->beta;
-  const double beta_next = sqrt(unorm2);
-  const double eps = st->sn2 * beta_d;
-  const double dbar = st->cs2 * beta_d;
-  const double delta = st->cs1 * dbar + st->sn1 * alpha_d;
-  const double gbar = -st->sn1 * dbar + st->cs1 * alpha_d;
-  const double gamma = hypot(gbar, beta_next);
-  if (!(gamma > 0.0) || !isfinite(gamma)) {
-    st->breakdown = 1;
-    st->stop = 1;
-    return;
+  // stage the state and the dots in shared memory: the scalar step below is a
+  // chain of dependent reads that would each wait on L2
+  __shared__ MinresState ss;
+  __shared__ double shd[kMaxLocal + 1];
+  constexpr int kWords = sizeof(MinresState) / sizeof(unsigned);
+  for (int i = threadIdx.x; i < kWords; i += kThreads)
+    reinterpret_cast<unsigned*>(&ss)[i] = __ldcg(reinterpret_cast<const unsigned*>(st) + i);
+  for (int k = threadIdx.x; k <= s; k += kThreads) shd[k] = __ldcg(b.hdots + k);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double unorm2 = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) unorm2 += sh[k];
+    ss.cnt_b = 0;
+    const double alpha_d = shd[s];
+    const double beta_d = ss.beta;
+    const double beta_next = sqrt(unorm2);
+    const double eps = ss.sn2 * beta_d;
+    const double dbar = ss.cs2 * beta_d;
+    const double delta = ss.cs1 * dbar + ss.sn1 * alpha_d;
+    const double gbar = -ss.sn1 * dbar + ss.cs1 * alpha_d;
+    const double gamma = hypot(gbar, beta_next);
+    if (!(gamma > 0.0) || !isfinite(gamma)) {
+      ss.breakdown = 1;
+      ss.stop = 1;
+    } else {
+      const double cs = gbar / gamma, sn = beta_next / gamma;
+      const double tau = cs * ss.eta;
+      ss.eta = -sn * ss.eta;
+      const double ig = 1.0 / gamma;
+      for (int k = 0; k < s; ++k) {
+        const double hh = (shd[k] - delta * ss.h1[k] - eps * ss.h2[k]) * ig;
+        ss.z[k] -= tau * hh;
+        ss.h2[k] = ss.h1[k];
+        ss.h1[k] = hh;
+      }
+      const int j = ss.iters;
+      if (alphas_rec && j < rec_cap) {
+        alphas_rec[j] = alpha_d;
+        betas_rec[j] = beta_next;
+      }
+      ss.delta = delta;
+      ss.eps = eps;
+      ss.inv_gamma = ig;
+      ss.tau = tau;
+      ss.inv_beta_next = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
+      ss.cs2 = ss.cs1;
+      ss.sn2 = ss.sn1;
+      ss.cs1 = cs;
+      ss.sn1 = sn;
+      ss.iters = j + 1;
+      ss.beta = beta_next;
+      ss.dir_pending = 1;
+      if (fabs(ss.eta) <= ss.tol_abs || beta_next == 0.0 || ss.iters >= ss.maxit) ss.stop = 1;
+    }
   }
-  const double cs = gbar / gamma, sn = beta_next / gamma;
-  const double tau = cs * st->eta;
-  st->eta = -sn * st->eta;
-  const double ig = 1.0 / gamma;
-  for (int k = 0; k < s; ++k) {
-    const double hk = b.hdots[k];
-    const double hh = (hk - delta * st->h1[k] - eps * st->h2[k]) * ig;
-    st->z[k] -= tau * hh;
-    st->h2[k] = st->h1[k];
-    st->h1[k] = hh;
-  }
-  const int j = st->iters;
-  if (alphas_rec && j < rec_cap) {
-    alphas_rec[j] = alpha_d;
-    betas_rec[j] = beta_next;
-  }
-  st->delta = delta;
-  st->eps = eps;
-  st->inv_gamma = ig;
-  st->tau = tau;
-  st->inv_beta_next = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
-  st->cs2 = st->cs1;
-  st->sn2 = st->sn1;
-  st->cs1 = cs;
-  st->sn1 = sn;
-  st->iters = j + 1;
-  st->beta = beta_next;
-  st->dir_pending = 1;
-  if (fabs(st->eta) <= st->tol_abs || beta_next == 0.0 || st->iters >= st->maxit) st->stop = 1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < kWords; i += kThreads)
+    reinterpret_cast<unsigned*>(st)[i] = reinterpret_cast<const unsigned*>(&ss)[i];
 }
 
 }  // namespace
@@ -217,11 +234,21 @@ template <typename T>
 cudaError_t mr_matvec(MinresState* st, const MrA<T>& a, int H, int W, const Taps& tp,
                       cudaStream_t s) {
   const size_t smem = (size_t)op_tile_smem_elems(tp.r) * sizeof(T);
-  static int cached = 0;
-  RK_TRY(ensure_smem(k_mr_matvec<T>, smem, &cached));
   dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH, 1);
-  k_mr_matvec<T><<<grid, kThreads, smem, s>>>(st, a, H, W, tp);
-  return launched();
+  auto go = [&](auto kernel, int* cached) -> cudaError_t {
+    RK_TRY(ensure_smem(kernel, smem, cached));
+    kernel<<<grid, kThreads, smem, s>>>(st, a, H, W, tp);
+    return launched();
+  };
+  static int c0 = 0, c4 = 0, c6 = 0, c8 = 0, c10 = 0, c12 = 0;
+  switch (tp.r) {
+    case 4: return go(k_mr_matvec<T, 4>, &c4);
+    case 6: return go(k_mr_matvec<T, 6>, &c6);
+    case 8: return go(k_mr_matvec<T, 8>, &c8);
+    case 10: return go(k_mr_matvec<T, 10>, &c10);
+    case 12: return go(k_mr_matvec<T, 12>, &c12);
+    default: return go(k_mr_matvec<T, 0>, &c0);
+  }
 }
 
 template <typename T>

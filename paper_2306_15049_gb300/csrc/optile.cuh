@@ -21,11 +21,11 @@ __host__ __device__ inline int op_tile_smem_elems(int r) {
   return AH * AW + AH * BW;
 }
 
-// Pixel q of this thread: tile coordinates (ti, tj).
+// Pixel q of this thread: tile coordinates (ti, tj). Warp w owns rows
+// 4w .. 4w+3, lane l column l, so the four pixels of a thread lie in one column.
 __device__ __forceinline__ void op_tile_pixel(int q, int& ti, int& tj) {
-  const int p = threadIdx.x + q * kThreads;
-  ti = p / kTileW;
-  tj = p - ti * kTileW;
+  ti = (threadIdx.x >> 5) * kPPT + q;
+  tj = threadIdx.x & 31;
 }
 
 // Computes, for the kPPT pixels this thread owns in tile (blockIdx.x, blockIdx.y):
@@ -117,6 +117,155 @@ __device__ __forceinline__ void op_tile(const T* __restrict__ src, T scale, cons
     T acc = T(0);
     for (int k = 0; k <= 2 * r; ++k) acc += sg[2 * r - k] * s[k * kTileW];
     ax[q] = acc;
+  }
+}
+
+// 16-byte vector type of T for shared-memory row loads.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T, int N>
+__device__ __forceinline__ void load_row(const T* p, T* win) {
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::n;
+  static_assert(N % VW == 0, "window must be a whole number of 16-byte vectors");
+#pragma unroll
+  for (int v = 0; v < N / VW; ++v) {
+    const V t = reinterpret_cast<const V*>(p)[v];
+    if constexpr (VW == 4) {
+      win[4 * v] = t.x; win[4 * v + 1] = t.y; win[4 * v + 2] = t.z; win[4 * v + 3] = t.w;
+    } else {
+      win[2 * v] = t.x; win[2 * v + 1] = t.y;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T* p, const T* o) {
+  if constexpr (Vec16<T>::n == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+  }
+}
+
+// Same contract as op_tile, for a compile-time even radius R: every 1-D pass
+// keeps a register window of 4 + 2R inputs per thread and produces 4 outputs
+// from it (row passes read the window with 16-byte shared loads; column
+// passes walk down one column), and no index needs a runtime division.
+template <typename T, int R>
+__device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
+                                             const T* __restrict__ w, int H, int W,
+                                             const double* taps, T* s0, T* s1, bool with_a,
+                                             T* ax, T* ex, T* vc) {
+  static_assert(R % 2 == 0 && R >= 2, "even radius");
+  constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
+  constexpr int BW = kTileW + 2 * R, CH = kTileH + 2 * R;
+  constexpr int NW = 4 + 2 * R;          // window of one 4-output group
+  const long n = (long)H * W;
+  const T* wx = w;
+  const T* wy = w + n;
+  const int i0 = blockIdx.y * kTileH, j0 = blockIdx.x * kTileW;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  T g[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * R; ++k) g[k] = T(taps[k]);
+
+  // stage scale * src with a halo of 2R (zero outside the image)
+  for (int a = ty; a < AH; a += kThreads / 32) {
+    const int gi = i0 - 2 * R + a;
+    const bool rin = gi >= 0 && gi < H;
+    for (int c = tx; c < AW; c += 32) {
+      const int gj = j0 - 2 * R + c;
+      s0[a * AW + c] = (rin && gj >= 0 && gj < W) ? src[(long)gi * W + gj] * scale : T(0);
+    }
+  }
+  __syncthreads();
+
+  // E v at the owned pixels (column tx, rows 4 ty .. 4 ty + 3)
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) {
+    const int ti = ty * kPPT + q, tj = tx;
+    const int gi = i0 + ti, gj = j0 + tj;
+    T e = T(0), xc = T(0);
+    if (gi < H && gj < W) {
+      const long gidx = (long)gi * W + gj;
+      const T* s = s0 + (ti + 2 * R) * AW + (tj + 2 * R);
+      xc = s[0];
+      if (gj >= 1) e += wx[gidx - 1] * (xc - s[-1]);
+      if (gj < W - 1) e -= wx[gidx] * (s[1] - xc);
+      if (gi >= 1) e += wy[gidx - W] * (xc - s[-AW]);
+      if (gi < H - 1) e -= wy[gidx] * (s[AW] - xc);
+    }
+    ex[q] = e;
+    vc[q] = xc;
+  }
+  if (!with_a) return;
+
+  // pass 1: T_w along rows of s0 -> s1 (AH x BW); output column c is image column j0 - R + c
+  for (int item = threadIdx.x; item < AH * (BW / 4); item += kThreads) {
+    const int a = item / (BW / 4), c0 = 4 * (item % (BW / 4));
+    T win[NW], o[4];
+    load_row<T, NW>(s0 + a * AW + c0, win);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc += g[k] * win[q + k];
+      o[q] = acc;
+    }
+    store4<T>(s1 + a * BW + c0, o);
+  }
+  __syncthreads();
+  T* s2 = s0;   // CH x BW, reuses s0
+  T* s3 = s1;   // CH x kTileW, reuses s1
+  // pass 2: T_h along columns of s1 -> s2 = H v on the tile plus a halo of R,
+  // zero outside the image; output row a is image row i0 - R + a
+  for (int item = threadIdx.x; item < BW * (CH / 4); item += kThreads) {
+    const int c = item % BW, a0 = 4 * (item / BW);
+    const int gj = j0 - R + c;
+    T win[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) win[k] = s1[(a0 + k) * BW + c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gi = i0 - R + a0 + q;
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc += g[k] * win[q + k];
+      s2[(a0 + q) * BW + c] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? acc : T(0);
+    }
+  }
+  __syncthreads();
+  // pass 3: T_w^T along rows of s2 -> s3 (reversed taps); output column c is j0 + c
+  for (int item = threadIdx.x; item < CH * (kTileW / 4); item += kThreads) {
+    const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
+    T win[NW], o[4];
+    load_row<T, NW>(s2 + a * BW + c0, win);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
+      o[q] = acc;
+    }
+    store4<T>(s3 + a * kTileW + c0, o);
+  }
+  __syncthreads();
+  // pass 4: T_h^T along columns of s3 -> A v at the owned pixels
+  {
+    T win[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) win[k] = s3[(ty * kPPT + k) * kTileW + tx];
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
+      ax[q] = acc;
+    }
   }
 }
 
