@@ -255,16 +255,24 @@ struct rs_problem {
   // CUDA graph of kChunk fused MINRES steps (built on first use)
   bool use_graph = true;
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  cudaEvent_t gev[2 * kChunk] = {};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // two instances: one runs while one is read
+  cudaEvent_t gev[2][2 * kChunk] = {};
+  // pipelined stop-flag polls: pinned host slots and their events
+  int* hpoll_pinned = nullptr;
+  cudaEvent_t pev[2] = {nullptr, nullptr};
   double* gcur = nullptr;
   double* partials_a = nullptr;
 
   ~rs_problem() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
-    for (cudaEvent_t e : gev)
+    for (auto& row : gev)
+      for (cudaEvent_t e : row)
+        if (e) cudaEventDestroy(e);
+    for (cudaGraphExec_t g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    for (cudaEvent_t e : pev)
       if (e) cudaEventDestroy(e);
-    if (gexec) cudaGraphExecDestroy(gexec);
+    if (hpoll_pinned) cudaFreeHost(hpoll_pinned);
     if (cap) cudaStreamDestroy(cap);
   }
 
@@ -468,23 +476,23 @@ int true_residual(rs_problem* P, double gamma, const double* x64, double* relres
 // starts at j = 2 mod 3 has the same operands) into a graph, with an event
 // pair around every kernel A for the timing.
 template <typename T, typename FA, typename FB>
-int ensure_graph(rs_problem* P, FA mkA, FB mkB) {
-  if (P->gexec) return RS_OK;
+int ensure_graph(rs_problem* P, int gi, FA mkA, FB mkB) {
+  if (P->gexec[gi]) return RS_OK;
   if (!P->cap) CU(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
   for (int i = 0; i < 2 * kChunk; ++i)
-    if (!P->gev[i]) CU(cudaEventCreate(&P->gev[i]));
+    if (!P->gev[gi][i]) CU(cudaEventCreate(&P->gev[gi][i]));
   const long n = P->z.n;
   CU(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < kChunk; ++i) {
     const int j = 2 + i;
-    cudaEventRecordWithFlags(P->gev[2 * i], P->cap, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(P->gev[gi][2 * i], P->cap, cudaEventRecordExternal);
     mr_matvec<T>(P->st, mkA(j), P->d.height, P->d.width, P->tp, P->cap);
-    cudaEventRecordWithFlags(P->gev[2 * i + 1], P->cap, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(P->gev[gi][2 * i + 1], P->cap, cudaEventRecordExternal);
     mr_lanczos<T>(P->st, mkB(j), n, nullptr, nullptr, 0, P->cap);
   }
   cudaGraph_t g = nullptr;
   CU(cudaStreamEndCapture(P->cap, &g));
-  cudaError_t e = cudaGraphInstantiate(&P->gexec, g, 0);
+  cudaError_t e = cudaGraphInstantiate(&P->gexec[gi], g, 0);
   cudaGraphDestroy(g);
   CU(e);
   return RS_OK;
@@ -492,11 +500,12 @@ int ensure_graph(rs_problem* P, FA mkA, FB mkB) {
 
 // Times of the kernel-A launches of the last graph replay (steps j0 ..
 // j0 + kChunk - 1); launches after the solve stopped were no-ops and are skipped.
-void graph_timing_flush(rs_problem* P, int j0, int iters_done, double bytes, double flops, long n) {
+void graph_timing_flush(rs_problem* P, int gi, int j0, int iters_done, double bytes, double flops,
+                        long n) {
   for (int i = 0; i < kChunk; ++i) {
     if (j0 + i > iters_done) break;
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, P->gev[2 * i], P->gev[2 * i + 1]) != cudaSuccess) continue;
+    if (cudaEventElapsedTime(&ms, P->gev[gi][2 * i], P->gev[gi][2 * i + 1]) != cudaSuccess) continue;
     P->t_ms[0] += ms;
     P->t_launches[0] += 1;
     P->t_pixels[0] += n;
@@ -543,7 +552,6 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
   };
   auto dptr = [&](int j) -> T* { return vp<T>(P->dring[((j % 3) + 3) % 3]); };
   const int* stop = &P->st->stop;
-  int hpoll[2] = {0, 0};
   const int rr = P->tp.r;
   const double a_bytes = (double)(11 + s_host) * n * sizeof(T);
   const double a_flops = (8.0 * (2 * rr + 1) + 12.0 + 2.0 * s_host) * n;
@@ -597,47 +605,59 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     CU(mr_lanczos<T>(P->st, mkB(j), n, keep ? P->arec : nullptr, keep ? P->brec : nullptr, keep, s));
     return RS_OK;
   };
-  auto poll = [&](bool graph_chunk, int j0) -> int {
-    CU(minres_poll(P->st, P->poll, s));
-    RS(read_back(P, hpoll, P->poll, sizeof hpoll));
-    if (graph_chunk) {
-      if (P->timing) graph_timing_flush(P, j0, hpoll[1], a_bytes, a_flops, n);
-    } else {
-      timed_flush(P, hpoll[1]);
-    }
+  const auto graph_ok = [&](int jj) {
+    return P->use_graph && jj > n_unfused && (jj % 3) == 2 && jj - 1 > keep && jj + kChunk - 1 <= maxit;
+  };
+  // Chunks of up to kChunk steps, each followed by an asynchronous copy of the
+  // stop flag into pinned host memory: the host checks chunk c-1 while chunk c
+  // runs, so the GPU does not idle on the poll. A chunk queued after the stop
+  // is all no-ops.
+  struct Chunk {
+    int j0, graph, slot;
+  };
+  Chunk inq[2];
+  int nq = 0, next_slot = 0, gnext = 0;
+  bool stopped = false;
+  auto retire = [&]() -> int {
+    const Chunk c = inq[0];
+    CU(cudaEventSynchronize(P->pev[c.slot]));
+    const int stopf = P->hpoll_pinned[2 * c.slot], its = P->hpoll_pinned[2 * c.slot + 1];
+    if (c.graph >= 0 && P->timing) graph_timing_flush(P, c.graph, c.j0, its, a_bytes, a_flops, n);
+    inq[0] = inq[1];
+    --nq;
+    if (stopf) stopped = true;
     return RS_OK;
   };
   if (n_unfused > 0) CU(scale_dev<T>(u, vptr(1), n, &P->st->inv_beta_next, 0, nullptr, s));
   int j = 1;
-  int since_poll = 0;
-  bool stopped = false;
   while (j <= maxit && !stopped) {
-    const bool graph_ok = P->use_graph && j > n_unfused && (j % 3) == 2 && j - 1 > keep &&
-                          j + kChunk - 1 <= maxit;
-    if (graph_ok) {
-      RS(ensure_graph<T>(P, mkA_ring, mkB_ring));
-      CU(cudaGraphLaunch(P->gexec, s));
+    Chunk c{j, -1, next_slot};
+    if (graph_ok(j)) {
+      const int gi = gnext;
+      gnext ^= 1;
+      RS(ensure_graph<T>(P, gi, mkA_ring, mkB_ring));
+      CU(cudaGraphLaunch(P->gexec[gi], s));
       add_launches(2 * kChunk);
-      const int j0 = j;
+      c.graph = gi;
       j += kChunk;
-      RS(poll(true, j0));
-      stopped = hpoll[0] != 0;
-      since_poll = 0;
-      continue;
-    }
-    if (j <= n_unfused) {
-      RS(unfused(j));
     } else {
-      RS(stepA(j, true));
-      RS(stepB(j));
+      for (int cnt = 0; cnt < kChunk && j <= maxit && (cnt == 0 || !graph_ok(j)); ++cnt, ++j) {
+        if (j <= n_unfused) {
+          RS(unfused(j));
+        } else {
+          RS(stepA(j, true));
+          RS(stepB(j));
+        }
+      }
     }
-    ++j;
-    if (++since_poll >= kChunk || j > maxit) {
-      RS(poll(false, 0));
-      stopped = hpoll[0] != 0;
-      since_poll = 0;
-    }
+    CU(minres_poll(P->st, P->poll, s));
+    CU(cudaMemcpyAsync(P->hpoll_pinned + 2 * c.slot, P->poll, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(P->pev[c.slot], s));
+    next_slot ^= 1;
+    inq[nq++] = c;
+    if (nq == 2) RS(retire());
   }
+  while (nq > 0) RS(retire());
   // a direction update of the last fused step may still be pending: kernel A
   // with the stop flag set does only that (and nothing after an unfused step)
   RS(stepA(j, false));
@@ -886,7 +906,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
   std::vector<char> gnz(z.M, 0);
   for (int l = 0; l < z.M; ++l) {
     const double gl = P->gammas[l];
-    const double ph0 = phase_begin(P);
+    double ph0 = phase_begin(P);
     rs_solve_stats sl{};
     sl.sweeps = 0;
     double* x = X + (long)l * n;    // caller's X is dense M x n
@@ -903,14 +923,22 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
     const int forced = over ? over[l] : -1;
     T* gl_buf = vp<T>(P->Gcur) + (long)l * ld;
     if (forced < 0 && sl.relres0 <= P->d.tol) {
-      CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
-      sl.relres_est = sl.relres0;
       phase_end(P, 3, ph0);
       RS(true_residual(P, gl, x, &sl.relres_true));
       sl.matvecs = 1;
-      sl.sweeps = 0;
-      if (stats) stats[l] = sl;
-      continue;
+      // FP64 mode: the image-based r0 is exact to rounding, the guess is the
+      // solution. Mixed precision: r0 came from FP32 images, so the FP64
+      // residual decides; if it misses the tolerance the shift is solved from it.
+      if (!P->mixed || sl.relres_true <= P->d.tol) {
+        CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
+        sl.relres_est = sl.relres0;
+        sl.sweeps = 0;
+        if (stats) stats[l] = sl;
+        continue;
+      }
+      sl.relres0 = sl.relres_true;
+      r02 = sl.relres_true * sl.relres_true * P->bnorm * P->bnorm;
+      ph0 = phase_begin(P);
     }
     // local space [W, g^(k-1,l), g^(k,l-1)] and its image
     const bool left = (l + 1) <= P->d.I_split;
@@ -1054,6 +1082,13 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   Carver cv{(char*)workspace_dev};
   carve(P, cv);
   const long n = P->z.n;
+  if (cudaHostAlloc(&P->hpoll_pinned, 4 * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->pev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->pev[1], cudaEventDisableTiming) != cudaSuccess) {
+    snprintf(g_err, sizeof g_err, "could not create the poll buffer / events");
+    delete P;
+    return RS_ECUDA;
+  }
   auto fail = [&](cudaError_t e) {
     snprintf(g_err, sizeof g_err, "CUDA error %s in rs_create_problem", cudaGetErrorString(e));
     delete P;

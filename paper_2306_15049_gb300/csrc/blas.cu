@@ -52,6 +52,33 @@ struct Acc<float> {
   __device__ double get() const { return a + (double)part; }
 };
 
+// Block sum of per-thread FP32-accumulated values: FP32 within the warp (the
+// partial sums of one thread are short), FP64 across the warps. GB300 runs
+// FP64 far below its FP32 rate, so the 5-step shuffle tree stays in FP32.
+__device__ __forceinline__ double block_sum_f(double v, double* sh) {
+  float f = (float)v;
+  const float lo = (float)(v - (double)f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  float l2 = lo;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)f + (double)l2;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+  }
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ double block_sum_t(double v, double* sh) {
+  if constexpr (sizeof(T) == 4) return block_sum_f(v, sh);
+  else return block_sum(v, sh);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_multidot(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host,
@@ -66,7 +93,7 @@ k_multidot(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host,
     Acc<T> acc;
     for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads)
       acc.add(xk[i], y[i]);
-    const double t = block_sum(acc.get(), sh);
+    const double t = block_sum_t<T>(acc.get(), sh);
     if (threadIdx.x == 0) partials[(long)blockIdx.x * stride + k] = t;
   }
 }
@@ -105,22 +132,44 @@ k_multi_axpy(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host
     acc.add(v, v);
   }
   if (norm_partials) {
-    const double t = block_sum(acc.get(), sh);
+    const double t = block_sum_t<T>(acc.get(), sh);
     if (threadIdx.x == 0) norm_partials[blockIdx.x] = t;
   }
 }
+
+// Accumulation type of the tall-skinny product: the working precision of the
+// tall operand (FP32 vectors accumulate in FP32: the results are initial
+// guesses and starting residuals, whose exact values are not prescribed).
+template <typename TX> struct GemmAcc { using type = double; };
+template <> struct GemmAcc<float> { using type = float; };
+constexpr int kGemmCs = 8192;
 
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(kThreads)
 k_gemm_ts(const TX* __restrict__ X, long ldx, int nx, const double* __restrict__ C, int ldc,
           int ny, double beta, TY* __restrict__ Y, long ldy, long n) {
+  using A = typename GemmAcc<TX>::type;
+  __shared__ A Cs[kGemmCs];
+  const bool staged = nx * ny <= kGemmCs;
+  if (staged) {
+    for (int idx = threadIdx.x; idx < nx * ny; idx += kThreads) {
+      const int j = idx % nx, l = idx / nx;
+      Cs[idx] = A(C[j + (long)l * ldc]);
+    }
+  }
+  __syncthreads();
   for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
     for (int l = 0; l < ny; ++l) {
-      double acc = 0.0;
-      const double* cl = C + (long)l * ldc;
-      for (int j = 0; j < nx; ++j) acc = fma((double)X[(long)j * ldx + i], cl[j], acc);
+      A acc = A(0);
+      if (staged) {
+        const A* cl = Cs + l * nx;
+        for (int j = 0; j < nx; ++j) acc = fma(A(X[(long)j * ldx + i]), cl[j], acc);
+      } else {
+        const double* cl = C + (long)l * ldc;
+        for (int j = 0; j < nx; ++j) acc = fma(A(X[(long)j * ldx + i]), A(cl[j]), acc);
+      }
       TY* yp = Y + (long)l * ldy + i;
-      *yp = (beta == 0.0) ? TY(acc) : TY(beta * (double)(*yp) + acc);
+      *yp = (beta == 0.0) ? TY(acc) : TY(beta * (double)(*yp) + (double)acc);
     }
   }
 }
@@ -202,7 +251,7 @@ k_norm2(const T* __restrict__ x, long n, double* partials) {
   Acc<T> acc;
   for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads)
     acc.add(x[i], x[i]);
-  const double t = block_sum(acc.get(), sh);
+  const double t = block_sum_t<T>(acc.get(), sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 

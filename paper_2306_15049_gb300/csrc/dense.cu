@@ -30,55 +30,70 @@ constexpr int kJacWarps = kJacThreads / 32;
 // sig[j] = ||X_out[:, j]|| and the columns of X and V are sorted by descending sig.
 __device__ void jacobi_body(double* X, int ldx, double* V, int ldv, int m, int nc, double* sig,
                             int* perm, int* changed, int* best) {
+  (void)perm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // four pairs per warp, eight lanes per pair: GB300 issues FP64 at a fraction
+  // of the FP32 rate, so the dots, their 3-step reductions, the rotation
+  // scalars and the rotations of four pairs share each FP64 warp instruction
+  const int grp = lane >> 3, gl = lane & 7;
+  const unsigned gmask = 0xffu << (grp * 8);
   const int N = nc + (nc & 1);                 // even number of slots (slot nc is a dummy)
-  for (int i = threadIdx.x; i < N; i += blockDim.x) perm[i] = i;
-  __syncthreads();
   const double tol = 1e-15;
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (threadIdx.x == 0) *changed = 0;
     __syncthreads();
     for (int round = 0; round < N - 1; ++round) {
-      for (int pr = warp; pr < N / 2; pr += kJacWarps) {
-        int p = perm[pr], q = perm[N - 1 - pr];
-        if (p >= nc || q >= nc) continue;
+      // circle method in closed form: slot 0 holds column 0, slot i >= 1 holds
+      // ((i - 1 - round) mod (N - 1)) + 1; slot k meets slot N - 1 - k
+      for (int pr = warp * 4 + grp; pr < N / 2; pr += kJacWarps * 4) {
+        const int sa = pr, sb = N - 1 - pr;
+        int p = sa == 0 ? 0 : ((sa - 1 - round) % (N - 1) + (N - 1)) % (N - 1) + 1;
+        int q = ((sb - 1 - round) % (N - 1) + (N - 1)) % (N - 1) + 1;
+        if (p >= nc || q >= nc) continue;      // the dummy slot (uniform in the 8-lane group)
         if (p > q) { const int t = p; p = q; q = t; }
         double* xp = X + (long)p * ldx;
         double* xq = X + (long)q * ldx;
         double a = 0.0, b = 0.0, c = 0.0;
-        for (int i = lane; i < m; i += 32) {
+        for (int i = gl; i < m; i += 8) {
           const double u = xp[i], v = xq[i];
           a = fma(u, u, a);
           b = fma(v, v, b);
           c = fma(u, v, c);
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        c = warp_sum(c);
-        if (c != 0.0 && fabs(c) > tol * sqrt(a * b)) {
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(gmask, a, o);
+          b += __shfl_xor_sync(gmask, b, o);
+          c += __shfl_xor_sync(gmask, c, o);
+        }
+        double cs = 1.0, sn = 0.0;
+        int rot = 0;
+        if (gl == 0 && c != 0.0 && fabs(c) > tol * sqrt(a * b)) {
           const double zeta = (b - a) / (2.0 * c);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = rsqrt(1.0 + t * t), sn = cs * t;
-          for (int i = lane; i < m; i += 32) {
+          cs = rsqrt(1.0 + t * t);
+          sn = cs * t;
+          rot = 1;
+        }
+        const int src = grp * 8;
+        rot = __shfl_sync(gmask, rot, src);
+        if (rot) {
+          cs = __shfl_sync(gmask, cs, src);
+          sn = __shfl_sync(gmask, sn, src);
+          for (int i = gl; i < m; i += 8) {
             const double u = xp[i], v = xq[i];
             xp[i] = cs * u - sn * v;
             xq[i] = sn * u + cs * v;
           }
           double* vp = V + (long)p * ldv;
           double* vq = V + (long)q * ldv;
-          for (int i = lane; i < nc; i += 32) {
+          for (int i = gl; i < nc; i += 8) {
             const double u = vp[i], v = vq[i];
             vp[i] = cs * u - sn * v;
             vq[i] = sn * u + cs * v;
           }
-          if (lane == 0) *changed = 1;
+          if (gl == 0) *changed = 1;
         }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const int last = perm[N - 1];
-        for (int i = N - 1; i > 1; --i) perm[i] = perm[i - 1];
-        perm[1] = last;
       }
       __syncthreads();
     }

@@ -28,6 +28,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int kDots = kMaxLocal + 1;
 
+// Warp sum in the vector type: FP32 vectors are reduced in FP32 within a warp
+// (at most 128 products per partial) and promoted to FP64 across warps and
+// CTAs; GB300 runs FP64 far below its FP32 rate.
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // R > 0: compile-time radius (register-window tile); R == 0: any radius.
 template <typename T, int R>
 __global__ void __launch_bounds__(kThreads)
@@ -42,6 +52,20 @@ k_mr_matvec(MinresState* st, MrA<T> a, int H, int W, Taps tp) {
   const int nblocks = gridDim.x * gridDim.y;
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
 
+  // operands of the pending direction update, loaded before the state is read
+  T pv[kPPT], p1[kPPT], p2[kPPT], px[kPPT];
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) {
+    int ti, tj;
+    op_tile_pixel(q, ti, tj);
+    const int gi = i0 + ti, gj = j0 + tj;
+    const long g = (long)gi * W + gj;
+    const bool in = gi < H && gj < W;
+    pv[q] = in ? a.vprev[g] : T(0);
+    p1[q] = in ? a.d1[g] : T(0);
+    p2[q] = in ? a.d2[g] : T(0);
+    px[q] = in ? a.xm[g] : T(0);
+  }
   if (pend) {
     const T de = T(st->delta), ep = T(st->eps), ig = T(st->inv_gamma), tau = T(st->tau);
 #pragma unroll
@@ -51,9 +75,9 @@ k_mr_matvec(MinresState* st, MrA<T> a, int H, int W, Taps tp) {
       const int gi = i0 + ti, gj = j0 + tj;
       if (gi < H && gj < W) {
         const long g = (long)gi * W + gj;
-        const T dv = (a.vprev[g] - de * a.d1[g] - ep * a.d2[g]) * ig;
+        const T dv = (pv[q] - de * p1[q] - ep * p2[q]) * ig;
         a.dout[g] = dv;
-        a.xm[g] += tau * dv;
+        a.xm[g] = px[q] + tau * dv;
       }
     }
   }
@@ -93,8 +117,8 @@ k_mr_matvec(MinresState* st, MrA<T> a, int H, int W, Taps tp) {
 #pragma unroll
     for (int k = 0; k < kDots; ++k) {
       if (k < s || k == kMaxLocal) {
-        const double t = warp_sum((double)acc[k]);
-        if (lane == 0) red[warp][k] = t;
+        const T t = warp_sum_t<T>(acc[k]);
+        if (lane == 0) red[warp][k] = (double)t;
       }
     }
     __syncthreads();
@@ -142,15 +166,45 @@ k_mr_lanczos(MinresState* st, MrB<T> b, long n, double* alphas_rec, double* beta
   const T alpha = T(b.hdots[s]);
   const T beta = T(st->beta);
   __syncthreads();
-  double acc = 0.0;
-  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
+  // one 16-byte vector per thread and iteration, every load issued up front
+  // (all operands are 256-byte aligned; a tail shorter than a vector is scalar)
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::n;
+  T acc = T(0);
+  const long nv = n / VW;
+  const long tid = blockIdx.x * (long)kThreads + threadIdx.x, nthr = (long)gridDim.x * kThreads;
+  for (long iv = tid; iv < nv; iv += nthr) {
+    const V yv = reinterpret_cast<const V*>(b.y)[iv];
+    const V vv = reinterpret_cast<const V*>(b.v)[iv];
+    const V pv = reinterpret_cast<const V*>(b.vprev)[iv];
+    V kv[kMaxLocal];
+#pragma unroll
+    for (int k = 0; k < kMaxLocal; ++k)
+      if (k < s) kv[k] = reinterpret_cast<const V*>(b.K + (long)k * b.ldk)[iv];
+    const T* ya = reinterpret_cast<const T*>(&yv);
+    const T* va = reinterpret_cast<const T*>(&vv);
+    const T* pa = reinterpret_cast<const T*>(&pv);
+    V uv;
+    T* ua = reinterpret_cast<T*>(&uv);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      T val = ya[e] - alpha * va[e] - beta * pa[e];
+#pragma unroll
+      for (int k = 0; k < kMaxLocal; ++k)
+        if (k < s) val -= sh_h[k] * reinterpret_cast<const T*>(&kv[k])[e];
+      ua[e] = val;
+      acc += val * val;
+    }
+    reinterpret_cast<V*>(b.u)[iv] = uv;
+  }
+  for (long i = nv * VW + tid; i < n; i += nthr) {
     T val = b.y[i] - alpha * b.v[i] - beta * b.vprev[i];
     for (int k = 0; k < s; ++k) val -= sh_h[k] * b.K[(long)k * b.ldk + i];
     b.u[i] = val;
-    acc += (double)val * (double)val;
+    acc += val * val;
   }
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  acc = warp_sum_t<T>(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;

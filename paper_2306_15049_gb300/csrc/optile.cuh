@@ -173,33 +173,56 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) g[k] = T(taps[k]);
 
-  // stage scale * src with a halo of 2R (zero outside the image)
-  for (int a = ty; a < AH; a += kThreads / 32) {
-    const int gi = i0 - 2 * R + a;
-    const bool rin = gi >= 0 && gi < H;
-    for (int c = tx; c < AW; c += 32) {
-      const int gj = j0 - 2 * R + c;
-      s0[a * AW + c] = (rin && gj >= 0 && gj < W) ? src[(long)gi * W + gj] * scale : T(0);
+  // stage scale * src with a halo of 2R (zero outside the image); every load of
+  // the thread is issued before the first one is used
+  {
+    constexpr int RPT = (AH + kThreads / 32 - 1) / (kThreads / 32);
+    constexpr int CPT = (AW + 31) / 32;
+    T st[RPT][CPT];
+#pragma unroll
+    for (int ri = 0; ri < RPT; ++ri) {
+      const int a = ty + ri * (kThreads / 32);
+      const int gi = i0 - 2 * R + a;
+      const bool rin = a < AH && gi >= 0 && gi < H;
+#pragma unroll
+      for (int ci = 0; ci < CPT; ++ci) {
+        const int c = tx + 32 * ci;
+        const int gj = j0 - 2 * R + c;
+        st[ri][ci] = (rin && c < AW && gj >= 0 && gj < W) ? src[(long)gi * W + gj] : T(0);
+      }
+    }
+#pragma unroll
+    for (int ri = 0; ri < RPT; ++ri) {
+      const int a = ty + ri * (kThreads / 32);
+#pragma unroll
+      for (int ci = 0; ci < CPT; ++ci) {
+        const int c = tx + 32 * ci;
+        if (a < AH && c < AW) s0[a * AW + c] = st[ri][ci] * scale;
+      }
     }
   }
   __syncthreads();
 
-  // E v at the owned pixels (column tx, rows 4 ty .. 4 ty + 3)
+  // E v at the owned pixels (column tx, rows 4 ty .. 4 ty + 3); the weights
+  // (zero where the difference is absent) are loaded first
+  T wl[kPPT], wr[kPPT], wu[kPPT], wd[kPPT];
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) {
+    const int gi = i0 + ty * kPPT + q, gj = j0 + tx;
+    const bool in = gi < H && gj < W;
+    const long gidx = (long)gi * W + gj;
+    wl[q] = (in && gj >= 1) ? wx[gidx - 1] : T(0);
+    wr[q] = (in && gj < W - 1) ? wx[gidx] : T(0);
+    wu[q] = (in && gi >= 1) ? wy[gidx - W] : T(0);
+    wd[q] = (in && gi < H - 1) ? wy[gidx] : T(0);
+  }
 #pragma unroll
   for (int q = 0; q < kPPT; ++q) {
     const int ti = ty * kPPT + q, tj = tx;
-    const int gi = i0 + ti, gj = j0 + tj;
-    T e = T(0), xc = T(0);
-    if (gi < H && gj < W) {
-      const long gidx = (long)gi * W + gj;
-      const T* s = s0 + (ti + 2 * R) * AW + (tj + 2 * R);
-      xc = s[0];
-      if (gj >= 1) e += wx[gidx - 1] * (xc - s[-1]);
-      if (gj < W - 1) e -= wx[gidx] * (s[1] - xc);
-      if (gi >= 1) e += wy[gidx - W] * (xc - s[-AW]);
-      if (gi < H - 1) e -= wy[gidx] * (s[AW] - xc);
-    }
-    ex[q] = e;
+    const T* s = s0 + (ti + 2 * R) * AW + (tj + 2 * R);
+    const T xc = s[0];
+    // outside the image s[.] are zero-filled and the weights zero: e = 0
+    ex[q] = wl[q] * (xc - s[-1]) - wr[q] * (s[1] - xc) + wu[q] * (xc - s[-AW]) - wd[q] * (s[AW] - xc);
     vc[q] = xc;
   }
   if (!with_a) return;
