@@ -371,9 +371,16 @@ def main():
     cat = 0 if tm["ms"][0] >= tm["ms"][1] else 1
     launches = max(1, tm["launches"][cat])
     avg_s = tm["ms"][cat] / 1000.0 / launches
-    kname = ("k_mr_matvec<%s> (fused MINRES step: direction update, v_j, (A+gamma E) v_j, K^T y)"
-             % ("float" if args.precision == "mixed" else "double")) if cat == 0 else \
-        "k_op_apply<double> (FP64 true / refinement residual matvec)"
+    tname = "float" if args.precision == "mixed" else "double"
+    persist = os.environ.get("RS_PERSIST", "1") != "0" and wl.radius in (4, 6, 8, 10, 12)
+    if cat == 1:
+        kname = "k_op_apply<double> (FP64 true / refinement residual matvec)"
+    elif persist:
+        kname = ("k_mr_persist<%s,%d> (one cooperative launch per solve: every MINRES step's "
+                 "direction update, (A+gamma E) v_j, projections and Lanczos update)" % (tname, wl.radius))
+    else:
+        kname = ("k_mr_matvec<%s> (fused MINRES step: direction update, v_j, (A+gamma E) v_j, K^T y)"
+                 % tname)
     if cat == 0 and args.precision == "mixed":
         achieved = tm["bytes"][cat] / (tm["ms"][cat] / 1000.0) / 1e9
         roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],

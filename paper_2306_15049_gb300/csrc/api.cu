@@ -262,6 +262,10 @@ struct rs_problem {
   cudaEvent_t pev[2] = {nullptr, nullptr};
   double* gcur = nullptr;
   double* partials_a = nullptr;
+  // persistent solve kernel (one cooperative launch per solve)
+  bool use_persist = true;
+  double* partials_p = nullptr;
+  GridBar* gbar = nullptr;
 
   ~rs_problem() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -367,6 +371,8 @@ void carve(rs_problem* P, Carver& cv) {
   P->st = cv.take<MinresState>(1);
   P->gcur = cv.take<double>(1);
   P->partials_a = cv.take<double>((size_t)mr_matvec_blocks(P->d.height, P->d.width) * (kMaxLocal + 1));
+  P->partials_p = cv.take<double>((size_t)kPersistMaxBlocks * (kMaxLocal + 2));
+  P->gbar = cv.take<GridBar>(1);
 }
 
 #define CU(...)                                                                         \
@@ -629,6 +635,60 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     return RS_OK;
   };
   if (n_unfused > 0) CU(scale_dev<T>(u, vptr(1), n, &P->st->inv_beta_next, 0, nullptr, s));
+  if (P->use_persist) {
+    // the unfused steps (their kernels are no-ops once the solve has stopped),
+    // then every remaining step in one cooperative launch that stops by itself
+    for (int jj = 1; jj <= n_unfused; ++jj) RS(unfused(jj));
+    const int tiles = mr_matvec_blocks(P->d.height, P->d.width);
+    MrP<T> mp{};
+    mp.u = u; mp.y = y; mp.xm = xm; mp.K = Kl; mp.ldk = ld; mp.w = wT; mp.gamma = P->gcur;
+    mp.vzero = vp<T>(P->vzero); mp.Vkeep = Vk; mp.ld = ld; mp.keep = keep;
+    for (int i = 0; i < 3; ++i) { mp.vring[i] = vp<T>(P->vring[i]); mp.dring[i] = vp<T>(P->dring[i]); }
+    mp.partA = P->partials_p;
+    mp.partB = P->partials_p + (long)kPersistMaxBlocks * (kMaxLocal + 1);
+    mp.arec = keep ? P->arec : nullptr;
+    mp.brec = keep ? P->brec : nullptr;
+    mp.rec_cap = keep;
+    mp.j0 = n_unfused + 1;
+    CU(cudaMemsetAsync(P->gbar, 0, sizeof(GridBar), s));
+    const int slot = timed_begin(P);
+    int G = 0;
+    const cudaError_t le = mr_persist<T>(P->st, mp, P->d.height, P->d.width, P->tp, P->gbar,
+                                         std::min(tiles, kPersistMaxBlocks), s, &G);
+    if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
+      // not co-resident on this device: the step kernels below take over
+      (void)cudaGetLastError();
+      P->use_persist = false;
+      if (slot >= 0) P->pending_used = (size_t)slot;
+      return run_minres<T>(P, gamma, r, use_K, tol_abs, maxit, keep, reorth, iters_out, eta_out,
+                           breakdown_out, s_host);
+    }
+    CU(le);
+    timed_end(P, slot, 0, -1, 0, 0.0, 0.0);
+    struct {
+      MinresState st;
+      GridBar bar;
+    } hs;
+    CU(cudaMemcpyAsync(&hs.st, P->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&hs.bar, P->gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (hs.bar.err)
+      return (rs_status)P->set_err(RS_ECUDA, "persistent MINRES kernel: grid barrier timed out");
+    // the launch did the steps after the unfused ones
+    const long steps = std::max(0, hs.st.iters - n_unfused);
+    if (slot >= 0) {
+      auto& rec = P->pending[slot];
+      rec.pixels = steps * n;
+      rec.bytes = (double)steps * (15 + 2 * s_host) * n * sizeof(T);
+      rec.flops = (double)steps * (a_flops + (6.0 + 2.0 * s_host) * n);
+    }
+    timed_flush(P, hs.st.iters);
+    *iters_out = hs.st.iters;
+    *eta_out = std::fabs(hs.st.eta);
+    if (breakdown_out) *breakdown_out = hs.st.breakdown;
+    P->mv_total += hs.st.iters;
+    return RS_OK;
+  }
   int j = 1;
   while (j <= maxit && !stopped) {
     Chunk c{j, -1, next_slot};
@@ -1078,6 +1138,10 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // RS_GRAPHS=0 launches the fused MINRES steps one by one instead of replaying
   // them from a CUDA graph (the same kernels; for profilers that handle graphs poorly)
   if (const char* g = std::getenv("RS_GRAPHS")) P->use_graph = std::strcmp(g, "0") != 0;
+  // RS_PERSIST=0 runs each solve as fused step kernels (graphs) instead of one
+  // persistent cooperative kernel
+  if (const char* g = std::getenv("RS_PERSIST")) P->use_persist = std::strcmp(g, "0") != 0;
+  if (!mr_persist_supported(desc->radius)) P->use_persist = false;
   P->gprev_nz.assign(desc->M, 0);
   Carver cv{(char*)workspace_dev};
   carve(P, cv);

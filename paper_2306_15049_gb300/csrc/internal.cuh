@@ -198,6 +198,44 @@ cudaError_t mr_lanczos(MinresState* st, const MrB<T>& b, long n, double* alphas_
                        double* betas_rec, int rec_cap, cudaStream_t s);
 int mr_matvec_blocks(int H, int W);
 
+// ---------------------------------------------------------------- mrpersist.cu
+// Grid barrier of the persistent solve kernel; zeroed before every launch.
+struct GridBar {
+  unsigned int count;    // CTAs arrived at the current barrier
+  unsigned int gen;      // barrier generation
+  int err;               // 1: a CTA's wait ran out of time (the solve is void)
+  int pad;
+};
+constexpr int kPersistMaxBlocks = 152 * 8;
+// Operands of the persistent solve: step j reads v_j from Vkeep (j <= keep) or
+// vring[j mod 3], d_j from dring[j mod 3].
+template <typename T>
+struct MrP {
+  T* u;                // unnormalised Lanczos residual
+  T* y;                // (A + gamma E) v_j
+  T* xm;               // V_m y accumulated
+  const T* K;          // local space, s columns of stride ldk
+  long ldk;
+  const T* w;          // E weights (2n)
+  const double* gamma; // the shift (device)
+  T* vzero;            // v_0 = 0
+  T* Vkeep;            // kept Lanczos vectors v_1 .. v_keep (stride ld)
+  long ld;
+  int keep;
+  T* vring[3];
+  T* dring[3];
+  double* partA;       // kPersistMaxBlocks x (kMaxLocal + 1)
+  double* partB;       // kPersistMaxBlocks
+  double* arec;        // alpha_j / beta_{j+1} records (rec_cap) or nullptr
+  double* brec;
+  int rec_cap;
+  int j0;              // first step of this launch
+};
+template <typename T>
+cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Taps& tp, GridBar* bar,
+                       int max_blocks, cudaStream_t s, int* launched_blocks);
+bool mr_persist_supported(int radius);
+
 // ---------------------------------------------------------------- cgs.cu
 struct CgsCtx {
   int* count;              // [0] kept columns s, [1] pending

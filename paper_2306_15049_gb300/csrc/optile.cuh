@@ -151,15 +151,25 @@ __device__ __forceinline__ void store4(T* p, const T* o) {
   }
 }
 
+// Loads of data that other CTAs of the same (persistent) kernel may have
+// written: L2 only, never a stale L1 line.
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_maybe_cg(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
 // Same contract as op_tile, for a compile-time even radius R: every 1-D pass
 // keeps a register window of 4 + 2R inputs per thread and produces 4 outputs
 // from it (row passes read the window with 16-byte shared loads; column
 // passes walk down one column), and no index needs a runtime division.
-template <typename T, int R>
+// CG: stage with L2-only loads; tile_y / tile_x: the tile (default: the CTA's).
+template <typename T, int R, bool CG = false>
 __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
                                              const T* __restrict__ w, int H, int W,
                                              const double* taps, T* s0, T* s1, bool with_a,
-                                             T* ax, T* ex, T* vc) {
+                                             T* ax, T* ex, T* vc, int tile_y = -1,
+                                             int tile_x = -1) {
   static_assert(R % 2 == 0 && R >= 2, "even radius");
   constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
   constexpr int BW = kTileW + 2 * R, CH = kTileH + 2 * R;
@@ -167,7 +177,8 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
   const long n = (long)H * W;
   const T* wx = w;
   const T* wy = w + n;
-  const int i0 = blockIdx.y * kTileH, j0 = blockIdx.x * kTileW;
+  const int i0 = (tile_y >= 0 ? tile_y : (int)blockIdx.y) * kTileH;
+  const int j0 = (tile_x >= 0 ? tile_x : (int)blockIdx.x) * kTileW;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   T g[2 * R + 1];
 #pragma unroll
@@ -188,7 +199,7 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
       for (int ci = 0; ci < CPT; ++ci) {
         const int c = tx + 32 * ci;
         const int gj = j0 - 2 * R + c;
-        st[ri][ci] = (rin && c < AW && gj >= 0 && gj < W) ? src[(long)gi * W + gj] : T(0);
+        st[ri][ci] = (rin && c < AW && gj >= 0 && gj < W) ? ld_maybe_cg<CG>(src + (long)gi * W + gj) : T(0);
       }
     }
 #pragma unroll
