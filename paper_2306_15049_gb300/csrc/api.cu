@@ -264,6 +264,7 @@ struct rs_problem {
   double* partials_a = nullptr;
   // persistent solve kernel (one cooperative launch per solve)
   bool use_persist = true;
+  int last_resident = -1;   // kind of the last persistent launch (1 resident, 0 streaming)
   double* partials_p = nullptr;
   GridBar* gbar = nullptr;
 
@@ -639,7 +640,6 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     // the unfused steps (their kernels are no-ops once the solve has stopped),
     // then every remaining step in one cooperative launch that stops by itself
     for (int jj = 1; jj <= n_unfused; ++jj) RS(unfused(jj));
-    const int tiles = mr_matvec_blocks(P->d.height, P->d.width);
     MrP<T> mp{};
     mp.u = u; mp.y = y; mp.xm = xm; mp.K = Kl; mp.ldk = ld; mp.w = wT; mp.gamma = P->gcur;
     mp.vzero = vp<T>(P->vzero); mp.Vkeep = Vk; mp.ld = ld; mp.keep = keep;
@@ -652,9 +652,10 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     mp.j0 = n_unfused + 1;
     CU(cudaMemsetAsync(P->gbar, 0, sizeof(GridBar), s));
     const int slot = timed_begin(P);
-    int G = 0;
+    int G = 0, resident = 0;
     const cudaError_t le = mr_persist<T>(P->st, mp, P->d.height, P->d.width, P->tp, P->gbar,
-                                         std::min(tiles, kPersistMaxBlocks), s, &G);
+                                         use_K ? std::max(s_host, 1) : 1, s, &G, &resident);
+    P->last_resident = resident;
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
       // not co-resident on this device: the step kernels below take over
       (void)cudaGetLastError();
@@ -672,6 +673,8 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     CU(cudaMemcpyAsync(&hs.st, P->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(&hs.bar, P->gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (hs.bar.err == 2)
+      return (rs_status)P->set_err(RS_ECUDA, "persistent MINRES kernel: local space wider than %d", s_host);
     if (hs.bar.err)
       return (rs_status)P->set_err(RS_ECUDA, "persistent MINRES kernel: grid barrier timed out");
     // the launch did the steps after the unfused ones

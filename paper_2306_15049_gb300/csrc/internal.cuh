@@ -201,9 +201,9 @@ int mr_matvec_blocks(int H, int W);
 // ---------------------------------------------------------------- mrpersist.cu
 // Grid barrier of the persistent solve kernel; zeroed before every launch.
 struct GridBar {
-  unsigned int count;    // CTAs arrived at the current barrier
-  unsigned int gen;      // barrier generation
-  int err;               // 1: a CTA's wait ran out of time (the solve is void)
+  unsigned long long count;   // arrivals so far (barrier b completes at b x CTAs)
+  int err;                    // 1: a CTA's wait ran out of time; 2: local space wider
+                              // than the launch's shared memory (the solve is void)
   int pad;
 };
 constexpr int kPersistMaxBlocks = 152 * 8;
@@ -224,16 +224,19 @@ struct MrP {
   int keep;
   T* vring[3];
   T* dring[3];
-  double* partA;       // kPersistMaxBlocks x (kMaxLocal + 1)
+  double* partA;       // (kMaxLocal + 1) x kPersistMaxBlocks
   double* partB;       // kPersistMaxBlocks
   double* arec;        // alpha_j / beta_{j+1} records (rec_cap) or nullptr
   double* brec;
   int rec_cap;
   int j0;              // first step of this launch
 };
+// One launch runs the solve to its stop. s_alloc: the widest local space the
+// resident kernel must hold in shared memory. resident (out): 1 if the
+// one-CTA-per-tile kernel ran, 0 for the streaming one.
 template <typename T>
 cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Taps& tp, GridBar* bar,
-                       int max_blocks, cudaStream_t s, int* launched_blocks);
+                       int s_alloc, cudaStream_t s, int* launched_blocks, int* resident);
 bool mr_persist_supported(int radius);
 
 // ---------------------------------------------------------------- cgs.cu

@@ -34,10 +34,10 @@ k_op_apply(const T* __restrict__ x, long ldx, const T* __restrict__ w, T* __rest
   T* bufA = reinterpret_cast<T*>(smem_raw);
   T* bufB = bufA + (kTileH + 4 * r) * (kTileW + 4 * r);
   T ax[kPPT], ex[kPPT], vc[kPPT];
+  if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
   if constexpr (R > 0) {
-    op_tile_fast<T, R>(x, T(1), w, H, W, tp.g, bufA, bufB, mode != 2, ax, ex, vc);
+    op_tile_fast<T, R>(x, T(1), w, H, W, sg, bufA, bufB, mode != 2, ax, ex, vc);
   } else {
-    if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
     op_tile<T>(x, T(1), w, H, W, sg, r, bufA, bufB, mode != 2, ax, ex, vc);
   }
   const int i0 = blockIdx.y * kTileH, j0 = blockIdx.x * kTileW;

@@ -87,10 +87,10 @@ k_mr_matvec(MinresState* st, MrA<T> a, int H, int W, Taps tp) {
     T* bufA = reinterpret_cast<T*>(smem_raw);
     T* bufB = bufA + (kTileH + 4 * r) * (kTileW + 4 * r);
     T ax[kPPT], ex[kPPT], vc[kPPT];
+    if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
     if constexpr (R > 0) {
-      op_tile_fast<T, R>(a.u, T(st->inv_beta_next), a.w, H, W, tp.g, bufA, bufB, true, ax, ex, vc);
+      op_tile_fast<T, R>(a.u, T(st->inv_beta_next), a.w, H, W, sg, bufA, bufB, true, ax, ex, vc);
     } else {
-      if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
       op_tile<T>(a.u, T(st->inv_beta_next), a.w, H, W, sg, r, bufA, bufB, true, ax, ex, vc);
     }
     const T gam = T(*a.gamma);

@@ -2,20 +2,27 @@
 // cooperatively launched kernel per solve.
 //
 // Every CTA keeps a shared-memory copy of the scalar state. One step j:
-//   phase A  (32 x 32 tiles, tile t on CTA t mod G): the direction update of
-//            step j-1, v_j = u / beta_j staged with its halo, y = (A + gamma E) v_j,
-//            per-CTA partial dots [K^T y; v_j^T y];
+//   phase A  (32 x 32 tiles): the direction update of step j-1, v_j = u / beta_j
+//            staged with its halo, y = (A + gamma E) v_j, per-CTA partial dots
+//            [K^T y; v_j^T y];
 //   barrier; every CTA adds all partial dots in the same fixed order;
-//   phase B  (16-byte vectors, grid-stride): u = y - K h - alpha v_j - beta v_{j-1},
-//            per-CTA partial ||u||^2;
+//   phase B  u = y - K h - alpha v_j - beta v_{j-1}, per-CTA partial ||u||^2;
 //   barrier; every CTA adds the partial norms in the same fixed order and takes
 //            the same scalar Givens step (rotations, tau, eta, hhat / z
 //            recurrences, stop test) on its copy of the state.
 // All CTAs therefore hold bit-identical states and leave the loop at the same
-// step; no host polling is needed. Data written by other CTAs inside the
-// kernel is read with L2-only loads. The grid barrier's wait is bounded in
-// time: on a timeout it raises an error flag, every CTA leaves, and the host
-// reports the failure instead of hanging.
+// step; no host polling is needed.
+//
+// Two kernels share this loop:
+//   k_mr_resident  one CTA per tile for the whole solve. v_j, v_{j-1}, the two
+//                  latest directions, x_m and y of the CTA's pixels stay in
+//                  registers and its K rows in shared memory; per step only u
+//                  (which neighbours read through the stencil halo) goes to memory.
+//   k_mr_persist   any number of tiles per CTA (images with more tiles than
+//                  co-resident CTAs): every vector lives in memory.
+// Data written by other CTAs inside the kernel is read with L2-only loads. The
+// grid barrier's wait is bounded in time: on a timeout it raises an error
+// flag, every CTA leaves, and the host reports the failure instead of hanging.
 #include "internal.cuh"
 #include "optile.cuh"
 
@@ -23,6 +30,7 @@ namespace rk {
 namespace {
 
 constexpr int kDots = kMaxLocal + 1;
+constexpr int kWarps = kThreads / 32;
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s, far beyond any phase
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -38,9 +46,9 @@ __device__ __forceinline__ T warp_sum_w(T v) {
   return v;
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -50,36 +58,233 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Generation barrier over the G co-resident CTAs of a cooperative launch.
-// Returns false if this CTA gave up (timeout, or another CTA's error flag).
-__device__ bool grid_sync(GridBar* bar, unsigned nblocks, int* ok_s) {
+// Barrier number nb (1, 2, ...) of the launch over its G co-resident CTAs: a
+// monotonic arrival counter (zeroed by the host before the launch) that every
+// CTA waits to reach nb * G. Returns false if this CTA gave up (timeout, or
+// another CTA's error flag).
+__device__ bool grid_sync(GridBar* bar, unsigned long long target, int* ok_s) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned gen = ld_acquire_u32(&bar->gen);
     __threadfence();
-    const unsigned arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
+    atomicAdd(&bar->count, 1ull);
+    if (ld_acquire_u64(&bar->count) < target) {
       const unsigned long long t0 = global_ns();
-      while (ld_acquire_u32(&bar->gen) == gen) {
-        if (*((volatile int*)&bar->err)) { ok = 0; break; }
-        if (global_ns() - t0 > kBarrierTimeoutNs) {
-          atomicExch(&bar->err, 1);
-          ok = 0;
-          break;
+      unsigned spins = 0;
+      while (ld_acquire_u64(&bar->count) < target) {
+        if ((++spins & 63u) == 0) {
+          if (*((volatile int*)&bar->err)) { ok = 0; break; }
+          if (global_ns() - t0 > kBarrierTimeoutNs) {
+            atomicExch(&bar->err, 1);
+            ok = 0;
+            break;
+          }
         }
-        __nanosleep(32);
       }
     }
-    __threadfence();
     *ok_s = ok;
   }
   __syncthreads();
   return *ok_s != 0;
+}
+
+// Reductions run in the vector type T: a float solve sums its partials in
+// float (a fixed pairwise-like tree: per thread, warp butterflies, warps, CTAs),
+// since GB300 executes FP64 arithmetic and conversions at a small fraction of
+// its FP32 rate and every CTA repeats the cross-CTA sums.
+//
+// Per-CTA partial dots acc[0..s-1] (K^T y) and acc[kMaxLocal] (v^T y) into
+// partA[pos * kPersistMaxBlocks + blockIdx.x], pos = 0..s (alpha at pos s).
+template <typename T>
+__device__ __forceinline__ void store_dot_partials(const T* acc, int s, T (*red)[kDots], T* partA) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kDots; ++k) {
+    if (k < s || k == kMaxLocal) {
+      const T t = warp_sum_w<T>(acc[k]);
+      if (lane == 0) red[warp][k] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kDots) {
+    const int k = threadIdx.x;
+    if (k < s || k == kMaxLocal) {
+      T t = T(0);
+#pragma unroll
+      for (int wv = 0; wv < kWarps; ++wv) t += red[wv][k];
+      partA[(long)(k == kMaxLocal ? s : k) * kPersistMaxBlocks + blockIdx.x] = t;
+    }
+  }
+}
+
+// hd[0..s] = sum over the G CTAs of partA (the same order in every CTA): thread
+// t takes CTAs t, t + kThreads, ...; all its loads are issued at once.
+template <typename T>
+__device__ __forceinline__ void reduce_dot_partials(const T* partA, unsigned G, int s,
+                                                    T (*red)[kDots], T* hd) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T t[kDots];
+#pragma unroll
+  for (int k = 0; k < kDots; ++k) t[k] = T(0);
+  for (unsigned g = threadIdx.x; g < G; g += kThreads) {
+    T l[kDots];
+#pragma unroll
+    for (int k = 0; k < kDots; ++k) l[k] = (k <= s) ? __ldcg(partA + (long)k * kPersistMaxBlocks + g) : T(0);
+#pragma unroll
+    for (int k = 0; k < kDots; ++k) t[k] += l[k];
+  }
+  __syncthreads();   // red is reused
+#pragma unroll
+  for (int k = 0; k < kDots; ++k) {
+    if (k <= s) {
+      const T v = warp_sum_w<T>(t[k]);
+      if (lane == 0) red[warp][k] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x <= s) {
+    T v = T(0);
+#pragma unroll
+    for (int wv = 0; wv < kWarps; ++wv) v += red[wv][threadIdx.x];
+    hd[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+// Per-CTA partial ||u||^2 into partB[blockIdx.x].
+template <typename T>
+__device__ __forceinline__ void store_norm_partial(T accb, T (*red)[kDots], T* partB) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  accb = warp_sum_w<T>(accb);
+  if (lane == 0) red[warp][0] = accb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T t = T(0);
+#pragma unroll
+    for (int wv = 0; wv < kWarps; ++wv) t += red[wv][0];
+    partB[blockIdx.x] = t;
+  }
+}
+
+// The step's coefficients in the vector type, converted once per step.
+template <typename T>
+struct StepCoef {
+  T delta, eps, inv_gamma, tau;   // direction update of the last step
+  T inv_beta_next;                // v_j = u / beta_j
+  T beta;                         // coefficient of v_{j-1}
+};
+
+template <typename T>
+__device__ __forceinline__ void coef_from_state(const MinresState& ss, StepCoef<T>& cf) {
+  cf.delta = T(ss.delta);
+  cf.eps = T(ss.eps);
+  cf.inv_gamma = T(ss.inv_gamma);
+  cf.tau = T(ss.tau);
+  cf.inv_beta_next = T(ss.inv_beta_next);
+  cf.beta = T(ss.beta);
+}
+
+// ||u||^2 from partB (the same order in every CTA), then the scalar step of
+// MINRES on the CTA's copy of the state (Paige-Saunders; the coupling
+// recurrences of Eq. minShift). Lane 0 of warp 0 takes the rotation (FP64);
+// lanes k < s then update hhat_k and z_k.
+template <typename T>
+__device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T* hd,
+                                            T (*red)[kDots], MinresState& ss, StepCoef<T>& cf,
+                                            double* sc, const MrP<T>& p) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T t = T(0);
+  for (unsigned g = threadIdx.x; g < G; g += kThreads) t += __ldcg(partB + g);
+  t = warp_sum_w<T>(t);
+  __syncthreads();   // red is reused
+  if (lane == 0) red[warp][0] = t;
+  __syncthreads();
+  if (warp == 0) {
+    T un = (lane < kWarps) ? red[lane][0] : T(0);
+    un = warp_sum_w<T>(un);
+    const int s = ss.s;
+    if (lane == 0) {
+      const double unorm2 = (double)un;
+      const double alpha_d = (double)hd[s];
+      const double beta_d = ss.beta;
+      const double eps = ss.sn2 * beta_d;
+      const double dbar = ss.cs2 * beta_d;
+      const double delta = ss.cs1 * dbar + ss.sn1 * alpha_d;
+      const double gbar = -ss.sn1 * dbar + ss.cs1 * alpha_d;
+      // beta_{j+1} = ||u|| and gamma = (gbar^2 + beta_{j+1}^2)^(1/2) side by side
+      const double beta_next = sqrt(unorm2);
+      const double gamma = sqrt(fma(gbar, gbar, unorm2));
+      if (!(gamma > 0.0) || !isfinite(gamma)) {
+        ss.breakdown = 1;
+        ss.stop = 1;
+        ss.dir_pending = 0;
+        sc[0] = 0.0;
+      } else {
+        const double ig = 1.0 / gamma;
+        const double ibn = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
+        const double cs = gbar * ig, sn = beta_next * ig;
+        const double eta = ss.eta;
+        const double tau = cs * eta;
+        const int it = ss.iters;
+        if (blockIdx.x == 0 && p.arec && it < p.rec_cap) {
+          p.arec[it] = alpha_d;
+          p.brec[it] = beta_next;
+        }
+        sc[0] = 1.0;
+        sc[1] = delta;
+        sc[2] = eps;
+        sc[3] = ig;
+        sc[4] = tau;
+        ss.eta = -sn * eta;
+        ss.delta = delta;
+        ss.eps = eps;
+        ss.inv_gamma = ig;
+        ss.tau = tau;
+        ss.inv_beta_next = ibn;
+        ss.cs2 = ss.cs1;
+        ss.sn2 = ss.sn1;
+        ss.cs1 = cs;
+        ss.sn1 = sn;
+        ss.iters = it + 1;
+        ss.beta = beta_next;
+        ss.dir_pending = 1;
+        if (fabs(ss.eta) <= ss.tol_abs || beta_next == 0.0 || ss.iters >= ss.maxit) ss.stop = 1;
+        cf.delta = T(delta);
+        cf.eps = T(eps);
+        cf.inv_gamma = T(ig);
+        cf.tau = T(tau);
+        cf.inv_beta_next = T(ibn);
+        cf.beta = T(beta_next);
+      }
+    }
+    __syncwarp();
+    if (lane < s && sc[0] != 0.0) {
+      const double h1 = ss.h1[lane];
+      const double hh = ((double)hd[lane] - sc[1] * h1 - sc[2] * ss.h2[lane]) * sc[3];
+      ss.z[lane] -= sc[4] * hh;
+      ss.h2[lane] = h1;
+      ss.h1[lane] = hh;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void load_state(const MinresState* st, MinresState& ss) {
+  constexpr int kWords = sizeof(MinresState) / sizeof(unsigned);
+  for (int i = threadIdx.x; i < kWords; i += kThreads)
+    reinterpret_cast<unsigned*>(&ss)[i] = __ldcg(reinterpret_cast<const unsigned*>(st) + i);
+}
+
+__device__ __forceinline__ void store_state(MinresState* st, MinresState& ss) {
+  constexpr int kWords = sizeof(MinresState) / sizeof(unsigned);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ss.dir_pending = 0;
+    ss.cnt_a = ss.cnt_b = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kWords; i += kThreads)
+    reinterpret_cast<unsigned*>(st)[i] = reinterpret_cast<const unsigned*>(&ss)[i];
 }
 
 template <typename T>
@@ -95,29 +300,181 @@ struct Ptrs {
   __device__ static T* pick(T* const (&a)[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
 };
 
+// ---------------------------------------------------------------------------
+// one CTA per tile, vectors of the CTA's pixels in registers
+// ---------------------------------------------------------------------------
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreads, 2)
+k_mr_resident(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar, int s_alloc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ MinresState ss;
+  __shared__ StepCoef<T> cf;
+  __shared__ T hd[kDots];
+  __shared__ T red[kWarps][kDots];
+  __shared__ T sg[kMaxTaps];
+  __shared__ double sc[5];
+  __shared__ int ok_s;
+  constexpr int kTile = kTileH * kTileW;
+  const unsigned G = gridDim.x;
+  const int tiles_x = (W + kTileW - 1) / kTileW;
+  const int tyi = blockIdx.x / tiles_x, txi = blockIdx.x - tyi * tiles_x;
+  const int i0 = tyi * kTileH, j0 = txi * kTileW;
+  T* bufA = reinterpret_cast<T*>(smem_raw);
+  T* bufB = bufA + (kTileH + 4 * R) * (kTileW + 4 * R);
+  T* Ks = bufA + op_tile_smem_elems(R);   // s_alloc x kTile, pixel index ti * 32 + tj
+  T* partA = reinterpret_cast<T*>(p.partA);
+  T* partB = reinterpret_cast<T*>(p.partB);
+  const Ptrs<T> ptr{p};
+  load_state(st, ss);
+  if (threadIdx.x <= 2 * R) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
+  const T gam = T(__ldcg(p.gamma));
+  __syncthreads();
+  if (threadIdx.x == 0) coef_from_state(ss, cf);
+  const int s = ss.s;
+  if (s > s_alloc) {   // the same decision in every CTA: nobody reaches a barrier
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&bar->err, 2);
+    return;
+  }
+  int j = p.j0;
+  long gix[kPPT];
+  bool in[kPPT];
+  int pix[kPPT];
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) {
+    int ti, tj;
+    op_tile_pixel(q, ti, tj);
+    in[q] = (i0 + ti) < H && (j0 + tj) < W;
+    gix[q] = (long)(i0 + ti) * W + (j0 + tj);
+    pix[q] = ti * kTileW + tj;
+  }
+  // registers: v_{j-1}, the two latest directions, x_m
+  T vprev[kPPT], d1[kPPT], d2[kPPT], xr[kPPT];
+  {
+    const bool pend0 = ss.dir_pending != 0;
+    const T* vp0 = ptr.v(j - 1);
+    const T* da = ptr.d(pend0 ? j - 2 : j - 1);
+    const T* db = ptr.d(pend0 ? j - 3 : j - 2);
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      vprev[q] = in[q] ? __ldcg(vp0 + gix[q]) : T(0);
+      d1[q] = in[q] ? __ldcg(da + gix[q]) : T(0);
+      d2[q] = in[q] ? __ldcg(db + gix[q]) : T(0);
+      xr[q] = in[q] ? __ldcg(p.xm + gix[q]) : T(0);
+    }
+  }
+  for (int k = 0; k < s; ++k)
+    for (int e = threadIdx.x; e < kTile; e += kThreads) {
+      const int ti = e / kTileW, tj = e - ti * kTileW;
+      const bool ok = (i0 + ti) < H && (j0 + tj) < W;
+      Ks[k * kTile + e] = ok ? p.K[(long)k * p.ldk + (long)(i0 + ti) * W + (j0 + tj)] : T(0);
+    }
+  __syncthreads();
+
+  unsigned long long nb = 0;
+  bool failed = false;
+  for (;;) {
+    if (ss.dir_pending) {
+      const T de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau;
+#pragma unroll
+      for (int q = 0; q < kPPT; ++q) {
+        const T dn = (vprev[q] - de * d1[q] - ep * d2[q]) * ig;
+        xr[q] += tau * dn;
+        d2[q] = d1[q];
+        d1[q] = dn;
+      }
+    }
+    if (ss.stop) break;
+    // ---------------- phase A ----------------
+    T ax[kPPT], ex[kPPT], vc[kPPT], yk[kPPT];
+    op_tile_fast<T, R, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, bufA, bufB, true, ax, ex, vc,
+                             tyi, txi);
+    T acc[kDots];
+#pragma unroll
+    for (int k = 0; k < kDots; ++k) acc[k] = T(0);
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      yk[q] = in[q] ? ax[q] + gam * ex[q] : T(0);
+      vc[q] = in[q] ? vc[q] : T(0);
+#pragma unroll
+      for (int k = 0; k < kMaxLocal; ++k)
+        if (k < s) acc[k] += Ks[k * kTile + pix[q]] * yk[q];
+      acc[kMaxLocal] += vc[q] * yk[q];
+    }
+    if (j <= p.keep) {   // kept Lanczos vector v_j
+      T* vk = p.Vkeep + (long)(j - 1) * p.ld;
+#pragma unroll
+      for (int q = 0; q < kPPT; ++q)
+        if (in[q]) vk[gix[q]] = vc[q];
+    }
+    store_dot_partials<T>(acc, s, red, partA);
+    if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    reduce_dot_partials<T>(partA, G, s, red, hd);
+    // ---------------- phase B (registers) ----------------
+    {
+      const T alpha = hd[s], beta = cf.beta;
+      T u[kPPT];
+#pragma unroll
+      for (int q = 0; q < kPPT; ++q) u[q] = yk[q] - alpha * vc[q] - beta * vprev[q];
+#pragma unroll
+      for (int k = 0; k < kMaxLocal; ++k) {
+        if (k < s) {
+          const T hk = hd[k];
+#pragma unroll
+          for (int q = 0; q < kPPT; ++q) u[q] -= hk * Ks[k * kTile + pix[q]];
+        }
+      }
+      T accb = T(0);
+#pragma unroll
+      for (int q = 0; q < kPPT; ++q) {
+        if (in[q]) p.u[gix[q]] = u[q]; else u[q] = T(0);
+        accb += u[q] * u[q];
+        vprev[q] = vc[q];
+      }
+      store_norm_partial<T>(accb, red, partB);
+    }
+    if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    scalar_step<T>(partB, G, hd, red, ss, cf, sc, p);
+    ++j;
+  }
+  if (failed) return;
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q)
+    if (in[q]) p.xm[gix[q]] = xr[q];
+  if (blockIdx.x == 0) store_state(st, ss);
+}
+
+// ---------------------------------------------------------------------------
+// any number of tiles per CTA, vectors in memory
+// ---------------------------------------------------------------------------
 template <typename T, int R>
 __global__ void __launch_bounds__(kThreads, 2)
 k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ MinresState ss;
-  __shared__ double hd[kDots];
-  __shared__ double red[kThreads / 32][kDots];
+  __shared__ StepCoef<T> cf;
+  __shared__ T hd[kDots];
+  __shared__ T red[kWarps][kDots];
+  __shared__ T sg[kMaxTaps];
+  __shared__ double sc[5];
   __shared__ int ok_s;
   const unsigned G = gridDim.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (H + kTileH - 1) / kTileH;
   const int ntiles = tiles_x * tiles_y;
   const long n = (long)H * W;
   T* bufA = reinterpret_cast<T*>(smem_raw);
   T* bufB = bufA + (kTileH + 4 * R) * (kTileW + 4 * R);
+  T* partA = reinterpret_cast<T*>(p.partA);
+  T* partB = reinterpret_cast<T*>(p.partB);
   const Ptrs<T> ptr{p};
-  constexpr int kWords = sizeof(MinresState) / sizeof(unsigned);
-  for (int i = threadIdx.x; i < kWords; i += kThreads)
-    reinterpret_cast<unsigned*>(&ss)[i] = __ldcg(reinterpret_cast<const unsigned*>(st) + i);
+  load_state(st, ss);
+  if (threadIdx.x <= 2 * R) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
   const T gam = T(__ldcg(p.gamma));
+  __syncthreads();
+  if (threadIdx.x == 0) coef_from_state(ss, cf);
   __syncthreads();
 
   int j = p.j0;
+  unsigned long long nb = 0;
   bool failed = false;
   for (;;) {
     const int pend = ss.dir_pending, stopped = ss.stop, s = ss.s;
@@ -134,7 +491,7 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
       const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
       const int i0 = tyi * kTileH, j0 = txi * kTileW;
       if (pend) {
-        const T de = T(ss.delta), ep = T(ss.eps), ig = T(ss.inv_gamma), tau = T(ss.tau);
+        const T de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau;
         T pv[kPPT], p1[kPPT], p2[kPPT], px[kPPT];
 #pragma unroll
         for (int q = 0; q < kPPT; ++q) {
@@ -163,7 +520,7 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
       }
       if (!stopped) {
         T ax[kPPT], ex[kPPT], vc[kPPT];
-        op_tile_fast<T, R, true>(p.u, T(ss.inv_beta_next), p.w, H, W, tp.g, bufA, bufB, true, ax, ex,
+        op_tile_fast<T, R, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, bufA, bufB, true, ax, ex,
                                  vc, tyi, txi);
 #pragma unroll
         for (int q = 0; q < kPPT; ++q) {
@@ -185,41 +542,17 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
       __syncthreads();   // the tile buffers are reused by the next tile
     }
     if (stopped) break;
-#pragma unroll
-    for (int k = 0; k < kDots; ++k) {
-      if (k < s || k == kMaxLocal) {
-        const T t = warp_sum_w<T>(acc[k]);
-        if (lane == 0) red[warp][k] = (double)t;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < kDots) {
-      const int k = threadIdx.x;
-      if (k < s || k == kMaxLocal) {
-        double t = 0.0;
-        for (int wv = 0; wv < kThreads / 32; ++wv) t += red[wv][k];
-        p.partA[(long)blockIdx.x * kDots + (k == kMaxLocal ? s : k)] = t;
-      }
-    }
-    if (!grid_sync(bar, G, &ok_s)) { failed = true; break; }
-    // every CTA: h_j and alpha_j from all partials, in the same order
-    for (int k = warp; k <= s; k += kThreads / 32) {
-      double t = 0.0;
-      for (unsigned g = lane; g < G; g += 32) t += __ldcg(p.partA + (long)g * kDots + k);
-      t = warp_sum_d(t);
-      if (lane == 0) hd[k] = t;
-    }
-    __syncthreads();
+    store_dot_partials<T>(acc, s, red, partA);
+    if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    reduce_dot_partials<T>(partA, G, s, red, hd);
     // ---------------- phase B: vectors ----------------
     {
       using V = typename Vec16<T>::type;
       constexpr int VW = Vec16<T>::n;
       T hk[kMaxLocal];
 #pragma unroll
-      for (int k = 0; k < kMaxLocal; ++k) hk[k] = (k < s) ? T(hd[k]) : T(0);
-      const T alpha = T(hd[s]), beta = T(ss.beta);
-      const T* yv_p = p.y;
-      const T* v_p = vj;
+      for (int k = 0; k < kMaxLocal; ++k) hk[k] = (k < s) ? hd[k] : T(0);
+      const T alpha = hd[s], beta = cf.beta;
       T accb = T(0);
       const long nv = n / VW;
       const long tid = blockIdx.x * (long)kThreads + threadIdx.x, nthr = (long)G * kThreads;
@@ -230,8 +563,8 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
 #pragma unroll
         for (int k = 0; k < KG; ++k)
           if (k < s) kv[k] = reinterpret_cast<const V*>(p.K + (long)k * p.ldk)[iv];
-        const V yv = __ldcg(reinterpret_cast<const V*>(yv_p) + iv);
-        const V vv = __ldcg(reinterpret_cast<const V*>(v_p) + iv);
+        const V yv = __ldcg(reinterpret_cast<const V*>(p.y) + iv);
+        const V vv = __ldcg(reinterpret_cast<const V*>(vj) + iv);
         const V pv = __ldcg(reinterpret_cast<const V*>(vprev) + iv);
         const T* ya = reinterpret_cast<const T*>(&yv);
         const T* va = reinterpret_cast<const T*>(&vv);
@@ -262,114 +595,82 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
         reinterpret_cast<V*>(p.u)[iv] = uv;
       }
       for (long i = nv * VW + tid; i < n; i += nthr) {
-        T val = __ldcg(yv_p + i) - alpha * __ldcg(v_p + i) - beta * __ldcg(vprev + i);
+        T val = __ldcg(p.y + i) - alpha * __ldcg(vj + i) - beta * __ldcg(vprev + i);
         for (int k = 0; k < s; ++k) val -= hk[k] * p.K[(long)k * p.ldk + i];
         p.u[i] = val;
         accb += val * val;
       }
-      accb = warp_sum_w<T>(accb);
-      if (lane == 0) red[warp][0] = (double)accb;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int wv = 0; wv < kThreads / 32; ++wv) t += red[wv][0];
-        p.partB[blockIdx.x] = t;
-      }
+      store_norm_partial<T>(accb, red, partB);
     }
-    if (!grid_sync(bar, G, &ok_s)) { failed = true; break; }
-    // every CTA: ||u||^2 in a fixed order, then the same scalar step
-    double t = 0.0;
-    for (unsigned g = threadIdx.x; g < G; g += kThreads) t += __ldcg(p.partB + g);
-    t = warp_sum_d(t);
-    if (lane == 0) red[warp][0] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double unorm2 = 0.0;
-      for (int wv = 0; wv < kThreads / 32; ++wv) unorm2 += red[wv][0];
-      const double alpha_d = hd[s];
-      const double beta_d = ss.beta;
-      const double beta_next = sqrt(unorm2);
-      const double eps = ss.sn2 * beta_d;
-      const double dbar = ss.cs2 * beta_d;
-      const double delta = ss.cs1 * dbar + ss.sn1 * alpha_d;
-      const double gbar = -ss.sn1 * dbar + ss.cs1 * alpha_d;
-      const double gamma = hypot(gbar, beta_next);
-      if (!(gamma > 0.0) || !isfinite(gamma)) {
-        ss.breakdown = 1;
-        ss.stop = 1;
-        ss.dir_pending = 0;
-      } else {
-        const double cs = gbar / gamma, sn = beta_next / gamma;
-        const double tau = cs * ss.eta;
-        ss.eta = -sn * ss.eta;
-        const double ig = 1.0 / gamma;
-        for (int k = 0; k < s; ++k) {
-          const double hh = (hd[k] - delta * ss.h1[k] - eps * ss.h2[k]) * ig;
-          ss.z[k] -= tau * hh;
-          ss.h2[k] = ss.h1[k];
-          ss.h1[k] = hh;
-        }
-        const int it = ss.iters;
-        if (blockIdx.x == 0 && p.arec && it < p.rec_cap) {
-          p.arec[it] = alpha_d;
-          p.brec[it] = beta_next;
-        }
-        ss.delta = delta;
-        ss.eps = eps;
-        ss.inv_gamma = ig;
-        ss.tau = tau;
-        ss.inv_beta_next = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
-        ss.cs2 = ss.cs1;
-        ss.sn2 = ss.sn1;
-        ss.cs1 = cs;
-        ss.sn1 = sn;
-        ss.iters = it + 1;
-        ss.beta = beta_next;
-        ss.dir_pending = 1;
-        if (fabs(ss.eta) <= ss.tol_abs || beta_next == 0.0 || ss.iters >= ss.maxit) ss.stop = 1;
-      }
-    }
-    __syncthreads();
+    if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    scalar_step<T>(partB, G, hd, red, ss, cf, sc, p);
     ++j;
   }
   // the pending direction update was applied by the last phase A
-  if (blockIdx.x == 0 && !failed) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      ss.dir_pending = 0;
-      ss.cnt_a = ss.cnt_b = 0;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kWords; i += kThreads)
-      reinterpret_cast<unsigned*>(st)[i] = reinterpret_cast<const unsigned*>(&ss)[i];
-  }
+  if (blockIdx.x == 0 && !failed) store_state(st, ss);
+}
+
+struct Occ {
+  int sms = 0;
+  int per_sm = -1;
+  size_t smem = 0;
+};
+
+template <typename K>
+cudaError_t occupancy(K kernel, size_t smem, Occ* o) {
+  if (o->per_sm >= 0 && o->smem == smem) return cudaSuccess;
+  int dev = 0;
+  RK_TRY(cudaGetDevice(&dev));
+  RK_TRY(cudaDeviceGetAttribute(&o->sms, cudaDevAttrMultiProcessorCount, dev));
+  RK_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->per_sm, kernel, kThreads, smem));
+  o->smem = smem;
+  return cudaSuccess;
 }
 
 template <typename T, int R>
 cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const Taps& tp,
-                           GridBar* bar, int max_blocks, cudaStream_t s, int* launched_blocks) {
-  const size_t smem = (size_t)op_tile_smem_elems(R) * sizeof(T);
-  static int cached = 0;
-  RK_TRY(ensure_smem(k_mr_persist<T, R>, smem, &cached));
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    RK_TRY(cudaGetDevice(&dev));
-    RK_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    RK_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mr_persist<T, R>, kThreads, smem));
-  }
-  int G = per_sm * sms;
-  if (G > max_blocks) G = max_blocks;
-  if (G < 1) return cudaErrorCooperativeLaunchTooLarge;
+                           GridBar* bar, int s_alloc, cudaStream_t s, int* launched_blocks,
+                           int* resident) {
+  const int ntiles = mr_matvec_blocks(H, W);
   MinresState* a0 = st;
   MrP<T> a1 = p;
   int a2 = H, a3 = W;
   Taps a4 = tp;
   GridBar* a5 = bar;
+  // resident: one CTA per tile, all tiles co-resident
+  {
+    const int sa = s_alloc < 1 ? 1 : s_alloc;
+    const size_t smem = ((size_t)op_tile_smem_elems(R) + (size_t)sa * kTileH * kTileW) * sizeof(T);
+    static int cached = 0;
+    static Occ occ;
+    if (smem <= 227 * 1024 && ntiles <= kPersistMaxBlocks) {
+      RK_TRY(ensure_smem(k_mr_resident<T, R>, smem, &cached));
+      RK_TRY(occupancy(k_mr_resident<T, R>, smem, &occ));
+      if (ntiles <= occ.per_sm * occ.sms) {
+        int a6 = sa;
+        void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
+        RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_resident<T, R>, dim3(ntiles),
+                                           dim3(kThreads), args, smem, s));
+        *launched_blocks = ntiles;
+        *resident = 1;
+        return launched();
+      }
+    }
+  }
+  const size_t smem = (size_t)op_tile_smem_elems(R) * sizeof(T);
+  static int cached = 0;
+  static Occ occ;
+  RK_TRY(ensure_smem(k_mr_persist<T, R>, smem, &cached));
+  RK_TRY(occupancy(k_mr_persist<T, R>, smem, &occ));
+  int G = occ.per_sm * occ.sms;
+  if (G > ntiles) G = ntiles;
+  if (G > kPersistMaxBlocks) G = kPersistMaxBlocks;
+  if (G < 1) return cudaErrorCooperativeLaunchTooLarge;
   void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
   RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_persist<T, R>, dim3(G), dim3(kThreads), args,
                                      smem, s));
   *launched_blocks = G;
+  *resident = 0;
   return launched();
 }
 
@@ -377,13 +678,13 @@ cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const
 
 template <typename T>
 cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Taps& tp, GridBar* bar,
-                       int max_blocks, cudaStream_t s, int* launched_blocks) {
+                       int s_alloc, cudaStream_t s, int* launched_blocks, int* resident) {
   switch (tp.r) {
-    case 4: return launch_persist<T, 4>(st, p, H, W, tp, bar, max_blocks, s, launched_blocks);
-    case 6: return launch_persist<T, 6>(st, p, H, W, tp, bar, max_blocks, s, launched_blocks);
-    case 8: return launch_persist<T, 8>(st, p, H, W, tp, bar, max_blocks, s, launched_blocks);
-    case 10: return launch_persist<T, 10>(st, p, H, W, tp, bar, max_blocks, s, launched_blocks);
-    case 12: return launch_persist<T, 12>(st, p, H, W, tp, bar, max_blocks, s, launched_blocks);
+    case 4: return launch_persist<T, 4>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
+    case 6: return launch_persist<T, 6>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
+    case 8: return launch_persist<T, 8>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
+    case 10: return launch_persist<T, 10>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
+    case 12: return launch_persist<T, 12>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
     default: return cudaErrorNotSupported;
   }
 }
@@ -393,8 +694,8 @@ bool mr_persist_supported(int radius) {
 }
 
 template cudaError_t mr_persist<float>(MinresState*, const MrP<float>&, int, int, const Taps&,
-                                       GridBar*, int, cudaStream_t, int*);
+                                       GridBar*, int, cudaStream_t, int*, int*);
 template cudaError_t mr_persist<double>(MinresState*, const MrP<double>&, int, int, const Taps&,
-                                        GridBar*, int, cudaStream_t, int*);
+                                        GridBar*, int, cudaStream_t, int*, int*);
 
 }  // namespace rk

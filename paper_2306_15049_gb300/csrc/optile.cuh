@@ -164,10 +164,12 @@ __device__ __forceinline__ T ld_maybe_cg(const T* p) {
 // from it (row passes read the window with 16-byte shared loads; column
 // passes walk down one column), and no index needs a runtime division.
 // CG: stage with L2-only loads; tile_y / tile_x: the tile (default: the CTA's).
-template <typename T, int R, bool CG = false>
+// taps: 2R+1 values, read after the staging barrier (so a caller may fill a
+// shared-memory copy just before the call).
+template <typename T, int R, bool CG = false, typename TP = double>
 __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
                                              const T* __restrict__ w, int H, int W,
-                                             const double* taps, T* s0, T* s1, bool with_a,
+                                             const TP* taps, T* s0, T* s1, bool with_a,
                                              T* ax, T* ex, T* vc, int tile_y = -1,
                                              int tile_x = -1) {
   static_assert(R % 2 == 0 && R >= 2, "even radius");
@@ -180,9 +182,6 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
   const int i0 = (tile_y >= 0 ? tile_y : (int)blockIdx.y) * kTileH;
   const int j0 = (tile_x >= 0 ? tile_x : (int)blockIdx.x) * kTileW;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  T g[2 * R + 1];
-#pragma unroll
-  for (int k = 0; k <= 2 * R; ++k) g[k] = T(taps[k]);
 
   // stage scale * src with a halo of 2R (zero outside the image); every load of
   // the thread is issued before the first one is used
@@ -213,6 +212,9 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
     }
   }
   __syncthreads();
+  T g[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * R; ++k) g[k] = T(taps[k]);
 
   // E v at the owned pixels (column tx, rows 4 ty .. 4 ty + 3); the weights
   // (zero where the difference is absent) are loaded first
