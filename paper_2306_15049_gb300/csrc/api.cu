@@ -265,6 +265,7 @@ struct rs_problem {
   // persistent solve kernel (one cooperative launch per solve)
   bool use_persist = true;
   int last_resident = -1;   // kind of the last persistent launch (1 resident, 0 streaming)
+  bool use_coop_cgs = true; // CGS2 blocks as one cooperative launch
   double* partials_p = nullptr;
   GridBar* gbar = nullptr;
 
@@ -753,6 +754,39 @@ CgsCtx cgs_ctx(rs_problem* P, int ldr, double* Rk, double* Rfull, int ldrf, doub
   return c;
 }
 
+// CGS2 (with the context's drop rule and R) of candidates B[:, 0..ncand-1]
+// into Q, starting from an empty Q: one cooperative launch when it fits,
+// else column by column. in_place: Q and B are the same columns (a candidate
+// is overwritten only after it has been read); otherwise B is left alone by
+// the column path (each candidate goes through the scratch vector u).
+template <typename T>
+int cgs2_all(rs_problem* P, const CgsCtx& c, T* Q, T* B, int ncand, bool in_place) {
+  const long n = P->z.n, ld = P->z.ld;
+  cudaStream_t s = P->s;
+  bool done = false;
+  if (P->use_coop_cgs) CU(cgs2_block<T>(c, Q, ld, B, ld, ncand, 1, n, P->gbar, s, &done));
+  if (done) return RS_OK;
+  CU(cgs_reset(c, s));
+  for (int j = 0; j < ncand; ++j) {
+    T* b = B + (long)j * ld;
+    if (!in_place) {
+      CU(cudaMemcpyAsync(P->u, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      b = vp<T>(P->u);
+    }
+    CU(cgs2_column<T>(c, Q, ld, b, j, n, s));
+  }
+  return RS_OK;
+}
+
+// The error flag of the last cooperative launch's grid barrier (read after a
+// stream synchronisation that covers it).
+int coop_check(rs_problem* P) {
+  int err = 0;
+  RS(read_back(P, &err, &P->gbar->err, sizeof err));
+  if (err) return P->set_err(RS_ECUDA, "cooperative kernel: grid barrier timed out (code %d)", err);
+  return RS_OK;
+}
+
 // Algorithm "Stabilized U" on the ncand columns of Ut_raw (FP64), then the
 // images, K, R, the matrices of Eq. orthupdate and Eq. hq, and the Ritz
 // vectors of Algorithm "interior" at gamma_{J_L}, gamma_{J_R}.
@@ -763,11 +797,10 @@ int finish_principal_body(rs_problem* P, int ncand) {
   cudaStream_t s = P->s;
   // stabilize: CGS2 (in place, normalised R per candidate), SVD of R
   CgsCtx c = cgs_ctx(P, z.cmax, nullptr, P->Rfull, z.cmax, kStabDrop);
-  CU(cgs_reset(c, s));
-  for (int j = 0; j < ncand; ++j)
-    CU(cgs2_column<double>(c, P->Ut_raw, ld, P->Ut_raw + (long)j * ld, j, n, s));
+  RS(cgs2_all<double>(P, c, P->Ut_raw, P->Ut_raw, ncand, true));
   int nk = 0;
   RS(read_back(P, &nk, P->cnt, sizeof nk));
+  RS(coop_check(P));
   int ncn = 0;
   if (nk > 0) {
     k_transpose_r<<<32, 256, 0, s>>>(P->Rfull, z.cmax, nk, ncand, P->XT);
@@ -797,8 +830,8 @@ int finish_principal_body(rs_problem* P, int ncand) {
   CU(cudaMemcpyAsync(Kp, AU, (size_t)ncn * ld * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CU(axpby<T, T>(EU, gstar, Kp, 1.0, (long)ncn * ld, s));
   CgsCtx ck = cgs_ctx(P, ncn, P->Rp, nullptr, 0, 0.0);   // R with leading dimension n_c
-  CU(cgs_reset(ck, s));
-  for (int j = 0; j < ncn; ++j) CU(cgs2_column<T>(ck, Kp, ld, Kp + (long)j * ld, j, n, s));
+  RS(cgs2_all<T>(P, ck, Kp, Kp, ncn, true));
+  RS(coop_check(P));
   int nkk = 0;
   RS(read_back(P, &nkk, P->cnt, sizeof nkk));
   if (nkk != ncn) return P->set_err(RS_EBREAKDOWN, "(A + gamma_* E) U~ is rank deficient (%d of %d)", nkk, ncn);
@@ -1042,14 +1075,11 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
       P->mv_total += 1;
     }
     CgsCtx c = cgs_ctx(P, kMaxLocal, P->Rk, nullptr, 0, kLocalDrop);
-    CU(cgs_reset(c, s));
-    for (int j = 0; j < ncand; ++j) {
-      // candidate j's image is in Bc[:, j]; kept columns are compacted into Kl
-      CU(cudaMemcpyAsync(P->u, Bc + (long)j * ld, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-      CU(cgs2_column<T>(c, Kl, ld, vp<T>(P->u), j, n, s));
-    }
+    // candidate j's image is in Bc[:, j]; kept columns are compacted into Kl
+    RS(cgs2_all<T>(P, c, Kl, Bc, ncand, false));
     int sdim = 0;
     RS(read_back(P, &sdim, P->cnt, sizeof sdim));
+    RS(coop_check(P));
     sl.local_dim = sdim;
     phase_end(P, 3, ph0);
     // sweeps: sweep 0 from r0; in mixed precision further sweeps from the FP64 residual
@@ -1145,6 +1175,8 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // persistent cooperative kernel
   if (const char* g = std::getenv("RS_PERSIST")) P->use_persist = std::strcmp(g, "0") != 0;
   if (!mr_persist_supported(desc->radius)) P->use_persist = false;
+  // RS_COOP_CGS=0 runs CGS2 column by column (several launches per candidate)
+  if (const char* g = std::getenv("RS_COOP_CGS")) P->use_coop_cgs = std::strcmp(g, "0") != 0;
   P->gprev_nz.assign(desc->M, 0);
   Carver cv{(char*)workspace_dev};
   carve(P, cv);

@@ -257,6 +257,13 @@ cudaError_t cgs_reset(const CgsCtx& c, cudaStream_t s);
 template <typename T>
 cudaError_t cgs2_column(const CgsCtx& c, T* Q, long ldq, T* b, int cand_index, long n,
                         cudaStream_t s);
+// cgs2_column for candidates j = 0 .. ncand-1 (column j at B + j ldb, candidate
+// index j) in one cooperative launch; reset: start from count 0. *done = false
+// when the launch does not fit this device (nothing was queued). The grid
+// barrier's error flag (bar->err) marks a void result.
+template <typename T>
+cudaError_t cgs2_block(const CgsCtx& c, T* Q, long ldq, T* B, long ldb, int ncand, int reset, long n,
+                       GridBar* bar, cudaStream_t s, bool* done);
 
 }  // namespace rk
 

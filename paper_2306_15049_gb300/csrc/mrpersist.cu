@@ -24,6 +24,7 @@
 // grid barrier's wait is bounded in time: on a timeout it raises an error
 // flag, every CTA leaves, and the host reports the failure instead of hanging.
 #include "internal.cuh"
+#include "gridsync.cuh"
 #include "optile.cuh"
 
 namespace rk {
@@ -31,7 +32,6 @@ namespace {
 
 constexpr int kDots = kMaxLocal + 1;
 constexpr int kWarps = kThreads / 32;
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s, far beyond any phase
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -44,48 +44,6 @@ __device__ __forceinline__ T warp_sum_w(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Barrier number nb (1, 2, ...) of the launch over its G co-resident CTAs: a
-// monotonic arrival counter (zeroed by the host before the launch) that every
-// CTA waits to reach nb * G. Returns false if this CTA gave up (timeout, or
-// another CTA's error flag).
-__device__ bool grid_sync(GridBar* bar, unsigned long long target, int* ok_s) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();
-    atomicAdd(&bar->count, 1ull);
-    if (ld_acquire_u64(&bar->count) < target) {
-      const unsigned long long t0 = global_ns();
-      unsigned spins = 0;
-      while (ld_acquire_u64(&bar->count) < target) {
-        if ((++spins & 63u) == 0) {
-          if (*((volatile int*)&bar->err)) { ok = 0; break; }
-          if (global_ns() - t0 > kBarrierTimeoutNs) {
-            atomicExch(&bar->err, 1);
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    *ok_s = ok;
-  }
-  __syncthreads();
-  return *ok_s != 0;
 }
 
 // Reductions run in the vector type T: a float solve sums its partials in
