@@ -7,9 +7,11 @@ curvature), and x^(k, l_*) defines the next weights.
 
 Readings: the corner is the interior point of maximum signed Menger curvature
 of consecutive points ordered by increasing gamma (ties: smaller l); the next
-weights are the IRN/TV weights w = ((L x)^2 + beta^2)^(-1/2) and
-||D_k L x|| = ||w_k^(1/2) .* L x||. The outer stop rule of Section 8.2 (the
-same l_* three times running) is ``same_lstar_three``.
+weights are the IRN/TV weights w = ((L x)^2 + beta^2)^(-1/2) (rule "irn") or
+the paper's cumulative weights D_{k+1} = diag(1 - (|D_k L x| / ||D_k L x||_inf)^p) D_k,
+w = D_{k+1}^2 (rule "gazzola", Section 2.1), and ||D_k L x|| = ||w_k^(1/2) .* L x||.
+The outer stop rule of Section 8.2 (the same l_* three times running) is
+``same_lstar_three``.
 """
 from __future__ import annotations
 
@@ -17,7 +19,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from .operator import Operator, irn_weights
+from .operator import Operator, gazzola_weights, irn_weights
 from .recycle import Params, State, outer_step
 
 
@@ -54,12 +56,16 @@ def same_lstar_three(history: List[int]) -> bool:
 
 
 def run(op: Operator, b: np.ndarray, d: np.ndarray, gammas: np.ndarray, prm: Params,
-        K_steps: int, beta: float, weights: Optional[List[np.ndarray]] = None):
+        K_steps: int, beta: float, weights: Optional[List[np.ndarray]] = None,
+        rule: str = "irn", p_gazzola: float = 2.0):
     """Run K_steps outer steps from W_0 = I. ``weights`` (optional) gives the
-    weights of every step explicitly instead of the L-curve/IRN rule."""
+    weights of every step explicitly instead of the L-curve rule; otherwise
+    ``rule`` ("irn" or "gazzola") makes the next weights from x^(k, l_*). The
+    weights used at each step are returned in ``steps[k].extra["w"]``."""
     S = State()
     n = b.shape[0]
     w = np.ones(2 * n) if weights is None else weights[0]
+    D = np.ones(2 * n)
     steps, lstars = [], []
     for k in range(K_steps):
         res = outer_step(op, b, gammas, w, S, prm)
@@ -67,8 +73,15 @@ def run(op: Operator, b: np.ndarray, d: np.ndarray, gammas: np.ndarray, prm: Par
         ls = lcurve_corner(rho, eta)
         res.extra["lstar"] = ls
         res.extra["rho"], res.extra["eta"] = rho, eta
+        res.extra["w"] = w
         lstars.append(ls)
         steps.append(res)
         if k + 1 < K_steps:
-            w = weights[k + 1] if weights is not None else irn_weights(op, res.X[ls], beta)
+            if weights is not None:
+                w = weights[k + 1]
+            elif rule == "gazzola":
+                D = gazzola_weights(op, res.X[ls], D, p_gazzola)
+                w = D * D
+            else:
+                w = irn_weights(op, res.X[ls], beta)
     return steps, lstars

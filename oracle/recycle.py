@@ -64,12 +64,17 @@ class Params:
     tol: float
     maxit: int
     batched_local: bool = False
+    # initial guesses: "orthogonal" (Eq. orthupdate), "oblique" (Eq. obliqueupdate,
+    # anchor gamma_*), "oblique2" (Eq. updates, anchors gamma_{I_L}, gamma_{I_R})
+    guess: str = "orthogonal"
+    I_L: int = 0
+    I_R: int = 0
 
     @staticmethod
-    def from_workload(wl, batched_local: bool = False) -> "Params":
+    def from_workload(wl, batched_local: bool = False, guess: str = "orthogonal") -> "Params":
         return Params(wl.M, wl.I_split, wl.i1, wl.i2, wl.i_star, wl.l_c, wl.J_L, wl.J_R,
                       wl.p, wl.a_ritz, wl.b_ritz, wl.n_ritz_local, wl.vnew_cap, wl.tol,
-                      wl.maxit, batched_local)
+                      wl.maxit, batched_local, guess, wl.i_star, wl.l_c)
 
 
 @dataclasses.dataclass
@@ -202,6 +207,58 @@ def principal_guesses(Ut, AU, EU, b, gammas, gamma_star):
 
 
 # ---------------------------------------------------------------------------
+# Section 7: oblique-projection initial guesses
+# ---------------------------------------------------------------------------
+def oblique_anchor(Ut, AU, EU, b, gamma_a):
+    """(A + gamma_a E) U~ = K R, U = U~ R^{-1}; returns (K^T E U, K^T b, R), the
+    quantities Eq. obliqueupdate needs (no (E U)^T (E U))."""
+    K, R = np.linalg.qr(AU + gamma_a * EU)
+    EUi = np.linalg.solve(R.T, EU.T).T
+    return K.T @ EUi, K.T @ b, R
+
+
+def oblique_guesses(Ut, AU, EU, b, gammas, gamma_left, gamma_right=None, I_split=None):
+    """For every shift, q from K^T b = (I + d K^T E U) q with d = gamma_l - gamma_a
+    (Eq. obliqueupdate: the residual is made orthogonal to K, not to
+    K + d E U), x0 = U q, r0 = b - (A + gamma_l E) x0. With ``gamma_right`` the
+    two-anchor form of Eq. updates: shifts l <= I_split (1-based) use the anchor
+    gamma_left, the others gamma_right. Returns (C, X0, R0) as principal_guesses."""
+    nc = Ut.shape[1]
+    M_ = len(gammas)
+    n = Ut.shape[0]
+    if nc == 0:
+        return np.zeros((0, M_)), np.zeros((M_, n)), np.tile(b, (M_, 1))
+    anchors = [(gamma_left,) + oblique_anchor(Ut, AU, EU, b, gamma_left)]
+    if gamma_right is not None:
+        anchors.append((gamma_right,) + oblique_anchor(Ut, AU, EU, b, gamma_right))
+    C = np.zeros((nc, M_))
+    X0 = np.zeros((M_, n))
+    R0 = np.zeros((M_, n))
+    for l, gl in enumerate(gammas):
+        right = gamma_right is not None and (l + 1) > I_split
+        ga, KtEU, Ktb, R = anchors[1 if right else 0]
+        q = np.linalg.solve(np.eye(nc) + (gl - ga) * KtEU, Ktb)
+        c = np.linalg.solve(R, q)
+        C[:, l] = c
+        X0[l] = Ut @ c
+        R0[l] = b - (AU @ c + gl * (EU @ c))
+    return C, X0, R0
+
+
+def initial_guesses(Ut, AU, EU, b, gammas, prm: "Params"):
+    """The initial guesses that ``prm.guess`` selects (Sections 4.1 and 7)."""
+    gstar = gammas[prm.i_star - 1]
+    if prm.guess == "orthogonal":
+        return principal_guesses(Ut, AU, EU, b, gammas, gstar)
+    if prm.guess == "oblique":
+        return oblique_guesses(Ut, AU, EU, b, gammas, gstar)
+    if prm.guess == "oblique2":
+        return oblique_guesses(Ut, AU, EU, b, gammas, gammas[prm.I_L - 1], gammas[prm.I_R - 1],
+                               prm.I_split)
+    raise ValueError(f"unknown initial guess kind {prm.guess!r}")
+
+
+# ---------------------------------------------------------------------------
 # Algorithm "interior"
 # ---------------------------------------------------------------------------
 def interior_ritz(Ah: np.ndarray, Eh: np.ndarray, gamma: float, nJ: int) -> np.ndarray:
@@ -264,8 +321,7 @@ def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
     overhead += nc
 
     # -- initial guesses -------------------------------------------------
-    gstar = gammas[prm.i_star - 1]
-    C, X0, R0 = principal_guesses(Ut, AU, EU, b, gammas, gstar)
+    C, X0, R0 = initial_guesses(Ut, AU, EU, b, gammas, prm)
 
     # -- Ritz vectors of the projected systems ----------------------------
     Ah = Ut.T @ AU

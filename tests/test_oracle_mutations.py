@@ -113,3 +113,37 @@ def test_stabilize_without_threshold_is_caught(monkeypatch):
     real = orc.stabilize
     monkeypatch.setattr(tr, "stabilize", lambda Ut, p_max, ratio=1e10: real(Ut, p_max, ratio=1e300))
     _expect_fail(tr.test_stabilize_drops_near_dependent_columns_at_ratio_1e10)
+
+
+def test_oblique_guess_with_a_flipped_shift_difference_is_caught(monkeypatch):
+    import tests.test_oracle_oblique as tob
+    real = orc.oblique_guesses
+
+    def flipped(Ut, AU, EU, b, gammas, gl, gr=None, I_split=None):
+        # d = gamma_a - gamma_l instead of gamma_l - gamma_a
+        mirrored = [2 * gl - g for g in gammas]
+        C, _, _ = real(Ut, AU, EU, b, mirrored, gl)
+        X0 = (Ut @ C).T
+        R0 = np.stack([b - (AU @ C[:, l] + g * (EU @ C[:, l])) for l, g in enumerate(gammas)])
+        return C, X0, R0
+    monkeypatch.setattr(tob, "oblique_guesses", flipped)
+    _expect_fail(tob.test_oblique_residual_is_orthogonal_to_K_and_the_guess_lies_in_range_U)
+
+
+def test_oblique_guess_with_the_orthogonal_right_hand_side_is_caught(monkeypatch):
+    import tests.test_oracle_oblique as tob
+
+    def mixed_rhs(Ut, AU, EU, b, gammas, ga, gr=None, I_split=None):
+        K, R = np.linalg.qr(AU + ga * EU)
+        EUi = np.linalg.solve(R.T, EU.T).T
+        nc = Ut.shape[1]
+        C = np.zeros((nc, len(gammas)))
+        for l, g in enumerate(gammas):
+            d = g - ga
+            q = np.linalg.solve(np.eye(nc) + d * K.T @ EUi, K.T @ b + d * EUi.T @ b)
+            C[:, l] = np.linalg.solve(R, q)
+        X0 = (Ut @ C).T
+        R0 = np.stack([b - (AU @ C[:, l] + g * (EU @ C[:, l])) for l, g in enumerate(gammas)])
+        return C, X0, R0
+    monkeypatch.setattr(tob, "oblique_guesses", mixed_rhs)
+    _expect_fail(tob.test_oblique_residual_is_orthogonal_to_K_and_the_guess_lies_in_range_U)
