@@ -16,6 +16,8 @@ computes, written from the paper's text:
   "updatelocal", "updatelocalV2") and the per-shift solves of one outer step
   (Algorithm "Shifted Recycling Algorithm").
 * ``outer``     -- the L-curve corner and the reweighting outer loop.
+* ``adjoint``   -- adjoint solves and the gradients of a loss of the solutions
+  with respect to the shifts and the weights.
 
 It shares no code with the CUDA path. Its only shared dependency is the seeded
 input generator ``synth`` (which holds no arithmetic of the method).

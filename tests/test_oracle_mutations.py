@@ -147,3 +147,17 @@ def test_oblique_guess_with_the_orthogonal_right_hand_side_is_caught(monkeypatch
         return C, X0, R0
     monkeypatch.setattr(tob, "oblique_guesses", mixed_rhs)
     _expect_fail(tob.test_oblique_residual_is_orthogonal_to_K_and_the_guess_lies_in_range_U)
+
+
+def test_weight_gradient_without_the_shift_factor_is_caught(monkeypatch):
+    import oracle.adjoint as oa
+    import tests.test_oracle_adjoint as tad
+
+    def no_gamma(op, gammas, w, X, Lam):
+        dg, _ = oa.shift_and_weight_gradients(op, gammas, w, X, Lam)
+        dw = np.zeros_like(w)
+        for l in range(len(gammas)):
+            dw -= op.grad(Lam[l]) * op.grad(X[l])
+        return dg, dw
+    monkeypatch.setattr(tad, "shift_and_weight_gradients", no_gamma)
+    _expect_fail(tad.test_gradients_match_central_finite_differences)
