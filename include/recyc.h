@@ -54,6 +54,16 @@ typedef enum {
 
 typedef enum { RS_INIT = 0, RS_UPDATE = 1 } rs_recycle_mode;
 
+/* Initial guesses from the principal space U~ (Sections 4.1 and 7). */
+typedef enum {
+  RS_GUESS_ORTHOGONAL = 0, /* residual orthogonal to (A + gamma_l E) U~ (Eq. orthupdate):
+                              the least-squares optimum over Range U~ */
+  RS_GUESS_OBLIQUE = 1,    /* residual orthogonal to K of (A + gamma_* E) U~ = K R
+                              (Eq. obliqueupdate): no (E U)^T (E U) needed */
+  RS_GUESS_OBLIQUE2 = 2    /* two anchors gamma_{I_L}, gamma_{I_R}: shifts l <= I_split use
+                              K_L, the others K_R (Eq. updates); one more QR per step */
+} rs_guess;
+
 /* Problem description. Index fields are 1-based like the paper's index table
  * (Section 5.5): I_split (the left/right shift groups, Section 5.4), i1, i2
  * (the two systems seeding the principal space, Section 5.1), i_star (gamma_*
@@ -76,6 +86,8 @@ typedef struct {
   int I_split, i1, i2, i_star, l_c, J_L, J_R;
   int precision;           /* rs_precision */
   int batched_local;       /* 0: paper's chain g^(k,l-1); 1: g^(k-1,l-1) instead */
+  int guess;               /* rs_guess: how the initial guesses are projected */
+  int I_L, I_R;            /* RS_GUESS_OBLIQUE2 anchors (1-based): 1 <= I_L <= I_split < I_R <= M */
 } rs_problem_desc;
 
 /* Per-shift results of rs_solve_shifts. */
@@ -132,7 +144,7 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev,
                             void* workspace_dev, size_t workspace_bytes, void* stream,
                             rs_problem** out);
 
-/* Start the next outer step k with weights w (2n doubles, finite, > 0):
+/* Start the next outer step k with weights w (2n doubles, finite, >= 0):
  * E_k = L^T diag(w) L (Section 2.1). The previous weights are kept for the
  * right-hand side of Eq. delta. */
 rs_status rs_set_weights(rs_problem* prob, const double* w_dev);
@@ -162,6 +174,30 @@ rs_status rs_set_recycle_basis(rs_problem* prob, const double* U_dev, int ncols)
 rs_status rs_solve_shifts(rs_problem* prob, double* X_dev, rs_solve_stats* stats_host,
                           const int* iters_override_host);
 
+/* Adjoint solves for the gradient of a loss of the solutions: (A + gamma_l E_k)
+ * lambda_l = g_l for every shift, g_l = row l of G_dev (M x n doubles, e.g. the
+ * loss gradient with respect to x^(k,l)); lambda_l goes to row l of Lam_dev
+ * (M x n doubles, must not alias G_dev). The operator is symmetric, so the
+ * adjoint systems share the current step's recycle space: initial guesses by
+ * the orthogonal projection of Eq. orthupdate onto U~ (with the right-hand sides
+ * K^T g_l and U^T E_k g_l; no matvec), the Ritz bases W of Algorithm interior,
+ * and local spaces [W, g_adj^(l-1)] chained over the adjoint corrections (only
+ * [W] with batched_local). Each system to tol relative to ||g_l||; g_l = 0
+ * gives lambda_l = 0. Precision follows the problem (RS_MIXED: FP32 Krylov,
+ * FP64 refinement). The forward state handed to the next outer step is left
+ * unchanged. Call after rs_update_recycle (normally after rs_solve_shifts). */
+rs_status rs_solve_adjoint(rs_problem* prob, const double* G_dev, double* Lam_dev,
+                           rs_solve_stats* stats_host);
+
+/* Gradients of the loss from the solutions X_dev and adjoint solutions Lam_dev
+ * (M x n doubles each) with E_k = L^T diag(w_k) L (differentiating
+ * (A + gamma_l E_k) x_l = b):
+ *   dgamma_host[l] = d loss / d gamma_l = -(L lambda_l)^T diag(w_k) (L x_l)   (M, host),
+ *   dw_dev         = d loss / d w_k    = -sum_l gamma_l (L lambda_l) .* (L x_l)  (2n, device).
+ * Deterministic (fixed-order reductions). Synchronises the problem's stream. */
+rs_status rs_shift_gradients(rs_problem* prob, const double* X_dev, const double* Lam_dev,
+                             double* dgamma_host, double* dw_dev);
+
 /* Initial guesses of Eq. orthupdate for all shifts (after update_recycle):
  * X0_dev and R0_dev receive M x n doubles each (x0 and r0 = b - Op x0). */
 rs_status rs_initial_guesses(rs_problem* prob, double* X0_dev, double* R0_dev);
@@ -181,6 +217,18 @@ rs_status rs_apply_operator(rs_problem* prob, double gamma, const double* x_dev,
 /* Edge-preserving weights w = ((L x)^2 + beta^2)^(-1/2) (2n doubles) of the
  * solution x (n doubles): the IRN / smoothed-TV reweighting of Section 2.1. */
 rs_status rs_irn_weights(rs_problem* prob, const double* x_dev, double beta, double* w_dev);
+
+/* Cumulative edge weights of Section 2.1 (the paper's own reweighting, after
+ * Gazzola et al.): with q = d_prev .* L x (2n entries, [x-direction; y-direction]),
+ * D_new = (1 - (|q| / ||q||_inf)^p) .* d_prev and w = D_new .* D_new, the weight
+ * vector of E_{k+1} = L^T D_new^2 L to pass to rs_set_weights (entries in
+ * [0, d_prev^2]; pixels on the strongest edge get weight 0). If q = 0, D_new =
+ * d_prev. x: n doubles; d_prev, d_new, w: 2n doubles (device); d_new may alias
+ * d_prev, w may alias neither x nor d_prev. The paper leaves the exponent p
+ * unstated; it must be finite and > 0. D_0 = 1 (E_0 = L^T L). Synchronises the
+ * problem's stream. */
+rs_status rs_gazzola_weights(rs_problem* prob, const double* x_dev, const double* d_prev_dev,
+                             double p, double* d_new_dev, double* w_dev);
 
 /* L-curve of Section 2.2 for count solutions X (count x n doubles): writes
  * rho[l] = ||H x_l - d|| and eta[l] = ||w_k^(1/2) .* L x_l|| (host arrays of

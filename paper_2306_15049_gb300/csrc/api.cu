@@ -166,6 +166,11 @@ bool valid_desc(const rs_problem_desc* d, std::string* why) {
       !idx_ok(d->l_c) || !idx_ok(d->J_L) || !idx_ok(d->J_R))
     return fail("index fields must be in [1, M]");
   if (d->precision != RS_FP64 && d->precision != RS_MIXED) return fail("precision must be RS_FP64 or RS_MIXED");
+  if (d->guess != RS_GUESS_ORTHOGONAL && d->guess != RS_GUESS_OBLIQUE && d->guess != RS_GUESS_OBLIQUE2)
+    return fail("guess must be RS_GUESS_ORTHOGONAL, RS_GUESS_OBLIQUE or RS_GUESS_OBLIQUE2");
+  if (d->guess == RS_GUESS_OBLIQUE2 &&
+      !(d->I_L >= 1 && d->I_L <= d->I_split && d->I_split < d->I_R && d->I_R <= d->M))
+    return fail("two-anchor oblique guesses need 1 <= I_L <= I_split < I_R <= M");
   const long n = (long)d->height * d->width;
   if (n > (1L << 28)) return fail("image too large");
   const int cmax = std::max(2 + d->a_ritz + d->b_ritz, d->a_ritz + 1 + d->vnew_cap + d->M);
@@ -233,6 +238,15 @@ struct rs_problem {
   double *Rfull = nullptr, *XT = nullptr, *Vsv = nullptr, *sig = nullptr, *hdots = nullptr;
   double *coef = nullptr, *scal = nullptr, *Ktr = nullptr, *Rk = nullptr, *zc = nullptr;
   double *arec = nullptr, *brec = nullptr, *lc = nullptr;
+  // oblique guesses with two anchors (Eq. updates): per anchor R_a, K_a^T E U_a, K_a^T b
+  void* Kan = nullptr;
+  // adjoint solves: per-shift right-hand sides in the working precision, their
+  // corrections (the local-space chain), norms and projected guesses
+  void* Gadj = nullptr;
+  double *Cadj = nullptr, *CAadj = nullptr, *CEadj = nullptr, *Ktg = nullptr, *Etg = nullptr;
+  double *gnrm = nullptr;
+  double *Ran[2] = {nullptr, nullptr}, *Man[2] = {nullptr, nullptr}, *Kban[2] = {nullptr, nullptr};
+  double *G_KEan = nullptr, *Nscr = nullptr, *UtEbscr = nullptr;
   int *cnt = nullptr, *flag = nullptr, *kept = nullptr, *perm = nullptr, *status = nullptr;
   int *poll = nullptr, *ok = nullptr, *lstar = nullptr;
   MinresState* st = nullptr;
@@ -375,6 +389,24 @@ void carve(rs_problem* P, Carver& cv) {
   P->partials_a = cv.take<double>((size_t)mr_matvec_blocks(P->d.height, P->d.width) * (kMaxLocal + 1));
   P->partials_p = cv.take<double>((size_t)kPersistMaxBlocks * (kMaxLocal + 2));
   P->gbar = cv.take<GridBar>(1);
+  P->Gadj = vec((long)z.M * z.ld);
+  P->Cadj = cv.take<double>((size_t)z.p * z.M);
+  P->CAadj = cv.take<double>((size_t)z.p * z.M);
+  P->CEadj = cv.take<double>((size_t)z.p * z.M);
+  P->Ktg = cv.take<double>((size_t)z.p * z.M);
+  P->Etg = cv.take<double>((size_t)z.p * z.M);
+  P->gnrm = cv.take<double>((size_t)z.M + 2);
+  if (P->d.guess == RS_GUESS_OBLIQUE2) {
+    P->Kan = vec((long)z.p * z.ld);
+    for (int a = 0; a < 2; ++a) {
+      P->Ran[a] = cv.take<double>(pp);
+      P->Man[a] = cv.take<double>(pp);
+      P->Kban[a] = cv.take<double>(z.p);
+    }
+    P->G_KEan = cv.take<double>(pp);
+    P->Nscr = cv.take<double>(pp);
+    P->UtEbscr = cv.take<double>(z.p);
+  }
 }
 
 #define CU(...)                                                                         \
@@ -463,19 +495,24 @@ void phase_end(rs_problem* P, int ph, double t0) {
 }
 
 // FP64 true residual: r64 = b - (A + gamma E) x64; returns ||r|| / ||b|| on the host.
-int true_residual(rs_problem* P, double gamma, const double* x64, double* relres) {
+int true_residual(rs_problem* P, double gamma, const double* x64, double* relres,
+                  const double* rhs = nullptr, double rhs_norm = 0.0) {
+  if (!rhs) {
+    rhs = P->b;
+    rhs_norm = P->bnorm;
+  }
   const double t0 = phase_begin(P);
   const int slot = timed_begin(P);
   CU(op_apply<double>(x64, P->z.ld, 1, P->w64, P->y64, nullptr, P->z.ld, P->d.height, P->d.width,
                       P->tp, gamma, 0, P->s));
   timed_end(P, slot, 1, -1, P->z.n, 32.0 * P->z.n, (8.0 * (2 * P->tp.r + 1) + 10.0) * P->z.n);
-  CU(residual64(P->b, P->y64, P->r64, P->z.n, P->partials, P->s));
+  CU(residual64(rhs, P->y64, P->r64, P->z.n, P->partials, P->s));
   CU(reduce_partials(P->partials, P->z.G, 1, 1, P->scal + 8, P->s, nullptr, 0, nullptr));
   double r2 = 0.0;
   RS(read_back(P, &r2, P->scal + 8, sizeof r2));
   timed_flush(P, 0);
   phase_end(P, 5, t0);
-  *relres = std::sqrt(r2) / P->bnorm;
+  *relres = std::sqrt(r2) / rhs_norm;
   P->mv_total += 1;
   return RS_OK;
 }
@@ -845,13 +882,46 @@ int finish_principal_body(rs_problem* P, int ncand) {
   CU(gram<T>(Ut, ld, ncn, EU, ld, ncn, n, P->partials, P->Eh, s));
   PrincipalSmall ps{P->Rp, P->G_KE, P->G_EE, P->G_Eb, P->Mm, P->Nm, P->UtEb};
   CU(principal_small(ps, ncn, P->T1, s));
-  CU(principal_solves(P->Mm, P->Nm, P->Ktb, P->UtEb, P->Rp, ncn, P->gam, gstar, z.M, P->C, P->status, s));
+  if (P->d.guess == RS_GUESS_ORTHOGONAL) {
+    CU(principal_solves(P->Mm, P->Nm, P->Ktb, P->UtEb, P->Rp, ncn, P->gam, gstar, z.M, P->C, P->status, s));
+  } else if (P->d.guess == RS_GUESS_OBLIQUE) {
+    // Eq. obliqueupdate with the anchor gamma_*: K, R, K^T E U and K^T b as above
+    ObliqueAnchors an{{P->Mm, P->Mm}, {P->Ktb, P->Ktb}, {P->Rp, P->Rp}, {gstar, gstar}};
+    CU(oblique_solves(an, ncn, P->gam, z.M, z.M, P->C, P->status, s));
+  } else {
+    // Eq. updates: (A + gamma_a E) U~ = K_a R_a for a = I_L, I_R (no matvecs: from A U~, E U~)
+    T* Ka = vp<T>(P->Kan);
+    const double ga[2] = {P->gammas[P->d.I_L - 1], P->gammas[P->d.I_R - 1]};
+    for (int a = 0; a < 2; ++a) {
+      CU(cudaMemcpyAsync(Ka, AU, (size_t)ncn * ld * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      CU(axpby<T, T>(EU, ga[a], Ka, 1.0, (long)ncn * ld, s));
+      CgsCtx ca = cgs_ctx(P, ncn, P->Ran[a], nullptr, 0, 0.0);
+      RS(cgs2_all<T>(P, ca, Ka, Ka, ncn, true));
+      RS(coop_check(P));
+      int nka = 0;
+      RS(read_back(P, &nka, P->cnt, sizeof nka));
+      if (nka != ncn)
+        return P->set_err(RS_EBREAKDOWN, "(A + gamma_%d E) U~ is rank deficient (%d of %d)",
+                          a == 0 ? P->d.I_L : P->d.I_R, nka, ncn);
+      CU(gram<T>(Ka, ld, ncn, EU, ld, ncn, n, P->partials, P->G_KEan, s));
+      CU(gram<T>(Ka, ld, ncn, bT, ld, 1, n, P->partials, P->Kban[a], s));
+      PrincipalSmall pa{P->Ran[a], P->G_KEan, P->G_EE, P->G_Eb, P->Man[a], P->Nscr, P->UtEbscr};
+      CU(principal_small(pa, ncn, P->T1, s));
+    }
+    ObliqueAnchors an{{P->Man[0], P->Man[1]}, {P->Kban[0], P->Kban[1]}, {P->Ran[0], P->Ran[1]},
+                      {ga[0], ga[1]}};
+    CU(oblique_solves(an, ncn, P->gam, P->d.I_split, z.M, P->C, P->status, s));
+  }
   k_coef_neg<<<8, 256, 0, s>>>(P->C, P->gam, ncn, z.M, P->CA, P->CE);
   CU(launched());
   std::vector<int> stt(z.M);
   RS(read_back(P, stt.data(), P->status, z.M * sizeof(int)));
   for (int l = 0; l < z.M; ++l)
-    if (stt[l]) return P->set_err(RS_EBREAKDOWN, "orthupdate matrix of shift %d is not SPD", l + 1);
+    if (stt[l])
+      return P->set_err(RS_EBREAKDOWN, P->d.guess == RS_GUESS_ORTHOGONAL
+                                           ? "orthupdate matrix of shift %d is not SPD"
+                                           : "oblique update matrix of shift %d is singular",
+                        l + 1);
   // Ritz vectors of the projected systems (Algorithm interior)
   const int J = std::min(z.J, ncn);
   for (int grp = 0; grp < 2; ++grp) {
@@ -986,41 +1056,61 @@ int update_principal(rs_problem* P) {
 // ---------------------------------------------------------------------------
 // the shifted solves of one outer step
 // ---------------------------------------------------------------------------
+// The shifted solves of the current step, l = 1..M in order. Forward solves
+// (G == nullptr) have the right-hand side b and feed the next outer step
+// (x^(k,l), g^(k,l)); adjoint solves (G: M x n, row l = g_l, norms gnorm) reuse
+// the same principal space and Ritz bases, chain their own corrections in the
+// local spaces [W, g_adj^(l-1)] and leave the forward state alone.
 template <typename T>
-int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) {
+int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
+              const double* G = nullptr, const double* gnorm = nullptr) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
   const int nc = P->nc;
   const int J = std::min(z.J, nc);
+  const bool adj = G != nullptr;
   T* Ut = vp<T>(P->Ut);
   T* Bc = vp<T>(P->Bc);
   T* Kl = vp<T>(P->Kl);
   T* wT = vp<T>(P->mixed ? P->wT : (void*)P->w64);
-  const double tol_abs = P->d.tol * P->bnorm;
+  const double* Cc = adj ? P->Cadj : P->C;
+  const double* CAc = adj ? P->CAadj : P->CA;
+  const double* CEc = adj ? P->CEadj : P->CE;
+  T* Gbuf = vp<T>(adj ? P->Gadj : P->Gcur);
   int any_noconv = 0;
   std::vector<char> gnz(z.M, 0);
   for (int l = 0; l < z.M; ++l) {
     const double gl = P->gammas[l];
+    const double* rhs = adj ? G + (long)l * n : P->b;
+    const double rnorm = adj ? gnorm[l] : P->bnorm;
+    const double tol_abs = P->d.tol * rnorm;
     double ph0 = phase_begin(P);
     rs_solve_stats sl{};
     sl.sweeps = 0;
     double* x = X + (long)l * n;    // caller's X is dense M x n
-    // initial guess x0 = U~ c_l and r0 = b - A U~ c_l - gamma_l E U~ c_l
-    CU(gemm_ts<T, double>(Ut, ld, nc, P->C + (long)l * nc, nc, 1, 0.0, x, n, n, s));
-    CU(cudaMemcpyAsync(P->r64, P->b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CU(gemm_ts<T, double>(vp<T>(P->AU), ld, nc, P->CA + (long)l * nc, nc, 1, 1.0, P->r64, ld, n, s));
-    CU(gemm_ts<T, double>(vp<T>(P->EU), ld, nc, P->CE + (long)l * nc, nc, 1, 1.0, P->r64, ld, n, s));
+    T* gl_buf = Gbuf + (long)l * ld;
+    if (adj && !(rnorm > 0.0)) {    // g_l = 0: lambda_l = 0
+      CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+      CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
+      phase_end(P, 3, ph0);
+      if (stats) stats[l] = sl;
+      continue;
+    }
+    // initial guess x0 = U~ c_l and r0 = rhs - A U~ c_l - gamma_l E U~ c_l
+    CU(gemm_ts<T, double>(Ut, ld, nc, Cc + (long)l * nc, nc, 1, 0.0, x, n, n, s));
+    CU(cudaMemcpyAsync(P->r64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(gemm_ts<T, double>(vp<T>(P->AU), ld, nc, CAc + (long)l * nc, nc, 1, 1.0, P->r64, ld, n, s));
+    CU(gemm_ts<T, double>(vp<T>(P->EU), ld, nc, CEc + (long)l * nc, nc, 1, 1.0, P->r64, ld, n, s));
     CU(norm2_partials<double>(P->r64, n, P->partials, s));
     CU(reduce_partials(P->partials, z.G, 1, 1, P->scal + 10, s, nullptr, 0, nullptr));
     double r02 = 0.0;
     RS(read_back(P, &r02, P->scal + 10, sizeof r02));
-    sl.relres0 = std::sqrt(r02) / P->bnorm;
+    sl.relres0 = std::sqrt(r02) / rnorm;
     const int forced = over ? over[l] : -1;
-    T* gl_buf = vp<T>(P->Gcur) + (long)l * ld;
     if (forced < 0 && sl.relres0 <= P->d.tol) {
       phase_end(P, 3, ph0);
-      RS(true_residual(P, gl, x, &sl.relres_true));
+      RS(true_residual(P, gl, x, &sl.relres_true, rhs, rnorm));
       sl.matvecs = 1;
       // FP64 mode: the image-based r0 is exact to rounding, the guess is the
       // solution. Mixed precision: r0 came from FP32 images, so the FP64
@@ -1033,7 +1123,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
         continue;
       }
       sl.relres0 = sl.relres_true;
-      r02 = sl.relres_true * sl.relres_true * P->bnorm * P->bnorm;
+      r02 = sl.relres_true * sl.relres_true * rnorm * rnorm;
       ph0 = phase_begin(P);
     }
     // local space [W, g^(k-1,l), g^(k,l-1)] and its image
@@ -1048,11 +1138,15 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
     }
     const T* gold = nullptr;
     const T* gnew = nullptr;
-    if (P->have_prev && P->gprev_nz[l]) gold = vp<T>(P->Gprev) + (long)l * ld;
-    if (P->d.batched_local) {
-      if (P->have_prev && l >= 1 && P->gprev_nz[l - 1]) gnew = vp<T>(P->Gprev) + (long)(l - 1) * ld;
+    if (adj) {
+      if (!P->d.batched_local && l >= 1 && gnz[l - 1]) gnew = Gbuf + (long)(l - 1) * ld;
     } else {
-      if (l >= 1 && gnz[l - 1]) gnew = vp<T>(P->Gcur) + (long)(l - 1) * ld;
+      if (P->have_prev && P->gprev_nz[l]) gold = vp<T>(P->Gprev) + (long)l * ld;
+      if (P->d.batched_local) {
+        if (P->have_prev && l >= 1 && P->gprev_nz[l - 1]) gnew = vp<T>(P->Gprev) + (long)(l - 1) * ld;
+      } else {
+        if (l >= 1 && gnz[l - 1]) gnew = Gbuf + (long)(l - 1) * ld;
+      }
     }
     if (gold && gnew) {
       // angle rule: keep only g^(k,l-1) when |cos| > 0.99
@@ -1095,7 +1189,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
                        sdim));
       sl.iters += it;
       sl.matvecs += it;
-      sl.relres_est = eta / P->bnorm;
+      sl.relres_est = eta / rnorm;
       sl.sweeps = sw + 1;
       if (sdim > 0) {
         CU(tri_solve_upper(P->Rk, kMaxLocal, P->cnt, P->st->z, P->zc, s));
@@ -1105,11 +1199,11 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
       if (sw == 0) CU(cudaMemcpyAsync(gl_buf, P->xm, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
       else CU(axpby<T, T>(vp<T>(P->xm), 1.0, gl_buf, 1.0, n, s));
       phase_end(P, 4, ph1);
-      RS(true_residual(P, gl, x, &sl.relres_true));
+      RS(true_residual(P, gl, x, &sl.relres_true, rhs, rnorm));
       sl.matvecs += 1;
       if (!P->mixed || sl.relres_true <= P->d.tol || forced >= 0) break;
       CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
-      inner_tol = std::max(0.5 * tol_abs, kInnerRho * sl.relres_true * P->bnorm);
+      inner_tol = std::max(0.5 * tol_abs, kInnerRho * sl.relres_true * rnorm);
       if (sw + 1 == max_sw) break;
     }
     gnz[l] = 1;
@@ -1118,6 +1212,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
     if (sl.status == RS_ENOCONV) any_noconv = 1;
     if (stats) stats[l] = sl;
   }
+  if (adj) return any_noconv ? P->set_err(RS_ENOCONV, "an adjoint shift reached maxit") : RS_OK;
   // hand over to the next outer step
   CU(cudaMemcpy2DAsync(P->Xprev, ld * sizeof(double), X, n * sizeof(double), n * sizeof(double), z.M,
                        cudaMemcpyDeviceToDevice, s));
@@ -1128,6 +1223,45 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over) 
 }
 
 }  // namespace
+
+// Adjoint solves (A + gamma_l E_k) lambda_l = g_l on the current step's recycle
+// space: orthogonal-projection initial guesses (the matrices of Eq. orthupdate
+// with the right-hand sides K^T g_l and U^T E g_l, from A U~ and E U~: no matvec),
+// then the shifted solves of solve_all with per-shift right-hand sides.
+template <typename T>
+int adjoint_all(rs_problem* P, const double* G, double* Lam, rs_solve_stats* stats) {
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  cudaStream_t s = P->s;
+  const int nc = P->nc, M = z.M;
+  T* Ga = vp<T>(P->Gadj);
+  for (int l = 0; l < M; ++l) {
+    const double* g = G + (long)l * n;
+    if (P->mixed) CU((convert<double, float>(g, (float*)Ga + (long)l * ld, n, s)));
+    else CU(cudaMemcpyAsync(Ga + (long)l * ld, g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(norm2_partials<double>(g, n, P->partials, s));
+    CU(reduce_partials(P->partials, z.G, 1, 1, P->gnrm + l, s, nullptr, 0, nullptr));
+  }
+  std::vector<double> gn(M);
+  RS(read_back(P, gn.data(), P->gnrm, M * sizeof(double)));
+  for (int l = 0; l < M; ++l) {
+    if (!std::isfinite(gn[l])) return P->set_err(RS_EINVAL, "right-hand side %d is not finite", l + 1);
+    gn[l] = std::sqrt(gn[l]);
+  }
+  const double gstar = P->gammas[P->d.i_star - 1];
+  CU(gram<T>(vp<T>(P->Kp), ld, nc, Ga, ld, M, n, P->partials, P->Ktg, s));
+  CU(gram<T>(vp<T>(P->EU), ld, nc, Ga, ld, M, n, P->partials, P->Etg, s));
+  // CAadj holds U^T E g_l until k_coef_neg overwrites it
+  CU(principal_solves_rhs(P->Mm, P->Nm, P->Ktg, P->Etg, P->CAadj, P->Rp, nc, P->gam, gstar, M,
+                          P->Cadj, P->status, s));
+  k_coef_neg<<<8, 256, 0, s>>>(P->Cadj, P->gam, nc, M, P->CAadj, P->CEadj);
+  CU(launched());
+  std::vector<int> stt(M);
+  RS(read_back(P, stt.data(), P->status, M * sizeof(int)));
+  for (int l = 0; l < M; ++l)
+    if (stt[l]) return P->set_err(RS_EBREAKDOWN, "orthupdate matrix of shift %d is not SPD", l + 1);
+  return solve_all<T>(P, Lam, stats, nullptr, G, gn.data());
+}
 
 // ===========================================================================
 // C ABI
@@ -1220,10 +1354,10 @@ rs_status rs_set_weights(rs_problem* P, const double* w_dev) {
   if (!P) return RS_EINVAL;
   if (!w_dev) return (rs_status)P->set_err(RS_EINVAL, "w_dev is NULL");
   const long n = P->z.n;
-  CU(check_finite(w_dev, 2 * n, 1, P->ok, P->s));
+  CU(check_finite(w_dev, 2 * n, 2, P->ok, P->s));
   int okh = 0;
   if (read_back(P, &okh, P->ok, sizeof okh)) return RS_ECUDA;
-  if (!okh) return (rs_status)P->set_err(RS_EINVAL, "weights must be finite and > 0");
+  if (!okh) return (rs_status)P->set_err(RS_EINVAL, "weights must be finite and >= 0");
   if (P->k >= 0) CU(cudaMemcpyAsync(P->wprev64, P->w64, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
   CU(cudaMemcpyAsync(P->w64, w_dev, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
   if (P->mixed) CU((convert<double, float>(P->w64, (float*)P->wT, 2 * n, P->s)));
@@ -1269,6 +1403,33 @@ rs_status rs_solve_shifts(rs_problem* P, double* X_dev, rs_solve_stats* stats_ho
       if (iters_override_host[l] < 0) return (rs_status)P->set_err(RS_EINVAL, "negative iteration override");
   if (P->mixed) return (rs_status)solve_all<float>(P, X_dev, stats_host, iters_override_host);
   return (rs_status)solve_all<double>(P, X_dev, stats_host, iters_override_host);
+}
+
+rs_status rs_solve_adjoint(rs_problem* P, const double* G_dev, double* Lam_dev,
+                           rs_solve_stats* stats_host) {
+  if (!P) return RS_EINVAL;
+  if (!P->have_recycle) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_update_recycle first");
+  if (!G_dev || !Lam_dev) return (rs_status)P->set_err(RS_EINVAL, "G_dev / Lam_dev is NULL");
+  if (G_dev == Lam_dev) return (rs_status)P->set_err(RS_EINVAL, "Lam_dev must not alias G_dev");
+  if (P->mixed) return (rs_status)adjoint_all<float>(P, G_dev, Lam_dev, stats_host);
+  return (rs_status)adjoint_all<double>(P, G_dev, Lam_dev, stats_host);
+}
+
+rs_status rs_shift_gradients(rs_problem* P, const double* X_dev, const double* Lam_dev,
+                             double* dgamma_host, double* dw_dev) {
+  if (!P) return RS_EINVAL;
+  if (P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  if (!X_dev || !Lam_dev || !dgamma_host || !dw_dev)
+    return (rs_status)P->set_err(RS_EINVAL, "NULL argument");
+  const int M = P->z.M, H = P->d.height, W = P->d.width;
+  cudaStream_t s = P->s;
+  CU(weight_gradient(X_dev, Lam_dev, P->gam, M, H, W, dw_dev, s));
+  CU(shift_gradient_partials(X_dev, Lam_dev, P->w64, M, H, W, P->partials, P->z.G, s));
+  CU(reduce_partials(P->partials, P->z.G, M, M, P->gnrm, s, nullptr, 0, nullptr));
+  std::vector<double> h(M);
+  if (read_back(P, h.data(), P->gnrm, M * sizeof(double))) return RS_ECUDA;
+  for (int l = 0; l < M; ++l) dgamma_host[l] = -h[l];
+  return RS_OK;
 }
 
 rs_status rs_initial_guesses(rs_problem* P, double* X0_dev, double* R0_dev) {
@@ -1336,6 +1497,18 @@ rs_status rs_irn_weights(rs_problem* P, const double* x_dev, double beta, double
   if (!P) return RS_EINVAL;
   if (!x_dev || !w_dev || !(beta > 0.0)) return (rs_status)P->set_err(RS_EINVAL, "need x, w and beta > 0");
   CU(irn_weights(x_dev, beta, w_dev, P->d.height, P->d.width, P->s));
+  CU(cudaStreamSynchronize(P->s));
+  return RS_OK;
+}
+
+rs_status rs_gazzola_weights(rs_problem* P, const double* x_dev, const double* d_prev_dev, double p,
+                             double* d_new_dev, double* w_dev) {
+  if (!P) return RS_EINVAL;
+  if (!x_dev || !d_prev_dev || !d_new_dev || !w_dev || !(p > 0.0) || !std::isfinite(p))
+    return (rs_status)P->set_err(RS_EINVAL, "need x, d_prev, d_new, w and a finite p > 0");
+  if ((const double*)w_dev == d_prev_dev || (const double*)w_dev == x_dev)
+    return (rs_status)P->set_err(RS_EINVAL, "w must not alias x or d_prev");
+  CU(gazzola_weights(x_dev, d_prev_dev, p, d_new_dev, w_dev, P->d.height, P->d.width, P->partials, P->s));
   CU(cudaStreamSynchronize(P->s));
   return RS_OK;
 }

@@ -269,11 +269,12 @@ k_residual64(const double* __restrict__ b, const double* __restrict__ y, double*
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
-__global__ void k_check_finite(const double* __restrict__ x, long n, int positive_only, int* ok) {
+// sign: 0 finite, 1 finite and > 0, 2 finite and >= 0
+__global__ void k_check_finite(const double* __restrict__ x, long n, int sign, int* ok) {
   int bad = 0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const double v = x[i];
-    if (!isfinite(v) || (positive_only && !(v > 0.0))) bad = 1;
+    if (!isfinite(v) || (sign == 1 && !(v > 0.0)) || (sign == 2 && !(v >= 0.0))) bad = 1;
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicAnd(ok, 0);
 }
@@ -376,10 +377,10 @@ cudaError_t residual64(const double* b, const double* y, double* r, long n, doub
   return launched();
 }
 
-cudaError_t check_finite(const double* x, long n, int positive_only, int* ok_dev, cudaStream_t s) {
+cudaError_t check_finite(const double* x, long n, int sign, int* ok_dev, cudaStream_t s) {
   const int one = 1;
   RK_TRY(cudaMemcpyAsync(ok_dev, &one, sizeof(int), cudaMemcpyHostToDevice, s));
-  k_check_finite<<<ew_grid(n), kThreads, 0, s>>>(x, n, positive_only, ok_dev);
+  k_check_finite<<<ew_grid(n), kThreads, 0, s>>>(x, n, sign, ok_dev);
   return launched();
 }
 

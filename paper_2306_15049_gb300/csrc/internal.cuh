@@ -44,6 +44,19 @@ cudaError_t blur_apply(const double* x, double* y, int H, int W, const Taps& tp,
                        cudaStream_t s);
 // w = ((L x)^2 + beta^2)^(-1/2) over 2n entries.
 cudaError_t irn_weights(const double* x, double beta, double* w, int H, int W, cudaStream_t s);
+// Cumulative weights of Section 2.1: D_new = (1 - (|q|/||q||_inf)^p) .* d_prev,
+// q = d_prev .* L x, and w = D_new^2 (2n doubles each; dnew may alias dprev).
+// partials: red_grid(H * W) doubles.
+// Gradients of a loss of the solutions x_l (rows of X, M x n) from the adjoint
+// solutions lambda_l (rows of Lam): dw = -sum_l gamma_l (L lambda_l) .* (L x_l)
+// (2n) and partials[g * M + l] = CTA g's share of (L lambda_l)^T diag(w) (L x_l)
+// over G CTAs (reduce with reduce_partials(partials, G, M, M, ...), then negate).
+cudaError_t weight_gradient(const double* X, const double* Lam, const double* gammas, int M, int H,
+                            int W, double* dw, cudaStream_t s);
+cudaError_t shift_gradient_partials(const double* X, const double* Lam, const double* w, int M,
+                                    int H, int W, double* partials, int G, cudaStream_t s);
+cudaError_t gazzola_weights(const double* x, const double* dprev, double p, double* dnew, double* w,
+                            int H, int W, double* partials, cudaStream_t s);
 // partials[g] = sum over CTA g of w .* (L x)^2 (for the L-curve seminorm).
 cudaError_t wgrad_norm2_partials(const double* x, const double* w, int H, int W, double* partials,
                                  int G, cudaStream_t s);
@@ -97,7 +110,8 @@ template <typename T>
 cudaError_t gather_axpy(const PtrList& cand, const int* kept_idx, const int* cnt_dev,
                         const double* coef, T* y, long n, cudaStream_t s);
 // *ok_dev = 1 if every entry is finite (and > 0 with positive_only), else 0.
-cudaError_t check_finite(const double* x, long n, int positive_only, int* ok_dev, cudaStream_t s);
+// sign: 0 finite, 1 finite and > 0, 2 finite and >= 0; *ok_dev = 0 if any entry fails
+cudaError_t check_finite(const double* x, long n, int sign, int* ok_dev, cudaStream_t s);
 
 // ---------------------------------------------------------------- dense.cu
 // One-sided Jacobi on the columns of X (m x nc, ld ldx, in place):
@@ -125,6 +139,27 @@ cudaError_t principal_small(const PrincipalSmall& ps, int nc, double* T1, cudaSt
 cudaError_t principal_solves(const double* Mm, const double* N, const double* Ktb,
                              const double* UtEb, const double* R, int nc, const double* gammas,
                              double gstar, int M, double* C, int* status, cudaStream_t s);
+// The one or two anchors of the oblique initial guesses (Section 7): for
+// anchor a, (A + gamma[a] E) U~ = K_a R[a], Mm[a] = K_a^T E U_a (nc x nc),
+// Ktb[a] = K_a^T b.
+struct ObliqueAnchors {
+  const double* Mm[2];
+  const double* Ktb[2];
+  const double* R[2];
+  double gamma[2];
+};
+// One CTA per shift l: (I + d Mm[a]) q = Ktb[a] with a = (l < split ? 0 : 1),
+// d = gammas[l] - gamma[a] (LU, partial pivoting); C[:, l] = R[a]^{-1} q;
+// status[l] = 1 on a zero pivot.
+cudaError_t oblique_solves(const ObliqueAnchors& an, int nc, const double* gammas, int split, int M,
+                           double* C, int* status, cudaStream_t s);
+// The same per-shift Cholesky solves with a right-hand side per shift:
+// Ktg (nc x M) = K^T g_l, Etg (nc x M) = (E U~)^T g_l; UtEg (nc x M, out) =
+// R^{-T} Etg; (I + d (M + M^T) + d^2 N) q = Ktg_l + d UtEg_l, C[:, l] = R^{-1} q.
+cudaError_t principal_solves_rhs(const double* Mm, const double* N, const double* Ktg,
+                                 const double* Etg, double* UtEg, const double* R, int nc,
+                                 const double* gammas, double gstar, int M, double* C, int* status,
+                                 cudaStream_t s);
 // out = R^{-1} z for the leading cnt x cnt block of an upper-triangular R.
 cudaError_t tri_solve_upper(const double* R, int ldr, const int* cnt_dev, const double* z,
                             double* out, cudaStream_t s);
@@ -203,7 +238,8 @@ int mr_matvec_blocks(int H, int W);
 struct GridBar {
   unsigned long long count;   // arrivals so far (barrier b completes at b x CTAs)
   int err;                    // 1: a CTA's wait ran out of time; 2: local space wider
-                              // than the launch's shared memory (the solve is void)
+                              // than the launch's shared memory (the solve is void);
+                              // 3: a wait for neighbouring tiles ran out of time
   int pad;
 };
 constexpr int kPersistMaxBlocks = 152 * 8;
@@ -230,7 +266,13 @@ struct MrP {
   double* brec;
   int rec_cap;
   int j0;              // first step of this launch
+  // pipelined resident kernel: per-step partial sums, double-buffered by step
+  // parity (2 x kPipeSlots x kPersistMaxBlocks entries of T), and per-tile
+  // progress flags (kPersistMaxBlocks ints, zero at launch)
+  double* partP;
+  int* tflags;
 };
+constexpr int kPipeSlots = kMaxLocal + 2;   // K^T y~ (s), u^T y~, u^T u
 // One launch runs the solve to its stop. s_alloc: the widest local space the
 // resident kernel must hold in shared memory. resident (out): 1 if the
 // one-CTA-per-tile kernel ran, 0 for the streaming one.

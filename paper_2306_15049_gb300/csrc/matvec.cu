@@ -108,6 +108,117 @@ __global__ void k_irn_weights(const double* __restrict__ x, double beta, double*
   }
 }
 
+// Cumulative weights of Section 2.1 (the paper's own reweighting), step 1:
+// the block's maximum of |q| over both gradient directions, q = d_prev .* L x.
+__global__ void __launch_bounds__(kThreads)
+k_gazzola_max(const double* __restrict__ x, const double* __restrict__ dprev, int H, int W,
+              double* __restrict__ partials) {
+  __shared__ double sh[kThreads / 32];
+  const long n = (long)H * W;
+  double m = 0.0;
+  for (long idx = blockIdx.x * (long)kThreads + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * kThreads) {
+    const int i = (int)(idx / W), j = (int)(idx - (long)i * W);
+    const double qx = (j < W - 1) ? dprev[idx] * (x[idx + 1] - x[idx]) : 0.0;
+    const double qy = (i < H - 1) ? dprev[n + idx] * (x[idx + W] - x[idx]) : 0.0;
+    m = fmax(m, fmax(fabs(qx), fabs(qy)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t = fmax(t, sh[k]);
+    partials[blockIdx.x] = t;
+  }
+}
+
+// Step 2: ||q||_inf from the G block maxima (exact in any order), then
+// D_new = (1 - (|q| / ||q||_inf)^p) .* d_prev and w = D_new^2 (the weights of
+// E = L^T D_new^2 L). Each entry reads and writes only its own index, so
+// dnew may alias dprev.
+__global__ void __launch_bounds__(kThreads)
+k_gazzola_apply(const double* __restrict__ x, const double* dprev, double p, int H, int W,
+                const double* __restrict__ partials, int G, double* dnew, double* __restrict__ w) {
+  __shared__ double qmax_s;
+  if (threadIdx.x < 32) {
+    double m = 0.0;
+    for (int g = threadIdx.x; g < G; g += 32) m = fmax(m, partials[g]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) qmax_s = m;
+  }
+  __syncthreads();
+  const double qmax = qmax_s;
+  const long n = (long)H * W;
+  for (long idx = blockIdx.x * (long)kThreads + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * kThreads) {
+    const int i = (int)(idx / W), j = (int)(idx - (long)i * W);
+    const double dx = dprev[idx], dy = dprev[n + idx];
+    const double qx = (j < W - 1) ? dx * (x[idx + 1] - x[idx]) : 0.0;
+    const double qy = (i < H - 1) ? dy * (x[idx + W] - x[idx]) : 0.0;
+    const double rx = qmax > 0.0 ? fabs(qx) / qmax : 0.0;
+    const double ry = qmax > 0.0 ? fabs(qy) / qmax : 0.0;
+    const double nx = (1.0 - pow(rx, p)) * dx, ny = (1.0 - pow(ry, p)) * dy;
+    dnew[idx] = nx;
+    dnew[n + idx] = ny;
+    w[idx] = nx * nx;
+    w[n + idx] = ny * ny;
+  }
+}
+
+// dw = -sum_l gamma_l (L lambda_l) .* (L x_l): pixel idx owns entries idx
+// (x-direction) and n + idx (y-direction); the sum over l runs in order.
+__global__ void __launch_bounds__(kThreads)
+k_weight_grad(const double* __restrict__ X, const double* __restrict__ Lam,
+              const double* __restrict__ gam, int M, int H, int W, double* __restrict__ dw) {
+  const long n = (long)H * W;
+  for (long idx = blockIdx.x * (long)kThreads + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * kThreads) {
+    const int i = (int)(idx / W), j = (int)(idx - (long)i * W);
+    double ax = 0.0, ay = 0.0;
+    for (int l = 0; l < M; ++l) {
+      const double* x = X + (long)l * n;
+      const double* lam = Lam + (long)l * n;
+      const double g = gam[l];
+      if (j < W - 1) ax += g * (lam[idx + 1] - lam[idx]) * (x[idx + 1] - x[idx]);
+      if (i < H - 1) ay += g * (lam[idx + W] - lam[idx]) * (x[idx + W] - x[idx]);
+    }
+    dw[idx] = -ax;
+    dw[n + idx] = -ay;
+  }
+}
+
+// partials[blockIdx.x * M + l] = this CTA's share of (L lambda_l)^T diag(w) (L x_l),
+// l = blockIdx.y.
+__global__ void __launch_bounds__(kThreads)
+k_shift_grad_partials(const double* __restrict__ X, const double* __restrict__ Lam,
+                      const double* __restrict__ w, int M, int H, int W,
+                      double* __restrict__ partials) {
+  __shared__ double sh[kThreads / 32];
+  const long n = (long)H * W;
+  const int l = blockIdx.y;
+  const double* x = X + (long)l * n;
+  const double* lam = Lam + (long)l * n;
+  double acc = 0.0;
+  for (long idx = blockIdx.x * (long)kThreads + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * kThreads) {
+    const int i = (int)(idx / W), j = (int)(idx - (long)i * W);
+    if (j < W - 1) acc += w[idx] * (lam[idx + 1] - lam[idx]) * (x[idx + 1] - x[idx]);
+    if (i < H - 1) acc += w[n + idx] * (lam[idx + W] - lam[idx]) * (x[idx + W] - x[idx]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+    partials[(long)blockIdx.x * M + l] = t;
+  }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -200,6 +311,28 @@ cudaError_t blur_apply(const double* x, double* y, int H, int W, const Taps& tp,
 cudaError_t irn_weights(const double* x, double beta, double* w, int H, int W, cudaStream_t s) {
   const long n = (long)H * W;
   k_irn_weights<<<red_grid(n), kThreads, 0, s>>>(x, beta, w, H, W);
+  return launched();
+}
+
+cudaError_t weight_gradient(const double* X, const double* Lam, const double* gammas, int M, int H,
+                            int W, double* dw, cudaStream_t s) {
+  k_weight_grad<<<red_grid((long)H * W), kThreads, 0, s>>>(X, Lam, gammas, M, H, W, dw);
+  return launched();
+}
+
+cudaError_t shift_gradient_partials(const double* X, const double* Lam, const double* w, int M,
+                                    int H, int W, double* partials, int G, cudaStream_t s) {
+  k_shift_grad_partials<<<dim3(G, M), kThreads, 0, s>>>(X, Lam, w, M, H, W, partials);
+  return launched();
+}
+
+cudaError_t gazzola_weights(const double* x, const double* dprev, double p, double* dnew, double* w,
+                            int H, int W, double* partials, cudaStream_t s) {
+  const long n = (long)H * W;
+  const int G = red_grid(n);
+  k_gazzola_max<<<G, kThreads, 0, s>>>(x, dprev, H, W, partials);
+  RK_TRY(launched());
+  k_gazzola_apply<<<G, kThreads, 0, s>>>(x, dprev, p, H, W, partials, G, dnew, w);
   return launched();
 }
 

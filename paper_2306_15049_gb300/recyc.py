@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "librecyc.so")
 RS_OK, RS_EINVAL, RS_ENOCONV, RS_EBREAKDOWN, RS_ENOTREADY, RS_ECUDA, RS_ENOMEM = range(7)
 RS_FP64, RS_MIXED = 0, 1
 RS_INIT, RS_UPDATE = 0, 1
+RS_GUESS_ORTHOGONAL, RS_GUESS_OBLIQUE, RS_GUESS_OBLIQUE2 = 0, 1, 2
 STATUS_NAMES = {0: "RS_OK", 1: "RS_EINVAL", 2: "RS_ENOCONV", 3: "RS_EBREAKDOWN",
                 4: "RS_ENOTREADY", 5: "RS_ECUDA", 6: "RS_ENOMEM"}
 
@@ -32,6 +33,7 @@ class rs_problem_desc(ctypes.Structure):
         ("I_split", ctypes.c_int), ("i1", ctypes.c_int), ("i2", ctypes.c_int),
         ("i_star", ctypes.c_int), ("l_c", ctypes.c_int), ("J_L", ctypes.c_int),
         ("J_R", ctypes.c_int), ("precision", ctypes.c_int), ("batched_local", ctypes.c_int),
+        ("guess", ctypes.c_int), ("I_L", ctypes.c_int), ("I_R", ctypes.c_int),
     ]
 
 
@@ -72,9 +74,12 @@ _SIGS = {
     "rs_set_recycle_basis": (_I, [_P, _P, _I]),
     "rs_solve_shifts": (_I, [_P, _P, ctypes.POINTER(rs_solve_stats), ctypes.POINTER(_I)]),
     "rs_initial_guesses": (_I, [_P, _P, _P]),
+    "rs_solve_adjoint": (_I, [_P, _P, _P, ctypes.POINTER(rs_solve_stats)]),
+    "rs_shift_gradients": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
     "rs_get_principal_basis": (_I, [_P, _P, ctypes.POINTER(_I)]),
     "rs_apply_operator": (_I, [_P, _D, _P, _P, _P, _I, _I]),
     "rs_irn_weights": (_I, [_P, _P, _D, _P]),
+    "rs_gazzola_weights": (_I, [_P, _P, _P, _D, _P, _P]),
     "rs_lcurve": (_I, [_P, _P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "rs_synthesize_data": (_I, [ctypes.POINTER(rs_problem_desc), _P, _P, _D, _P, _P,
                                 ctypes.c_size_t, _P]),
@@ -120,13 +125,17 @@ def _ptr(t) -> int:
 def make_desc(height: int, width: int, sigma: float, radius: int, gammas: Sequence[float],
               tol: float, maxit: int, p_max: int, a_ritz: int, b_ritz: int, n_ritz_local: int,
               vnew_cap: int, I_split: int, i1: int, i2: int, i_star: int, l_c: int, J_L: int,
-              J_R: int, precision: int = RS_FP64, batched_local: int = 0):
-    """An rs_problem_desc; the returned tuple keeps the shift array alive."""
+              J_R: int, precision: int = RS_FP64, batched_local: int = 0,
+              guess: int = RS_GUESS_ORTHOGONAL, I_L: Optional[int] = None,
+              I_R: Optional[int] = None):
+    """An rs_problem_desc; the returned tuple keeps the shift array alive.
+    I_L / I_R (two-anchor oblique guesses) default to i_star and l_c."""
     garr = (ctypes.c_double * len(gammas))(*[float(g) for g in gammas])
     d = rs_problem_desc(height, width, float(sigma), radius, len(gammas),
                         ctypes.cast(garr, ctypes.POINTER(ctypes.c_double)), float(tol), maxit,
                         p_max, a_ritz, b_ritz, n_ritz_local, vnew_cap, I_split, i1, i2, i_star,
-                        l_c, J_L, J_R, precision, batched_local)
+                        l_c, J_L, J_R, precision, batched_local, guess,
+                        i_star if I_L is None else I_L, l_c if I_R is None else I_R)
     return d, garr
 
 
@@ -216,6 +225,17 @@ class Problem:
         self._check(st, (RS_OK, RS_ENOCONV) if allow_noconv else (RS_OK,))
         return [dict((f, getattr(s, f)) for f, _ in rs_solve_stats._fields_) for s in stats]
 
+    def rs_solve_adjoint(self, G_dev, Lam_dev, allow_noconv=False):
+        stats = (rs_solve_stats * self.M)()
+        st = self.lib.rs_solve_adjoint(self.h, _ptr(G_dev), _ptr(Lam_dev), stats)
+        self._check(st, (RS_OK, RS_ENOCONV) if allow_noconv else (RS_OK,))
+        return [dict((f, getattr(s, f)) for f, _ in rs_solve_stats._fields_) for s in stats]
+
+    def rs_shift_gradients(self, X_dev, Lam_dev, dw_dev) -> List[float]:
+        dg = (ctypes.c_double * self.M)()
+        self._check(self.lib.rs_shift_gradients(self.h, _ptr(X_dev), _ptr(Lam_dev), dg, _ptr(dw_dev)))
+        return list(dg)
+
     def rs_initial_guesses(self, X0_dev, R0_dev):
         return self._check(self.lib.rs_initial_guesses(self.h, _ptr(X0_dev), _ptr(R0_dev)))
 
@@ -231,6 +251,10 @@ class Problem:
 
     def rs_irn_weights(self, x_dev, beta: float, w_dev):
         return self._check(self.lib.rs_irn_weights(self.h, _ptr(x_dev), float(beta), _ptr(w_dev)))
+
+    def rs_gazzola_weights(self, x_dev, d_prev_dev, p: float, d_new_dev, w_dev):
+        return self._check(self.lib.rs_gazzola_weights(self.h, _ptr(x_dev), _ptr(d_prev_dev), float(p),
+                                                       _ptr(d_new_dev), _ptr(w_dev)))
 
     def rs_lcurve(self, X_dev, count: int):
         rho = (ctypes.c_double * count)()

@@ -23,7 +23,7 @@ def lib_ready():
 class Pair:
     """Oracle and GPU views of one workload."""
 
-    def __init__(self, wl, precision=0, batched_local=0, maxit=None, x_image=None):
+    def __init__(self, wl, precision=0, batched_local=0, maxit=None, x_image=None, guess=0):
         torch = torch_cuda()
         lib_ready()
         from paper_2306_15049_gb300 import recyc
@@ -42,7 +42,7 @@ class Pair:
         self.prm.maxit = min(self.prm.maxit, 20000) if maxit is None else maxit
         self.gammas = wl.gammas()
         self.desc = desc_for(wl, precision=precision, batched_local=batched_local,
-                             maxit=self.prm.maxit)
+                             maxit=self.prm.maxit, guess=guess)
         dev = torch.device("cuda:0")
         xt = torch.tensor(self.x_true, dtype=torch.float64, device=dev)
         zt = torch.tensor(z.reshape(-1), dtype=torch.float64, device=dev)

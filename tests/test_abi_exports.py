@@ -53,3 +53,20 @@ def test_workspace_size_and_validation_need_no_gpu(lib):
     bad.radius = 4
     bad.i_star = 0
     assert recyc.rs_workspace_bytes(bad) == 0
+
+
+def test_guess_kind_validation_needs_no_gpu(lib):
+    import synth
+    from paper_2306_15049_gb300 import recyc
+    from paper_2306_15049_gb300.workloads import desc_for
+    wl = synth.C1
+    base = recyc.rs_workspace_bytes(desc_for(wl)[0])
+    assert recyc.rs_workspace_bytes(desc_for(wl, guess=recyc.RS_GUESS_OBLIQUE)[0]) == base
+    # two anchors carry one more n x p block and small matrices
+    assert recyc.rs_workspace_bytes(desc_for(wl, guess=recyc.RS_GUESS_OBLIQUE2)[0]) > base
+    for I_L, I_R in [(0, wl.M), (wl.I_split + 1, wl.M), (1, wl.I_split), (1, wl.M + 1)]:
+        d, keep = desc_for(wl, guess=recyc.RS_GUESS_OBLIQUE2, I_L=I_L, I_R=I_R)
+        assert recyc.rs_workspace_bytes(d) == 0, (I_L, I_R)
+    d, keep = desc_for(wl)
+    d.guess = 3
+    assert recyc.rs_workspace_bytes(d) == 0
