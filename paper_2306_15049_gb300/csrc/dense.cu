@@ -183,9 +183,9 @@ k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* per
 // cluster: GB300 issues FP64 at about 4 flop per clock per SM, so one CTA is
 // bound by its SM's FP64 pipe. Column j (its m entries of X followed by its nc
 // entries of V) lives in the shared memory of CTA j % C, slot j / C. A round's
-// disjoint pairs (the same circle-method order and the same per-pair
-// arithmetic as jacobi_body, so the result is bit-identical) are dealt out to
-// the CTAs: each CTA pulls its pairs' columns from their home CTAs into local
+// disjoint pairs (the same circle-method order and rotation formulas as
+// jacobi_body; a warp per pair, so sums differ from it only by rounding) are
+// dealt out to the CTAs: each CTA pulls its pairs' columns from their home CTAs into local
 // shared memory in one wave of distributed-shared-memory loads, rotates them
 // there, pushes them back, and a cluster barrier ends the round. Every CTA
 // takes every barrier and the same (cluster-wide) convergence decision, so no
@@ -228,8 +228,6 @@ k_jacobi_cluster(double* X, int m, int nc, int ldx, double* V, double* sig) {
   }
   cl.sync();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int grp = lane >> 3, gl = lane & 7;
-  const unsigned gmask = 0xffu << (grp * 8);
   const int N = nc + (nc & 1);
   const double tol = 1e-15;
   for (int sweep = 0; sweep < 40; ++sweep) {
@@ -258,43 +256,45 @@ k_jacobi_cluster(double* X, int m, int nc, int ldx, double* V, double* sig) {
         if (j >= 0) stage[idx] = cl.map_shared_rank(cols, j % C)[(long)(j / C) * LD + i];
       }
       __syncthreads();
-      for (int t = warp * 4 + grp; t < npr; t += 4 * kJcWarps) {
-        if (pp_s[2 * t] < 0) continue;           // uniform in the 8-lane group
+      // one warp per pair: GB300 issues a warp's FP64 instruction over many
+      // cycles, so a pair's chain of FP64 instructions is kept short by
+      // spreading its rows over all 32 lanes
+      for (int t = warp; t < npr; t += kJcWarps) {
+        if (pp_s[2 * t] < 0) continue;           // uniform in the warp
         double* xp = stage + (long)(2 * t) * LD;
         double* xq = xp + LD;
         double a = 0.0, b = 0.0, c = 0.0;
-        for (int i = gl; i < m; i += 8) {
+        for (int i = lane; i < m; i += 32) {
           const double u = xp[i], v = xq[i];
           a = fma(u, u, a);
           b = fma(v, v, b);
           c = fma(u, v, c);
         }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(gmask, a, o);
-          b += __shfl_xor_sync(gmask, b, o);
-          c += __shfl_xor_sync(gmask, c, o);
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          c += __shfl_xor_sync(0xffffffffu, c, o);
         }
         double cs = 1.0, sn = 0.0;
         int rot = 0;
-        if (gl == 0 && c != 0.0 && fabs(c) > tol * sqrt(a * b)) {
+        if (lane == 0 && c != 0.0 && fabs(c) > tol * sqrt(a * b)) {
           const double zeta = (b - a) / (2.0 * c);
           const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           cs = rsqrt(1.0 + tt * tt);
           sn = cs * tt;
           rot = 1;
         }
-        const int src = grp * 8;
-        rot = __shfl_sync(gmask, rot, src);
+        rot = __shfl_sync(0xffffffffu, rot, 0);
         if (rot) {
-          cs = __shfl_sync(gmask, cs, src);
-          sn = __shfl_sync(gmask, sn, src);
-          for (int i = gl; i < LD; i += 8) {
+          cs = __shfl_sync(0xffffffffu, cs, 0);
+          sn = __shfl_sync(0xffffffffu, sn, 0);
+          for (int i = lane; i < LD; i += 32) {
             const double u = xp[i], v = xq[i];
             xp[i] = cs * u - sn * v;
             xq[i] = sn * u + cs * v;
           }
-          if (gl == 0) changed_s = 1;
+          if (lane == 0) changed_s = 1;
         }
       }
       __syncthreads();
