@@ -128,3 +128,70 @@ def make_data(op: Operator, x_true: np.ndarray, z: np.ndarray, eta: float):
     zz = z.reshape(-1)
     d = hx + eta * np.linalg.norm(hx) / np.linalg.norm(zz) * zz
     return d, op.blur_adjoint(d)
+
+
+# ---------------------------------------------------------------------------
+# Second forward operator: parallel-beam Radon transform (Section 8.3)
+# ---------------------------------------------------------------------------
+def radon_bins(height: int, width: int) -> int:
+    """Detector bins: odd, centred, covering the image diagonal with a margin:
+    2 ceil(sqrt(((h-1)/2)^2 + ((w-1)/2)^2)) + 3."""
+    half = np.sqrt(((height - 1) / 2.0) ** 2 + ((width - 1) / 2.0) ** 2)
+    return 2 * int(np.ceil(half)) + 3
+
+
+def radon_angles(n_angles: int) -> np.ndarray:
+    """Projection angles in radians: 1, 2, ..., n_angles degrees (Section 8.3 uses 1..135)."""
+    return np.deg2rad(np.arange(1, n_angles + 1, dtype=np.float64))
+
+
+def radon_matrix(height: int, width: int, n_angles: int):
+    """C[(a, k), p] = c max(0, 1 - |f_p(a) - k|), f_p(a) = t_p(a) + (nb - 1)/2,
+    t_p(a) = x_j cos(theta_a) + y_i sin(theta_a): pixel p = (i, j) with centre
+    x_j = j - (w-1)/2, y_i = (h-1)/2 - i is projected onto the detector and split
+    between its two nearest bins by linear interpolation; c makes ||C||_F = 1
+    (Section 8.3). Rows ordered a * nb + k. Built pixel by pixel (sparse)."""
+    import scipy.sparse as sp
+    nb = radon_bins(height, width)
+    th = radon_angles(n_angles)
+    cen = (nb - 1) / 2.0
+    rows, cols, vals = [], [], []
+    jj, ii = np.meshgrid(np.arange(width), np.arange(height))
+    xj = (jj - (width - 1) / 2.0).reshape(-1)
+    yi = ((height - 1) / 2.0 - ii).reshape(-1)
+    pix = np.arange(height * width)
+    for a, t in enumerate(th):
+        f = (xj * np.cos(t) + yi * np.sin(t)) + cen
+        k0 = np.floor(f)
+        for kk in (k0, k0 + 1.0):
+            wgt = np.maximum(0.0, 1.0 - np.abs(f - kk))
+            rows.append(a * nb + kk.astype(np.int64))
+            cols.append(pix)
+            vals.append(wgt)
+    C = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n_angles * nb, height * width))
+    C.eliminate_zeros()
+    return C / np.sqrt(np.sum(C.data ** 2))
+
+
+class RadonOperator(Operator):
+    """The shifted operator with C the Radon transform of ``radon_matrix`` in
+    place of the blur: A = C^T C, b = C^T d, d a sinogram of m = n_angles * nb
+    entries. L and E are unchanged."""
+
+    def __init__(self, height: int, width: int, n_angles: int):
+        self.height, self.width = height, width
+        self.n = height * width
+        self.n_angles = n_angles
+        self.nb = radon_bins(height, width)
+        self.m = n_angles * self.nb
+        self.C = radon_matrix(height, width, n_angles)
+        self.taps = np.ones(1)
+
+    def blur(self, x: np.ndarray) -> np.ndarray:
+        """C x (a sinogram, m entries)."""
+        return self.C @ x.reshape(-1)
+
+    def blur_adjoint(self, y: np.ndarray) -> np.ndarray:
+        """C^T y."""
+        return self.C.T @ y.reshape(-1)
