@@ -144,12 +144,17 @@ __device__ __forceinline__ void coef_from_state(const MinresState& ss, StepCoef<
 
 // ||u||^2 from partB (the same order in every CTA), then the scalar step of
 // MINRES on the CTA's copy of the state (Paige-Saunders; the coupling
-// recurrences of Eq. minShift). Lane 0 of warp 0 takes the rotation (FP64);
-// lanes k < s then update hhat_k and z_k.
+// recurrences of Eq. minShift). Lane 0 of warp 0 takes the rotation; lanes
+// k < s then update hhat_k and z_k. The scalars are computed in the vector
+// type: FP64 for FP64 solves; FP32 for the FP32 inner solves of mixed
+// precision, which need a relative residual reduction of 1e-4 per refinement
+// sweep (an FP64 scalar chain costs a long latency per step on GB300). The
+// state itself is kept in FP64.
 template <typename T>
 __device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T* hd,
                                             T (*red)[kDots], MinresState& ss, StepCoef<T>& cf,
                                             double* sc, const MrP<T>& p) {
+  using S = T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T t = T(0);
   for (unsigned g = threadIdx.x; g < G; g += kThreads) t += __ldcg(partB + g);
@@ -162,51 +167,52 @@ __device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T*
     un = warp_sum_w<T>(un);
     const int s = ss.s;
     if (lane == 0) {
-      const double unorm2 = (double)un;
-      const double alpha_d = (double)hd[s];
-      const double beta_d = ss.beta;
-      const double eps = ss.sn2 * beta_d;
-      const double dbar = ss.cs2 * beta_d;
-      const double delta = ss.cs1 * dbar + ss.sn1 * alpha_d;
-      const double gbar = -ss.sn1 * dbar + ss.cs1 * alpha_d;
+      const S unorm2 = S(un);
+      const S alpha_d = S(hd[s]);
+      const S beta_d = S(ss.beta);
+      const S cs1 = S(ss.cs1), sn1 = S(ss.sn1);
+      const S eps = S(ss.sn2) * beta_d;
+      const S dbar = S(ss.cs2) * beta_d;
+      const S delta = cs1 * dbar + sn1 * alpha_d;
+      const S gbar = -sn1 * dbar + cs1 * alpha_d;
       // beta_{j+1} = ||u|| and gamma = (gbar^2 + beta_{j+1}^2)^(1/2) side by side
-      const double beta_next = sqrt(unorm2);
-      const double gamma = sqrt(fma(gbar, gbar, unorm2));
-      if (!(gamma > 0.0) || !isfinite(gamma)) {
+      const S beta_next = sqrt(unorm2);
+      const S gamma = sqrt(fma(gbar, gbar, unorm2));
+      if (!(gamma > S(0)) || !isfinite((double)gamma)) {
         ss.breakdown = 1;
         ss.stop = 1;
         ss.dir_pending = 0;
         sc[0] = 0.0;
       } else {
-        const double ig = 1.0 / gamma;
-        const double ibn = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
-        const double cs = gbar * ig, sn = beta_next * ig;
-        const double eta = ss.eta;
-        const double tau = cs * eta;
+        const S ig = S(1) / gamma;
+        const S ibn = (beta_next > S(0)) ? S(1) / beta_next : S(0);
+        const S cs = gbar * ig, sn = beta_next * ig;
+        const S eta = S(ss.eta);
+        const S tau = cs * eta;
         const int it = ss.iters;
         if (blockIdx.x == 0 && p.arec && it < p.rec_cap) {
-          p.arec[it] = alpha_d;
-          p.brec[it] = beta_next;
+          p.arec[it] = (double)alpha_d;
+          p.brec[it] = (double)beta_next;
         }
         sc[0] = 1.0;
-        sc[1] = delta;
-        sc[2] = eps;
-        sc[3] = ig;
-        sc[4] = tau;
-        ss.eta = -sn * eta;
-        ss.delta = delta;
-        ss.eps = eps;
-        ss.inv_gamma = ig;
-        ss.tau = tau;
-        ss.inv_beta_next = ibn;
+        sc[1] = (double)delta;
+        sc[2] = (double)eps;
+        sc[3] = (double)ig;
+        sc[4] = (double)tau;
+        ss.eta = (double)(-sn * eta);
+        ss.delta = (double)delta;
+        ss.eps = (double)eps;
+        ss.inv_gamma = (double)ig;
+        ss.tau = (double)tau;
+        ss.inv_beta_next = (double)ibn;
         ss.cs2 = ss.cs1;
         ss.sn2 = ss.sn1;
-        ss.cs1 = cs;
-        ss.sn1 = sn;
+        ss.cs1 = (double)cs;
+        ss.sn1 = (double)sn;
         ss.iters = it + 1;
-        ss.beta = beta_next;
+        ss.beta = (double)beta_next;
         ss.dir_pending = 1;
-        if (fabs(ss.eta) <= ss.tol_abs || beta_next == 0.0 || ss.iters >= ss.maxit) ss.stop = 1;
+        if (fabs(ss.eta) <= ss.tol_abs || !(beta_next > S(0)) || ss.iters >= ss.maxit) ss.stop = 1;
         cf.delta = T(delta);
         cf.eps = T(eps);
         cf.inv_gamma = T(ig);
@@ -217,11 +223,11 @@ __device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T*
     }
     __syncwarp();
     if (lane < s && sc[0] != 0.0) {
-      const double h1 = ss.h1[lane];
-      const double hh = ((double)hd[lane] - sc[1] * h1 - sc[2] * ss.h2[lane]) * sc[3];
-      ss.z[lane] -= sc[4] * hh;
-      ss.h2[lane] = h1;
-      ss.h1[lane] = hh;
+      const S h1 = S(ss.h1[lane]);
+      const S hh = (S(hd[lane]) - S(sc[1]) * h1 - S(sc[2]) * S(ss.h2[lane])) * S(sc[3]);
+      ss.z[lane] = (double)(S(ss.z[lane]) - S(sc[4]) * hh);
+      ss.h2[lane] = (double)h1;
+      ss.h1[lane] = (double)hh;
     }
   }
   __syncthreads();
