@@ -88,7 +88,18 @@ typedef struct {
   int batched_local;       /* 0: paper's chain g^(k,l-1); 1: g^(k-1,l-1) instead */
   int guess;               /* rs_guess: how the initial guesses are projected */
   int I_L, I_R;            /* RS_GUESS_OBLIQUE2 anchors (1-based): 1 <= I_L <= I_split < I_R <= M */
+  int radon_angles;        /* 0: C = H, the blur (sigma, radius). 1..3600: C = the parallel-beam
+                              Radon transform of Section 8.3 with angles 1, 2, .., radon_angles
+                              degrees (sigma, radius ignored); see below */
 } rs_problem_desc;
+
+/* The Radon forward operator (radon_angles > 0): pixel p = (i, j) has centre
+ * x_j = j - (width-1)/2, y_i = (height-1)/2 - i; at angle th_a = (a+1) degrees it
+ * projects to f = x_j cos th_a + y_i sin th_a + (nb-1)/2 and is split between the
+ * detector bins floor(f) and floor(f)+1 by linear interpolation, nb =
+ * 2 ceil(sqrt(((height-1)/2)^2 + ((width-1)/2)^2)) + 3 bins; C is scaled to unit
+ * Frobenius norm. Data d (rs_create_problem, rs_lcurve, rs_synthesize_data) is
+ * then a sinogram of m = radon_angles * nb doubles, entry a * nb + k. */
 
 /* Per-shift results of rs_solve_shifts. */
 typedef struct {
@@ -111,6 +122,9 @@ typedef struct {
   long long matvecs_overhead; /* principal-space construction and images */
   int ld;                  /* leading dimension of device blocks (elements) */
   long long kernel_launches; /* CUDA kernels launched by the library in this process */
+  int minres_kernel;       /* kernel of the last persistent MINRES solve: 1 one CTA per tile,
+                              vectors in registers; 0 tiles streamed through memory (not all
+                              co-resident); -1 none yet (step kernels only) */
 } rs_info;
 
 /* Per-kernel device time, gathered with CUDA events around every launch of
@@ -136,7 +150,8 @@ typedef struct {
  * for an invalid description. */
 size_t rs_workspace_bytes(const rs_problem_desc* desc);
 
-/* Create a problem. d_dev (n doubles) is the data image; b = H^T d is formed
+/* Create a problem. d_dev (n doubles; a sinogram of m doubles for the Radon
+ * operator) is the data; b = C^T d is formed
  * on the device. workspace_dev must be 256-byte aligned and at least
  * rs_workspace_bytes(desc) bytes; stream is a cudaStream_t (NULL: default).
  * On success *out receives the problem (free it with rs_destroy). */
@@ -207,9 +222,11 @@ rs_status rs_initial_guesses(rs_problem* prob, double* X0_dev, double* R0_dev);
 rs_status rs_get_principal_basis(rs_problem* prob, double* U_dev, int* nc_host);
 
 /* y = (A + gamma E_k) x  (mode 0), or y = A x and y2 = E_k x (mode 1), or
- * y = E_k x (mode 2), or y = H x (mode 3). x, y, y2: n doubles on the device,
- * computed in the problem's working precision for modes 0-2 when
- * use_working_precision is 1, else in FP64. Counts as one matvec (modes 0-2). */
+ * y = E_k x (mode 2), or y = C x (mode 3: the blur H, or the Radon transform with
+ * y of m doubles), or y = C^T x (mode 4: x of m doubles). Otherwise x, y, y2 are
+ * n doubles on the device, computed in the problem's working precision for modes
+ * 0-2 when use_working_precision is 1, else in FP64. Counts as one matvec
+ * (modes 0-2). */
 rs_status rs_apply_operator(rs_problem* prob, double gamma, const double* x_dev,
                             double* y_dev, double* y2_dev, int mode,
                             int use_working_precision);
@@ -237,9 +254,11 @@ rs_status rs_gazzola_weights(rs_problem* prob, const double* x_dev, const double
 rs_status rs_lcurve(rs_problem* prob, const double* X_dev, int count, double* rho_host,
                     double* eta_host, int* l_star_host);
 
-/* Synthetic data: d = H x + eta ||H x|| / ||z|| z (Section 2.1, Eq. forward)
- * for an image x and a noise direction z (n doubles each, device). Uses only
- * the description's image size and blur; needs no problem. */
+/* Synthetic data: d = C x + eta ||C x|| / ||z|| z (Section 2.1, Eq. forward)
+ * for an image x (n doubles) and a noise direction z (n doubles, or m for the
+ * Radon operator; device). Uses only the description's image size and forward
+ * operator; needs no problem. workspace_dev: at least
+ * (red_grid + 8 + 2 radon_angles) doubles, where red_grid <= 304. */
 rs_status rs_synthesize_data(const rs_problem_desc* desc, const double* x_dev,
                              const double* z_dev, double eta, double* d_out_dev,
                              void* workspace_dev, size_t workspace_bytes, void* stream);

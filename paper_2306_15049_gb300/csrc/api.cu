@@ -140,6 +140,7 @@ struct Carver {
 
 struct Dims {
   long n, ld, ld2;
+  long m, ldm;          // data entries (n for the blur, nang * nb sinogram bins for the Radon operator)
   int M, p, J, a, bq, cap, cmax, keep, smax, G, psz;
 };
 
@@ -147,8 +148,11 @@ bool valid_desc(const rs_problem_desc* d, std::string* why) {
   auto fail = [&](const char* m) { if (why) *why = m; return false; };
   if (!d) return fail("desc is NULL");
   if (d->height < 1 || d->width < 1) return fail("height and width must be >= 1");
-  if (!(d->sigma > 0.0) || !std::isfinite(d->sigma)) return fail("sigma must be > 0");
-  if (d->radius < 0 || d->radius > 16) return fail("radius must be in [0, 16]");
+  if (d->radon_angles < 0 || d->radon_angles > 3600) return fail("radon_angles must be in [0, 3600]");
+  if (d->radon_angles == 0) {
+    if (!(d->sigma > 0.0) || !std::isfinite(d->sigma)) return fail("sigma must be > 0");
+    if (d->radius < 0 || d->radius > 16) return fail("radius must be in [0, 16]");
+  }
   if (d->M < 1 || d->M > 256) return fail("M must be in [1, 256]");
   if (!d->gammas_host) return fail("gammas_host is NULL");
   for (int l = 0; l < d->M; ++l) {
@@ -183,6 +187,8 @@ Dims dims_of(const rs_problem_desc* d) {
   z.n = (long)d->height * d->width;
   z.ld = round_up(z.n, 64);
   z.ld2 = round_up(2 * z.n, 64);
+  z.m = d->radon_angles > 0 ? (long)d->radon_angles * radon_bins(d->height, d->width) : z.n;
+  z.ldm = std::max(z.ld, round_up(z.m, 64));
   z.M = d->M;
   z.p = d->p_max;
   z.J = d->n_ritz_local;
@@ -240,6 +246,9 @@ struct rs_problem {
   double *arec = nullptr, *brec = nullptr, *lc = nullptr;
   // oblique guesses with two anchors (Eq. updates): per anchor R_a, K_a^T E U_a, K_a^T b
   void* Kan = nullptr;
+  // Radon forward operator: (cos, sin) table and the sinogram buffer of op_apply
+  double* radon_cs = nullptr;
+  double* sino = nullptr;
   // adjoint solves: per-shift right-hand sides in the working precision, their
   // corrections (the local-space chain), norms and projected guesses
   void* Gadj = nullptr;
@@ -314,10 +323,10 @@ void carve(rs_problem* P, Carver& cv) {
   const size_t vt = P->mixed ? sizeof(float) : sizeof(double);
   auto vec = [&](long count) -> void* { return cv.take<char>((size_t)count * vt); };
   P->b = cv.take<double>(z.ld);
-  P->dimg = cv.take<double>(z.ld);
+  P->dimg = cv.take<double>(z.ldm);
   P->r64 = cv.take<double>(z.ld);
   P->y64 = cv.take<double>(z.ld);
-  P->t64 = cv.take<double>(z.ld);
+  P->t64 = cv.take<double>(z.ldm);
   P->w64 = cv.take<double>(z.ld2);
   P->wprev64 = cv.take<double>(z.ld2);
   P->dw64 = cv.take<double>(z.ld2);
@@ -389,6 +398,10 @@ void carve(rs_problem* P, Carver& cv) {
   P->partials_a = cv.take<double>((size_t)mr_matvec_blocks(P->d.height, P->d.width) * (kMaxLocal + 1));
   P->partials_p = cv.take<double>((size_t)kPersistMaxBlocks * (kMaxLocal + 2));
   P->gbar = cv.take<GridBar>(1);
+  if (P->d.radon_angles > 0) {
+    P->radon_cs = cv.take<double>(2 * (size_t)P->d.radon_angles);
+    P->sino = cv.take<double>(z.ldm);
+  }
   P->Gadj = vec((long)z.M * z.ld);
   P->Cadj = cv.take<double>((size_t)z.p * z.M);
   P->CAadj = cv.take<double>((size_t)z.p * z.M);
@@ -429,6 +442,21 @@ int read_back(rs_problem* P, void* host, const void* dev, size_t bytes) {
   CU(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, P->s));
   CU(cudaStreamSynchronize(P->s));
   return RS_OK;
+}
+
+// y = C x with the problem's forward operator (the blur H, or the Radon
+// transform: y then has z.m entries), and x = C^T y, both in FP64.
+cudaError_t forward_apply(rs_problem* P, const double* x, double* y) {
+  if (P->tp.radon.nang > 0)
+    return radon_forward<double>(x, y, P->d.height, P->d.width, P->tp.radon, P->s, nullptr);
+  return blur_apply(x, y, P->d.height, P->d.width, P->tp, 0, P->s);
+}
+
+cudaError_t adjoint_apply(rs_problem* P, const double* y, double* x) {
+  if (P->tp.radon.nang > 0)
+    return radon_adjoint_op<double>(y, nullptr, nullptr, x, nullptr, P->d.height, P->d.width,
+                                    P->tp.radon, 0.0, 3, P->s, nullptr);
+  return blur_apply(y, x, P->d.height, P->d.width, P->tp, 1, P->s);
 }
 
 // Event pair around one timed launch; returns the slot or -1 when timing is off.
@@ -608,14 +636,17 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
   // replayed from a CUDA graph once the operands repeat (j = 2 mod 3, ring
   // buffers only). Switching from unfused to fused needs nothing: the unfused
   // step leaves v_{j+1} written and no direction update pending.
-  const int n_unfused = reorth ? std::min(keep - 1, maxit) : 0;
+  // steps run unfused while kept Lanczos vectors are re-orthogonalized, and
+  // always with the Radon operator (the fused kernels apply the blur stencil)
+  const bool generic_op = P->tp.radon.nang > 0;
+  const int n_unfused = generic_op ? maxit : (reorth ? std::min(keep - 1, maxit) : 0);
   auto unfused = [&](int j) -> int {
     T* vj = vptr(j);
     CU(op_apply<T>(vj, ld, 1, wT, y, nullptr, ld, P->d.height, P->d.width, P->tp, gamma, 0, s, stop));
     CU(multidot<T>(Kl, ld, cnt_use, 0, vj, y, n, P->partials, kDotStride, s, stop));
     CU(reduce_partials(P->partials, z.G, kMaxLocal + 1, kDotStride, P->hdots, s, cnt_use, 1, stop));
     CU(lanczos_update<T>(P->st, Kl, ld, P->hdots, y, vj, vptr(j - 1), u, n, P->partials, s));
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; reorth && j < keep && pass < 2; ++pass) {
       CU(multidot<T>(Vk, ld, nullptr, j, nullptr, u, n, P->partials + (long)z.G * 4, z.cmax + 2, s, stop));
       CU(reduce_partials(P->partials + (long)z.G * 4, z.G, j, z.cmax + 2, P->coef, s, nullptr, 0, stop));
       CU(multi_axpy<T>(Vk, ld, nullptr, j, P->coef, -1.0, u, n, pass == 1 ? P->partials : nullptr, s, stop));
@@ -761,7 +792,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
   while (nq > 0) RS(retire());
   // a direction update of the last fused step may still be pending: kernel A
   // with the stop flag set does only that (and nothing after an unfused step)
-  RS(stepA(j, false));
+  if (!generic_op) RS(stepA(j, false));
   MinresState hs;
   RS(read_back(P, &hs, P->st, sizeof hs));
   timed_flush(P, hs.iters);
@@ -1300,7 +1331,7 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   P->s = (cudaStream_t)stream;
   P->mixed = desc->precision == RS_MIXED;
   P->z = dims_of(desc);
-  P->tp = make_taps(desc->sigma, desc->radius);
+  P->tp = desc->radon_angles > 0 ? Taps{} : make_taps(desc->sigma, desc->radius);
   P->need = need;
   // RS_GRAPHS=0 launches the fused MINRES steps one by one instead of replaying
   // them from a CUDA graph (the same kernels; for profilers that handle graphs poorly)
@@ -1309,6 +1340,9 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // persistent cooperative kernel
   if (const char* g = std::getenv("RS_PERSIST")) P->use_persist = std::strcmp(g, "0") != 0;
   if (!mr_persist_supported(desc->radius)) P->use_persist = false;
+  // the persistent and fused MINRES kernels apply the blur stencil in place;
+  // with the Radon operator every step runs as separate kernels
+  if (desc->radon_angles > 0) P->use_persist = P->use_graph = false;
   // RS_COOP_CGS=0 runs CGS2 column by column (several launches per candidate)
   if (const char* g = std::getenv("RS_COOP_CGS")) P->use_coop_cgs = std::strcmp(g, "0") != 0;
   P->gprev_nz.assign(desc->M, 0);
@@ -1329,13 +1363,27 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   };
   cudaError_t e;
   if ((e = cudaMemcpyAsync(P->gam, P->gammas.data(), desc->M * sizeof(double), cudaMemcpyHostToDevice, P->s))) return fail(e);
-  if ((e = cudaMemcpyAsync(P->dimg, d_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, P->s))) return fail(e);
-  if ((e = check_finite(P->dimg, n, 0, P->ok, P->s))) return fail(e);
+  const long m = P->z.m;
+  if ((e = cudaMemcpyAsync(P->dimg, d_dev, m * sizeof(double), cudaMemcpyDeviceToDevice, P->s))) return fail(e);
+  if ((e = check_finite(P->dimg, m, 0, P->ok, P->s))) return fail(e);
   int okh = 0;
   if ((e = cudaMemcpyAsync(&okh, P->ok, sizeof(int), cudaMemcpyDeviceToHost, P->s))) return fail(e);
   if ((e = cudaStreamSynchronize(P->s))) return fail(e);
   if (!okh) { snprintf(g_err, sizeof g_err, "d contains NaN or Inf"); delete P; return RS_EINVAL; }
-  if ((e = blur_apply(P->dimg, P->b, desc->height, desc->width, P->tp, 1, P->s))) return fail(e);
+  if (desc->radon_angles > 0) {
+    // (cos, sin) per angle and c = 1 / ||C||_F
+    const int nb = radon_bins(desc->height, desc->width);
+    if ((e = radon_setup(desc->height, desc->width, desc->radon_angles, nb, P->radon_cs, P->partials,
+                         P->z.G, P->s)) ||
+        (e = reduce_partials(P->partials, P->z.G, 1, 1, P->scal + 15, P->s, nullptr, 0, nullptr)))
+      return fail(e);
+    double fro2 = 0.0;
+    if ((e = cudaMemcpyAsync(&fro2, P->scal + 15, sizeof fro2, cudaMemcpyDeviceToHost, P->s))) return fail(e);
+    if ((e = cudaStreamSynchronize(P->s))) return fail(e);
+    P->tp.radon = RadonGeom{desc->radon_angles, nb, P->radon_cs, 1.0 / std::sqrt(fro2)};
+    P->tp.sino = P->sino;
+  }
+  if ((e = adjoint_apply(P, P->dimg, P->b))) return fail(e);
   if ((e = norm2_partials<double>(P->b, n, P->partials, P->s))) return fail(e);
   if ((e = reduce_partials(P->partials, P->z.G, 1, 1, P->scal + 15, P->s, nullptr, 0, nullptr))) return fail(e);
   double b2 = 0.0;
@@ -1470,12 +1518,14 @@ rs_status rs_apply_operator(rs_problem* P, double gamma, const double* x_dev, do
                             double* y2_dev, int mode, int use_working_precision) {
   if (!P) return RS_EINVAL;
   if (!x_dev || !y_dev || (mode == 1 && !y2_dev)) return (rs_status)P->set_err(RS_EINVAL, "NULL vector");
-  if (mode < 0 || mode > 3) return (rs_status)P->set_err(RS_EINVAL, "mode must be 0..3");
-  if (mode != 3 && P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  if (mode < 0 || mode > 4) return (rs_status)P->set_err(RS_EINVAL, "mode must be 0..4");
+  if (mode < 3 && P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
   const long n = P->z.n, ld = P->z.ld;
   const int H = P->d.height, W = P->d.width;
   if (mode == 3) {
-    CU(blur_apply(x_dev, y_dev, H, W, P->tp, 0, P->s));
+    CU(forward_apply(P, x_dev, y_dev));
+  } else if (mode == 4) {
+    CU(adjoint_apply(P, x_dev, y_dev));
   } else if (P->mixed && use_working_precision) {
     float* xf = (float*)P->u;
     float* yf = (float*)P->y;
@@ -1522,8 +1572,8 @@ rs_status rs_lcurve(rs_problem* P, const double* X_dev, int count, double* rho_h
   const long n = P->z.n;
   for (int l = 0; l < count; ++l) {
     const double* x = X_dev + (long)l * n;
-    CU(blur_apply(x, P->t64, P->d.height, P->d.width, P->tp, 0, P->s));
-    CU(residual64(P->dimg, P->t64, nullptr, n, P->partials, P->s));
+    CU(forward_apply(P, x, P->t64));
+    CU(residual64(P->dimg, P->t64, nullptr, P->z.m, P->partials, P->s));
     CU(reduce_partials(P->partials, P->z.G, 1, 1, P->lc + l, P->s, nullptr, 0, nullptr));
     CU(wgrad_norm2_partials(x, P->w64, P->d.height, P->d.width, P->partials, P->z.G, P->s));
     CU(reduce_partials(P->partials, P->z.G, 1, 1, P->lc + P->z.M + l, P->s, nullptr, 0, nullptr));
@@ -1543,8 +1593,10 @@ rs_status rs_lcurve(rs_problem* P, const double* X_dev, int count, double* rho_h
 rs_status rs_synthesize_data(const rs_problem_desc* desc, const double* x_dev, const double* z_dev,
                              double eta, double* d_out_dev, void* workspace_dev, size_t workspace_bytes,
                              void* stream) {
-  if (!desc || desc->height < 1 || desc->width < 1 || !(desc->sigma > 0.0) || desc->radius < 0 ||
-      desc->radius > 16) {
+  const bool radon = desc && desc->radon_angles > 0;
+  if (!desc || desc->height < 1 || desc->width < 1 || desc->radon_angles < 0 ||
+      desc->radon_angles > 3600 ||
+      (!radon && (!(desc->sigma > 0.0) || desc->radius < 0 || desc->radius > 16))) {
     snprintf(g_err, sizeof g_err, "bad description");
     return RS_EINVAL;
   }
@@ -1553,25 +1605,44 @@ rs_status rs_synthesize_data(const rs_problem_desc* desc, const double* x_dev, c
     return RS_EINVAL;
   }
   const long n = (long)desc->height * desc->width;
-  const int G = red_grid(n);
-  if (workspace_bytes < (size_t)(G + 8) * sizeof(double)) {
-    snprintf(g_err, sizeof g_err, "workspace too small");
+  const int nb = radon ? radon_bins(desc->height, desc->width) : 0;
+  const long m = radon ? (long)desc->radon_angles * nb : n;
+  const int G = red_grid(std::max(n, m));
+  const size_t need = (size_t)(G + 8 + (radon ? 2 * desc->radon_angles : 0)) * sizeof(double);
+  if (workspace_bytes < need) {
+    snprintf(g_err, sizeof g_err, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
     return RS_ENOMEM;
   }
   cudaStream_t s = (cudaStream_t)stream;
   double* part = (double*)workspace_dev;
   double* sc = part + G;
-  const Taps tp = make_taps(desc->sigma, desc->radius);
   cudaError_t e;
-  if ((e = blur_apply(x_dev, d_out_dev, desc->height, desc->width, tp, 0, s)) ||
-      (e = norm2_partials<double>(d_out_dev, n, part, s)) ||
-      (e = reduce_partials(part, G, 1, 1, sc, s, nullptr, 0, nullptr)) ||
-      (e = norm2_partials<double>(z_dev, n, part, s)) ||
-      (e = reduce_partials(part, G, 1, 1, sc + 1, s, nullptr, 0, nullptr))) {
+  if (radon) {
+    // C x with C scaled to unit Frobenius norm (Section 8.3)
+    double* cs = sc + 8;
+    double fro2 = 0.0;
+    if ((e = radon_setup(desc->height, desc->width, desc->radon_angles, nb, cs, part, red_grid(n), s)) ||
+        (e = reduce_partials(part, red_grid(n), 1, 1, sc + 2, s, nullptr, 0, nullptr)) ||
+        (e = cudaMemcpyAsync(&fro2, sc + 2, sizeof fro2, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+      snprintf(g_err, sizeof g_err, "CUDA error %s", cudaGetErrorString(e));
+      return RS_ECUDA;
+    }
+    const RadonGeom g{desc->radon_angles, nb, cs, 1.0 / std::sqrt(fro2)};
+    e = radon_forward<double>(x_dev, d_out_dev, desc->height, desc->width, g, s, nullptr);
+  } else {
+    const Taps tp = make_taps(desc->sigma, desc->radius);
+    e = blur_apply(x_dev, d_out_dev, desc->height, desc->width, tp, 0, s);
+  }
+  const int Gm = red_grid(m);
+  if (e || (e = norm2_partials<double>(d_out_dev, m, part, s)) ||
+      (e = reduce_partials(part, Gm, 1, 1, sc, s, nullptr, 0, nullptr)) ||
+      (e = norm2_partials<double>(z_dev, m, part, s)) ||
+      (e = reduce_partials(part, Gm, 1, 1, sc + 1, s, nullptr, 0, nullptr))) {
     snprintf(g_err, sizeof g_err, "CUDA error %s", cudaGetErrorString(e));
     return RS_ECUDA;
   }
-  k_add_scaled<<<64, 256, 0, s>>>(z_dev, sc, sc + 1, eta, d_out_dev, n);
+  k_add_scaled<<<64, 256, 0, s>>>(z_dev, sc, sc + 1, eta, d_out_dev, m);
   if ((e = launched()) || (e = cudaStreamSynchronize(s))) {
     snprintf(g_err, sizeof g_err, "CUDA error %s", cudaGetErrorString(e));
     return RS_ECUDA;
@@ -1588,6 +1659,7 @@ rs_status rs_get_info(const rs_problem* P, rs_info* info) {
   info->matvecs_overhead = P->mv_over;
   info->ld = (int)P->z.ld;
   info->kernel_launches = launch_count();
+  info->minres_kernel = P->last_resident;
   return RS_OK;
 }
 

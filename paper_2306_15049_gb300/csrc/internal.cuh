@@ -13,9 +13,24 @@ constexpr int kMaxLocal = 16;        // columns of a local recycle space K_l
 constexpr int kMaxDots = 256;        // dots reduced by one k_reduce launch
 constexpr int kMaxP = 110;           // principal recycle dimension cap
 
+// Geometry of the parallel-beam Radon operator (radon.cu): nang angles of
+// (a + 1) degrees, nb detector bins, cs = device table of (cos, sin) per angle,
+// scale = 1 / ||C||_F of the unscaled interpolation weights. nang = 0: none.
+struct RadonGeom {
+  int nang;
+  int nb;
+  const double* cs;
+  double scale;
+};
+
+// The forward operator of a problem: the Gaussian blur taps (radon.nang == 0)
+// or the Radon geometry with a device sinogram buffer (nang * nb entries of
+// the vector type) for op_apply.
 struct Taps {
   double g[kMaxTaps];
   int r;
+  RadonGeom radon;
+  void* sino;
 };
 
 // Every kernel launch of the library goes through launched(): it returns the
@@ -60,6 +75,22 @@ cudaError_t gazzola_weights(const double* x, const double* dprev, double p, doub
 // partials[g] = sum over CTA g of w .* (L x)^2 (for the L-curve seminorm).
 cudaError_t wgrad_norm2_partials(const double* x, const double* w, int H, int W, double* partials,
                                  int G, cudaStream_t s);
+
+// ---------------------------------------------------------------- radon.cu
+int radon_bins(int H, int W);
+// cs (2 nang doubles) = (cos, sin) of each angle; partials[g] (G CTAs) = shares
+// of the squared unscaled weights (reduce, then scale = 1 / sqrt(sum)).
+cudaError_t radon_setup(int H, int W, int nang, int nb, double* cs, double* partials, int G,
+                        cudaStream_t s);
+// sino = C x (nang * nb entries).
+template <typename T>
+cudaError_t radon_forward(const T* x, T* sino, int H, int W, const RadonGeom& g, cudaStream_t s,
+                          const int* stop);
+// mode 0: y = C^T sino + gamma E x; 1: y = C^T sino, y2 = E x; 2: y = E x; 3: y = C^T sino.
+template <typename T>
+cudaError_t radon_adjoint_op(const T* sino, const T* x, const T* w, T* y, T* y2, int H, int W,
+                             const RadonGeom& g, double gamma, int mode, cudaStream_t s,
+                             const int* stop);
 
 // ---------------------------------------------------------------- blas.cu
 // Kernels given a non-null `stop` do nothing when *stop != 0 (a finished
@@ -238,8 +269,7 @@ int mr_matvec_blocks(int H, int W);
 struct GridBar {
   unsigned long long count;   // arrivals so far (barrier b completes at b x CTAs)
   int err;                    // 1: a CTA's wait ran out of time; 2: local space wider
-                              // than the launch's shared memory (the solve is void);
-                              // 3: a wait for neighbouring tiles ran out of time
+                              // than the launch's shared memory (the solve is void)
   int pad;
 };
 constexpr int kPersistMaxBlocks = 152 * 8;
@@ -266,13 +296,7 @@ struct MrP {
   double* brec;
   int rec_cap;
   int j0;              // first step of this launch
-  // pipelined resident kernel: per-step partial sums, double-buffered by step
-  // parity (2 x kPipeSlots x kPersistMaxBlocks entries of T), and per-tile
-  // progress flags (kPersistMaxBlocks ints, zero at launch)
-  double* partP;
-  int* tflags;
 };
-constexpr int kPipeSlots = kMaxLocal + 2;   // K^T y~ (s), u^T y~, u^T u
 // One launch runs the solve to its stop. s_alloc: the widest local space the
 // resident kernel must hold in shared memory. resident (out): 1 if the
 // one-CTA-per-tile kernel ran, 0 for the streaming one.

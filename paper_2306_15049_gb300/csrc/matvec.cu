@@ -279,6 +279,17 @@ cudaError_t op_apply(const T* x, long ldx, int ncols, const T* w, T* y, T* y2, l
                      int W, const Taps& tp, double gamma, int mode, cudaStream_t s,
                      const int* stop) {
   if (ncols <= 0) return cudaSuccess;
+  if (tp.radon.nang > 0) {
+    // A = C^T C: the sinogram of each column through the problem's buffer
+    T* sino = reinterpret_cast<T*>(tp.sino);
+    for (int c = 0; c < ncols; ++c) {
+      const T* xc = x + (long)c * ldx;
+      if (mode != 2) RK_TRY(radon_forward<T>(xc, sino, H, W, tp.radon, s, stop));
+      RK_TRY(radon_adjoint_op<T>(sino, xc, w, y + (long)c * ldy, y2 ? y2 + (long)c * ldy : nullptr, H,
+                                 W, tp.radon, gamma, mode, s, stop));
+    }
+    return cudaSuccess;
+  }
   const size_t smem = (size_t)op_tile_smem_elems(tp.r) * sizeof(T);
   dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, ncols);
   auto go = [&](auto kernel, int* cached) -> cudaError_t {

@@ -70,6 +70,8 @@ extern "C" rs_status rs_synthesize_data_noalloc(const rs_problem_desc* desc, con
   if (!desc || desc->height < 1 || desc->width < 1 || !(desc->sigma > 0.0) || desc->radius < 0 ||
       desc->radius > 16)
     return fail(RS_EINVAL, "bad description (height, width >= 1, sigma > 0, 0 <= radius <= 16)");
+  if (desc->radon_angles != 0)
+    return fail(RS_EINVAL, "the allocation-free synthesis takes the blur operator only (radon_angles = 0)");
   if (!x_dev || !z_dev || !d_out_dev) return fail(RS_EINVAL, "NULL pointer");
   const long n = (long)desc->height * desc->width;
   if (n > kMaxPixels) return fail(RS_EINVAL, "image larger than 2^28 pixels");

@@ -34,6 +34,7 @@ class rs_problem_desc(ctypes.Structure):
         ("i_star", ctypes.c_int), ("l_c", ctypes.c_int), ("J_L", ctypes.c_int),
         ("J_R", ctypes.c_int), ("precision", ctypes.c_int), ("batched_local", ctypes.c_int),
         ("guess", ctypes.c_int), ("I_L", ctypes.c_int), ("I_R", ctypes.c_int),
+        ("radon_angles", ctypes.c_int),
     ]
 
 
@@ -49,7 +50,7 @@ class rs_info(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int), ("k", ctypes.c_int), ("nc", ctypes.c_int),
         ("matvecs_total", ctypes.c_longlong), ("matvecs_overhead", ctypes.c_longlong),
-        ("ld", ctypes.c_int), ("kernel_launches", ctypes.c_longlong),
+        ("ld", ctypes.c_int), ("kernel_launches", ctypes.c_longlong), ("minres_kernel", ctypes.c_int),
     ]
 
 
@@ -127,7 +128,7 @@ def make_desc(height: int, width: int, sigma: float, radius: int, gammas: Sequen
               vnew_cap: int, I_split: int, i1: int, i2: int, i_star: int, l_c: int, J_L: int,
               J_R: int, precision: int = RS_FP64, batched_local: int = 0,
               guess: int = RS_GUESS_ORTHOGONAL, I_L: Optional[int] = None,
-              I_R: Optional[int] = None):
+              I_R: Optional[int] = None, radon_angles: int = 0):
     """An rs_problem_desc; the returned tuple keeps the shift array alive.
     I_L / I_R (two-anchor oblique guesses) default to i_star and l_c."""
     garr = (ctypes.c_double * len(gammas))(*[float(g) for g in gammas])
@@ -135,7 +136,7 @@ def make_desc(height: int, width: int, sigma: float, radius: int, gammas: Sequen
                         ctypes.cast(garr, ctypes.POINTER(ctypes.c_double)), float(tol), maxit,
                         p_max, a_ritz, b_ritz, n_ritz_local, vnew_cap, I_split, i1, i2, i_star,
                         l_c, J_L, J_R, precision, batched_local, guess,
-                        i_star if I_L is None else I_L, l_c if I_R is None else I_R)
+                        i_star if I_L is None else I_L, l_c if I_R is None else I_R, radon_angles)
     return d, garr
 
 

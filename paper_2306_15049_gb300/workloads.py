@@ -11,4 +11,4 @@ def desc_for(wl, precision: int = RS_FP64, batched_local: int = 0, maxit=None,
                      int(maxit if maxit is not None else min(wl.maxit, 100_000)), wl.p,
                      wl.a_ritz, wl.b_ritz, wl.n_ritz_local, wl.vnew_cap, wl.I_split, wl.i1,
                      wl.i2, wl.i_star, wl.l_c, wl.J_L, wl.J_R, precision, batched_local,
-                     guess, I_L, I_R)
+                     guess, I_L, I_R, getattr(wl, "radon_angles", 0))

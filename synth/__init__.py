@@ -20,7 +20,8 @@ Recipe (one image, seed ``s``):
   overwrite earlier ones.
 * ``z`` is a standard normal vector of the image size (the noise direction);
   each side forms ``d = H x_true + eta * ||H x_true|| / ||z|| * z`` with its own
-  blur.
+  blur. CT workloads draw ``z`` of the sinogram size instead
+  (``sinogram_noise``) and use their own Radon transform in place of H.
 * shifts ``gamma = logspace(lo, hi, M)``.
 * seeds ``20230615 + 10 * config_index + image_index``.
 """
@@ -56,6 +57,7 @@ class Workload:
     tol: float = 1e-8
     beta: float = 1e-3    # smoothing of the edge-preserving weights
     seed: int = SEED_BASE
+    radon_angles: int = 0  # > 0: CT forward model (angles 1..radon_angles degrees) instead of the blur
 
     # ---- derived index choices (readings scaled from Ex. 1 / Ex. 2) ----
     @property
@@ -149,6 +151,12 @@ def noise_direction(height: int, width: int, seed: int) -> np.ndarray:
     return rng.standard_normal((height, width))
 
 
+def sinogram_noise(m: int, seed: int) -> np.ndarray:
+    """Standard normal noise direction of the m sinogram entries (CT workloads)."""
+    rng = np.random.default_rng(seed + 7919)
+    return rng.standard_normal(m)
+
+
 def random_weights(n: int, seed: int, lo: float = 0.5, hi: float = 50.0) -> np.ndarray:
     """Positive test weights of length 2n spread log-uniformly in [lo, hi]."""
     rng = np.random.default_rng(seed + 104729)
@@ -179,13 +187,21 @@ C4 = Workload("C4-1024x1024", 1024, 1024, 3.0, 10, 0.02, 16, -5.0, 0.0, 1, 40, 8
 C5 = Workload("C5-2048x2048", 2048, 2048, 4.0, 12, 0.03, 64, -6.0, 0.0, 8, 100, 8,
               seed=SEED_BASE + 50)
 
-WORKLOADS = {"C1": C1, "C2": C2, "C4": C4, "C5": C5}
+# Stand-in for the CT example of Section 8.3: an 82 x 82 piecewise-constant image,
+# parallel-beam projections at 1..135 degrees, 1 % noise, 20 shifts
+# gamma = lambda^2 with lambda log-spaced over 1e-4..1e1; principal dimension 30
+# and 8 local Ritz vectors (not stated for this example).
+CT82 = Workload("CT82-135deg", 82, 82, 1.0, 0, 0.01, 20, -8.0, 2.0, 3, 30, 8,
+                seed=SEED_BASE + 60, radon_angles=135)
+
+WORKLOADS = {"C1": C1, "C2": C2, "C4": C4, "C5": C5, "CT82": CT82}
 
 
 def tiny(height: int, width: int, sigma: float = 1.0, radius: int = 2, M: int = 6,
          p: int = 8, n_ritz_local: int = 3, K: int = 2, seed: int = SEED_BASE + 1,
          log_lo: float = -3.0, log_hi: float = 0.0, eta: float = 0.01,
-         tol: float = 1e-10) -> Workload:
+         tol: float = 1e-10, radon_angles: int = 0) -> Workload:
     """A small workload for dense-matrix checks (any image size, odd sizes allowed)."""
     return Workload(f"tiny-{height}x{width}", height, width, sigma, radius, eta, M,
-                    log_lo, log_hi, K, p, n_ritz_local, tol=tol, seed=seed)
+                    log_lo, log_hi, K, p, n_ritz_local, tol=tol, seed=seed,
+                    radon_angles=radon_angles)

@@ -4,7 +4,7 @@ synthetic inputs."""
 import numpy as np
 
 import synth
-from oracle.operator import Operator, make_data
+from oracle.operator import Operator, RadonOperator, make_data
 from oracle.recycle import Params
 
 
@@ -29,11 +29,17 @@ class Pair:
         from paper_2306_15049_gb300 import recyc
         from paper_2306_15049_gb300.workloads import desc_for
         self.wl = wl
-        self.op = Operator(wl.height, wl.width, wl.sigma, wl.radius)
+        if wl.radon_angles:
+            self.op = RadonOperator(wl.height, wl.width, wl.radon_angles)
+        else:
+            self.op = Operator(wl.height, wl.width, wl.sigma, wl.radius)
         x = synth.piecewise_constant_image(wl.height, wl.width, wl.seed)
         if x_image is not None:
             x = np.asarray(x_image, dtype=np.float64).reshape(wl.height, wl.width)
-        z = synth.noise_direction(wl.height, wl.width, wl.seed)
+        if wl.radon_angles:
+            z = synth.sinogram_noise(self.op.m, wl.seed)
+        else:
+            z = synth.noise_direction(wl.height, wl.width, wl.seed)
         self.x_true = x.reshape(-1)
         self.d, self.b = make_data(self.op, x, z, wl.eta)
         self.prm = Params.from_workload(wl, batched_local=bool(batched_local))
@@ -46,7 +52,7 @@ class Pair:
         dev = torch.device("cuda:0")
         xt = torch.tensor(self.x_true, dtype=torch.float64, device=dev)
         zt = torch.tensor(z.reshape(-1), dtype=torch.float64, device=dev)
-        dg = torch.empty_like(xt)
+        dg = torch.empty(self.d.shape[0], dtype=torch.float64, device=dev)
         ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
         recyc.rs_synthesize_data(self.desc[0], xt, zt, wl.eta, dg, ws)
         self.d_gpu = dg
