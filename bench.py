@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the differentiation measurement on the 1024x1024 workload")
     ap.add_argument("--profile-case", nargs="?", const="full", choices=["full", "small"],
                     help="run the workload once for a profiler and exit (small: every shift of "
                          "the first outer step on a random principal basis, 24 MINRES steps each)")
@@ -150,6 +152,63 @@ def clocks_stop(p, path):
             "samples": len(sm)}
 
 
+def adjoint_rate(precision, dev, reps=2):
+    """Differentiation workload (1024 x 1024, sigma 3, radius 10, 16 shifts): one
+    forward pass (k = 0 principal space and all shifted solves) plus the adjoint
+    solves on the same recycle space and d loss / d gamma, d loss / d w for the
+    loss sum_l ||x_l - x_true||^2. Returns forward+backward passes per second
+    (CUDA events, after one untimed pass) and the solve counts."""
+    import torch
+
+    import synth
+    from paper_2306_15049_gb300 import recyc
+    from paper_2306_15049_gb300.workloads import desc_for
+    wl = synth.C4
+    desc = desc_for(wl, precision=recyc.RS_MIXED if precision == "mixed" else recyc.RS_FP64)
+    x = torch.tensor(synth.piecewise_constant_image(wl.height, wl.width, wl.seed).reshape(-1),
+                     dtype=torch.float64, device=dev)
+    z = torch.tensor(synth.noise_direction(wl.height, wl.width, wl.seed).reshape(-1),
+                     dtype=torch.float64, device=dev)
+    d = torch.empty_like(x)
+    recyc.rs_synthesize_data(desc[0], x, z, wl.eta, d, torch.empty(1 << 20, dtype=torch.uint8, device=dev))
+    ws = torch.empty(recyc.rs_workspace_bytes(desc[0]), dtype=torch.uint8, device=dev)
+    w = torch.ones(2 * wl.n, dtype=torch.float64, device=dev)
+    X = torch.empty(wl.M, wl.n, dtype=torch.float64, device=dev)
+    G = torch.empty_like(X)
+    Lam = torch.empty_like(X)
+    dw = torch.empty(2 * wl.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def one():
+        P = recyc.Problem(desc, d, workspace=ws)
+        P.rs_set_weights(w)
+        P.rs_update_recycle(recyc.RS_INIT)
+        P.rs_solve_shifts(X)
+        torch.sub(X, x, out=G)
+        G.mul_(2.0)
+        st = P.rs_solve_adjoint(G, Lam)
+        dg = P.rs_shift_gradients(X, Lam, dw)
+        P.close()
+        return st, dg
+
+    one()
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        st, dg = one()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / reps
+    return {"value": 1000.0 / ms, "unit": "forward+adjoint gradient passes/s",
+            "ms_per_pass": ms, "precision": precision,
+            "workload": "1024x1024, sigma 3, radius 10, 16 shifts 1e-5..1, p=40, |J|=8, k=0; "
+                        "loss sum_l ||x_l - x_true||^2; gradients w.r.t. the 16 shifts and the 2n weights",
+            "adjoint_iters": sum(s_["iters"] for s_ in st),
+            "worst_adjoint_relres": max(s_["relres_true"] for s_ in st)}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -227,7 +286,8 @@ class Runner:
                 self.timing["phase_ms"][k] = self.timing["phase_ms"].get(k, 0.0) + v
         P.close()
         self.last = {"solves": solves, "matvecs": info["matvecs_total"], "worst_relres": worst,
-                     "iters": iters, "nc": info["nc"], "kernel_launches": info["kernel_launches"]}
+                     "iters": iters, "nc": info["nc"], "kernel_launches": info["kernel_launches"],
+                     "minres_kernel": info["minres_kernel"]}
         return self.last
 
 
@@ -372,12 +432,15 @@ def main():
     launches = max(1, tm["launches"][cat])
     avg_s = tm["ms"][cat] / 1000.0 / launches
     tname = "float" if args.precision == "mixed" else "double"
-    persist = os.environ.get("RS_PERSIST", "1") != "0" and wl.radius in (4, 6, 8, 10, 12)
+    mk = runner.last.get("minres_kernel", -1)
     if cat == 1:
         kname = "k_op_apply<double> (FP64 true / refinement residual matvec)"
-    elif persist:
-        kname = ("k_mr_persist<%s,%d> (one cooperative launch per solve: every MINRES step's "
-                 "direction update, (A+gamma E) v_j, projections and Lanczos update)" % (tname, wl.radius))
+    elif mk == 1:
+        kname = ("k_mr_resident<%s,%d> (one cooperative launch per solve, one CTA per 32x32 tile, "
+                 "two grid-wide barriers per MINRES step)" % (tname, wl.radius))
+    elif mk == 0:
+        kname = ("k_mr_persist<%s,%d> (one cooperative launch per solve, tiles streamed through "
+                 "memory)" % (tname, wl.radius))
     else:
         kname = ("k_mr_matvec<%s> (fused MINRES step: direction update, v_j, (A+gamma E) v_j, K^T y)"
                  % tname)
@@ -411,6 +474,8 @@ def main():
         "gpu_launches": int(launches_timed), "clocks": clocks, "roofline": roof, "e2e": e2e,
     }
 
+    if not args.no_adjoint and world == 1:
+        line["adjoint_C4"] = {"mixed": adjoint_rate("mixed", dev), "fp64": adjoint_rate("fp64", dev, reps=1)}
     if not args.no_fp64_compare and args.precision == "mixed":
         r64 = Runner(wl, "fp64", dev)
         r64.step()
