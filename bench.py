@@ -33,6 +33,10 @@ if ROOT not in sys.path:
 
 METRIC = "shifted solves/sec & matvecs/sec at rel. residual 1e-8; HBM GB/s vs roofline"
 FP64_PEAK_GFLOPS = 152 * 2070e6 * 4 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2070 MHz (nominal 1.25 TF)
+# DRAM bytes (read + write) per MINRES step of k_mr_resident<float, 8> on a 512 x 512
+# image, from one ncu capture of 24-step launches (profiles/k_mr_resident_float_r8_512x512.md:
+# 15.78 MB + 0.04 MB per launch); scaled to a launch by its steps
+MR_RESIDENT_DRAM_BYTES_PER_STEP = {(512, 512, 8, "float"): (15.78e6 + 0.04e6) / 24}
 
 
 def parse():
@@ -444,10 +448,14 @@ def main():
     else:
         kname = ("k_mr_matvec<%s> (fused MINRES step: direction update, v_j, (A+gamma E) v_j, K^T y)"
                  % tname)
+    traffic = None
+    per_step = MR_RESIDENT_DRAM_BYTES_PER_STEP.get((wl.height, wl.width, wl.radius, tname))
+    if cat == 0 and mk == 1 and per_step is not None:
+        traffic = per_step * tm["pixels"][0] / wl.n / launches
     if cat == 0 and args.precision == "mixed":
         achieved = tm["bytes"][cat] / (tm["ms"][cat] / 1000.0) / 1e9
         roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": tm["bytes"][cat] / launches}
     else:
@@ -456,6 +464,9 @@ def main():
                 "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
                 "traffic": None, "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2070 MHz",
                 "algorithmic_flops_per_launch": tm["flops"][cat] / launches}
+    if traffic is not None:
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of 24-step launches "
+                                  "of the same kernel, scaled by the timed launches' steps per launch")
     roof["launches"] = tm["launches"][cat]
     roof["avg_launch_us"] = avg_s * 1e6
     roof["kernel_time_share_of_step"] = tm["ms"][cat] / ms if ms > 0 else None
