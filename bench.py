@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-local-space measurement of the same workload")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiation measurement on the 1024x1024 workload")
     ap.add_argument("--profile-case", nargs="?", const="full", choices=["full", "small"],
@@ -213,6 +215,82 @@ def adjoint_rate(precision, dev, reps=2):
             "worst_adjoint_relres": max(s_["relres_true"] for s_ in st)}
 
 
+def batched_images_rate(precision, dev, reps=2):
+    """Batched workload: the four images of uneven size (256^2 .. 1024^2, sigma
+    1.5 .. 3, radius 4 .. 10), 32 shifts each, batched local spaces; one outer step
+    (k = 0) of all four solved jointly (every shift of every image in one
+    persistent launch) against the four solved one after another. Returns
+    solves per second of both (CUDA events, after one untimed pass)."""
+    import torch
+
+    import synth
+    from paper_2306_15049_gb300 import recyc
+    from paper_2306_15049_gb300.workloads import desc_for
+    prec = recyc.RS_MIXED if precision == "mixed" else recyc.RS_FP64
+    items = []
+    for wl in synth.C3:
+        desc = desc_for(wl, precision=prec, batched_local=1)
+        x = torch.tensor(synth.piecewise_constant_image(wl.height, wl.width, wl.seed).reshape(-1),
+                         dtype=torch.float64, device=dev)
+        z = torch.tensor(synth.noise_direction(wl.height, wl.width, wl.seed).reshape(-1),
+                         dtype=torch.float64, device=dev)
+        d = torch.empty_like(x)
+        recyc.rs_synthesize_data(desc[0], x, z, wl.eta, d, torch.empty(1 << 20, dtype=torch.uint8, device=dev))
+        ws = torch.empty(recyc.rs_workspace_bytes(desc[0]), dtype=torch.uint8, device=dev)
+        X = torch.empty(wl.M, wl.n, dtype=torch.float64, device=dev)
+        w = torch.ones(2 * wl.n, dtype=torch.float64, device=dev)
+        items.append((wl, desc, d, ws, X, w))
+    stream = torch.cuda.current_stream(dev)
+
+    def one(joint):
+        probs = []
+        for wl, desc, d, ws, X, w in items:
+            P = recyc.Problem(desc, d, workspace=ws)
+            P.rs_set_weights(w)
+            P.rs_update_recycle(recyc.RS_INIT)
+            probs.append(P)
+        if joint:
+            st = recyc.rs_solve_shifts_batched(probs, [it[4] for it in items])
+        else:
+            st = [P.rs_solve_shifts(it[4]) for P, it in zip(probs, items)]
+        for P in probs:
+            P.close()
+        return st
+
+    out = {}
+    for joint in (True, False):
+        one(joint)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            st = one(joint)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / reps
+        solves = sum(len(x) for x in st)
+        out["joint" if joint else "one_by_one"] = {
+            "value": solves / (ms / 1000.0), "unit": "solves/s", "ms_per_step": ms,
+            "worst_true_relres": max(s_["relres_true"] for x in st for s_ in x)}
+    out["workload"] = ("images 256^2, 384^2, 512^2, 1024^2 (sigma 1.5, 2, 2.5, 3; radius 4, 6, 8, 10), "
+                       "32 shifts 1e-5..1 each, p=40, |J|=8, batched local spaces, k=0; a step = "
+                       "principal spaces of the four images + all 128 shifted solves")
+    out["precision"] = precision
+    return out
+
+
+def reduce_over_ranks(dist, ms, counts, device):
+    """Whole-job aggregation of the replicas: the slowest rank's time (max over
+    ranks) and the work of all ranks (sum of the counts)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(v) for v in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t.item()), [int(round(v)) for v in c.tolist()]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -224,7 +302,7 @@ def measured_peaks():
 class Runner:
     """One replica of the workload on one GPU, through the C ABI."""
 
-    def __init__(self, wl, precision, dev):
+    def __init__(self, wl, precision, dev, batched_local=0):
         import numpy as np
         import torch
 
@@ -232,7 +310,8 @@ class Runner:
         from paper_2306_15049_gb300 import recyc
         from paper_2306_15049_gb300.workloads import desc_for
         self.torch, self.recyc, self.wl, self.dev = torch, recyc, wl, dev
-        self.desc = desc_for(wl, precision=recyc.RS_MIXED if precision == "mixed" else recyc.RS_FP64)
+        self.desc = desc_for(wl, precision=recyc.RS_MIXED if precision == "mixed" else recyc.RS_FP64,
+                             batched_local=batched_local)
         x = synth.piecewise_constant_image(wl.height, wl.width, wl.seed).reshape(-1)
         z = synth.noise_direction(wl.height, wl.width, wl.seed).reshape(-1)
         xt = torch.tensor(x, dtype=torch.float64, device=dev)
@@ -408,12 +487,7 @@ def main():
     launches_timed = runner.last["kernel_launches"] - launches_before
     run_stats = dict(runner.last)
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        cnt = torch.tensor([solves, mvs], dtype=torch.float64, device=dev)
-        dist.all_reduce(cnt)
-        solves, mvs = int(cnt[0].item()), int(cnt[1].item())
+        ms, (solves, mvs) = reduce_over_ranks(dist, ms, [solves, mvs], dev)
     ms_per_step = ms / args.steps
     value = solves / (ms / 1000.0)
 
@@ -421,10 +495,7 @@ def main():
     runner.step(e2e=True)
     e_ms, e_solves, _ = timed(runner, args.steps, flush, e2e=True)
     if dist:
-        t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-        e_solves *= world
+        e_ms, (e_solves,) = reduce_over_ranks(dist, e_ms, [e_solves], dev)
     e2e = {"value": e_solves / (e_ms / 1000.0), "unit": "solves/s",
            "h2d_bytes_per_step": 8 * (wl.n + 2 * wl.n),
            "d2h_bytes_per_step": 8 * wl.K * wl.M * wl.n}
@@ -439,6 +510,9 @@ def main():
     mk = runner.last.get("minres_kernel", -1)
     if cat == 1:
         kname = "k_op_apply<double> (FP64 true / refinement residual matvec)"
+    elif mk == 3:
+        kname = ("k_mr_batch<%s,%d> (one cooperative launch for all shifts of a step, "
+                 "convergence masks)" % (tname, wl.radius))
     elif mk == 1:
         kname = ("k_mr_resident<%s,%d> (one cooperative launch per solve, one CTA per 32x32 tile, "
                  "two grid-wide barriers per MINRES step)" % (tname, wl.radius))
@@ -485,6 +559,21 @@ def main():
         "gpu_launches": int(launches_timed), "clocks": clocks, "roofline": roof, "e2e": e2e,
     }
 
+    if not args.no_batched:
+        # the same workload with batched local spaces: all 16 shifts of a step in
+        # one cooperative launch (convergence masks), against the shift-by-shift path
+        rb = Runner(wl, args.precision, dev, batched_local=1)
+        rb.step()
+        b_ms, b_solves, b_mvs = timed(rb, max(1, args.steps), flush)
+        line["batched_local"] = {"value": b_solves / (b_ms / 1000.0), "unit": "solves/s",
+                                 "ms_per_step": b_ms / max(1, args.steps),
+                                 "matvecs_per_s": b_mvs / (b_ms / 1000.0),
+                                 "worst_true_relres": rb.last["worst_relres"],
+                                 "iters_per_step": rb.last["iters"],
+                                 "variant": "local spaces [W, g^(k-1,l), g^(k-1,l-1)]; every shift "
+                                            "of a step in one persistent cooperative launch"}
+    if not args.no_batched and world == 1:
+        line["batched_images_C3"] = batched_images_rate(args.precision, dev)
     if not args.no_adjoint and world == 1:
         line["adjoint_C4"] = {"mixed": adjoint_rate("mixed", dev), "fp64": adjoint_rate("fp64", dev, reps=1)}
     if not args.no_fp64_compare and args.precision == "mixed":

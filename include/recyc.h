@@ -122,9 +122,10 @@ typedef struct {
   long long matvecs_overhead; /* principal-space construction and images */
   int ld;                  /* leading dimension of device blocks (elements) */
   long long kernel_launches; /* CUDA kernels launched by the library in this process */
-  int minres_kernel;       /* kernel of the last persistent MINRES solve: 1 one CTA per tile,
-                              vectors in registers; 0 tiles streamed through memory (not all
-                              co-resident); -1 none yet (step kernels only) */
+  int minres_kernel;       /* kernel of the last persistent MINRES solve: 3 all shifts of a
+                              batched_local step in one launch; 1 one CTA per tile, vectors in
+                              registers; 0 tiles streamed through memory (not all co-resident);
+                              -1 none yet (step kernels only) */
 } rs_info;
 
 /* Per-kernel device time, gathered with CUDA events around every launch of
@@ -212,6 +213,25 @@ rs_status rs_solve_adjoint(rs_problem* prob, const double* G_dev, double* Lam_de
  * Deterministic (fixed-order reductions). Synchronises the problem's stream. */
 rs_status rs_shift_gradients(rs_problem* prob, const double* X_dev, const double* Lam_dev,
                              double* dgamma_host, double* dw_dev);
+
+/* Bytes of 256-byte aligned device scratch rs_solve_shifts_batched needs for
+ * `count` problems with `total_shifts` shifts together (0 if invalid). */
+size_t rs_batch_scratch_bytes(int count, int total_shifts);
+
+/* The current step of several problems (e.g. images of different sizes, each
+ * with its own blur, weights and shifts) solved together: every problem must
+ * have batched_local = 1 (its local spaces [W, g^(k-1,l), g^(k-1,l-1)] make its
+ * shifts independent), the blur operator with radius 4, 6, 8, 10 or 12, the same
+ * precision and the same stream, and a current recycle space (rs_update_recycle).
+ * All shifts of all problems advance in one persistent cooperative launch with
+ * per-shift convergence masks (relaunched on more CTAs per shift as shifts
+ * finish; the last two continue one at a time), then each problem's solutions,
+ * refinement sweeps (RS_MIXED) and hand-over to its next step are as in
+ * rs_solve_shifts. X_dev[i]: problem i's M x n solutions; stats_host[i] may be
+ * NULL (or stats_host itself). Errors: rs_last_error(NULL). */
+rs_status rs_solve_shifts_batched(rs_problem* const* probs, int count, double* const* X_dev,
+                                  rs_solve_stats* const* stats_host, void* scratch_dev,
+                                  size_t scratch_bytes);
 
 /* Initial guesses of Eq. orthupdate for all shifts (after update_recycle):
  * X0_dev and R0_dev receive M x n doubles each (x0 and r0 = b - Op x0). */

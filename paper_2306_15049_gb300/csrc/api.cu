@@ -33,6 +33,7 @@ constexpr int kPoll = 8;                   // MINRES steps between stop-flag pol
 constexpr int kMaxSweeps = 12;             // FP64 refinement sweeps (mixed precision)
 constexpr double kInnerRho = 1e-4;         // inner relative reduction per sweep (mixed)
 constexpr int kDotStride = kMaxLocal + 1;
+constexpr int kBatchTail = 2;               // batched solves: the last shifts run one by one
 constexpr int kChunk = 6;                  // MINRES steps per CUDA-graph replay (a multiple of 3)
 
 long round_up(long x, long a) { return (x + a - 1) / a * a; }
@@ -246,6 +247,20 @@ struct rs_problem {
   double *arec = nullptr, *brec = nullptr, *lc = nullptr;
   // oblique guesses with two anchors (Eq. updates): per anchor R_a, K_a^T E U_a, K_a^T b
   void* Kan = nullptr;
+  // batched solves (batched_local = 1): every shift's local space, MINRES vectors
+  // and state at once, for one cooperative launch over all shifts
+  bool use_batch = true;
+  void *KlB = nullptr, *vecB = nullptr;
+  double *RkB = nullptr, *R0B = nullptr, *KtrB = nullptr, *scalB = nullptr, *zcB = nullptr;
+  int *cntB = nullptr, *keptB = nullptr, *sysidxB = nullptr, *stopfB = nullptr;
+  MinresState* stB = nullptr;
+  void* sysB = nullptr;
+  std::vector<char> sys_host;
+  double* taps_dev = nullptr;          // blur taps centred at kTapsCentre (batched kernel)
+  std::vector<double> taps_host;
+  std::vector<int> idx_host;
+  std::vector<MinresState> st_host;
+  int last_batch_launches = 0;
   // Radon forward operator: (cos, sin) table and the sinogram buffer of op_apply
   double* radon_cs = nullptr;
   double* sino = nullptr;
@@ -398,6 +413,22 @@ void carve(rs_problem* P, Carver& cv) {
   P->partials_a = cv.take<double>((size_t)mr_matvec_blocks(P->d.height, P->d.width) * (kMaxLocal + 1));
   P->partials_p = cv.take<double>((size_t)kPersistMaxBlocks * (kMaxLocal + 2));
   P->gbar = cv.take<GridBar>(1);
+  if (P->d.batched_local) {
+    P->KlB = vec((long)z.M * z.smax * z.ld);
+    P->vecB = vec((long)z.M * 9 * z.ld);
+    P->RkB = cv.take<double>((size_t)z.M * kMaxLocal * kMaxLocal);
+    P->R0B = cv.take<double>((size_t)z.M * z.ld);
+    P->KtrB = cv.take<double>((size_t)z.M * kMaxLocal);
+    P->scalB = cv.take<double>((size_t)z.M);
+    P->zcB = cv.take<double>((size_t)z.M * kMaxLocal);
+    P->cntB = cv.take<int>((size_t)z.M);
+    P->keptB = cv.take<int>((size_t)z.M * kMaxLocal);
+    P->sysidxB = cv.take<int>((size_t)z.M);
+    P->stopfB = cv.take<int>((size_t)z.M);
+    P->stB = cv.take<MinresState>((size_t)z.M);
+    P->sysB = cv.take<MrBatchSys<double>>((size_t)z.M);
+    P->taps_dev = cv.take<double>(2 * kMaxTaps);
+  }
   if (P->d.radon_angles > 0) {
     P->radon_cs = cv.take<double>(2 * (size_t)P->d.radon_angles);
     P->sino = cv.take<double>(z.ldm);
@@ -428,6 +459,14 @@ void carve(rs_problem* P, Carver& cv) {
     if (_e != cudaSuccess)                                                              \
       return (rs_status)P->set_err(RS_ECUDA, "CUDA error %s at %s:%d",                 \
                                    cudaGetErrorString(_e), __FILE__, __LINE__);         \
+  } while (0)
+// CU with the error recorded on the first problem of a multi-problem call
+#define CU0(...)                                                                        \
+  do {                                                                                  \
+    cudaError_t _e = (__VA_ARGS__);                                                     \
+    if (_e != cudaSuccess)                                                              \
+      return (rs_status)ws[0].P->set_err(RS_ECUDA, "CUDA error %s at %s:%d",           \
+                                         cudaGetErrorString(_e), __FILE__, __LINE__);   \
   } while (0)
 #define RS(...)                     \
   do {                              \
@@ -1255,6 +1294,411 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
 
 }  // namespace
 
+// The shifted solves of the current step with batched local spaces
+// [W, g^(k-1,l), g^(k-1,l-1)] (batched_local = 1): the shifts no longer depend
+// on one another within the step, so every shift's initial guess and local
+// space are built first and all recycled MINRES solves advance together in
+// one cooperative launch (k_mr_batch; per-shift convergence masks), possibly
+// together with the shifts of other problems (other images). When fewer than
+// half of a launch's shifts are still running, the rest continue in a new
+// launch with more CTAs each; the last kBatchTail continue one at a time in the
+// one-CTA-per-tile kernel. In mixed precision the shifts that miss the
+// tolerance after a sweep are refined together in the next sweep.
+
+// Per-problem bookkeeping of a batched solve.
+template <typename T>
+struct BatchWork {
+  rs_problem* P = nullptr;
+  double* X = nullptr;
+  int base = 0;                     // first index of this problem's shifts in the system array
+  std::vector<rs_solve_stats> st;
+  std::vector<PtrList> cand;
+  std::vector<int> run;             // shifts that go to MINRES in this sweep
+  std::vector<double> rnorm2, inner;
+  std::vector<int> sdim;
+  std::vector<char> gnz;
+};
+
+// Device buffers of the joint launches.
+struct BatchScratch {
+  void* sys;            // MrBatchSys entries of every problem (at each problem's base)
+  int* sysidx;
+  int* stopf;
+  double* part;         // kPersistMaxBlocks x (kMaxLocal + 2)
+  GridBar* gbar;
+  cudaStream_t s;
+};
+
+template <typename T> T* bvec(rs_problem* P, int l, int k) {
+  return vp<T>(P->vecB) + ((long)l * 9 + k) * P->z.ld;
+}
+template <typename T> T* bkl(rs_problem* P, int l) {
+  return vp<T>(P->KlB) + (long)l * P->z.smax * P->z.ld;
+}
+
+// Initial guesses, the shifts that need MINRES, their local spaces and the
+// problem's MrBatchSys entries (host copy in P->sys_host).
+template <typename T>
+int batch_prepare(BatchWork<T>& bw) {
+  rs_problem* P = bw.P;
+  double* X = bw.X;
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  cudaStream_t s = P->s;
+  const int nc = P->nc, M = z.M;
+  const int J = std::min(z.J, nc);
+  T* Ut = vp<T>(P->Ut);
+  T* Bc = vp<T>(P->Bc);
+  T* wT = vp<T>(P->mixed ? P->wT : (void*)P->w64);
+  const double tol_abs = P->d.tol * P->bnorm;
+  bw.st.assign(M, rs_solve_stats{});
+  bw.cand.assign(M, PtrList{});
+  bw.run.clear();
+  bw.rnorm2.assign(M, 0.0);
+  bw.inner.assign(M, 0.0);
+  bw.sdim.assign(M, 0);
+  bw.gnz.assign(M, 0);
+  double ph0 = phase_begin(P);
+  for (int l = 0; l < M; ++l) {
+    double* x = X + (long)l * n;
+    double* r = P->R0B + (long)l * ld;
+    CU(gemm_ts<T, double>(Ut, ld, nc, P->C + (long)l * nc, nc, 1, 0.0, x, n, n, s));
+    CU(cudaMemcpyAsync(r, P->b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(gemm_ts<T, double>(vp<T>(P->AU), ld, nc, P->CA + (long)l * nc, nc, 1, 1.0, r, ld, n, s));
+    CU(gemm_ts<T, double>(vp<T>(P->EU), ld, nc, P->CE + (long)l * nc, nc, 1, 1.0, r, ld, n, s));
+    CU(norm2_partials<double>(r, n, P->partials, s));
+    CU(reduce_partials(P->partials, z.G, 1, 1, P->scalB + l, s, nullptr, 0, nullptr));
+  }
+  RS(read_back(P, bw.rnorm2.data(), P->scalB, M * sizeof(double)));
+  for (int l = 0; l < M; ++l) {
+    rs_solve_stats& sl = bw.st[l];
+    sl.relres0 = std::sqrt(bw.rnorm2[l]) / P->bnorm;
+    if (sl.relres0 <= P->d.tol) {
+      phase_end(P, 3, ph0);
+      RS(true_residual(P, P->gammas[l], X + (long)l * n, &sl.relres_true));
+      sl.matvecs = 1;
+      ph0 = phase_begin(P);
+      if (!P->mixed || sl.relres_true <= P->d.tol) {
+        CU(cudaMemsetAsync(vp<T>(P->Gcur) + (long)l * ld, 0, n * sizeof(T), s));
+        sl.relres_est = sl.relres0;
+        continue;
+      }
+      // the FP64 residual of a mixed-precision guess decides
+      sl.relres0 = sl.relres_true;
+      bw.rnorm2[l] = sl.relres_true * sl.relres_true * P->bnorm * P->bnorm;
+      CU(cudaMemcpyAsync(P->R0B + (long)l * ld, P->r64, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    bw.run.push_back(l);
+  }
+  for (int l : bw.run) {
+    const double gl = P->gammas[l];
+    const bool left = (l + 1) <= P->d.I_split;
+    T* Wv = vp<T>(left ? P->WL : P->WR);
+    int ncand = 0;
+    if (J > 0) {
+      CU(cudaMemcpyAsync(Bc, left ? P->AWL : P->AWR, (size_t)J * ld * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      CU(axpby<T, T>(vp<T>(left ? P->EWL : P->EWR), gl, Bc, 1.0, (long)J * ld, s));
+      for (int j = 0; j < J; ++j) bw.cand[l].p[ncand++] = Wv + (long)j * ld;
+    }
+    const T* gold = (P->have_prev && P->gprev_nz[l]) ? vp<T>(P->Gprev) + (long)l * ld : nullptr;
+    const T* gnew = (P->have_prev && l >= 1 && P->gprev_nz[l - 1]) ? vp<T>(P->Gprev) + (long)(l - 1) * ld : nullptr;
+    if (gold && gnew) {
+      CU(multidot<T>(gold, 0, nullptr, 1, nullptr, gnew, n, P->partials, 3, s, nullptr));
+      CU(multidot<T>(gold, 0, nullptr, 1, nullptr, gold, n, P->partials + 1, 3, s, nullptr));
+      CU(multidot<T>(gnew, 0, nullptr, 1, nullptr, gnew, n, P->partials + 2, 3, s, nullptr));
+      CU(reduce_partials(P->partials, z.G, 3, 3, P->scal + 11, s, nullptr, 0, nullptr));
+      k_cosine<<<1, 32, 0, s>>>(P->scal + 11, P->scal + 14);
+      CU(launched());
+      double cs = 0.0;
+      RS(read_back(P, &cs, P->scal + 14, sizeof cs));
+      if (cs > kAngleCos) gold = nullptr;
+    }
+    for (const T* gv : {gold, gnew}) {
+      if (!gv) continue;
+      CU(op_apply<T>(gv, ld, 1, wT, Bc + (long)ncand * ld, nullptr, ld, P->d.height, P->d.width,
+                     P->tp, gl, 0, s));
+      bw.cand[l].p[ncand++] = gv;
+      bw.st[l].matvecs += 1;
+      P->mv_total += 1;
+    }
+    CgsCtx c = cgs_ctx(P, kMaxLocal, P->Rk, nullptr, 0, kLocalDrop);
+    RS(cgs2_all<T>(P, c, bkl<T>(P, l), Bc, ncand, false));
+    RS(coop_check(P));
+    CU(cudaMemcpyAsync(P->cntB + l, P->cnt, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(P->keptB + (long)l * kMaxLocal, P->kept, kMaxLocal * sizeof(int),
+                       cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(P->RkB + (long)l * kMaxLocal * kMaxLocal, P->Rk,
+                       (size_t)kMaxLocal * kMaxLocal * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  if (!bw.run.empty()) {
+    std::vector<int> tmp(M);
+    RS(read_back(P, tmp.data(), P->cntB, M * sizeof(int)));
+    for (int l : bw.run) bw.sdim[l] = tmp[l];
+  }
+  phase_end(P, 3, ph0);
+  for (int l : bw.run)
+    bw.inner[l] = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * std::sqrt(bw.rnorm2[l])) : tol_abs;
+  P->sys_host.assign((size_t)M * sizeof(MrBatchSys<T>), 0);
+  MrBatchSys<T>* sh = reinterpret_cast<MrBatchSys<T>*>(P->sys_host.data());
+  for (int l = 0; l < M; ++l) {
+    sh[l].st = P->stB + l;
+    sh[l].w = wT;
+    sh[l].vzero = vp<T>(P->vzero);
+    sh[l].taps = P->taps_dev;
+    sh[l].H = P->d.height;
+    sh[l].W = P->d.width;
+    sh[l].u = bvec<T>(P, l, 0);
+    sh[l].y = bvec<T>(P, l, 1);
+    sh[l].xm = bvec<T>(P, l, 2);
+    sh[l].K = bkl<T>(P, l);
+    sh[l].ldk = ld;
+    for (int i = 0; i < 3; ++i) {
+      sh[l].vring[i] = bvec<T>(P, l, 3 + i);
+      sh[l].dring[i] = bvec<T>(P, l, 6 + i);
+    }
+    sh[l].gamma = P->gammas[l];
+  }
+  CU(cudaMemsetAsync(P->vzero, 0, n * sizeof(T), s));
+  P->st_host.assign(M, MinresState{});
+  return RS_OK;
+}
+
+// MINRES start of every running shift: u = (I - K_l K_l^T) r, xi, K_l^T r.
+template <typename T>
+int batch_sweep_init(BatchWork<T>& bw) {
+  rs_problem* P = bw.P;
+  const long n = P->z.n, ld = P->z.ld;
+  cudaStream_t s = P->s;
+  for (int l : bw.run) {
+    T* u = bvec<T>(P, l, 0);
+    const int* cnt = P->cntB + l;
+    CU((convert<double, T>(P->R0B + (long)l * ld, u, n, s)));
+    CU(multidot<T>(bkl<T>(P, l), ld, cnt, 0, nullptr, u, n, P->partials, kDotStride, s, nullptr));
+    CU(reduce_partials(P->partials, P->z.G, kMaxLocal, kDotStride, P->KtrB + (long)l * kMaxLocal, s, cnt, 0, nullptr));
+    CU(multi_axpy<T>(bkl<T>(P, l), ld, cnt, 0, P->KtrB + (long)l * kMaxLocal, -1.0, u, n, P->partials, s, nullptr));
+    CU(reduce_partials(P->partials, P->z.G, 1, 1, P->scalB + l, s, nullptr, 0, nullptr));
+    CU(minres_init(P->stB + l, P->scalB + l, P->KtrB + (long)l * kMaxLocal, cnt, bw.inner[l], P->d.maxit, s));
+    CU(cudaMemsetAsync(bvec<T>(P, l, 2), 0, n * sizeof(T), s));
+    for (int i = 0; i < 3; ++i) CU(cudaMemsetAsync(bvec<T>(P, l, 6 + i), 0, n * sizeof(T), s));
+  }
+  return RS_OK;
+}
+
+// Joint launches over the running shifts of every problem until all stopped.
+// Launch time is recorded in the first problem's timing.
+template <typename T>
+int batch_run(std::vector<BatchWork<T>>& ws, const BatchScratch& sc, int capacity, int R) {
+  rs_problem* P0 = ws[0].P;
+  cudaStream_t s = sc.s;
+  struct Mem { int w, l; };
+  std::vector<Mem> live;
+  for (int i = 0; i < (int)ws.size(); ++i)
+    for (int l : ws[i].run) live.push_back({i, l});
+  bool first_launch = true;
+  std::vector<int> idx;
+  while (!live.empty()) {
+    const int B = (int)live.size();
+    if (B <= kBatchTail) {
+      // the last few shifts: each continues alone in the one-CTA-per-tile
+      // kernel (vectors in registers), from the step and state the batch left
+      for (const Mem& m : live) {
+        rs_problem* P = ws[m.w].P;
+        const int l = m.l;
+        const long n = P->z.n, ld = P->z.ld;
+        if (!P->use_persist) return P->set_err(RS_ECUDA, "batched solve without the persistent kernels");
+        MrP<T> mp{};
+        mp.u = bvec<T>(P, l, 0); mp.y = bvec<T>(P, l, 1); mp.xm = bvec<T>(P, l, 2);
+        mp.K = bkl<T>(P, l); mp.ldk = ld; mp.w = vp<T>(P->mixed ? P->wT : (void*)P->w64);
+        mp.gamma = P->gam + l;
+        mp.vzero = vp<T>(P->vzero); mp.Vkeep = nullptr; mp.ld = ld; mp.keep = 0;
+        for (int i = 0; i < 3; ++i) { mp.vring[i] = bvec<T>(P, l, 3 + i); mp.dring[i] = bvec<T>(P, l, 6 + i); }
+        mp.partA = P->partials_p;
+        mp.partB = P->partials_p + (long)kPersistMaxBlocks * (kMaxLocal + 1);
+        mp.j0 = first_launch ? 1 : P->st_host[l].next_j;
+        const int it_before = first_launch ? 0 : P->st_host[l].iters;
+        CU(cudaMemsetAsync(P->gbar, 0, sizeof(GridBar), P->s));
+        const int slot = timed_begin(P);
+        int G = 0, resident = 0;
+        CU(mr_persist<T>(P->stB + l, mp, P->d.height, P->d.width, P->tp, P->gbar,
+                         std::max(ws[m.w].sdim[l], 1), P->s, &G, &resident));
+        timed_end(P, slot, 0, -1, 0, 0.0, 0.0);
+        RS(read_back(P, &P->st_host[l], P->stB + l, sizeof(MinresState)));
+        RS(coop_check(P));
+        const long dsteps = std::max(0, P->st_host[l].iters - it_before);
+        if (slot >= 0) {
+          auto& rec = P->pending[slot];
+          rec.pixels = dsteps * n;
+          rec.bytes = (double)dsteps * (15 + 2 * ws[m.w].sdim[l]) * n * sizeof(T);
+          rec.flops = (double)dsteps * (8.0 * (2 * P->tp.r + 1) + 18.0 + 4.0 * ws[m.w].sdim[l]) * n;
+        }
+        timed_flush(P, 1);
+        P->last_resident = 3;
+      }
+      break;
+    }
+    const int gper = std::max(1, capacity / B);
+    idx.resize(B);
+    for (int i = 0; i < B; ++i) idx[i] = ws[live[i].w].base + live[i].l;
+    CU0(cudaMemcpyAsync(sc.sysidx, idx.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    CU0(cudaMemsetAsync(sc.stopf, 0, B * sizeof(int), s));
+    CU0(cudaMemsetAsync(sc.gbar, 0, sizeof(GridBar), s));
+    MrBatch<T> bt{};
+    bt.sys = reinterpret_cast<const MrBatchSys<T>*>(sc.sys);
+    bt.sysidx = sc.sysidx;
+    bt.B = B;
+    bt.gper = gper;
+    bt.min_active = (gper * 2 <= capacity) ? (B + 1) / 2 : 0;
+    bt.part = sc.part;
+    bt.stopf = sc.stopf;
+    std::vector<int> it0(B, 0);   // steps before this launch (0: minres_init just ran)
+    if (!first_launch)
+      for (int i = 0; i < B; ++i) it0[i] = ws[live[i].w].P->st_host[live[i].l].iters;
+    first_launch = false;
+    const int slot = timed_begin(P0);
+    int launched_g = 0;
+    CU0(mr_batch<T>(bt, R, sc.gbar, s, &launched_g));
+    timed_end(P0, slot, 0, -1, 0, 0.0, 0.0);
+    // states of every problem involved
+    for (auto& w : ws)
+      RS(read_back(w.P, w.P->st_host.data(), w.P->stB, w.P->z.M * sizeof(MinresState)));
+    int gerr = 0;
+    if (read_back(P0, &gerr, &sc.gbar->err, sizeof gerr)) return RS_ECUDA;
+    if (gerr) return P0->set_err(RS_ECUDA, "batched MINRES kernel: grid barrier timed out (code %d)", gerr);
+    long steps = 0;
+    double sbytes = 0.0;
+    std::vector<Mem> next;
+    for (int i = 0; i < B; ++i) {
+      const BatchWork<T>& w = ws[live[i].w];
+      const MinresState& m = w.P->st_host[live[i].l];
+      const long dsteps = std::max(0, m.iters - it0[i]);
+      steps += dsteps;
+      sbytes += (double)dsteps * (15 + 2 * w.sdim[live[i].l]) * w.P->z.n * sizeof(T);
+      if (!m.stop) next.push_back(live[i]);
+      w.P->last_resident = 3;
+    }
+    if (slot >= 0) {
+      auto& rec = P0->pending[slot];
+      rec.pixels = steps * P0->z.n;
+      rec.bytes = sbytes;
+      rec.flops = 0.0;
+    }
+    timed_flush(P0, 1);
+    if (next.size() == live.size() && bt.min_active == 0)
+      return P0->set_err(RS_ECUDA, "batched MINRES launch returned with every shift running");
+    live.swap(next);
+  }
+  return RS_OK;
+}
+
+// Assembly g = V_m y + U_l R_l^{-1} z, x += g, FP64 true residual; the shifts
+// that still miss the tolerance (mixed precision) form the next sweep's run.
+template <typename T>
+int batch_assemble(BatchWork<T>& bw, int sw) {
+  rs_problem* P = bw.P;
+  const long n = P->z.n, ld = P->z.ld;
+  cudaStream_t s = P->s;
+  const double tol_abs = P->d.tol * P->bnorm;
+  std::vector<int> again;
+  for (int l : bw.run) {
+    const MinresState& m = P->st_host[l];
+    rs_solve_stats& sl = bw.st[l];
+    T* xm = bvec<T>(P, l, 2);
+    sl.iters += m.iters;
+    sl.matvecs += m.iters;
+    P->mv_total += m.iters;
+    sl.relres_est = std::fabs(m.eta) / P->bnorm;
+    sl.sweeps = sw + 1;
+    sl.local_dim = bw.sdim[l];
+    if (bw.sdim[l] > 0) {
+      CU(tri_solve_upper(P->RkB + (long)l * kMaxLocal * kMaxLocal, kMaxLocal, P->cntB + l,
+                         P->stB[l].z, P->zcB + (long)l * kMaxLocal, s));
+      CU(gather_axpy<T>(bw.cand[l], P->keptB + (long)l * kMaxLocal, P->cntB + l,
+                        P->zcB + (long)l * kMaxLocal, xm, n, s));
+    }
+    double* x = bw.X + (long)l * n;
+    CU(axpby<T, double>(xm, 1.0, x, 1.0, n, s));
+    T* gl_buf = vp<T>(P->Gcur) + (long)l * ld;
+    if (sw == 0) CU(cudaMemcpyAsync(gl_buf, xm, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    else CU(axpby<T, T>(xm, 1.0, gl_buf, 1.0, n, s));
+    RS(true_residual(P, P->gammas[l], x, &sl.relres_true));
+    sl.matvecs += 1;
+    bw.gnz[l] = 1;
+    if (P->mixed && sl.relres_true > P->d.tol) {
+      CU(cudaMemcpyAsync(P->R0B + (long)l * ld, P->r64, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      bw.inner[l] = std::max(0.5 * tol_abs, kInnerRho * sl.relres_true * P->bnorm);
+      again.push_back(l);
+    }
+  }
+  bw.run.swap(again);
+  return RS_OK;
+}
+
+// Statuses, stats, and the hand-over to the next outer step.
+template <typename T>
+int batch_finish(BatchWork<T>& bw, rs_solve_stats* stats) {
+  rs_problem* P = bw.P;
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  int any_noconv = 0;
+  for (int l = 0; l < z.M; ++l) {
+    rs_solve_stats& sl = bw.st[l];
+    sl.status = (sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) && sl.iters >= P->d.maxit)
+                    ? RS_ENOCONV : RS_OK;
+    if (sl.status == RS_ENOCONV) any_noconv = 1;
+    if (stats) stats[l] = sl;
+  }
+  CU(cudaMemcpy2DAsync(P->Xprev, ld * sizeof(double), bw.X, n * sizeof(double), n * sizeof(double), z.M,
+                       cudaMemcpyDeviceToDevice, P->s));
+  std::swap(P->Gcur, P->Gprev);
+  P->gprev_nz = bw.gnz;
+  P->have_prev = true;
+  return any_noconv ? P->set_err(RS_ENOCONV, "a shift reached maxit") : RS_OK;
+}
+
+// The batched solves of several problems (images) in joint launches.
+template <typename T>
+int solve_batched_multi(std::vector<BatchWork<T>>& ws, const BatchScratch& sc, int capacity, int R,
+                        rs_solve_stats* const* stats) {
+  for (auto& w : ws) {
+    RS(batch_prepare<T>(w));
+    CU0(cudaMemcpyAsync(vp<char>(sc.sys) + (size_t)w.base * sizeof(MrBatchSys<T>), w.P->sys_host.data(),
+                        w.P->sys_host.size(), cudaMemcpyHostToDevice, sc.s));
+  }
+  const int max_sw = ws[0].P->mixed ? kMaxSweeps : 1;
+  for (int sw = 0; sw < max_sw; ++sw) {
+    bool any = false;
+    for (auto& w : ws) any = any || !w.run.empty();
+    if (!any) break;
+    std::vector<double> ph(ws.size());
+    for (size_t i = 0; i < ws.size(); ++i) {
+      ph[i] = phase_begin(ws[i].P);
+      RS(batch_sweep_init<T>(ws[i]));
+    }
+    RS(batch_run<T>(ws, sc, capacity, R));
+    for (size_t i = 0; i < ws.size(); ++i) {
+      RS(batch_assemble<T>(ws[i], sw));
+      phase_end(ws[i].P, 4, ph[i]);
+    }
+  }
+  int rc = RS_OK;
+  for (size_t i = 0; i < ws.size(); ++i) {
+    const int r = batch_finish<T>(ws[i], stats ? stats[i] : nullptr);
+    if (r != RS_OK && rc == RS_OK) rc = r;
+  }
+  return rc;
+}
+
+template <typename T>
+int solve_batched(rs_problem* P, double* X, rs_solve_stats* stats, int capacity) {
+  std::vector<BatchWork<T>> ws(1);
+  ws[0].P = P;
+  ws[0].X = X;
+  ws[0].base = 0;
+  BatchScratch sc{P->sysB, P->sysidxB, P->stopfB, P->partials_p, P->gbar, P->s};
+  rs_solve_stats* st[1] = {stats};
+  return solve_batched_multi<T>(ws, sc, capacity, P->tp.r, st);
+}
+
 // Adjoint solves (A + gamma_l E_k) lambda_l = g_l on the current step's recycle
 // space: orthogonal-projection initial guesses (the matrices of Eq. orthupdate
 // with the right-hand sides K^T g_l and U^T E g_l, from A U~ and E U~: no matvec),
@@ -1343,6 +1787,8 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // the persistent and fused MINRES kernels apply the blur stencil in place;
   // with the Radon operator every step runs as separate kernels
   if (desc->radon_angles > 0) P->use_persist = P->use_graph = false;
+  // RS_BATCH=0 solves the shifts of a batched_local problem one after another
+  if (const char* g = std::getenv("RS_BATCH")) P->use_batch = std::strcmp(g, "0") != 0;
   // RS_COOP_CGS=0 runs CGS2 column by column (several launches per candidate)
   if (const char* g = std::getenv("RS_COOP_CGS")) P->use_coop_cgs = std::strcmp(g, "0") != 0;
   P->gprev_nz.assign(desc->M, 0);
@@ -1382,6 +1828,12 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
     if ((e = cudaStreamSynchronize(P->s))) return fail(e);
     P->tp.radon = RadonGeom{desc->radon_angles, nb, P->radon_cs, 1.0 / std::sqrt(fro2)};
     P->tp.sino = P->sino;
+  }
+  if (P->taps_dev) {
+    P->taps_host.assign(2 * kMaxTaps, 0.0);
+    for (int k = 0; k <= 2 * P->tp.r; ++k) P->taps_host[kTapsCentre - P->tp.r + k] = P->tp.g[k];
+    if ((e = cudaMemcpyAsync(P->taps_dev, P->taps_host.data(), 2 * kMaxTaps * sizeof(double),
+                             cudaMemcpyHostToDevice, P->s))) return fail(e);
   }
   if ((e = adjoint_apply(P, P->dimg, P->b))) return fail(e);
   if ((e = norm2_partials<double>(P->b, n, P->partials, P->s))) return fail(e);
@@ -1449,8 +1901,79 @@ rs_status rs_solve_shifts(rs_problem* P, double* X_dev, rs_solve_stats* stats_ho
   if (iters_override_host)
     for (int l = 0; l < P->z.M; ++l)
       if (iters_override_host[l] < 0) return (rs_status)P->set_err(RS_EINVAL, "negative iteration override");
+  // batched local spaces: every shift in one cooperative launch where it fits
+  if (P->d.batched_local && P->use_batch && !iters_override_host && P->tp.radon.nang == 0) {
+    const int cap = mr_batch_capacity(P->d.radius, P->mixed ? 4 : 8);
+    if (cap >= P->z.M) {
+      if (P->mixed) return (rs_status)solve_batched<float>(P, X_dev, stats_host, cap);
+      return (rs_status)solve_batched<double>(P, X_dev, stats_host, cap);
+    }
+  }
   if (P->mixed) return (rs_status)solve_all<float>(P, X_dev, stats_host, iters_override_host);
   return (rs_status)solve_all<double>(P, X_dev, stats_host, iters_override_host);
+}
+
+size_t rs_batch_scratch_bytes(int count, int total_shifts) {
+  if (count < 1 || total_shifts < 1) return 0;
+  Carver cv{nullptr};
+  cv.take<MrBatchSys<double>>((size_t)total_shifts);
+  cv.take<int>((size_t)total_shifts);
+  cv.take<int>((size_t)total_shifts);
+  cv.take<double>((size_t)kPersistMaxBlocks * (kMaxLocal + 2));
+  cv.take<GridBar>(1);
+  return cv.off + 256;
+}
+
+rs_status rs_solve_shifts_batched(rs_problem* const* probs, int count, double* const* X_dev,
+                                  rs_solve_stats* const* stats_host, void* scratch_dev,
+                                  size_t scratch_bytes) {
+  auto bad = [&](const char* m) { set_null_error(m); return RS_EINVAL; };
+  if (!probs || count < 1 || !X_dev || !scratch_dev) return bad("need problems, outputs and scratch");
+  if (((uintptr_t)scratch_dev) % 256) return bad("scratch must be 256-byte aligned");
+  int total = 0, R = 0;
+  for (int i = 0; i < count; ++i) {
+    rs_problem* P = probs[i];
+    if (!P || !X_dev[i]) return bad("NULL problem or output");
+    if (!P->have_recycle) return bad("call rs_update_recycle on every problem first");
+    if (!P->d.batched_local) return bad("every problem must have batched_local = 1");
+    if (P->tp.radon.nang > 0 || !mr_persist_supported(P->d.radius) || !P->use_persist)
+      return bad("every problem must use the blur operator with radius 4, 6, 8, 10 or 12");
+    if (P->mixed != probs[0]->mixed) return bad("every problem must have the same precision");
+    if (P->s != probs[0]->s) return bad("every problem must use the same stream");
+    for (int j = 0; j < i; ++j)
+      if (probs[j] == P) return bad("a problem appears twice");
+    total += P->z.M;
+    R = std::max(R, P->d.radius);
+  }
+  if (scratch_bytes < rs_batch_scratch_bytes(count, total)) {
+    set_null_error("scratch too small (rs_batch_scratch_bytes)");
+    return RS_ENOMEM;
+  }
+  const int cap = mr_batch_capacity(R, probs[0]->mixed ? 4 : 8);
+  if (cap < total) return bad("more shifts than co-resident CTAs of the batched kernel");
+  Carver cv{(char*)scratch_dev};
+  BatchScratch sc{};
+  sc.sys = cv.take<MrBatchSys<double>>((size_t)total);
+  sc.sysidx = cv.take<int>((size_t)total);
+  sc.stopf = cv.take<int>((size_t)total);
+  sc.part = cv.take<double>((size_t)kPersistMaxBlocks * (kMaxLocal + 2));
+  sc.gbar = cv.take<GridBar>(1);
+  sc.s = probs[0]->s;
+  int rc;
+  if (probs[0]->mixed) {
+    std::vector<BatchWork<float>> ws(count);
+    for (int i = 0, b = 0; i < count; b += probs[i]->z.M, ++i) { ws[i].P = probs[i]; ws[i].X = X_dev[i]; ws[i].base = b; }
+    rc = solve_batched_multi<float>(ws, sc, cap, R, stats_host);
+  } else {
+    std::vector<BatchWork<double>> ws(count);
+    for (int i = 0, b = 0; i < count; b += probs[i]->z.M, ++i) { ws[i].P = probs[i]; ws[i].X = X_dev[i]; ws[i].base = b; }
+    rc = solve_batched_multi<double>(ws, sc, cap, R, stats_host);
+  }
+  if (rc != RS_OK) {
+    for (int i = 0; i < count; ++i)
+      if (probs[i]->err != "no error") { set_null_error(probs[i]->err.c_str()); break; }
+  }
+  return (rs_status)rc;
 }
 
 rs_status rs_solve_adjoint(rs_problem* P, const double* G_dev, double* Lam_dev,

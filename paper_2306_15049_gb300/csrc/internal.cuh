@@ -207,6 +207,7 @@ struct MinresState {
   double xi;
   int iters, maxit, stop, performed, breakdown, s;
   int dir_pending;         // fused path: the direction update of the last step is due
+  int next_j;              // batched kernel: the step a later launch resumes at (1 at start)
   unsigned int cnt_a, cnt_b;   // last-CTA tickets of the fused kernels (0 between launches)
   double h[kMaxLocal];     // K^T Op v_j
   double h1[kMaxLocal], h2[kMaxLocal];
@@ -297,6 +298,50 @@ struct MrP {
   int rec_cap;
   int j0;              // first step of this launch
 };
+// One system of a batched solve: its state, image (H x W, its own weights w
+// and blur taps: 2 kMaxTaps - 1 entries centred at kMaxTaps - 1, zero beyond
+// its radius), its vectors (n entries of T), its local space K (s columns,
+// stride ldk; s is in its state) and its shift. Systems of one launch may come
+// from different images.
+template <typename T>
+struct MrBatchSys {
+  MinresState* st;
+  const T* w;
+  T* vzero;
+  const double* taps;
+  int H, W;
+  T* u;
+  T* y;
+  T* xm;
+  const T* K;
+  long ldk;
+  T* vring[3];
+  T* dring[3];
+  double gamma;
+  // selects instead of an indexed parameter array (which would live in local memory)
+  __device__ static T* pick(T* const (&a)[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
+};
+constexpr int kTapsCentre = kMaxTaps - 1;   // index of the central tap in MrBatchSys::taps
+// A batch: B systems (ids sysidx[0..B-1] into sys), gper CTAs each.
+template <typename T>
+struct MrBatch {
+  const MrBatchSys<T>* sys;
+  const int* sysidx;
+  int B;
+  int gper;
+  int min_active;      // leave the launch when fewer systems are running
+  double* part;        // B x (kMaxLocal + 2) x gper partial sums (entries of T)
+  int* stopf;          // B
+};
+// Run the batch with the stencil of radius R (>= every system's radius) until
+// every system has stopped or fewer than min_active run (the host relaunches
+// the rest). Needs all G = B * gper CTAs co-resident.
+template <typename T>
+cudaError_t mr_batch(const MrBatch<T>& bt, int R, GridBar* bar, cudaStream_t s,
+                     int* launched_blocks);
+// CTAs a batched launch may use (all co-resident), 0 if none.
+int mr_batch_capacity(int radius, int precision_bytes);
+
 // One launch runs the solve to its stop. s_alloc: the widest local space the
 // resident kernel must hold in shared memory. resident (out): 1 if the
 // one-CTA-per-tile kernel ran, 0 for the streaming one.

@@ -42,6 +42,7 @@ __global__ void k_minres_init(MinresState* st, const double* xi2, const double* 
   st->performed = 0;
   st->breakdown = 0;
   st->dir_pending = 0;
+  st->next_j = 1;
   st->cnt_a = 0;
   st->cnt_b = 0;
   st->s = s;

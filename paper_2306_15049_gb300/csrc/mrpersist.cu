@@ -264,6 +264,50 @@ struct Ptrs {
   __device__ static T* pick(T* const (&a)[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
 };
 
+// The streaming kernels' phase A tail for one tile: store y = A v + gamma E v
+// and v_j at the thread's pixels, then add K^T y and v_j^T y. The K loads of a
+// group of 4 columns are all issued before their products (K is read-only in
+// the kernel; restrict-qualified stores cannot alias it), so a tile waits for a
+// few memory round trips instead of one per column and pixel.
+template <typename T>
+__device__ __forceinline__ void tile_store_dots(const T* ax, const T* ex, const T* vc, T gam,
+                                                int i0, int j0, int H, int W, int s,
+                                                T* __restrict__ y, T* __restrict__ vj,
+                                                const T* __restrict__ K, long ldk, T* acc) {
+  long g[kPPT];
+  bool in[kPPT];
+  T yk[kPPT];
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) {
+    int ti, tj;
+    op_tile_pixel(q, ti, tj);
+    const int gi = i0 + ti, gj = j0 + tj;
+    in[q] = gi < H && gj < W;
+    g[q] = in[q] ? (long)gi * W + gj : 0;
+    yk[q] = in[q] ? ax[q] + gam * ex[q] : T(0);
+    if (in[q]) {
+      y[g[q]] = yk[q];
+      vj[g[q]] = vc[q];
+      acc[kMaxLocal] += vc[q] * yk[q];
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < kMaxLocal; kk += 4) {
+    if (kk < s) {
+      T kv[4][kPPT];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int q = 0; q < kPPT; ++q)
+          kv[c][q] = (kk + c < s && in[q]) ? __ldg(K + (long)(kk + c) * ldk + g[q]) : T(0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int q = 0; q < kPPT; ++q) acc[kk + c] += kv[c][q] * yk[q];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // one CTA per tile, vectors of the CTA's pixels in registers
 // ---------------------------------------------------------------------------
@@ -486,22 +530,7 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
         T ax[kPPT], ex[kPPT], vc[kPPT];
         op_tile_fast<T, R, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, bufA, bufB, true, ax, ex,
                                  vc, tyi, txi);
-#pragma unroll
-        for (int q = 0; q < kPPT; ++q) {
-          int ti, tj;
-          op_tile_pixel(q, ti, tj);
-          const int gi = i0 + ti, gj = j0 + tj;
-          if (gi < H && gj < W) {
-            const long g = (long)gi * W + gj;
-            const T yv = ax[q] + gam * ex[q];
-            p.y[g] = yv;
-            vj[g] = vc[q];
-#pragma unroll
-            for (int k = 0; k < kMaxLocal; ++k)
-              if (k < s) acc[k] += p.K[(long)k * p.ldk + g] * yv;
-            acc[kMaxLocal] += vc[q] * yv;
-          }
-        }
+        tile_store_dots<T>(ax, ex, vc, gam, i0, j0, H, W, s, p.y, vj, p.K, p.ldk, acc);
       }
       __syncthreads();   // the tile buffers are reused by the next tile
     }
@@ -572,6 +601,285 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
   }
   // the pending direction update was applied by the last phase A
   if (blockIdx.x == 0 && !failed) store_state(st, ss);
+}
+
+// ---------------------------------------------------------------------------
+// batched: many independent solves (the shifts of a step with batched local
+// spaces) advancing together in one cooperative launch
+// ---------------------------------------------------------------------------
+// CTA c serves system b = c / gper (its tiles r, r + gper, .. with r = c % gper);
+// every system has its own state, vectors and local space. Per step: phase A
+// (pending direction update, stencil, dots) for the system's tiles, grid
+// barrier, each CTA reduces its own system's gper partial sums, phase B (the
+// Lanczos update) over the system's pixels, grid barrier, the scalar step on
+// the CTA's copy of its system's state. A system that has stopped applies its
+// last direction update at the next phase A and then idles (convergence mask);
+// its leader publishes that in a stop flag before the first barrier, and every
+// CTA reads all flags after it, so all leave at the same barrier: when every
+// system is done, or when fewer than `min_active` remain (the host relaunches
+// those on more CTAs each).
+template <typename T>
+__device__ __forceinline__ void batch_store_dots(const T* acc, int s, T (*red)[kDots], T* part,
+                                                 int stride, int col) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kDots; ++k) {
+    if (k < s || k == kMaxLocal) {
+      const T t = warp_sum_w<T>(acc[k]);
+      if (lane == 0) red[warp][k] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kDots) {
+    const int k = threadIdx.x;
+    if (k < s || k == kMaxLocal) {
+      T t = T(0);
+#pragma unroll
+      for (int wv = 0; wv < kWarps; ++wv) t += red[wv][k];
+      part[(long)(k == kMaxLocal ? s : k) * stride + col] = t;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void batch_reduce_dots(const T* part, int stride, int ncol, int s,
+                                                  T (*red)[kDots], T* hd) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T t[kDots];
+#pragma unroll
+  for (int k = 0; k < kDots; ++k) t[k] = T(0);
+  for (int g = threadIdx.x; g < ncol; g += kThreads) {
+    T l[kDots];
+#pragma unroll
+    for (int k = 0; k < kDots; ++k) l[k] = (k <= s) ? __ldcg(part + (long)k * stride + g) : T(0);
+#pragma unroll
+    for (int k = 0; k < kDots; ++k) t[k] += l[k];
+  }
+  __syncthreads();   // red is reused
+#pragma unroll
+  for (int k = 0; k < kDots; ++k) {
+    if (k <= s) {
+      const T v = warp_sum_w<T>(t[k]);
+      if (lane == 0) red[warp][k] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x <= s) {
+    T v = T(0);
+#pragma unroll
+    for (int wv = 0; wv < kWarps; ++wv) v += red[wv][threadIdx.x];
+    hd[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreads, 2)
+k_mr_batch(MrBatch<T> bt, GridBar* bar) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ MinresState ss;
+  __shared__ StepCoef<T> cf;
+  __shared__ T hd[kDots];
+  __shared__ T red[kWarps][kDots];
+  __shared__ T sg[kMaxTaps];
+  __shared__ double sc[5];
+  __shared__ int ok_s, all_s;
+  const unsigned G = gridDim.x;
+  const int b = blockIdx.x / bt.gper, r = blockIdx.x - b * bt.gper;
+  const bool member = b < bt.B;
+  T* bufA = reinterpret_cast<T*>(smem_raw);
+  T* bufB = bufA + (kTileH + 4 * R) * (kTileW + 4 * R);
+  const int sysid = member ? bt.sysidx[b] : bt.sysidx[0];
+  const MrBatchSys<T> sy = bt.sys[sysid];
+  const int H = sy.H, W = sy.W;
+  const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (H + kTileH - 1) / kTileH;
+  const int ntiles = tiles_x * tiles_y;
+  const long n = (long)H * W;
+  // per-system partial sums: rows 0..s dots, row kMaxLocal + 1 the norm
+  T* part = reinterpret_cast<T*>(bt.part) + (long)(member ? b : 0) * (kMaxLocal + 2) * bt.gper;
+  T* partn = part + (long)(kMaxLocal + 1) * bt.gper;
+  MrP<T> nop{};      // scalar_step records no alpha / beta (no Ritz extraction here)
+  if (member) load_state(sy.st, ss);
+  if (threadIdx.x <= 2 * R) sg[threadIdx.x] = T(sy.taps[kTapsCentre - R + threadIdx.x]);
+  const T gam = T(sy.gamma);
+  __syncthreads();
+  if (threadIdx.x == 0 && member) coef_from_state(ss, cf);
+  __syncthreads();
+  auto vptr = [&](int j) -> T* { return j <= 0 ? sy.vzero : MrBatchSys<T>::pick(sy.vring, j % 3); };
+  auto dptr = [&](int j) -> T* { return MrBatchSys<T>::pick(sy.dring, ((j % 3) + 3) % 3); };
+
+  bool done = !member;
+  int j = member ? ss.next_j : 1;   // the system's step (launches of one batch may differ)
+  unsigned long long nb = 0;
+  bool failed = false;
+  for (;;) {
+    const int s = member ? ss.s : 0;
+    if (!done) {
+      const int pend = ss.dir_pending, stopped = ss.stop;
+      T acc[kDots];
+#pragma unroll
+      for (int k = 0; k < kDots; ++k) acc[k] = T(0);
+      const T* vprev = vptr(j - 1);
+      const T* d1 = dptr(j - 2);
+      const T* d2 = dptr(j - 3);
+      T* dout = dptr(j - 1);
+      T* vj = vptr(j);
+      for (int t = r; t < ntiles; t += bt.gper) {
+        const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
+        const int i0 = tyi * kTileH, j0 = txi * kTileW;
+        if (pend) {
+          const T de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau;
+          T pv[kPPT], p1[kPPT], p2[kPPT], px[kPPT];
+          long gq[kPPT];
+          bool iq[kPPT];
+#pragma unroll
+          for (int q = 0; q < kPPT; ++q) {   // every load first
+            int ti, tj;
+            op_tile_pixel(q, ti, tj);
+            const int gi = i0 + ti, gj = j0 + tj;
+            iq[q] = gi < H && gj < W;
+            gq[q] = iq[q] ? (long)gi * W + gj : 0;
+            pv[q] = iq[q] ? __ldcg(vprev + gq[q]) : T(0);
+            p1[q] = iq[q] ? __ldcg(d1 + gq[q]) : T(0);
+            p2[q] = iq[q] ? __ldcg(d2 + gq[q]) : T(0);
+            px[q] = iq[q] ? __ldcg(sy.xm + gq[q]) : T(0);
+          }
+#pragma unroll
+          for (int q = 0; q < kPPT; ++q) {
+            if (iq[q]) {
+              const T dv = (pv[q] - de * p1[q] - ep * p2[q]) * ig;
+              dout[gq[q]] = dv;
+              sy.xm[gq[q]] = px[q] + tau * dv;
+            }
+          }
+        }
+        if (!stopped) {
+          T ax[kPPT], ex[kPPT], vc[kPPT];
+          op_tile_fast<T, R, true>(sy.u, cf.inv_beta_next, sy.w, H, W, sg, bufA, bufB, true, ax, ex,
+                                   vc, tyi, txi);
+          tile_store_dots<T>(ax, ex, vc, gam, i0, j0, H, W, s, sy.y, vj, sy.K, sy.ldk, acc);
+        }
+        __syncthreads();   // the tile buffers are reused by the next tile
+      }
+      if (stopped) {
+        done = true;       // the last direction update is applied
+      } else {
+        batch_store_dots<T>(acc, s, red, part, bt.gper, r);
+      }
+    }
+    if (member && r == 0 && threadIdx.x == 0) bt.stopf[b] = done ? 1 : 0;
+    if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    {
+      // every CTA reads the same flags: leave when all systems are done, or
+      // when fewer than min_active are still running (phase A of step j is
+      // then repeated by the next launch, without its direction update)
+      if (threadIdx.x == 0) all_s = 0;
+      __syncthreads();
+      int act = 0;
+      for (int q = threadIdx.x; q < bt.B; q += kThreads) act += __ldcg(bt.stopf + q) ? 0 : 1;
+      if (act) atomicAdd(&all_s, act);
+      __syncthreads();
+      const int active = all_s;
+      if (active == 0 || active < bt.min_active) break;
+    }
+    if (!done) {
+      batch_reduce_dots<T>(part, bt.gper, bt.gper, s, red, hd);
+      using V = typename Vec16<T>::type;
+      constexpr int VW = Vec16<T>::n;
+      const T alpha = hd[s], beta = cf.beta;
+      T accb = T(0);
+      const long nv = n / VW;
+      const long tid = (long)r * kThreads + threadIdx.x, nthr = (long)bt.gper * kThreads;
+      const T* vj = vptr(j);
+      const T* vprev = vptr(j - 1);
+      // two vectors per pass, every load of a group of 4 K columns issued before
+      // its products (K is read-only; u is only written)
+      for (long iv0 = tid; iv0 < nv; iv0 += 2 * nthr) {
+        const long ivs[2] = {iv0, iv0 + nthr};
+        const bool has1 = ivs[1] < nv;
+        V uv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const long iv = (h == 0 || has1) ? ivs[h] : ivs[0];
+          const V yv = __ldcg(reinterpret_cast<const V*>(sy.y) + iv);
+          const V vv = __ldcg(reinterpret_cast<const V*>(vj) + iv);
+          const V pv = __ldcg(reinterpret_cast<const V*>(vprev) + iv);
+          const T* ya = reinterpret_cast<const T*>(&yv);
+          const T* va = reinterpret_cast<const T*>(&vv);
+          const T* pa = reinterpret_cast<const T*>(&pv);
+          T* ua = reinterpret_cast<T*>(&uv[h]);
+#pragma unroll
+          for (int e = 0; e < VW; ++e) ua[e] = ya[e] - alpha * va[e] - beta * pa[e];
+        }
+#pragma unroll
+        for (int kk = 0; kk < kMaxLocal; kk += 4) {
+          if (kk < s) {
+            V kv[4][2];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const long iv = (h == 0 || has1) ? ivs[h] : ivs[0];
+                kv[c][h] = (kk + c < s) ? __ldg(reinterpret_cast<const V*>(sy.K + (long)(kk + c) * sy.ldk) + iv) : V{};
+              }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const T hk = (kk + c < s) ? hd[kk + c] : T(0);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                T* ua = reinterpret_cast<T*>(&uv[h]);
+                const T* ka = reinterpret_cast<const T*>(&kv[c][h]);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) ua[e] -= hk * ka[e];
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !has1) break;
+          const T* ua = reinterpret_cast<const T*>(&uv[h]);
+#pragma unroll
+          for (int e = 0; e < VW; ++e) accb += ua[e] * ua[e];
+          reinterpret_cast<V*>(sy.u)[ivs[h]] = uv[h];
+        }
+      }
+      for (long i = nv * VW + tid; i < n; i += nthr) {
+        T val = __ldcg(sy.y + i) - alpha * __ldcg(vj + i) - beta * __ldcg(vprev + i);
+        for (int k = 0; k < s; ++k) val -= hd[k] * sy.K[(long)k * sy.ldk + i];
+        sy.u[i] = val;
+        accb += val * val;
+      }
+      // the CTA's share of ||u||^2 into its column of the norm row
+      {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        accb = warp_sum_w<T>(accb);
+        if (lane == 0) red[warp][0] = accb;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          T t = T(0);
+#pragma unroll
+          for (int wv = 0; wv < kWarps; ++wv) t += red[wv][0];
+          partn[r] = t;
+        }
+      }
+    }
+    if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    if (!done) scalar_step<T>(partn, (unsigned)bt.gper, hd, red, ss, cf, sc, nop);
+    ++j;
+  }
+  if (failed || !member || r != 0) return;
+  // the leader stores the state: the direction update of the last phase A is
+  // applied, and a system still running continues in the next launch at step j
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ss.next_j = j;
+    ss.dir_pending = 0;
+  }
+  __syncthreads();
+  constexpr int kWords = sizeof(MinresState) / sizeof(unsigned);
+  for (int i = threadIdx.x; i < kWords; i += kThreads)
+    reinterpret_cast<unsigned*>(sy.st)[i] = reinterpret_cast<const unsigned*>(&ss)[i];
 }
 
 struct Occ {
@@ -652,6 +960,65 @@ cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Tap
     default: return cudaErrorNotSupported;
   }
 }
+
+namespace {
+template <typename T, int R>
+cudaError_t launch_batch(const MrBatch<T>& bt, GridBar* bar, cudaStream_t s, int G) {
+  const size_t smem = (size_t)op_tile_smem_elems(R) * sizeof(T);
+  static int cached = 0;
+  RK_TRY(ensure_smem(k_mr_batch<T, R>, smem, &cached));
+  MrBatch<T> a0 = bt;
+  GridBar* a1 = bar;
+  void* args[] = {&a0, &a1};
+  RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_batch<T, R>, dim3(G), dim3(kThreads), args,
+                                     smem, s));
+  return launched();
+}
+
+template <typename T, int R>
+int batch_capacity() {
+  static Occ occ;
+  const size_t smem = (size_t)op_tile_smem_elems(R) * sizeof(T);
+  static int cached = 0;
+  if (ensure_smem(k_mr_batch<T, R>, smem, &cached) != cudaSuccess ||
+      occupancy(k_mr_batch<T, R>, smem, &occ) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  const int G = occ.per_sm * occ.sms;
+  return G < kPersistMaxBlocks ? G : kPersistMaxBlocks;
+}
+}  // namespace
+
+template <typename T>
+cudaError_t mr_batch(const MrBatch<T>& bt, int R, GridBar* bar, cudaStream_t s,
+                     int* launched_blocks) {
+  const int G = bt.B * bt.gper;
+  *launched_blocks = G;
+  switch (R) {
+    case 4: return launch_batch<T, 4>(bt, bar, s, G);
+    case 6: return launch_batch<T, 6>(bt, bar, s, G);
+    case 8: return launch_batch<T, 8>(bt, bar, s, G);
+    case 10: return launch_batch<T, 10>(bt, bar, s, G);
+    case 12: return launch_batch<T, 12>(bt, bar, s, G);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+int mr_batch_capacity(int radius, int precision_bytes) {
+  const bool f = precision_bytes == 4;
+  switch (radius) {
+    case 4: return f ? batch_capacity<float, 4>() : batch_capacity<double, 4>();
+    case 6: return f ? batch_capacity<float, 6>() : batch_capacity<double, 6>();
+    case 8: return f ? batch_capacity<float, 8>() : batch_capacity<double, 8>();
+    case 10: return f ? batch_capacity<float, 10>() : batch_capacity<double, 10>();
+    case 12: return f ? batch_capacity<float, 12>() : batch_capacity<double, 12>();
+    default: return 0;
+  }
+}
+
+template cudaError_t mr_batch<float>(const MrBatch<float>&, int, GridBar*, cudaStream_t, int*);
+template cudaError_t mr_batch<double>(const MrBatch<double>&, int, GridBar*, cudaStream_t, int*);
 
 bool mr_persist_supported(int radius) {
   return radius == 4 || radius == 6 || radius == 8 || radius == 10 || radius == 12;

@@ -76,6 +76,9 @@ _SIGS = {
     "rs_solve_shifts": (_I, [_P, _P, ctypes.POINTER(rs_solve_stats), ctypes.POINTER(_I)]),
     "rs_initial_guesses": (_I, [_P, _P, _P]),
     "rs_solve_adjoint": (_I, [_P, _P, _P, ctypes.POINTER(rs_solve_stats)]),
+    "rs_batch_scratch_bytes": (ctypes.c_size_t, [_I, _I]),
+    "rs_solve_shifts_batched": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P),
+                                     ctypes.POINTER(ctypes.POINTER(rs_solve_stats)), _P, ctypes.c_size_t]),
     "rs_shift_gradients": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
     "rs_get_principal_basis": (_I, [_P, _P, ctypes.POINTER(_I)]),
     "rs_apply_operator": (_I, [_P, _D, _P, _P, _P, _I, _I]),
@@ -160,6 +163,28 @@ def rs_synthesize_data_noalloc(desc, x_dev, z_dev, eta: float, d_out_dev, stream
                                         _ptr(d_out_dev), stream)
     if st != RS_OK:
         raise RecycError(st, lib.rs_last_error(None).decode())
+
+
+def rs_solve_shifts_batched(problems, X_list, scratch=None):
+    """Solve the current step of several batched_local problems together (one
+    cooperative launch for all their shifts). Returns one stats list per problem."""
+    import torch
+    lib = load()
+    count = len(problems)
+    total = sum(p.M for p in problems)
+    nbytes = int(lib.rs_batch_scratch_bytes(count, total))
+    if nbytes == 0:
+        raise RecycError(RS_EINVAL, "invalid batch")
+    if scratch is None or scratch.numel() * scratch.element_size() < nbytes:
+        scratch = torch.empty(nbytes, dtype=torch.uint8, device=X_list[0].device)
+    probs = (ctypes.c_void_p * count)(*[p.h for p in problems])
+    xs = (ctypes.c_void_p * count)(*[_ptr(x) for x in X_list])
+    stats = [(rs_solve_stats * p.M)() for p in problems]
+    sp = (ctypes.POINTER(rs_solve_stats) * count)(*[ctypes.cast(st, ctypes.POINTER(rs_solve_stats)) for st in stats])
+    st = lib.rs_solve_shifts_batched(probs, count, xs, sp, _ptr(scratch), nbytes)
+    if st not in (RS_OK, RS_ENOCONV):
+        raise RecycError(st, lib.rs_last_error(None).decode())
+    return [[dict((f, getattr(s_, f)) for f, _ in rs_solve_stats._fields_) for s_ in stl] for stl in stats]
 
 
 class Problem:
