@@ -253,6 +253,7 @@ struct rs_problem {
   void *KlB = nullptr, *vecB = nullptr;
   double *RkB = nullptr, *R0B = nullptr, *KtrB = nullptr, *scalB = nullptr, *zcB = nullptr;
   int *cntB = nullptr, *keptB = nullptr, *sysidxB = nullptr, *stopfB = nullptr;
+  int4* ctaB = nullptr;
   MinresState* stB = nullptr;
   void* sysB = nullptr;
   std::vector<char> sys_host;
@@ -425,6 +426,7 @@ void carve(rs_problem* P, Carver& cv) {
     P->keptB = cv.take<int>((size_t)z.M * kMaxLocal);
     P->sysidxB = cv.take<int>((size_t)z.M);
     P->stopfB = cv.take<int>((size_t)z.M);
+    P->ctaB = cv.take<int4>((size_t)kPersistMaxBlocks);
     P->stB = cv.take<MinresState>((size_t)z.M);
     P->sysB = cv.take<MrBatchSys<double>>((size_t)z.M);
     P->taps_dev = cv.take<double>(2 * kMaxTaps);
@@ -1324,6 +1326,7 @@ struct BatchScratch {
   void* sys;            // MrBatchSys entries of every problem (at each problem's base)
   int* sysidx;
   int* stopf;
+  int4* cta;            // kPersistMaxBlocks CTA assignments
   double* part;         // kPersistMaxBlocks x (kMaxLocal + 2)
   GridBar* gbar;
   cudaStream_t s;
@@ -1496,6 +1499,7 @@ int batch_run(std::vector<BatchWork<T>>& ws, const BatchScratch& sc, int capacit
     for (int l : ws[i].run) live.push_back({i, l});
   bool first_launch = true;
   std::vector<int> idx;
+  std::vector<int4> cta_host;
   while (!live.empty()) {
     const int B = (int)live.size();
     if (B <= kBatchTail) {
@@ -1536,18 +1540,41 @@ int batch_run(std::vector<BatchWork<T>>& ws, const BatchScratch& sc, int capacit
       }
       break;
     }
-    const int gper = std::max(1, capacity / B);
     idx.resize(B);
     for (int i = 0; i < B; ++i) idx[i] = ws[live[i].w].base + live[i].l;
+    // CTAs per shift in proportion to its image's pixels (at least one each)
+    double ntot = 0.0;
+    for (int i = 0; i < B; ++i) ntot += (double)ws[live[i].w].P->z.n;
+    std::vector<int> gcnt(B);
+    int G = 0;
+    for (int i = 0; i < B; ++i) {
+      gcnt[i] = std::max(1, (int)std::floor((double)(capacity - B) * ws[live[i].w].P->z.n / ntot) + 1);
+      G += gcnt[i];
+    }
+    while (G > capacity) {          // rounding: take CTAs back from the largest groups
+      int imax = 0;
+      for (int i = 1; i < B; ++i) if (gcnt[i] > gcnt[imax]) imax = i;
+      if (gcnt[imax] <= 1) break;
+      --gcnt[imax];
+      --G;
+    }
+    cta_host.assign(G, make_int4(-1, 0, 1, 0));
+    for (int i = 0, c = 0, off = 0; i < B; ++i) {
+      for (int r = 0; r < gcnt[i]; ++r, ++c) cta_host[c] = make_int4(i, r, gcnt[i], off);
+      off += (kMaxLocal + 2) * gcnt[i];
+    }
+    int gmin = gcnt[0];
+    for (int i = 1; i < B; ++i) gmin = std::min(gmin, gcnt[i]);
     CU0(cudaMemcpyAsync(sc.sysidx, idx.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    CU0(cudaMemcpyAsync(sc.cta, cta_host.data(), G * sizeof(int4), cudaMemcpyHostToDevice, s));
     CU0(cudaMemsetAsync(sc.stopf, 0, B * sizeof(int), s));
     CU0(cudaMemsetAsync(sc.gbar, 0, sizeof(GridBar), s));
     MrBatch<T> bt{};
     bt.sys = reinterpret_cast<const MrBatchSys<T>*>(sc.sys);
     bt.sysidx = sc.sysidx;
+    bt.cta = sc.cta;
     bt.B = B;
-    bt.gper = gper;
-    bt.min_active = (gper * 2 <= capacity) ? (B + 1) / 2 : 0;
+    bt.min_active = (gmin * 2 <= capacity / std::max(1, B / 2)) ? (B + 1) / 2 : 0;
     bt.part = sc.part;
     bt.stopf = sc.stopf;
     std::vector<int> it0(B, 0);   // steps before this launch (0: minres_init just ran)
@@ -1555,8 +1582,7 @@ int batch_run(std::vector<BatchWork<T>>& ws, const BatchScratch& sc, int capacit
       for (int i = 0; i < B; ++i) it0[i] = ws[live[i].w].P->st_host[live[i].l].iters;
     first_launch = false;
     const int slot = timed_begin(P0);
-    int launched_g = 0;
-    CU0(mr_batch<T>(bt, R, sc.gbar, s, &launched_g));
+    CU0(mr_batch<T>(bt, G, R, sc.gbar, s));
     timed_end(P0, slot, 0, -1, 0, 0.0, 0.0);
     // states of every problem involved
     for (auto& w : ws)
@@ -1694,7 +1720,7 @@ int solve_batched(rs_problem* P, double* X, rs_solve_stats* stats, int capacity)
   ws[0].P = P;
   ws[0].X = X;
   ws[0].base = 0;
-  BatchScratch sc{P->sysB, P->sysidxB, P->stopfB, P->partials_p, P->gbar, P->s};
+  BatchScratch sc{P->sysB, P->sysidxB, P->stopfB, P->ctaB, P->partials_p, P->gbar, P->s};
   rs_solve_stats* st[1] = {stats};
   return solve_batched_multi<T>(ws, sc, capacity, P->tp.r, st);
 }
@@ -1919,6 +1945,7 @@ size_t rs_batch_scratch_bytes(int count, int total_shifts) {
   cv.take<MrBatchSys<double>>((size_t)total_shifts);
   cv.take<int>((size_t)total_shifts);
   cv.take<int>((size_t)total_shifts);
+  cv.take<int4>((size_t)kPersistMaxBlocks);
   cv.take<double>((size_t)kPersistMaxBlocks * (kMaxLocal + 2));
   cv.take<GridBar>(1);
   return cv.off + 256;
@@ -1956,6 +1983,7 @@ rs_status rs_solve_shifts_batched(rs_problem* const* probs, int count, double* c
   sc.sys = cv.take<MrBatchSys<double>>((size_t)total);
   sc.sysidx = cv.take<int>((size_t)total);
   sc.stopf = cv.take<int>((size_t)total);
+  sc.cta = cv.take<int4>((size_t)kPersistMaxBlocks);
   sc.part = cv.take<double>((size_t)kPersistMaxBlocks * (kMaxLocal + 2));
   sc.gbar = cv.take<GridBar>(1);
   sc.s = probs[0]->s;

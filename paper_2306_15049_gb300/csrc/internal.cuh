@@ -322,23 +322,25 @@ struct MrBatchSys {
   __device__ static T* pick(T* const (&a)[3], int i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
 };
 constexpr int kTapsCentre = kMaxTaps - 1;   // index of the central tap in MrBatchSys::taps
-// A batch: B systems (ids sysidx[0..B-1] into sys), gper CTAs each.
+// A batch: B systems (ids sysidx[0..B-1] into sys). CTA c serves system slot
+// cta[c].x (-1: idle) as its member cta[c].y of cta[c].z, and that system's
+// partial sums start at part + cta[c].w (entries of T; (kMaxLocal + 2) rows of
+// cta[c].z columns).
 template <typename T>
 struct MrBatch {
   const MrBatchSys<T>* sys;
   const int* sysidx;
+  const int4* cta;
   int B;
-  int gper;
   int min_active;      // leave the launch when fewer systems are running
-  double* part;        // B x (kMaxLocal + 2) x gper partial sums (entries of T)
+  double* part;        // partial sums (entries of T)
   int* stopf;          // B
 };
-// Run the batch with the stencil of radius R (>= every system's radius) until
-// every system has stopped or fewer than min_active run (the host relaunches
-// the rest). Needs all G = B * gper CTAs co-resident.
+// Run the batch (G CTAs) with the stencil of radius R (>= every system's
+// radius) until every system has stopped or fewer than min_active run (the host
+// relaunches the rest). Needs all G CTAs co-resident.
 template <typename T>
-cudaError_t mr_batch(const MrBatch<T>& bt, int R, GridBar* bar, cudaStream_t s,
-                     int* launched_blocks);
+cudaError_t mr_batch(const MrBatch<T>& bt, int G, int R, GridBar* bar, cudaStream_t s);
 // CTAs a batched launch may use (all co-resident), 0 if none.
 int mr_batch_capacity(int radius, int precision_bytes);
 

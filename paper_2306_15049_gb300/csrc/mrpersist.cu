@@ -607,8 +607,10 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
 // batched: many independent solves (the shifts of a step with batched local
 // spaces) advancing together in one cooperative launch
 // ---------------------------------------------------------------------------
-// CTA c serves system b = c / gper (its tiles r, r + gper, .. with r = c % gper);
-// every system has its own state, vectors and local space. Per step: phase A
+// CTA c serves system slot b as member r of g_b CTAs (its tiles r, r + g_b, ..;
+// g_b in proportion to the system's pixels, so images of different sizes take
+// about the same time per step); every system has its own state, vectors and
+// local space. Per step: phase A
 // (pending direction update, stencil, dots) for the system's tiles, grid
 // barrier, each CTA reduces its own system's gper partial sums, phase B (the
 // Lanczos update) over the system's pixels, grid barrier, the scalar step on
@@ -685,8 +687,9 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
   __shared__ double sc[5];
   __shared__ int ok_s, all_s;
   const unsigned G = gridDim.x;
-  const int b = blockIdx.x / bt.gper, r = blockIdx.x - b * bt.gper;
-  const bool member = b < bt.B;
+  const int4 cm = bt.cta[blockIdx.x];
+  const int b = cm.x, r = cm.y, gb = cm.z > 0 ? cm.z : 1;
+  const bool member = b >= 0;
   T* bufA = reinterpret_cast<T*>(smem_raw);
   T* bufB = bufA + (kTileH + 4 * R) * (kTileW + 4 * R);
   const int sysid = member ? bt.sysidx[b] : bt.sysidx[0];
@@ -696,8 +699,8 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
   const int ntiles = tiles_x * tiles_y;
   const long n = (long)H * W;
   // per-system partial sums: rows 0..s dots, row kMaxLocal + 1 the norm
-  T* part = reinterpret_cast<T*>(bt.part) + (long)(member ? b : 0) * (kMaxLocal + 2) * bt.gper;
-  T* partn = part + (long)(kMaxLocal + 1) * bt.gper;
+  T* part = reinterpret_cast<T*>(bt.part) + (member ? cm.w : 0);
+  T* partn = part + (long)(kMaxLocal + 1) * gb;
   MrP<T> nop{};      // scalar_step records no alpha / beta (no Ritz extraction here)
   if (member) load_state(sy.st, ss);
   if (threadIdx.x <= 2 * R) sg[threadIdx.x] = T(sy.taps[kTapsCentre - R + threadIdx.x]);
@@ -724,7 +727,7 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
       const T* d2 = dptr(j - 3);
       T* dout = dptr(j - 1);
       T* vj = vptr(j);
-      for (int t = r; t < ntiles; t += bt.gper) {
+      for (int t = r; t < ntiles; t += gb) {
         const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
         const int i0 = tyi * kTileH, j0 = txi * kTileW;
         if (pend) {
@@ -764,7 +767,7 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
       if (stopped) {
         done = true;       // the last direction update is applied
       } else {
-        batch_store_dots<T>(acc, s, red, part, bt.gper, r);
+        batch_store_dots<T>(acc, s, red, part, gb, r);
       }
     }
     if (member && r == 0 && threadIdx.x == 0) bt.stopf[b] = done ? 1 : 0;
@@ -783,13 +786,13 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
       if (active == 0 || active < bt.min_active) break;
     }
     if (!done) {
-      batch_reduce_dots<T>(part, bt.gper, bt.gper, s, red, hd);
+      batch_reduce_dots<T>(part, gb, gb, s, red, hd);
       using V = typename Vec16<T>::type;
       constexpr int VW = Vec16<T>::n;
       const T alpha = hd[s], beta = cf.beta;
       T accb = T(0);
       const long nv = n / VW;
-      const long tid = (long)r * kThreads + threadIdx.x, nthr = (long)bt.gper * kThreads;
+      const long tid = (long)r * kThreads + threadIdx.x, nthr = (long)gb * kThreads;
       const T* vj = vptr(j);
       const T* vprev = vptr(j - 1);
       // two vectors per pass, every load of a group of 4 K columns issued before
@@ -865,7 +868,7 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
       }
     }
     if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
-    if (!done) scalar_step<T>(partn, (unsigned)bt.gper, hd, red, ss, cf, sc, nop);
+    if (!done) scalar_step<T>(partn, (unsigned)gb, hd, red, ss, cf, sc, nop);
     ++j;
   }
   if (failed || !member || r != 0) return;
@@ -991,10 +994,7 @@ int batch_capacity() {
 }  // namespace
 
 template <typename T>
-cudaError_t mr_batch(const MrBatch<T>& bt, int R, GridBar* bar, cudaStream_t s,
-                     int* launched_blocks) {
-  const int G = bt.B * bt.gper;
-  *launched_blocks = G;
+cudaError_t mr_batch(const MrBatch<T>& bt, int G, int R, GridBar* bar, cudaStream_t s) {
   switch (R) {
     case 4: return launch_batch<T, 4>(bt, bar, s, G);
     case 6: return launch_batch<T, 6>(bt, bar, s, G);
@@ -1017,8 +1017,8 @@ int mr_batch_capacity(int radius, int precision_bytes) {
   }
 }
 
-template cudaError_t mr_batch<float>(const MrBatch<float>&, int, GridBar*, cudaStream_t, int*);
-template cudaError_t mr_batch<double>(const MrBatch<double>&, int, GridBar*, cudaStream_t, int*);
+template cudaError_t mr_batch<float>(const MrBatch<float>&, int, int, GridBar*, cudaStream_t);
+template cudaError_t mr_batch<double>(const MrBatch<double>&, int, int, GridBar*, cudaStream_t);
 
 bool mr_persist_supported(int radius) {
   return radius == 4 || radius == 6 || radius == 8 || radius == 10 || radius == 12;
