@@ -126,6 +126,72 @@ def recycled_minres(op_apply: Callable[[np.ndarray], np.ndarray], r: np.ndarray,
     return res
 
 
+def recycled_cg(op_apply: Callable[[np.ndarray], np.ndarray], r: np.ndarray,
+                K: Optional[np.ndarray], tol_abs: float, maxit: int) -> MinresResult:
+    """Projected (recycled) CG on Op g = r with recycle space (U, K), K = Op U: the
+    same Lanczos process on (I - K K^T) Op from v_1 = (I - K K^T) r / xi as
+    ``recycled_minres`` (Op is SPD on the complement of K, where the projected
+    operator is self-adjoint), but y_m solves the square system T_m y = xi e_1
+    (Galerkin) instead of the least-squares problem. The LDL^T factorisation of
+    T_m gives short recurrences (Lanczos form of CG):
+
+        lambda_j = beta_j / eta_{j-1},  zeta_j = -lambda_j zeta_{j-1}  (zeta_1 = xi),
+        eta_j = alpha_j - lambda_j beta_j,
+        p_j = (v_j - beta_j p_{j-1}) / eta_j,  V_m y = sum_j zeta_j p_j,
+
+    the same recurrence on h_j = K^T Op v_j gives K^T Op V_m y, so
+    z = K^T r - K^T Op V_m y as for MINRES. The residual r - Op (V_m y + U z) is
+    -beta_{m+1} (zeta_m / eta_m) v_{m+1}: its norm is the stopping test.
+    ``eta_hist`` holds these residual norms."""
+    n = r.shape[0]
+    s = 0 if K is None else K.shape[1]
+    Ktr = K.T @ r if s else np.zeros(0)
+    u = r - K @ Ktr if s else r.copy()
+    xi = float(np.linalg.norm(u))
+    xm = np.zeros(n)
+    z = Ktr.copy()
+    res = MinresResult(xm, z, 0, [xi], [], [], np.zeros((n, 0)), xi)
+    if xi <= tol_abs or xi == 0.0 or maxit <= 0:
+        return res
+    v_prev = np.zeros(n)
+    v = u / xi
+    beta = 0.0                       # beta_j, the coefficient of v_{j-1}
+    eta_prev, zeta = 1.0, xi
+    p = np.zeros(n)                  # p_{j-1}
+    hp = np.zeros(s)                 # K^T Op p_{j-1}
+    for j in range(1, maxit + 1):
+        y = op_apply(v)
+        h = K.T @ y if s else np.zeros(0)
+        alpha = float(v @ y)
+        u = y - alpha * v - beta * v_prev
+        if s:
+            u = u - K @ h
+        beta_next = float(np.linalg.norm(u))
+        if j > 1:
+            lam = beta / eta_prev
+            zeta = -lam * zeta
+        else:
+            lam = 0.0
+        eta = alpha - lam * beta
+        p = (v - beta * p) / eta
+        xm = xm + zeta * p
+        if s:
+            hp = (h - beta * hp) / eta
+            z = z - zeta * hp
+        resn = beta_next * abs(zeta / eta)
+        res.alphas.append(alpha)
+        res.betas.append(beta_next)
+        res.eta_hist.append(resn)
+        res.iters = j
+        eta_prev = eta
+        if resn <= tol_abs or beta_next == 0.0:
+            break
+        v_prev, v = v, u / beta_next
+        beta = beta_next
+    res.xm, res.z = xm, z
+    return res
+
+
 def lanczos_tridiagonal(alphas: List[float], betas: List[float], m: int) -> np.ndarray:
     """The m x m Lanczos matrix T_m (alpha on the diagonal, beta_2..beta_m off it)."""
     T = np.diag(np.asarray(alphas[:m], dtype=np.float64))

@@ -36,7 +36,7 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from .minres import lanczos_tridiagonal, recycled_minres
+from .minres import lanczos_tridiagonal, recycled_cg, recycled_minres
 from .operator import Operator
 
 STABILIZE_RATIO = 1e10
@@ -69,6 +69,9 @@ class Params:
     guess: str = "orthogonal"
     I_L: int = 0
     I_R: int = 0
+    # inner solver of the per-shift corrections: "minres" (the paper's, Eq. minShift)
+    # or "cg" (projected CG: the Galerkin solution of the same projected Lanczos process)
+    inner: str = "minres"
 
     @staticmethod
     def from_workload(wl, batched_local: bool = False, guess: str = "orthogonal") -> "Params":
@@ -380,10 +383,11 @@ def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
         Ul_t = Ul_t[:, kept]
         local_dim[l] = Kl.shape[1]
 
+        solver = recycled_cg if prm.inner == "cg" else recycled_minres
         if forced is not None:
-            res = recycled_minres(apply_l, r0, Kl if Kl.shape[1] else None, 0.0, forced)
+            res = solver(apply_l, r0, Kl if Kl.shape[1] else None, 0.0, forced)
         else:
-            res = recycled_minres(apply_l, r0, Kl if Kl.shape[1] else None, tol_abs, prm.maxit)
+            res = solver(apply_l, r0, Kl if Kl.shape[1] else None, tol_abs, prm.maxit)
         iters[l] = res.iters
         matvecs[l] += res.iters
         g = res.xm.copy()

@@ -70,3 +70,19 @@ def test_guess_kind_validation_needs_no_gpu(lib):
     d, keep = desc_for(wl)
     d.guess = 3
     assert recyc.rs_workspace_bytes(d) == 0
+
+
+def test_joint_solve_sizes_and_argument_checks_need_no_gpu(lib):
+    import ctypes
+
+    from paper_2306_15049_gb300 import recyc
+    assert lib.rs_batch_scratch_bytes(0, 10) == 0
+    assert lib.rs_batch_scratch_bytes(2, 0) == 0
+    assert lib.rs_batch_scratch_bytes(4, 128) > lib.rs_batch_scratch_bytes(1, 16) > 0
+    st = lib.rs_solve_shifts_batched(None, 0, None, None, None, 0)
+    assert st == recyc.RS_EINVAL
+    assert b"need problems" in lib.rs_last_error(None)
+    probs = (ctypes.c_void_p * 1)(None)
+    xs = (ctypes.c_void_p * 1)(None)
+    st = lib.rs_solve_shifts_batched(probs, 1, xs, None, ctypes.c_void_p(256), 1 << 20)
+    assert st == recyc.RS_EINVAL

@@ -161,3 +161,18 @@ def test_weight_gradient_without_the_shift_factor_is_caught(monkeypatch):
         return dg, dw
     monkeypatch.setattr(tad, "shift_and_weight_gradients", no_gamma)
     _expect_fail(tad.test_gradients_match_central_finite_differences)
+
+
+def test_cg_without_the_sign_of_zeta_is_caught(monkeypatch):
+    import tests.test_oracle_cg as tcg
+    real = om.recycled_cg
+
+    def wrong(op_apply, r, K, tol_abs, maxit):
+        # negate every other correction: zeta_j = +lambda_j zeta_{j-1}
+        res = real(op_apply, r, K, tol_abs, maxit)
+        if res.iters >= 2:
+            res2 = real(op_apply, r, K, tol_abs, res.iters - 1)
+            res.xm = 2 * res2.xm - res.xm
+        return res
+    monkeypatch.setattr(tcg, "recycled_cg", wrong)
+    _expect_fail(tcg.test_without_recycling_it_is_textbook_cg)
