@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-local-space measurement of the same workload")
+    ap.add_argument("--batched-local", action="store_true",
+                    help="run the workload with batched local spaces (all shifts of a step in one launch)")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the unrecycled comparison solver (every shift from x0 = 0)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiation measurement on the 1024x1024 workload")
     ap.add_argument("--profile-case", nargs="?", const="full", choices=["full", "small"],
@@ -302,7 +306,7 @@ def measured_peaks():
 class Runner:
     """One replica of the workload on one GPU, through the C ABI."""
 
-    def __init__(self, wl, precision, dev, batched_local=0):
+    def __init__(self, wl, precision, dev, batched_local=0, plain=False):
         import numpy as np
         import torch
 
@@ -330,6 +334,8 @@ class Runner:
                        "flops": [0.0, 0.0], "phase_ms": {}}
         self.last = None
         self.np = np
+        # plain: the paper's comparison solver (every shift from x0 = 0, no recycling)
+        self.plain = plain
 
     def step(self, timing=False, e2e=False):
         """The whole workload: K outer steps of all M shifts. Returns work counts."""
@@ -345,8 +351,11 @@ class Runner:
         solves, worst, iters = 0, 0.0, 0
         for k in range(wl.K):
             P.rs_set_weights(self.w)
-            P.rs_update_recycle(recyc.RS_INIT if k == 0 else recyc.RS_UPDATE)
-            stats = P.rs_solve_shifts(self.X)
+            if self.plain:
+                stats = P.rs_solve_plain(self.X)
+            else:
+                P.rs_update_recycle(recyc.RS_INIT if k == 0 else recyc.RS_UPDATE)
+                stats = P.rs_solve_shifts(self.X)
             if e2e:
                 self.X_host.copy_(self.X, non_blocking=True)
             solves += wl.M
@@ -405,6 +414,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     config = workload_config(wl, args.precision)
+    if args.batched_local:
+        config["local_spaces"] = "batched: [W, g^(k-1,l), g^(k-1,l-1)], every shift of a step in one launch"
 
     if args.impl == "reference":
         # the FP64 oracle on the host cores; under torchrun only rank 0 works
@@ -450,7 +461,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    runner = Runner(wl, args.precision, dev)
+    runner = Runner(wl, args.precision, dev, batched_local=int(args.batched_local))
     if args.profile_case == "full":
         r = runner.step()
         torch.cuda.synchronize(dev)
@@ -583,6 +594,19 @@ def main():
         line["fp64_gpu"] = {"value": f_solves / (f_ms / 1000.0), "unit": "solves/s",
                             "ms_per_step": f_ms, "matvecs_per_s": f_mvs / (f_ms / 1000.0),
                             "worst_true_relres": r64.last["worst_relres"]}
+    if not args.no_plain and world == 1:
+        # the paper's comparison: the same outer iteration with every shift solved
+        # from x0 = 0 without recycling (same inner solver, tolerance and precision)
+        rp = Runner(wl, args.precision, dev, plain=True)
+        rp.step()
+        p_ms, p_solves, p_mvs = timed(rp, 1, flush)
+        line["no_recycling"] = {"value": p_solves / (p_ms / 1000.0), "unit": "solves/s",
+                                "ms_per_step": p_ms, "matvecs_per_solve": p_mvs / p_solves,
+                                "recycled_matvecs_per_solve": run_stats["matvecs"] / run_stats["solves"],
+                                "iters_per_step": rp.last["iters"],
+                                "worst_true_relres": rp.last["worst_relres"],
+                                "note": "recycled matvecs include the recycle space's own "
+                                        "(seeding solves, V_new steps, AU/EU images, local images)"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(wl, args.workload, args.cpu_seconds)
         line["cpu_baseline"] = cb

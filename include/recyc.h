@@ -54,6 +54,14 @@ typedef enum {
 
 typedef enum { RS_INIT = 0, RS_UPDATE = 1 } rs_recycle_mode;
 
+/* Inner solver of the per-shift corrections (Eq. corr_g). Both run the same
+ * Lanczos process on (I - K_l K_l^T)(A + gamma_l E), which is self-adjoint and
+ * positive definite on the complement of K_l; MINRES (the paper's, Eq. minShift)
+ * minimises the residual over [U_l, V_m], projected CG takes the Galerkin
+ * solution (T_m y = xi e_1; the residual is orthogonal to K_l and V_m). The
+ * principal-space solves of rs_update_recycle always use MINRES. */
+typedef enum { RS_MINRES = 0, RS_CG = 1 } rs_inner;
+
 /* Initial guesses from the principal space U~ (Sections 4.1 and 7). */
 typedef enum {
   RS_GUESS_ORTHOGONAL = 0, /* residual orthogonal to (A + gamma_l E) U~ (Eq. orthupdate):
@@ -88,6 +96,7 @@ typedef struct {
   int batched_local;       /* 0: paper's chain g^(k,l-1); 1: g^(k-1,l-1) instead */
   int guess;               /* rs_guess: how the initial guesses are projected */
   int I_L, I_R;            /* RS_GUESS_OBLIQUE2 anchors (1-based): 1 <= I_L <= I_split < I_R <= M */
+  int inner;               /* rs_inner: RS_MINRES (the paper's) or RS_CG */
   int radon_angles;        /* 0: C = H, the blur (sigma, radius). 1..3600: C = the parallel-beam
                               Radon transform of Section 8.3 with angles 1, 2, .., radon_angles
                               degrees (sigma, radius ignored); see below */
@@ -189,6 +198,16 @@ rs_status rs_set_recycle_basis(rs_problem* prob, const double* U_dev, int ncols)
  * shift reached maxit. */
 rs_status rs_solve_shifts(rs_problem* prob, double* X_dev, rs_solve_stats* stats_host,
                           const int* iters_override_host);
+
+/* The comparison solver of the paper's experiments (Section 8): each shifted
+ * system (A + gamma_l E_k) x = b of the current weights solved from x0 = 0 by
+ * the inner solver of `inner` with no recycling at all (no principal space, no
+ * local space), to the same tolerance (RS_MIXED: FP32 Krylov with FP64
+ * refinement sweeps). X_dev receives M x n doubles; stats_host (M entries) may
+ * be NULL. Needs only rs_set_weights; the recycled solver's state (the previous
+ * step's solutions and corrections) is left unchanged. Returns RS_ENOCONV if a
+ * shift reached maxit. */
+rs_status rs_solve_plain(rs_problem* prob, double* X_dev, rs_solve_stats* stats_host);
 
 /* Adjoint solves for the gradient of a loss of the solutions: (A + gamma_l E_k)
  * lambda_l = g_l for every shift, g_l = row l of G_dev (M x n doubles, e.g. the

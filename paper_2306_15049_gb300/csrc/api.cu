@@ -171,6 +171,7 @@ bool valid_desc(const rs_problem_desc* d, std::string* why) {
       !idx_ok(d->l_c) || !idx_ok(d->J_L) || !idx_ok(d->J_R))
     return fail("index fields must be in [1, M]");
   if (d->precision != RS_FP64 && d->precision != RS_MIXED) return fail("precision must be RS_FP64 or RS_MIXED");
+  if (d->inner != RS_MINRES && d->inner != RS_CG) return fail("inner must be RS_MINRES or RS_CG");
   if (d->guess != RS_GUESS_ORTHOGONAL && d->guess != RS_GUESS_OBLIQUE && d->guess != RS_GUESS_OBLIQUE2)
     return fail("guess must be RS_GUESS_ORTHOGONAL, RS_GUESS_OBLIQUE or RS_GUESS_OBLIQUE2");
   if (d->guess == RS_GUESS_OBLIQUE2 &&
@@ -635,7 +636,7 @@ void graph_timing_flush(rs_problem* P, int gi, int j0, int iters_done, double by
 template <typename T>
 int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_abs, int maxit,
                int keep, bool reorth, int* iters_out, double* eta_out, int* breakdown_out,
-               int s_host = 0) {
+               int s_host = 0, int cg = 0) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
@@ -655,7 +656,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
   CU(cudaMemcpyAsync(u, r, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CU(multi_axpy<T>(Kl, ld, cnt_use, 0, P->Ktr, -1.0, u, n, P->partials, s, nullptr));
   CU(reduce_partials(P->partials, z.G, 1, 1, P->scal + 0, s, nullptr, 0, nullptr));
-  CU(minres_init(P->st, P->scal + 0, P->Ktr, cnt_use, tol_abs, maxit, s));
+  CU(minres_init(P->st, P->scal + 0, P->Ktr, cnt_use, tol_abs, maxit, s, cg));
   CU(cudaMemsetAsync(xm, 0, n * sizeof(T), s));
   CU(cudaMemsetAsync(P->vzero, 0, n * sizeof(T), s));
   for (int i = 0; i < 3; ++i) CU(cudaMemsetAsync(P->dring[i], 0, n * sizeof(T), s));
@@ -772,7 +773,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
       P->use_persist = false;
       if (slot >= 0) P->pending_used = (size_t)slot;
       return run_minres<T>(P, gamma, r, use_K, tol_abs, maxit, keep, reorth, iters_out, eta_out,
-                           breakdown_out, s_host);
+                           breakdown_out, s_host, cg);
     }
     CU(le);
     timed_end(P, slot, 0, -1, 0, 0.0, 0.0);
@@ -1252,17 +1253,19 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
     CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
     double inner_tol = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * std::sqrt(r02)) : tol_abs;
     const int max_sw = P->mixed ? kMaxSweeps : 1;
+    int broke = 0;
     for (int sw = 0; sw < max_sw; ++sw) {
       int it = 0, bd = 0;
       double eta = 0.0;
       const int mi = forced >= 0 ? forced : P->d.maxit;
       const double ph1 = phase_begin(P);
       RS(run_minres<T>(P, gl, vp<T>(P->rT), sdim > 0, forced >= 0 ? 0.0 : inner_tol, mi, 0, false, &it, &eta, &bd,
-                       sdim));
+                       sdim, P->d.inner == RS_CG ? 1 : 0));
       sl.iters += it;
       sl.matvecs += it;
       sl.relres_est = eta / rnorm;
       sl.sweeps = sw + 1;
+      broke |= bd;
       if (sdim > 0) {
         CU(tri_solve_upper(P->Rk, kMaxLocal, P->cnt, P->st->z, P->zc, s));
         CU(gather_axpy<T>(cand, P->kept, P->cnt, P->zc, vp<T>(P->xm), n, s));
@@ -1279,7 +1282,10 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
       if (sw + 1 == max_sw) break;
     }
     gnz[l] = 1;
-    sl.status = (forced < 0 && sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) && sl.iters >= P->d.maxit)
+    // not converged: out of steps, or a CG pivot that vanished (MINRES breaks down only when
+    // the Krylov space is invariant, where its iterate is exact)
+    sl.status = (forced < 0 && sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) &&
+                 (sl.iters >= P->d.maxit || (broke && P->d.inner == RS_CG)))
                     ? RS_ENOCONV : RS_OK;
     if (sl.status == RS_ENOCONV) any_noconv = 1;
     if (stats) stats[l] = sl;
@@ -1291,6 +1297,57 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
   std::swap(P->Gcur, P->Gprev);
   P->gprev_nz = gnz;
   P->have_prev = true;
+  return any_noconv ? P->set_err(RS_ENOCONV, "a shift reached maxit") : RS_OK;
+}
+
+// The comparison solver of the paper's experiments (Section 8): every shift of
+// the current weights solved from x0 = 0 by the same inner solver with no
+// recycle space at all (no principal guess, no local space), to the same
+// tolerance, with the same refinement sweeps in mixed precision. It reads only
+// b and w_k and leaves the recycled solver's state alone.
+template <typename T>
+int solve_plain(rs_problem* P, double* X, rs_solve_stats* stats) {
+  const Dims& z = P->z;
+  const long n = z.n;
+  cudaStream_t s = P->s;
+  const double rnorm = P->bnorm;
+  const double tol_abs = P->d.tol * rnorm;
+  const int cg = P->d.inner == RS_CG ? 1 : 0;
+  int any_noconv = 0;
+  for (int l = 0; l < z.M; ++l) {
+    const double gl = P->gammas[l];
+    rs_solve_stats sl{};
+    double* x = X + (long)l * n;
+    CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    CU(convert<double, T>(P->b, vp<T>(P->rT), n, s));
+    sl.relres0 = 1.0;
+    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * rnorm) : tol_abs;
+    const int max_sw = P->mixed ? kMaxSweeps : 1;
+    int broke = 0;
+    for (int sw = 0; sw < max_sw; ++sw) {
+      int it = 0, bd = 0;
+      double eta = 0.0;
+      const double ph1 = phase_begin(P);
+      RS(run_minres<T>(P, gl, vp<T>(P->rT), false, inner_tol, P->d.maxit, 0, false, &it, &eta, &bd, 0, cg));
+      sl.iters += it;
+      sl.matvecs += it;
+      sl.relres_est = eta / rnorm;
+      sl.sweeps = sw + 1;
+      broke |= bd;
+      CU(axpby<T, double>(vp<T>(P->xm), 1.0, x, 1.0, n, s));
+      phase_end(P, 4, ph1);
+      RS(true_residual(P, gl, x, &sl.relres_true));
+      sl.matvecs += 1;
+      if (!P->mixed || sl.relres_true <= P->d.tol) break;
+      CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
+      inner_tol = std::max(0.5 * tol_abs, kInnerRho * sl.relres_true * rnorm);
+    }
+    sl.status = (sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) &&
+                 (sl.iters >= P->d.maxit || (broke && cg)))
+                    ? RS_ENOCONV : RS_OK;
+    if (sl.status == RS_ENOCONV) any_noconv = 1;
+    if (stats) stats[l] = sl;
+  }
   return any_noconv ? P->set_err(RS_ENOCONV, "a shift reached maxit") : RS_OK;
 }
 
@@ -1319,6 +1376,7 @@ struct BatchWork {
   std::vector<double> rnorm2, inner;
   std::vector<int> sdim;
   std::vector<char> gnz;
+  std::vector<char> broke;          // a CG pivot vanished in some sweep
 };
 
 // Device buffers of the joint launches.
@@ -1361,6 +1419,7 @@ int batch_prepare(BatchWork<T>& bw) {
   bw.inner.assign(M, 0.0);
   bw.sdim.assign(M, 0);
   bw.gnz.assign(M, 0);
+  bw.broke.assign(M, 0);
   double ph0 = phase_begin(P);
   for (int l = 0; l < M; ++l) {
     double* x = X + (long)l * n;
@@ -1480,7 +1539,8 @@ int batch_sweep_init(BatchWork<T>& bw) {
     CU(reduce_partials(P->partials, P->z.G, kMaxLocal, kDotStride, P->KtrB + (long)l * kMaxLocal, s, cnt, 0, nullptr));
     CU(multi_axpy<T>(bkl<T>(P, l), ld, cnt, 0, P->KtrB + (long)l * kMaxLocal, -1.0, u, n, P->partials, s, nullptr));
     CU(reduce_partials(P->partials, P->z.G, 1, 1, P->scalB + l, s, nullptr, 0, nullptr));
-    CU(minres_init(P->stB + l, P->scalB + l, P->KtrB + (long)l * kMaxLocal, cnt, bw.inner[l], P->d.maxit, s));
+    CU(minres_init(P->stB + l, P->scalB + l, P->KtrB + (long)l * kMaxLocal, cnt, bw.inner[l], P->d.maxit, s,
+                   P->d.inner == RS_CG ? 1 : 0));
     CU(cudaMemsetAsync(bvec<T>(P, l, 2), 0, n * sizeof(T), s));
     for (int i = 0; i < 3; ++i) CU(cudaMemsetAsync(bvec<T>(P, l, 6 + i), 0, n * sizeof(T), s));
   }
@@ -1635,6 +1695,7 @@ int batch_assemble(BatchWork<T>& bw, int sw) {
     sl.relres_est = std::fabs(m.eta) / P->bnorm;
     sl.sweeps = sw + 1;
     sl.local_dim = bw.sdim[l];
+    if (m.breakdown && P->d.inner == RS_CG) bw.broke[l] = 1;
     if (bw.sdim[l] > 0) {
       CU(tri_solve_upper(P->RkB + (long)l * kMaxLocal * kMaxLocal, kMaxLocal, P->cntB + l,
                          P->stB[l].z, P->zcB + (long)l * kMaxLocal, s));
@@ -1668,7 +1729,8 @@ int batch_finish(BatchWork<T>& bw, rs_solve_stats* stats) {
   int any_noconv = 0;
   for (int l = 0; l < z.M; ++l) {
     rs_solve_stats& sl = bw.st[l];
-    sl.status = (sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) && sl.iters >= P->d.maxit)
+    sl.status = (sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) &&
+                 (sl.iters >= P->d.maxit || bw.broke[l]))
                     ? RS_ENOCONV : RS_OK;
     if (sl.status == RS_ENOCONV) any_noconv = 1;
     if (stats) stats[l] = sl;
@@ -2002,6 +2064,14 @@ rs_status rs_solve_shifts_batched(rs_problem* const* probs, int count, double* c
       if (probs[i]->err != "no error") { set_null_error(probs[i]->err.c_str()); break; }
   }
   return (rs_status)rc;
+}
+
+rs_status rs_solve_plain(rs_problem* P, double* X_dev, rs_solve_stats* stats_host) {
+  if (!P) return RS_EINVAL;
+  if (P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  if (!X_dev) return (rs_status)P->set_err(RS_EINVAL, "X_dev is NULL");
+  if (P->mixed) return (rs_status)solve_plain<float>(P, X_dev, stats_host);
+  return (rs_status)solve_plain<double>(P, X_dev, stats_host);
 }
 
 rs_status rs_solve_adjoint(rs_problem* P, const double* G_dev, double* Lam_dev,

@@ -208,13 +208,43 @@ struct MinresState {
   int iters, maxit, stop, performed, breakdown, s;
   int dir_pending;         // fused path: the direction update of the last step is due
   int next_j;              // batched kernel: the step a later launch resumes at (1 at start)
+  int cg;                  // 1: projected CG recurrences instead of MINRES (same Lanczos process)
+  double cg_eta, cg_zeta;  // CG: the last pivot eta_{j-1} and coefficient zeta_{j-1}
   unsigned int cnt_a, cnt_b;   // last-CTA tickets of the fused kernels (0 between launches)
   double h[kMaxLocal];     // K^T Op v_j
   double h1[kMaxLocal], h2[kMaxLocal];
   double z[kMaxLocal];     // K^T r - sum_j tau_j hhat_j
 };
 cudaError_t minres_init(MinresState* st, const double* xi2, const double* Ktr, const int* s_dev,
-                        double tol_abs, int maxit, cudaStream_t s);
+                        double tol_abs, int maxit, cudaStream_t s, int cg = 0);
+
+// The CG scalar step (Lanczos form of CG: the LDL^T factorisation of T_m) on
+// column j of T_m in the arithmetic type S, from alpha_j, beta_j (st.beta) and
+// beta_{j+1}: lambda_j = beta_j / eta_{j-1}, zeta_j = -lambda_j zeta_{j-1}
+// (zeta_1 = xi), eta_j = alpha_j - lambda_j beta_j. The direction coefficients
+// come in the MINRES layout, d_j = (v_j - delta d_{j-1} - eps d_{j-2}) / gamma and
+// x += tau d_j, with delta = beta_j, eps = 0, 1/gamma = 1/eta_j, tau = zeta_j, so
+// the same direction and coupling (z) updates serve both; st.eta receives the
+// residual norm beta_{j+1} |zeta_j / eta_j|. Returns false on a zero pivot.
+template <typename S>
+__device__ inline bool cg_scalar(MinresState& st, S alpha, S beta_next, S* delta, S* eps, S* ig,
+                                 S* tau) {
+  const S beta = S(st.beta);
+  const bool first = st.iters == 0;
+  const S lam = first ? S(0) : beta / S(st.cg_eta);
+  const S zeta = first ? S(st.xi) : -lam * S(st.cg_zeta);
+  const S eta = alpha - lam * beta;
+  if (!(eta != S(0)) || !isfinite((double)eta)) return false;
+  const S ie = S(1) / eta;
+  *delta = beta;
+  *eps = S(0);
+  *ig = ie;
+  *tau = zeta;
+  st.cg_eta = (double)eta;
+  st.cg_zeta = (double)zeta;
+  st.eta = (double)(beta_next * fabs(zeta * ie));
+  return true;
+}
 cudaError_t minres_step(MinresState* st, const double* hdots, const double* partials, int G,
                         double* alphas_rec, double* betas_rec, int rec_cap, cudaStream_t s);
 template <typename T>

@@ -27,7 +27,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 __global__ void k_minres_init(MinresState* st, const double* xi2, const double* Ktr,
-                              const int* s_dev, double tol_abs, int maxit) {
+                              const int* s_dev, double tol_abs, int maxit, int cg) {
   if (threadIdx.x != 0) return;
   const int s = s_dev ? *s_dev : 0;
   const double xi = sqrt(xi2 ? *xi2 : 0.0);
@@ -43,6 +43,9 @@ __global__ void k_minres_init(MinresState* st, const double* xi2, const double* 
   st->breakdown = 0;
   st->dir_pending = 0;
   st->next_j = 1;
+  st->cg = cg;
+  st->cg_eta = 1.0;
+  st->cg_zeta = xi;
   st->cnt_a = 0;
   st->cnt_b = 0;
   st->s = s;
@@ -76,6 +79,41 @@ __global__ void k_minres_step(MinresState* st, const double* __restrict__ hdots,
   const double alpha = hdots[s];
   const double beta = st->beta;
   const double beta_next = sqrt(unorm2);
+  if (st->cg) {
+    double delta, eps, ig, tau;
+    MinresState& m = *st;
+    if (!cg_scalar<double>(m, alpha, beta_next, &delta, &eps, &ig, &tau)) {
+      st->breakdown = 1;
+      st->stop = 1;
+      st->performed = 0;
+      return;
+    }
+    for (int k = 0; k < s; ++k) {
+      const double hk = hdots[k];
+      const double hh = (hk - delta * st->h1[k]) * ig;
+      st->z[k] -= tau * hh;
+      st->h2[k] = st->h1[k];
+      st->h1[k] = hh;
+      st->h[k] = hk;
+    }
+    const int j = st->iters;
+    if (alphas_rec && j < rec_cap) {
+      alphas_rec[j] = alpha;
+      betas_rec[j] = beta_next;
+    }
+    st->alpha = alpha;
+    st->beta_next = beta_next;
+    st->delta = delta;
+    st->eps = eps;
+    st->inv_gamma = ig;
+    st->tau = tau;
+    st->inv_beta_next = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
+    st->iters = j + 1;
+    st->performed = 1;
+    st->beta = beta_next;
+    if (fabs(st->eta) <= st->tol_abs || beta_next == 0.0 || st->iters >= st->maxit) st->stop = 1;
+    return;
+  }
   const double eps = st->sn2 * beta;
   const double dbar = st->cs2 * beta;
   const double delta = st->cs1 * dbar + st->sn1 * alpha;
@@ -175,8 +213,8 @@ __global__ void k_poll(const MinresState* st, int* out) {
 }  // namespace
 
 cudaError_t minres_init(MinresState* st, const double* xi2, const double* Ktr, const int* s_dev,
-                        double tol_abs, int maxit, cudaStream_t s) {
-  k_minres_init<<<1, 32, 0, s>>>(st, xi2, Ktr, s_dev, tol_abs, maxit);
+                        double tol_abs, int maxit, cudaStream_t s, int cg) {
+  k_minres_init<<<1, 32, 0, s>>>(st, xi2, Ktr, s_dev, tol_abs, maxit, cg);
   return launched();
 }
 

@@ -238,6 +238,34 @@ k_mr_lanczos(MinresState* st, MrB<T> b, long n, double* alphas_rec, double* beta
     const double alpha_d = shd[s];
     const double beta_d = ss.beta;
     const double beta_next = sqrt(unorm2);
+    if (ss.cg) {
+      double delta, eps, ig, tau;
+      if (!cg_scalar<double>(ss, alpha_d, beta_next, &delta, &eps, &ig, &tau)) {
+        ss.breakdown = 1;
+        ss.stop = 1;
+      } else {
+        for (int k = 0; k < s; ++k) {
+          const double hh = (shd[k] - delta * ss.h1[k]) * ig;
+          ss.z[k] -= tau * hh;
+          ss.h2[k] = ss.h1[k];
+          ss.h1[k] = hh;
+        }
+        const int j = ss.iters;
+        if (alphas_rec && j < rec_cap) {
+          alphas_rec[j] = alpha_d;
+          betas_rec[j] = beta_next;
+        }
+        ss.delta = delta;
+        ss.eps = eps;
+        ss.inv_gamma = ig;
+        ss.tau = tau;
+        ss.inv_beta_next = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
+        ss.iters = j + 1;
+        ss.beta = beta_next;
+        ss.dir_pending = 1;
+        if (fabs(ss.eta) <= ss.tol_abs || beta_next == 0.0 || ss.iters >= ss.maxit) ss.stop = 1;
+      }
+    } else {
     const double eps = ss.sn2 * beta_d;
     const double dbar = ss.cs2 * beta_d;
     const double delta = ss.cs1 * dbar + ss.sn1 * alpha_d;
@@ -275,6 +303,7 @@ k_mr_lanczos(MinresState* st, MrB<T> b, long n, double* alphas_rec, double* beta
       ss.beta = beta_next;
       ss.dir_pending = 1;
       if (fabs(ss.eta) <= ss.tol_abs || beta_next == 0.0 || ss.iters >= ss.maxit) ss.stop = 1;
+    }
     }
   }
   __syncthreads();

@@ -166,7 +166,44 @@ __device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T*
     T un = (lane < kWarps) ? red[lane][0] : T(0);
     un = warp_sum_w<T>(un);
     const int s = ss.s;
-    if (lane == 0) {
+    if (lane == 0 && ss.cg) {
+      const S beta_next = sqrt(S(un));
+      const S alpha_d = S(hd[s]);
+      S delta, eps, ig, tau;
+      if (!cg_scalar<S>(ss, alpha_d, beta_next, &delta, &eps, &ig, &tau)) {
+        ss.breakdown = 1;
+        ss.stop = 1;
+        ss.dir_pending = 0;
+        sc[0] = 0.0;
+      } else {
+        const S ibn = (beta_next > S(0)) ? S(1) / beta_next : S(0);
+        const int it = ss.iters;
+        if (blockIdx.x == 0 && p.arec && it < p.rec_cap) {
+          p.arec[it] = (double)alpha_d;
+          p.brec[it] = (double)beta_next;
+        }
+        sc[0] = 1.0;
+        sc[1] = (double)delta;
+        sc[2] = (double)eps;
+        sc[3] = (double)ig;
+        sc[4] = (double)tau;
+        ss.delta = (double)delta;
+        ss.eps = (double)eps;
+        ss.inv_gamma = (double)ig;
+        ss.tau = (double)tau;
+        ss.inv_beta_next = (double)ibn;
+        ss.iters = it + 1;
+        ss.beta = (double)beta_next;
+        ss.dir_pending = 1;
+        if (fabs(ss.eta) <= ss.tol_abs || !(beta_next > S(0)) || ss.iters >= ss.maxit) ss.stop = 1;
+        cf.delta = T(delta);
+        cf.eps = T(eps);
+        cf.inv_gamma = T(ig);
+        cf.tau = T(tau);
+        cf.inv_beta_next = T(ibn);
+        cf.beta = T(beta_next);
+      }
+    } else if (lane == 0) {
       const S unorm2 = S(un);
       const S alpha_d = S(hd[s]);
       const S beta_d = S(ss.beta);

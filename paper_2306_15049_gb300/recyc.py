@@ -18,6 +18,7 @@ RS_OK, RS_EINVAL, RS_ENOCONV, RS_EBREAKDOWN, RS_ENOTREADY, RS_ECUDA, RS_ENOMEM =
 RS_FP64, RS_MIXED = 0, 1
 RS_INIT, RS_UPDATE = 0, 1
 RS_GUESS_ORTHOGONAL, RS_GUESS_OBLIQUE, RS_GUESS_OBLIQUE2 = 0, 1, 2
+RS_MINRES, RS_CG = 0, 1
 STATUS_NAMES = {0: "RS_OK", 1: "RS_EINVAL", 2: "RS_ENOCONV", 3: "RS_EBREAKDOWN",
                 4: "RS_ENOTREADY", 5: "RS_ECUDA", 6: "RS_ENOMEM"}
 
@@ -34,7 +35,7 @@ class rs_problem_desc(ctypes.Structure):
         ("i_star", ctypes.c_int), ("l_c", ctypes.c_int), ("J_L", ctypes.c_int),
         ("J_R", ctypes.c_int), ("precision", ctypes.c_int), ("batched_local", ctypes.c_int),
         ("guess", ctypes.c_int), ("I_L", ctypes.c_int), ("I_R", ctypes.c_int),
-        ("radon_angles", ctypes.c_int),
+        ("inner", ctypes.c_int), ("radon_angles", ctypes.c_int),
     ]
 
 
@@ -75,6 +76,7 @@ _SIGS = {
     "rs_set_recycle_basis": (_I, [_P, _P, _I]),
     "rs_solve_shifts": (_I, [_P, _P, ctypes.POINTER(rs_solve_stats), ctypes.POINTER(_I)]),
     "rs_initial_guesses": (_I, [_P, _P, _P]),
+    "rs_solve_plain": (_I, [_P, _P, ctypes.POINTER(rs_solve_stats)]),
     "rs_solve_adjoint": (_I, [_P, _P, _P, ctypes.POINTER(rs_solve_stats)]),
     "rs_batch_scratch_bytes": (ctypes.c_size_t, [_I, _I]),
     "rs_solve_shifts_batched": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P),
@@ -131,7 +133,7 @@ def make_desc(height: int, width: int, sigma: float, radius: int, gammas: Sequen
               vnew_cap: int, I_split: int, i1: int, i2: int, i_star: int, l_c: int, J_L: int,
               J_R: int, precision: int = RS_FP64, batched_local: int = 0,
               guess: int = RS_GUESS_ORTHOGONAL, I_L: Optional[int] = None,
-              I_R: Optional[int] = None, radon_angles: int = 0):
+              I_R: Optional[int] = None, radon_angles: int = 0, inner: int = RS_MINRES):
     """An rs_problem_desc; the returned tuple keeps the shift array alive.
     I_L / I_R (two-anchor oblique guesses) default to i_star and l_c."""
     garr = (ctypes.c_double * len(gammas))(*[float(g) for g in gammas])
@@ -139,7 +141,8 @@ def make_desc(height: int, width: int, sigma: float, radius: int, gammas: Sequen
                         ctypes.cast(garr, ctypes.POINTER(ctypes.c_double)), float(tol), maxit,
                         p_max, a_ritz, b_ritz, n_ritz_local, vnew_cap, I_split, i1, i2, i_star,
                         l_c, J_L, J_R, precision, batched_local, guess,
-                        i_star if I_L is None else I_L, l_c if I_R is None else I_R, radon_angles)
+                        i_star if I_L is None else I_L, l_c if I_R is None else I_R, inner,
+                        radon_angles)
     return d, garr
 
 
@@ -248,6 +251,12 @@ class Problem:
         if iters_override is not None:
             ov = (ctypes.c_int * self.M)(*[int(v) for v in iters_override])
         st = self.lib.rs_solve_shifts(self.h, _ptr(X_dev), stats, ov)
+        self._check(st, (RS_OK, RS_ENOCONV) if allow_noconv else (RS_OK,))
+        return [dict((f, getattr(s, f)) for f, _ in rs_solve_stats._fields_) for s in stats]
+
+    def rs_solve_plain(self, X_dev, allow_noconv=False):
+        stats = (rs_solve_stats * self.M)()
+        st = self.lib.rs_solve_plain(self.h, _ptr(X_dev), stats)
         self._check(st, (RS_OK, RS_ENOCONV) if allow_noconv else (RS_OK,))
         return [dict((f, getattr(s, f)) for f, _ in rs_solve_stats._fields_) for s in stats]
 

@@ -23,7 +23,7 @@ def lib_ready():
 class Pair:
     """Oracle and GPU views of one workload."""
 
-    def __init__(self, wl, precision=0, batched_local=0, maxit=None, x_image=None, guess=0):
+    def __init__(self, wl, precision=0, batched_local=0, maxit=None, x_image=None, guess=0, inner=0):
         torch = torch_cuda()
         lib_ready()
         from paper_2306_15049_gb300 import recyc
@@ -43,12 +43,13 @@ class Pair:
         self.x_true = x.reshape(-1)
         self.d, self.b = make_data(self.op, x, z, wl.eta)
         self.prm = Params.from_workload(wl, batched_local=bool(batched_local))
+        self.prm.inner = "cg" if inner else "minres"
         # every workload here converges in a few thousand steps; a cap keeps a
         # regression from running for hours
         self.prm.maxit = min(self.prm.maxit, 20000) if maxit is None else maxit
         self.gammas = wl.gammas()
         self.desc = desc_for(wl, precision=precision, batched_local=batched_local,
-                             maxit=self.prm.maxit, guess=guess)
+                             maxit=self.prm.maxit, guess=guess, inner=inner)
         dev = torch.device("cuda:0")
         xt = torch.tensor(self.x_true, dtype=torch.float64, device=dev)
         zt = torch.tensor(z.reshape(-1), dtype=torch.float64, device=dev)

@@ -1,0 +1,82 @@
+"""GPU parity of the projected-CG inner solver (rs_problem_desc.inner = RS_CG:
+the Galerkin solution of the same projected Lanczos process) against the FP64
+oracle's projected CG, through the C ABI: whole outer steps shift by shift, in
+mixed precision, and with batched local spaces in one launch.
+
+Tolerances as for MINRES: FP64 solutions within 1e-6 where both ran the same
+step counts (1e-4 otherwise, counts within 1 %+2); mixed 1e-4; every system to
+its tolerance."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.outer import run as oracle_run
+from oracle.recycle import State, outer_step
+from paper_2306_15049_gb300.recyc import RS_CG
+from tests.gpu_util import Pair, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c1_cg():
+    wl = synth.C1
+    pr = Pair(wl, inner=RS_CG)
+    steps, lstars = oracle_run(pr.op, pr.b, pr.d, pr.gammas, pr.prm, wl.K, wl.beta)
+    return wl, steps
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c1_outer_steps_with_projected_cg_match_oracle(c1_cg, precision):
+    wl, steps = c1_cg
+    pr = Pair(wl, precision=precision, inner=RS_CG)
+    n_eq = n_tot = 0
+    for k in range(wl.K):
+        pr.P.rs_set_weights(pr.t(steps[k].extra["w"]))
+        pr.P.rs_update_recycle(0 if k == 0 else 1)
+        X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+        stats = pr.P.rs_solve_shifts(X)
+        Xn = pr.n(X)
+        for l in range(wl.M):
+            st = stats[l]
+            assert st["relres_true"] <= wl.tol * (1 + 1e-6), (k, l, st)
+            e = rel(Xn[l], steps[k].X[l])
+            n_tot += 1
+            if precision == 0:
+                assert abs(st["iters"] - steps[k].iters[l]) <= max(2, 0.01 * steps[k].iters[l]), (k, l)
+                if st["iters"] == steps[k].iters[l]:
+                    n_eq += 1
+                    assert e <= 1e-6, (k, l, e)
+                else:
+                    assert e <= 1e-4, (k, l, e)
+            else:
+                assert e <= 1e-4, (k, l, e)
+    if precision == 0:
+        assert n_eq >= 0.75 * n_tot
+
+
+def test_projected_cg_in_the_batched_launch_matches_oracle():
+    wl = synth.tiny(64, 56, sigma=1.5, radius=4, M=8, p=10, n_ritz_local=4, seed=12, tol=1e-9)
+    old = os.environ.get("RS_BATCH")
+    os.environ["RS_BATCH"] = "1"
+    try:
+        pr = Pair(wl, precision=0, batched_local=1, inner=RS_CG)
+    finally:
+        if old is None:
+            del os.environ["RS_BATCH"]
+        else:
+            os.environ["RS_BATCH"] = old
+    S = State()
+    for k, w in enumerate([np.ones(2 * wl.n), synth.random_weights(wl.n, 5, lo=1.0, hi=300.0)]):
+        o = outer_step(pr.op, pr.b, pr.gammas, w, S, pr.prm)
+        pr.P.rs_set_weights(pr.t(w))
+        pr.P.rs_update_recycle(0 if k == 0 else 1)
+        X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+        stats = pr.P.rs_solve_shifts(X)
+        assert pr.P.rs_get_info()["minres_kernel"] == 3
+        for l in range(wl.M):
+            assert stats[l]["relres_true"] <= wl.tol * (1 + 1e-6), (k, l, stats[l])
+            lim = 1e-6 if stats[l]["iters"] == o.iters[l] else 1e-4
+            assert rel(pr.n(X)[l], o.X[l]) <= lim, (k, l)
