@@ -3,9 +3,9 @@ the Galerkin solution of the same projected Lanczos process) against the FP64
 oracle's projected CG, through the C ABI: whole outer steps shift by shift, in
 mixed precision, and with batched local spaces in one launch.
 
-Tolerances as for MINRES: FP64 solutions within 1e-6 where both ran the same
-step counts (1e-4 otherwise, counts within 1 %+2); mixed 1e-4; every system to
-its tolerance."""
+Tolerances: FP64 solutions within 1e-6 where both ran the same step counts
+(1e-4 otherwise, counts within 3 % or 3 steps: CG's stopping step is sensitive
+to rounding); mixed 1e-4; every system to its tolerance."""
 import os
 
 import numpy as np
@@ -45,7 +45,10 @@ def test_c1_outer_steps_with_projected_cg_match_oracle(c1_cg, precision):
             e = rel(Xn[l], steps[k].X[l])
             n_tot += 1
             if precision == 0:
-                assert abs(st["iters"] - steps[k].iters[l]) <= max(2, 0.01 * steps[k].iters[l]), (k, l)
+                # CG's residual oscillates about the tolerance for several steps, so its
+                # stopping step moves with rounding (the oracle's own count on C1's first
+                # plain solve spans 283..290 under 1e-14 relative perturbations of b)
+                assert abs(st["iters"] - steps[k].iters[l]) <= max(3, 0.03 * steps[k].iters[l]), (k, l)
                 if st["iters"] == steps[k].iters[l]:
                     n_eq += 1
                     assert e <= 1e-6, (k, l, e)

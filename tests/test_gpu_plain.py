@@ -42,7 +42,12 @@ def test_plain_solves_match_the_oracle_without_recycling(inner, precision):
             assert st["relres0"] == 1.0 and st["local_dim"] == 0
             e = rel(Xn[l], Xo[l])
             if precision == 0:
-                assert abs(st["iters"] - its[l]) <= 1, (l, st["iters"], its[l])
+                # MINRES's residual decreases monotonically, so the stopping step is robust
+                # to rounding; CG's residual oscillates about the tolerance for several steps
+                # (on C1's first shift the oracle's own count moves over 283..290 when b is
+                # perturbed by 1e-14 relative)
+                lim_it = 1 if inner == RS_MINRES else max(3, int(0.03 * its[l]))
+                assert abs(st["iters"] - its[l]) <= lim_it, (l, st["iters"], its[l])
                 assert e <= (1e-6 if st["iters"] == its[l] else 1e-4), (l, e)
                 assert st["matvecs"] == st["iters"] + 1
             else:
