@@ -306,6 +306,8 @@ struct rs_problem {
   bool use_persist = true;
   int last_resident = -1;   // kind of the last persistent launch (1 resident, 0 streaming)
   bool use_coop_cgs = true; // CGS2 blocks as one cooperative launch
+  int stream_ctas = 0;       // > 0: persistent solves stream tiles on at most this many CTAs
+  bool use_prefetch = true;  // persistent MINRES kernels stage tiles ahead with cp.async
   double* partials_p = nullptr;
   GridBar* gbar = nullptr;
 
@@ -761,11 +763,13 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     mp.brec = keep ? P->brec : nullptr;
     mp.rec_cap = keep;
     mp.j0 = n_unfused + 1;
+    mp.prefetch = P->use_prefetch ? 1 : 0;
     CU(cudaMemsetAsync(P->gbar, 0, sizeof(GridBar), s));
     const int slot = timed_begin(P);
     int G = 0, resident = 0;
     const cudaError_t le = mr_persist<T>(P->st, mp, P->d.height, P->d.width, P->tp, P->gbar,
-                                         use_K ? std::max(s_host, 1) : 1, s, &G, &resident);
+                                         use_K ? std::max(s_host, 1) : 1, s, &G, &resident,
+                                         P->stream_ctas);
     P->last_resident = resident;
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
       // not co-resident on this device: the step kernels below take over
@@ -1579,12 +1583,13 @@ int batch_run(std::vector<BatchWork<T>>& ws, const BatchScratch& sc, int capacit
         mp.partA = P->partials_p;
         mp.partB = P->partials_p + (long)kPersistMaxBlocks * (kMaxLocal + 1);
         mp.j0 = first_launch ? 1 : P->st_host[l].next_j;
+        mp.prefetch = P->use_prefetch ? 1 : 0;
         const int it_before = first_launch ? 0 : P->st_host[l].iters;
         CU(cudaMemsetAsync(P->gbar, 0, sizeof(GridBar), P->s));
         const int slot = timed_begin(P);
         int G = 0, resident = 0;
         CU(mr_persist<T>(P->stB + l, mp, P->d.height, P->d.width, P->tp, P->gbar,
-                         std::max(ws[m.w].sdim[l], 1), P->s, &G, &resident));
+                         std::max(ws[m.w].sdim[l], 1), P->s, &G, &resident, P->stream_ctas));
         timed_end(P, slot, 0, -1, 0, 0.0, 0.0);
         RS(read_back(P, &P->st_host[l], P->stB + l, sizeof(MinresState)));
         RS(coop_check(P));
@@ -1637,6 +1642,7 @@ int batch_run(std::vector<BatchWork<T>>& ws, const BatchScratch& sc, int capacit
     bt.min_active = (gmin * 2 <= capacity / std::max(1, B / 2)) ? (B + 1) / 2 : 0;
     bt.part = sc.part;
     bt.stopf = sc.stopf;
+    bt.prefetch = P0->use_prefetch ? 1 : 0;
     std::vector<int> it0(B, 0);   // steps before this launch (0: minres_init just ran)
     if (!first_launch)
       for (int i = 0; i < B; ++i) it0[i] = ws[live[i].w].P->st_host[live[i].l].iters;
@@ -1879,6 +1885,11 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   if (const char* g = std::getenv("RS_BATCH")) P->use_batch = std::strcmp(g, "0") != 0;
   // RS_COOP_CGS=0 runs CGS2 column by column (several launches per candidate)
   if (const char* g = std::getenv("RS_COOP_CGS")) P->use_coop_cgs = std::strcmp(g, "0") != 0;
+  // RS_STREAM_CTAS=N (N >= 1) runs every persistent solve in the streaming kernel on at
+  // most N CTAs, so that small images exercise the multi-tile path (tests)
+  if (const char* g = std::getenv("RS_STREAM_CTAS")) P->stream_ctas = std::max(0, std::atoi(g));
+  // RS_PREFETCH=0 stages every tile synchronously in the persistent MINRES kernels
+  if (const char* g = std::getenv("RS_PREFETCH")) P->use_prefetch = std::strcmp(g, "0") != 0;
   P->gprev_nz.assign(desc->M, 0);
   Carver cv{(char*)workspace_dev};
   carve(P, cv);

@@ -327,6 +327,7 @@ struct MrP {
   double* brec;
   int rec_cap;
   int j0;              // first step of this launch
+  int prefetch;        // stage tiles with cp.async ahead of their use (where the layout allows)
 };
 // One system of a batched solve: its state, image (H x W, its own weights w
 // and blur taps: 2 kMaxTaps - 1 entries centred at kMaxTaps - 1, zero beyond
@@ -365,6 +366,7 @@ struct MrBatch {
   int min_active;      // leave the launch when fewer systems are running
   double* part;        // partial sums (entries of T)
   int* stopf;          // B
+  int prefetch;        // stage tiles with cp.async ahead of their use (where the layout allows)
 };
 // Run the batch (G CTAs) with the stencil of radius R (>= every system's
 // radius) until every system has stopped or fewer than min_active run (the host
@@ -376,10 +378,12 @@ int mr_batch_capacity(int radius, int precision_bytes);
 
 // One launch runs the solve to its stop. s_alloc: the widest local space the
 // resident kernel must hold in shared memory. resident (out): 1 if the
-// one-CTA-per-tile kernel ran, 0 for the streaming one.
+// one-CTA-per-tile kernel ran, 0 for the streaming one. max_ctas > 0 forces
+// the streaming kernel on at most that many CTAs.
 template <typename T>
 cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Taps& tp, GridBar* bar,
-                       int s_alloc, cudaStream_t s, int* launched_blocks, int* resident);
+                       int s_alloc, cudaStream_t s, int* launched_blocks, int* resident,
+                       int max_ctas = 0);
 bool mr_persist_supported(int radius);
 
 // ---------------------------------------------------------------- cgs.cu

@@ -345,6 +345,17 @@ __device__ __forceinline__ void tile_store_dots(const T* ax, const T* ex, const 
   }
 }
 
+// Whether k_mr_persist double-buffers its staged tile (FP32: two CTAs per SM
+// still fit), and its dynamic shared memory in elements of T.
+template <typename T>
+__host__ __device__ constexpr bool persist_prefetch() { return sizeof(T) == 4; }
+
+template <typename T>
+__host__ __device__ inline size_t persist_smem_elems(int r) {
+  return (size_t)op_tile_smem_elems(r) +
+         (persist_prefetch<T>() ? (size_t)(kTileH + 4 * r) * (kTileW + 4 * r) : 0);
+}
+
 // ---------------------------------------------------------------------------
 // one CTA per tile, vectors of the CTA's pixels in registers
 // ---------------------------------------------------------------------------
@@ -413,6 +424,13 @@ k_mr_resident(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar, in
       const bool ok = (i0 + ti) < H && (j0 + tj) < W;
       Ks[k * kTile + e] = ok ? p.K[(long)k * p.ldk + (long)(i0 + ti) * W + (j0 + tj)] : T(0);
     }
+  // The next step's u tile (with its halo) is copied into shared memory
+  // asynchronously right after the barrier that publishes it, so that its L2
+  // round trip overlaps the reduction of the norm partials and the scalar step
+  // (the same decision in every CTA).
+  const bool pre = p.prefetch && (W % Vec16<T>::n) == 0 &&
+                   (reinterpret_cast<unsigned long long>(p.u) & 15ull) == 0;
+  if (pre) stage_halo_async<T, R>(p.u, H, W, bufA, tyi, txi);
   __syncthreads();
 
   unsigned long long nb = 0;
@@ -431,8 +449,15 @@ k_mr_resident(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar, in
     if (ss.stop) break;
     // ---------------- phase A ----------------
     T ax[kPPT], ex[kPPT], vc[kPPT], yk[kPPT];
-    op_tile_fast<T, R, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, bufA, bufB, true, ax, ex, vc,
-                             tyi, txi);
+    if (pre) {
+      cp_async_wait_all();
+      __syncthreads();
+      op_tile_fast<T, R, true, T, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, bufA, bufB, true, ax,
+                                        ex, vc, tyi, txi);
+    } else {
+      op_tile_fast<T, R, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, bufA, bufB, true, ax, ex, vc,
+                               tyi, txi);
+    }
     T acc[kDots];
 #pragma unroll
     for (int k = 0; k < kDots; ++k) acc[k] = T(0);
@@ -478,9 +503,11 @@ k_mr_resident(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar, in
       store_norm_partial<T>(accb, red, partB);
     }
     if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    if (pre) stage_halo_async<T, R>(p.u, H, W, bufA, tyi, txi);
     scalar_step<T>(partB, G, hd, red, ss, cf, sc, p);
     ++j;
   }
+  if (pre) cp_async_wait_all();   // no copy may land after the CTA has left
   if (failed) return;
 #pragma unroll
   for (int q = 0; q < kPPT; ++q)
@@ -506,8 +533,17 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (H + kTileH - 1) / kTileH;
   const int ntiles = tiles_x * tiles_y;
   const long n = (long)H * W;
+  constexpr int kStage = (kTileH + 4 * R) * (kTileW + 4 * R);
   T* bufA = reinterpret_cast<T*>(smem_raw);
-  T* bufB = bufA + (kTileH + 4 * R) * (kTileW + 4 * R);
+  T* bufB = bufA + kStage;
+  // FP32 solves (two CTAs per SM still fit) double-buffer the staged tile:
+  // while a tile's stencil runs, the next tile's halo is already on its way
+  // (cp.async); the first tile of a step is requested right after the barrier
+  // that publishes u, before the scalar step. The same decision in every CTA.
+  constexpr bool kPF = persist_prefetch<T>();
+  T* bufA2 = bufB + (kTileH + 4 * R) * (kTileW + 2 * R);
+  const bool pre = kPF && p.prefetch && (W % Vec16<T>::n) == 0 &&
+                   (reinterpret_cast<unsigned long long>(p.u) & 15ull) == 0;
   T* partA = reinterpret_cast<T*>(p.partA);
   T* partB = reinterpret_cast<T*>(p.partB);
   const Ptrs<T> ptr{p};
@@ -516,6 +552,8 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
   const T gam = T(__ldcg(p.gamma));
   __syncthreads();
   if (threadIdx.x == 0) coef_from_state(ss, cf);
+  if (pre && (int)blockIdx.x < ntiles)
+    stage_halo_async<T, R>(p.u, H, W, bufA, (int)blockIdx.x / tiles_x, (int)blockIdx.x % tiles_x);
   __syncthreads();
 
   int j = p.j0;
@@ -532,9 +570,16 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
     const T* d2 = ptr.d(j - 3);
     T* dout = ptr.d(j - 1);
     T* vj = ptr.v(j);
-    for (int t = blockIdx.x; t < ntiles; t += G) {
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += G, ++it) {
       const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
       const int i0 = tyi * kTileH, j0 = txi * kTileW;
+      T* cur = (it & 1) ? bufA2 : bufA;
+      const bool more = t + (int)G < ntiles;
+      if (pre && !stopped && more) {
+        const int tn = t + (int)G;
+        stage_halo_async<T, R>(p.u, H, W, (it & 1) ? bufA : bufA2, tn / tiles_x, tn % tiles_x);
+      }
       if (pend) {
         const T de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau;
         T pv[kPPT], p1[kPPT], p2[kPPT], px[kPPT];
@@ -565,8 +610,16 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
       }
       if (!stopped) {
         T ax[kPPT], ex[kPPT], vc[kPPT];
-        op_tile_fast<T, R, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, bufA, bufB, true, ax, ex,
-                                 vc, tyi, txi);
+        if (pre) {
+          if (more) cp_async_wait_group<1>();
+          else cp_async_wait_all();
+          __syncthreads();
+          op_tile_fast<T, R, true, T, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, cur, bufB, true, ax,
+                                            ex, vc, tyi, txi);
+        } else {
+          op_tile_fast<T, R, true>(p.u, cf.inv_beta_next, p.w, H, W, sg, bufA, bufB, true, ax, ex,
+                                   vc, tyi, txi);
+        }
         tile_store_dots<T>(ax, ex, vc, gam, i0, j0, H, W, s, p.y, vj, p.K, p.ldk, acc);
       }
       __syncthreads();   // the tile buffers are reused by the next tile
@@ -633,9 +686,12 @@ k_mr_persist(MinresState* st, MrP<T> p, int H, int W, Taps tp, GridBar* bar) {
       store_norm_partial<T>(accb, red, partB);
     }
     if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    if (pre && (int)blockIdx.x < ntiles)
+      stage_halo_async<T, R>(p.u, H, W, bufA, (int)blockIdx.x / tiles_x, (int)blockIdx.x % tiles_x);
     scalar_step<T>(partB, G, hd, red, ss, cf, sc, p);
     ++j;
   }
+  if (pre) cp_async_wait_all();   // no copy may land after the CTA has left
   // the pending direction update was applied by the last phase A
   if (blockIdx.x == 0 && !failed) store_state(st, ss);
 }
@@ -729,12 +785,16 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
   const bool member = b >= 0;
   T* bufA = reinterpret_cast<T*>(smem_raw);
   T* bufB = bufA + (kTileH + 4 * R) * (kTileW + 4 * R);
+  T* bufA2 = bufB + (kTileH + 4 * R) * (kTileW + 2 * R);   // second staging buffer (prefetch)
   const int sysid = member ? bt.sysidx[b] : bt.sysidx[0];
   const MrBatchSys<T> sy = bt.sys[sysid];
   const int H = sy.H, W = sy.W;
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (H + kTileH - 1) / kTileH;
   const int ntiles = tiles_x * tiles_y;
   const long n = (long)H * W;
+  // FP32: double-buffered tile staging as in k_mr_persist (a per-CTA decision)
+  const bool pre = persist_prefetch<T>() && bt.prefetch && member && (W % Vec16<T>::n) == 0 &&
+                   (reinterpret_cast<unsigned long long>(sy.u) & 15ull) == 0;
   // per-system partial sums: rows 0..s dots, row kMaxLocal + 1 the norm
   T* part = reinterpret_cast<T*>(bt.part) + (member ? cm.w : 0);
   T* partn = part + (long)(kMaxLocal + 1) * gb;
@@ -744,6 +804,7 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
   const T gam = T(sy.gamma);
   __syncthreads();
   if (threadIdx.x == 0 && member) coef_from_state(ss, cf);
+  if (pre && r < ntiles) stage_halo_async<T, R>(sy.u, H, W, bufA, r / tiles_x, r % tiles_x);
   __syncthreads();
   auto vptr = [&](int j) -> T* { return j <= 0 ? sy.vzero : MrBatchSys<T>::pick(sy.vring, j % 3); };
   auto dptr = [&](int j) -> T* { return MrBatchSys<T>::pick(sy.dring, ((j % 3) + 3) % 3); };
@@ -764,9 +825,14 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
       const T* d2 = dptr(j - 3);
       T* dout = dptr(j - 1);
       T* vj = vptr(j);
-      for (int t = r; t < ntiles; t += gb) {
+      int it = 0;
+      for (int t = r; t < ntiles; t += gb, ++it) {
         const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
         const int i0 = tyi * kTileH, j0 = txi * kTileW;
+        T* cur = (it & 1) ? bufA2 : bufA;
+        const bool more = t + gb < ntiles;
+        if (pre && !stopped && more)
+          stage_halo_async<T, R>(sy.u, H, W, (it & 1) ? bufA : bufA2, (t + gb) / tiles_x, (t + gb) % tiles_x);
         if (pend) {
           const T de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau;
           T pv[kPPT], p1[kPPT], p2[kPPT], px[kPPT];
@@ -795,8 +861,16 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
         }
         if (!stopped) {
           T ax[kPPT], ex[kPPT], vc[kPPT];
-          op_tile_fast<T, R, true>(sy.u, cf.inv_beta_next, sy.w, H, W, sg, bufA, bufB, true, ax, ex,
-                                   vc, tyi, txi);
+          if (pre) {
+            if (more) cp_async_wait_group<1>();
+            else cp_async_wait_all();
+            __syncthreads();
+            op_tile_fast<T, R, true, T, true>(sy.u, cf.inv_beta_next, sy.w, H, W, sg, cur, bufB, true,
+                                              ax, ex, vc, tyi, txi);
+          } else {
+            op_tile_fast<T, R, true>(sy.u, cf.inv_beta_next, sy.w, H, W, sg, bufA, bufB, true, ax, ex,
+                                     vc, tyi, txi);
+          }
           tile_store_dots<T>(ax, ex, vc, gam, i0, j0, H, W, s, sy.y, vj, sy.K, sy.ldk, acc);
         }
         __syncthreads();   // the tile buffers are reused by the next tile
@@ -905,9 +979,11 @@ k_mr_batch(MrBatch<T> bt, GridBar* bar) {
       }
     }
     if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    if (pre && !done && r < ntiles) stage_halo_async<T, R>(sy.u, H, W, bufA, r / tiles_x, r % tiles_x);
     if (!done) scalar_step<T>(partn, (unsigned)gb, hd, red, ss, cf, sc, nop);
     ++j;
   }
+  if (pre) cp_async_wait_all();   // no copy may land after the CTA has left
   if (failed || !member || r != 0) return;
   // the leader stores the state: the direction update of the last phase A is
   // applied, and a system still running continues in the next launch at step j
@@ -942,7 +1018,7 @@ cudaError_t occupancy(K kernel, size_t smem, Occ* o) {
 template <typename T, int R>
 cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const Taps& tp,
                            GridBar* bar, int s_alloc, cudaStream_t s, int* launched_blocks,
-                           int* resident) {
+                           int* resident, int max_ctas) {
   const int ntiles = mr_matvec_blocks(H, W);
   MinresState* a0 = st;
   MrP<T> a1 = p;
@@ -955,7 +1031,7 @@ cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const
     const size_t smem = ((size_t)op_tile_smem_elems(R) + (size_t)sa * kTileH * kTileW) * sizeof(T);
     static int cached = 0;
     static Occ occ;
-    if (smem <= 227 * 1024 && ntiles <= kPersistMaxBlocks) {
+    if (max_ctas <= 0 && smem <= 227 * 1024 && ntiles <= kPersistMaxBlocks) {
       RK_TRY(ensure_smem(k_mr_resident<T, R>, smem, &cached));
       RK_TRY(occupancy(k_mr_resident<T, R>, smem, &occ));
       if (ntiles <= occ.per_sm * occ.sms) {
@@ -969,7 +1045,7 @@ cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const
       }
     }
   }
-  const size_t smem = (size_t)op_tile_smem_elems(R) * sizeof(T);
+  const size_t smem = persist_smem_elems<T>(R) * sizeof(T);
   static int cached = 0;
   static Occ occ;
   RK_TRY(ensure_smem(k_mr_persist<T, R>, smem, &cached));
@@ -977,6 +1053,7 @@ cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const
   int G = occ.per_sm * occ.sms;
   if (G > ntiles) G = ntiles;
   if (G > kPersistMaxBlocks) G = kPersistMaxBlocks;
+  if (max_ctas > 0 && G > max_ctas) G = max_ctas;
   if (G < 1) return cudaErrorCooperativeLaunchTooLarge;
   void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
   RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_persist<T, R>, dim3(G), dim3(kThreads), args,
@@ -990,13 +1067,13 @@ cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const
 
 template <typename T>
 cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Taps& tp, GridBar* bar,
-                       int s_alloc, cudaStream_t s, int* launched_blocks, int* resident) {
+                       int s_alloc, cudaStream_t s, int* launched_blocks, int* resident, int max_ctas) {
   switch (tp.r) {
-    case 4: return launch_persist<T, 4>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
-    case 6: return launch_persist<T, 6>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
-    case 8: return launch_persist<T, 8>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
-    case 10: return launch_persist<T, 10>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
-    case 12: return launch_persist<T, 12>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident);
+    case 4: return launch_persist<T, 4>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident, max_ctas);
+    case 6: return launch_persist<T, 6>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident, max_ctas);
+    case 8: return launch_persist<T, 8>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident, max_ctas);
+    case 10: return launch_persist<T, 10>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident, max_ctas);
+    case 12: return launch_persist<T, 12>(st, p, H, W, tp, bar, s_alloc, s, launched_blocks, resident, max_ctas);
     default: return cudaErrorNotSupported;
   }
 }
@@ -1004,7 +1081,7 @@ cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Tap
 namespace {
 template <typename T, int R>
 cudaError_t launch_batch(const MrBatch<T>& bt, GridBar* bar, cudaStream_t s, int G) {
-  const size_t smem = (size_t)op_tile_smem_elems(R) * sizeof(T);
+  const size_t smem = persist_smem_elems<T>(R) * sizeof(T);
   static int cached = 0;
   RK_TRY(ensure_smem(k_mr_batch<T, R>, smem, &cached));
   MrBatch<T> a0 = bt;
@@ -1018,7 +1095,7 @@ cudaError_t launch_batch(const MrBatch<T>& bt, GridBar* bar, cudaStream_t s, int
 template <typename T, int R>
 int batch_capacity() {
   static Occ occ;
-  const size_t smem = (size_t)op_tile_smem_elems(R) * sizeof(T);
+  const size_t smem = persist_smem_elems<T>(R) * sizeof(T);
   static int cached = 0;
   if (ensure_smem(k_mr_batch<T, R>, smem, &cached) != cudaSuccess ||
       occupancy(k_mr_batch<T, R>, smem, &occ) != cudaSuccess) {
@@ -1062,8 +1139,8 @@ bool mr_persist_supported(int radius) {
 }
 
 template cudaError_t mr_persist<float>(MinresState*, const MrP<float>&, int, int, const Taps&,
-                                       GridBar*, int, cudaStream_t, int*, int*);
+                                       GridBar*, int, cudaStream_t, int*, int*, int);
 template cudaError_t mr_persist<double>(MinresState*, const MrP<double>&, int, int, const Taps&,
-                                        GridBar*, int, cudaStream_t, int*, int*);
+                                        GridBar*, int, cudaStream_t, int*, int*, int);
 
 }  // namespace rk

@@ -159,14 +159,53 @@ __device__ __forceinline__ T ld_maybe_cg(const T* p) {
   else return *p;
 }
 
+// Asynchronous staging of src (unscaled) with a halo of 2R into s0 (AH x AW,
+// zero outside the image): 16-byte cp.async copies that bypass L1, so data
+// that other CTAs of a persistent kernel wrote before a grid barrier is read
+// from L2. Every chunk lies wholly inside or outside the image because tile
+// columns start at multiples of 32, 2R is a multiple of 4 and the caller
+// guarantees W * sizeof(T) % 16 == 0 and a 16-byte aligned src; chunks outside
+// are zero-filled (source size 0, a valid address passed all the same). The
+// copies form one committed group; wait with cp_async_wait_all, then
+// __syncthreads, before reading s0.
+template <typename T, int R>
+__device__ __forceinline__ void stage_halo_async(const T* src, int H, int W, T* s0, int tile_y,
+                                                 int tile_x) {
+  constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
+  constexpr int VW = Vec16<T>::n;
+  constexpr int CPR = AW / VW;
+  static_assert(AW % VW == 0 && (2 * R) % VW == 0, "halo rows must be whole 16-byte chunks");
+  const int i0 = tile_y * kTileH, j0 = tile_x * kTileW;
+  for (int idx = threadIdx.x; idx < AH * CPR; idx += kThreads) {
+    const int a = idx / CPR, c = (idx - a * CPR) * VW;
+    const int gi = i0 - 2 * R + a, gj = j0 - 2 * R + c;
+    const bool in = gi >= 0 && gi < H && gj >= 0 && gj < W;
+    const T* g = in ? src + (long)gi * W + gj : src;
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s0 + a * AW + c);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(g), "r"(in ? 16 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// wait until at most N of this thread's committed copy groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Same contract as op_tile, for a compile-time even radius R: every 1-D pass
 // keeps a register window of 4 + 2R inputs per thread and produces 4 outputs
 // from it (row passes read the window with 16-byte shared loads; column
 // passes walk down one column), and no index needs a runtime division.
 // CG: stage with L2-only loads; tile_y / tile_x: the tile (default: the CTA's).
 // taps: 2R+1 values, read after the staging barrier (so a caller may fill a
-// shared-memory copy just before the call).
-template <typename T, int R, bool CG = false, typename TP = double>
+// shared-memory copy just before the call). PRE: s0 already holds the unscaled
+// tile with its halo (stage_halo_async, waited for and synchronised); the
+// outputs are scaled instead (the operator is linear).
+template <typename T, int R, bool CG = false, typename TP = double, bool PRE = false>
 __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
                                              const T* __restrict__ w, int H, int W,
                                              const TP* taps, T* s0, T* s1, bool with_a,
@@ -185,7 +224,7 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
 
   // stage scale * src with a halo of 2R (zero outside the image); every load of
   // the thread is issued before the first one is used
-  {
+  if constexpr (!PRE) {
     constexpr int RPT = (AH + kThreads / 32 - 1) / (kThreads / 32);
     constexpr int CPT = (AW + 31) / 32;
     T st[RPT][CPT];
@@ -210,8 +249,8 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
         if (a < AH && c < AW) s0[a * AW + c] = st[ri][ci] * scale;
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
   T g[2 * R + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) g[k] = T(taps[k]);
@@ -237,6 +276,10 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
     // outside the image s[.] are zero-filled and the weights zero: e = 0
     ex[q] = wl[q] * (xc - s[-1]) - wr[q] * (s[1] - xc) + wu[q] * (xc - s[-AW]) - wd[q] * (s[AW] - xc);
     vc[q] = xc;
+    if constexpr (PRE) {
+      ex[q] *= scale;
+      vc[q] *= scale;
+    }
   }
   if (!with_a) return;
 
@@ -300,7 +343,7 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
       T acc = T(0);
 #pragma unroll
       for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
-      ax[q] = acc;
+      ax[q] = PRE ? acc * scale : acc;
     }
   }
 }

@@ -1,0 +1,61 @@
+"""The streaming persistent MINRES kernel (several 32x32 tiles per CTA; in FP32
+the next tile's halo is copied in while the current tile's stencil runs)
+against the FP64 oracle, through the C ABI. RS_STREAM_CTAS forces this kernel
+on images small enough for the oracle, with a ragged last tile row and column
+and uneven tile counts per CTA."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.recycle import State, outer_step
+from tests.gpu_util import Pair, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(wl, precision, ctas):
+    old = os.environ.get("RS_STREAM_CTAS")
+    os.environ["RS_STREAM_CTAS"] = str(ctas)
+    try:
+        return Pair(wl, precision=precision)
+    finally:
+        if old is None:
+            del os.environ["RS_STREAM_CTAS"]
+        else:
+            os.environ["RS_STREAM_CTAS"] = old
+
+
+@pytest.mark.parametrize("ctas", [1, 4])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_streaming_kernel_matches_oracle(precision, ctas):
+    # 96 x 80: 3 x 3 tiles, the last column 16 pixels wide
+    wl = synth.tiny(96, 80, sigma=1.5, radius=4, M=6, p=8, n_ritz_local=3, seed=41, tol=1e-9)
+    pr = _pair(wl, precision, ctas)
+    S = State()
+    n_eq = n_tot = 0
+    for k, w in enumerate([np.ones(2 * wl.n), synth.random_weights(wl.n, 43, lo=1.0, hi=300.0)]):
+        o = outer_step(pr.op, pr.b, pr.gammas, w, S, pr.prm)
+        pr.P.rs_set_weights(pr.t(w))
+        pr.P.rs_update_recycle(0 if k == 0 else 1)
+        X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+        stats = pr.P.rs_solve_shifts(X)
+        Xn = pr.n(X)
+        assert pr.P.rs_get_info()["minres_kernel"] == 0     # the streaming kernel ran
+        for l in range(wl.M):
+            st = stats[l]
+            assert st["relres_true"] <= wl.tol * (1 + 1e-6), (k, l, st)
+            e = rel(Xn[l], o.X[l])
+            if precision == 0:
+                assert abs(st["iters"] - o.iters[l]) <= max(2, 0.01 * o.iters[l]), (k, l)
+                n_tot += 1
+                if st["iters"] == o.iters[l]:
+                    n_eq += 1
+                    assert e <= 1e-6, (k, l, e)
+                else:
+                    assert e <= 1e-4, (k, l, e)
+            else:
+                assert e <= 1e-4, (k, l, e)
+    if precision == 0:
+        assert n_eq >= 0.75 * n_tot
