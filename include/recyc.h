@@ -135,6 +135,8 @@ typedef struct {
                               batched_local step in one launch; 1 one CTA per tile, vectors in
                               registers; 0 tiles streamed through memory (not all co-resident);
                               -1 none yet (step kernels only) */
+  int stab_sweeps;         /* sweeps of the one-sided Jacobi SVD in the last stabilize
+                              (Algorithm "Stabilized U"); 40 is its cap */
 } rs_info;
 
 /* Per-kernel device time, gathered with CUDA events around every launch of

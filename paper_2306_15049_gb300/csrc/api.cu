@@ -305,6 +305,7 @@ struct rs_problem {
   // persistent solve kernel (one cooperative launch per solve)
   bool use_persist = true;
   int last_resident = -1;   // kind of the last persistent launch (1 resident, 0 streaming)
+  int stab_sweeps = 0;       // Jacobi sweeps of the last stabilize
   bool use_coop_cgs = true; // CGS2 blocks as one cooperative launch
   int stream_ctas = 0;       // > 0: persistent solves stream tiles on at most this many CTAs
   bool use_prefetch = true;  // persistent MINRES kernels stage tiles ahead with cp.async
@@ -919,9 +920,10 @@ int finish_principal_body(rs_problem* P, int ncand) {
   if (nk > 0) {
     k_transpose_r<<<32, 256, 0, s>>>(P->Rfull, z.cmax, nk, ncand, P->XT);
     CU(launched());
-    CU(jacobi_svd(P->XT, ncand, nk, ncand, P->Vsv, P->sig, P->perm, s));
+    CU(jacobi_svd(P->XT, ncand, nk, ncand, P->Vsv, P->sig, P->perm, s, P->cnt + 3));
     std::vector<double> sg(nk);
     RS(read_back(P, sg.data(), P->sig, nk * sizeof(double)));
+    RS(read_back(P, &P->stab_sweeps, P->cnt + 3, sizeof(int)));
     for (int i = 0; i < nk; ++i)
       if (sg[0] > 0.0 && sg[i] > 0.0 && sg[0] / sg[i] < kStabilizeRatio) ++ncn;
     ncn = std::min(ncn, z.p);
@@ -2292,6 +2294,7 @@ rs_status rs_get_info(const rs_problem* P, rs_info* info) {
   info->ld = (int)P->z.ld;
   info->kernel_launches = launch_count();
   info->minres_kernel = P->last_resident;
+  info->stab_sweeps = P->stab_sweeps;
   return RS_OK;
 }
 

@@ -32,8 +32,8 @@ constexpr int kJacWarps = kJacThreads / 32;
 // warp per pair; slot i meets slot N-1-i, slot 0 stays and the others rotate.
 // On exit X_out = X_in V, the columns of X_out are mutually orthogonal,
 // sig[j] = ||X_out[:, j]|| and the columns of X and V are sorted by descending sig.
-__device__ void jacobi_body(double* X, int ldx, double* V, int ldv, int m, int nc, double* sig,
-                            int* perm, int* changed, int* best) {
+__device__ int jacobi_body(double* X, int ldx, double* V, int ldv, int m, int nc, double* sig,
+                           int* perm, int* changed, int* best, double tol) {
   (void)perm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // four pairs per warp, eight lanes per pair: GB300 issues FP64 at a fraction
@@ -42,7 +42,7 @@ __device__ void jacobi_body(double* X, int ldx, double* V, int ldv, int m, int n
   const int grp = lane >> 3, gl = lane & 7;
   const unsigned gmask = 0xffu << (grp * 8);
   const int N = nc + (nc & 1);                 // even number of slots (slot nc is a dummy)
-  const double tol = 1e-15;
+  int sweeps = 40;
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (threadIdx.x == 0) *changed = 0;
     __syncthreads();
@@ -101,7 +101,10 @@ __device__ void jacobi_body(double* X, int ldx, double* V, int ldv, int m, int n
       }
       __syncthreads();
     }
-    if (!*changed) break;
+    if (!*changed) {
+      sweeps = sweep + 1;
+      break;
+    }
     __syncthreads();
   }
   // singular values and a stable descending sort (selection, swapping columns)
@@ -141,12 +144,14 @@ __device__ void jacobi_body(double* X, int ldx, double* V, int ldv, int m, int n
     }
     __syncthreads();
   }
+  return sweeps;
 }
 
 // in_smem: X and V are copied into shared memory (m*nc + nc*nc doubles),
 // rotated there and copied back; otherwise they are rotated in place.
 __global__ void __launch_bounds__(kJacThreads)
-k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws, int in_smem) {
+k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws, int in_smem,
+             int* sweeps_out, double tol) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int changed, best;
   __shared__ double sig_s[256];
@@ -166,7 +171,9 @@ k_jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* per
   for (int i = threadIdx.x; i < nc * nc; i += blockDim.x) Vw[i] = ((i % nc) == (i / nc)) ? 1.0 : 0.0;
   __syncthreads();
   const bool small = nc <= 256;
-  jacobi_body(Xw, lx, Vw, lv, m, nc, small ? sig_s : sig, small ? perm_s : perm_ws, &changed, &best);
+  const int sw = jacobi_body(Xw, lx, Vw, lv, m, nc, small ? sig_s : sig, small ? perm_s : perm_ws,
+                             &changed, &best, tol);
+  if (sweeps_out && threadIdx.x == 0) *sweeps_out = sw;
   __syncthreads();
   if (small)
     for (int j = threadIdx.x; j < nc; j += blockDim.x) sig[j] = sig_s[j];
@@ -205,7 +212,8 @@ __host__ __device__ inline size_t jc_smem_doubles(int m, int nc, int C) {
 }
 
 __global__ void __launch_bounds__(kJcThreads)
-k_jacobi_cluster(double* X, int m, int nc, int ldx, double* V, double* sig) {
+k_jacobi_cluster(double* X, int m, int nc, int ldx, double* V, double* sig, int* sweeps_out,
+                 double tol) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int changed_s;
   __shared__ int pp_s[2 * 128];                    // this round's (p, q) per local pair
@@ -229,7 +237,7 @@ k_jacobi_cluster(double* X, int m, int nc, int ldx, double* V, double* sig) {
   cl.sync();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int N = nc + (nc & 1);
-  const double tol = 1e-15;
+  int sweeps = 40;
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (threadIdx.x == 0) changed_s = 0;
     for (int round = 0; round < N - 1; ++round) {
@@ -312,8 +320,12 @@ k_jacobi_cluster(double* X, int m, int nc, int ldx, double* V, double* sig) {
       for (int r = threadIdx.x; r < C; r += 32) any |= *cl.map_shared_rank(&changed_s, r);
     any = __syncthreads_or(any);
     cl.sync();   // nobody resets its flag before every CTA has read it
-    if (!any) break;
+    if (!any) {
+      sweeps = sweep + 1;
+      break;
+    }
   }
+  if (sweeps_out && rank == 0 && threadIdx.x == 0) *sweeps_out = sweeps;
   // norms of the home columns into rank 0's sig_all
   double* sig0 = cl.map_shared_rank(sig_all, 0);
   for (int t = warp; t < slots; t += kJcWarps) {
@@ -573,7 +585,7 @@ namespace {
 // One cluster of C CTAs; returns cudaErrorNotSupported when the shape does not
 // fit (the single-CTA kernel then runs instead).
 cudaError_t launch_jacobi_cluster(double* X, int m, int nc, int ldx, double* V, double* sig,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int* sweeps_out, double tol) {
   static int cluster = -1;     // 16, 8 or 0 (no cluster launch on this device)
   static size_t cached = 0;
   if (cluster == 0) return cudaErrorNotSupported;
@@ -622,13 +634,13 @@ cudaError_t launch_jacobi_cluster(double* X, int m, int nc, int ldx, double* V, 
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  RK_TRY(cudaLaunchKernelEx(&cfg, k_jacobi_cluster, X, m, nc, ldx, V, sig));
+  RK_TRY(cudaLaunchKernelEx(&cfg, k_jacobi_cluster, X, m, nc, ldx, V, sig, sweeps_out, tol));
   return launched();
 }
 
 cudaError_t launch_jacobi(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws,
-                          cudaStream_t s) {
-  const cudaError_t ce = launch_jacobi_cluster(X, m, nc, ldx, V, sig, s);
+                          cudaStream_t s, int* sweeps_out = nullptr, double tol = kJacobiTol) {
+  const cudaError_t ce = launch_jacobi_cluster(X, m, nc, ldx, V, sig, s, sweeps_out, tol);
   if (ce != cudaErrorNotSupported) return ce;
   const size_t bytes = ((size_t)m * nc + (size_t)nc * nc) * sizeof(double);
   const int in_smem = bytes <= 200 * 1024 ? 1 : 0;
@@ -637,15 +649,16 @@ cudaError_t launch_jacobi(double* X, int m, int nc, int ldx, double* V, double* 
     RK_TRY(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     cached = (int)bytes;
   }
-  k_jacobi_svd<<<1, kJacThreads, in_smem ? bytes : 0, s>>>(X, m, nc, ldx, V, sig, perm_ws, in_smem);
+  k_jacobi_svd<<<1, kJacThreads, in_smem ? bytes : 0, s>>>(X, m, nc, ldx, V, sig, perm_ws, in_smem,
+                                                           sweeps_out, tol);
   return launched();
 }
 }  // namespace
 
 cudaError_t jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws,
-                       cudaStream_t s) {
+                       cudaStream_t s, int* sweeps_out, double tol) {
   if (nc <= 0) return cudaSuccess;
-  return launch_jacobi(X, m, nc, ldx, V, sig, perm_ws, s);
+  return launch_jacobi(X, m, nc, ldx, V, sig, perm_ws, s, sweeps_out, tol);
 }
 
 cudaError_t spd_eig(const double* S, int n, double* lam, double* Q, double* work, int* perm_ws,

@@ -147,9 +147,12 @@ cudaError_t check_finite(const double* x, long n, int sign, int* ok_dev, cudaStr
 // ---------------------------------------------------------------- dense.cu
 // One-sided Jacobi on the columns of X (m x nc, ld ldx, in place):
 // X_out = X_in V with orthogonal columns sorted by descending norm sig.
-// V: nc x nc. perm_ws: nc + 1 ints. One CTA.
+// V: nc x nc. perm_ws: nc + 1 ints. sweeps_out (device, may be null): the
+// number of sweeps taken (40 = the cap). A pair is rotated while
+// |x_p^T x_q| > tol ||x_p|| ||x_q||; a sweep without rotations ends it.
+constexpr double kJacobiTol = 1e-15;
 cudaError_t jacobi_svd(double* X, int m, int nc, int ldx, double* V, double* sig, int* perm_ws,
-                       cudaStream_t s);
+                       cudaStream_t s, int* sweeps_out = nullptr, double tol = kJacobiTol);
 // Ascending eigenvalues lam and eigenvectors Q (n x n) of a small SPD S.
 // work: 2 n^2 + n doubles.
 cudaError_t spd_eig(const double* S, int n, double* lam, double* Q, double* work, int* perm_ws,
