@@ -35,8 +35,8 @@ METRIC = "shifted solves/sec & matvecs/sec at rel. residual 1e-8; HBM GB/s vs ro
 FP64_PEAK_GFLOPS = 152 * 2070e6 * 4 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2070 MHz (nominal 1.25 TF)
 # DRAM bytes (read + write) per MINRES step of k_mr_resident<float, 8> on a 512 x 512
 # image, from one ncu capture of 24-step launches (profiles/k_mr_resident_float_r8_512x512.md:
-# 15.79 MB + 0.11 MB per launch); scaled to a launch by its steps
-MR_RESIDENT_DRAM_BYTES_PER_STEP = {(512, 512, 8, "float"): (15.79e6 + 0.11e6) / 24}
+# 15.79 MB + 0.05 MB per launch); scaled to a launch by its steps
+MR_RESIDENT_DRAM_BYTES_PER_STEP = {(512, 512, 8, "float"): (15.79e6 + 0.046e6) / 24}
 
 
 def parse():
@@ -71,7 +71,7 @@ def workload_config(wl, precision):
                     f"{wl.K} outer IRN steps; p={wl.p}, |J|={wl.n_ritz_local}; tol {wl.tol:g}",
         "n": wl.n, "shifts": wl.M, "outer_steps": wl.K, "p": wl.p, "local_ritz": wl.n_ritz_local,
         "precision": precision,
-        "l2": "flushed between timed steps (256 MB write); one step's working set is 0.3-0.6 GB",
+        "l2": "flushed between timed steps (256 MB write)",
         "parallelism": "replicas (one independent workload per GPU)",
     }
 
@@ -462,6 +462,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     runner = Runner(wl, args.precision, dev, batched_local=int(args.batched_local))
+    config["device_workspace_gb"] = round(runner.workspace.numel() / 1e9, 3)
     if args.profile_case == "full":
         r = runner.step()
         torch.cuda.synchronize(dev)
