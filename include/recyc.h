@@ -137,6 +137,8 @@ typedef struct {
                               -1 none yet (step kernels only) */
   int stab_sweeps;         /* sweeps of the one-sided Jacobi SVD in the last stabilize
                               (Algorithm "Stabilized U"); 40 is its cap */
+  int stab_candidates;     /* columns of U~ handed to the last stabilize */
+  int stab_kept;           /* of those, kept by its CGS2 (before the singular-value cut) */
 } rs_info;
 
 /* Per-kernel device time, gathered with CUDA events around every launch of

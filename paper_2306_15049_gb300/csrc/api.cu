@@ -220,6 +220,7 @@ struct rs_problem {
   int k = -1;
   int nc = 0;
   int nk_stab = 0;
+  int ncand_stab = 0;
   bool have_recycle = false;
   bool have_prev = false;
   long long mv_total = 0, mv_over = 0;
@@ -306,6 +307,7 @@ struct rs_problem {
   bool use_persist = true;
   int last_resident = -1;   // kind of the last persistent launch (1 resident, 0 streaming)
   int stab_sweeps = 0;       // Jacobi sweeps of the last stabilize
+  double inner_rho = kInnerRho;  // relative reduction asked of each FP32 inner solve (mixed)
   bool use_coop_cgs = true; // CGS2 blocks as one cooperative launch
   int stream_ctas = 0;       // > 0: persistent solves stream tiles on at most this many CTAs
   bool use_prefetch = true;  // persistent MINRES kernels stage tiles ahead with cp.async
@@ -639,7 +641,7 @@ void graph_timing_flush(rs_problem* P, int gi, int j0, int iters_done, double by
 template <typename T>
 int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_abs, int maxit,
                int keep, bool reorth, int* iters_out, double* eta_out, int* breakdown_out,
-               int s_host = 0, int cg = 0) {
+               int s_host = 0, int cg = 0, int min_iters = 0) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
@@ -659,7 +661,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
   CU(cudaMemcpyAsync(u, r, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CU(multi_axpy<T>(Kl, ld, cnt_use, 0, P->Ktr, -1.0, u, n, P->partials, s, nullptr));
   CU(reduce_partials(P->partials, z.G, 1, 1, P->scal + 0, s, nullptr, 0, nullptr));
-  CU(minres_init(P->st, P->scal + 0, P->Ktr, cnt_use, tol_abs, maxit, s, cg));
+  CU(minres_init(P->st, P->scal + 0, P->Ktr, cnt_use, tol_abs, maxit, s, cg, min_iters));
   CU(cudaMemsetAsync(xm, 0, n * sizeof(T), s));
   CU(cudaMemsetAsync(P->vzero, 0, n * sizeof(T), s));
   for (int i = 0; i < 3; ++i) CU(cudaMemsetAsync(P->dring[i], 0, n * sizeof(T), s));
@@ -778,7 +780,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
       P->use_persist = false;
       if (slot >= 0) P->pending_used = (size_t)slot;
       return run_minres<T>(P, gamma, r, use_K, tol_abs, maxit, keep, reorth, iters_out, eta_out,
-                           breakdown_out, s_host, cg);
+                           breakdown_out, s_host, cg, min_iters);
     }
     CU(le);
     timed_end(P, slot, 0, -1, 0, 0.0, 0.0);
@@ -930,6 +932,7 @@ int finish_principal_body(rs_problem* P, int ncand) {
   }
   P->nc = ncn;
   P->nk_stab = nk;
+  P->ncand_stab = ncand;
   if (ncn == 0) return P->set_err(RS_EBREAKDOWN, "principal recycle space is empty");
   T* Ut = vp<T>(P->Ut);
   T* AU = vp<T>(P->AU);
@@ -1048,8 +1051,12 @@ int init_principal(rs_problem* P) {
     int it = 0, bd = 0;
     double eta = 0.0;
     const double tol_abs = P->d.tol * P->bnorm;
-    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * P->bnorm) : tol_abs;
-    RS(run_minres<T>(P, g, vp<T>(P->rT), false, inner_tol, P->d.maxit, z.a, true, &it, &eta, &bd));
+    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, P->inner_rho * P->bnorm) : tol_abs;
+    // in mixed precision the first FP32 sweep runs at least a steps, so that T_a and
+    // the kept Lanczos vectors have the size of the FP64 solve's whatever the sweep's
+    // tolerance (a breakdown of the Lanczos process still ends it)
+    RS(run_minres<T>(P, g, vp<T>(P->rT), false, inner_tol, P->d.maxit, z.a, true, &it, &eta, &bd, 0, 0,
+                     P->mixed ? z.a : 0));
     P->mv_over += it;
     const int m = std::min(it, z.a);
     CU(axpby<T, double>(vp<T>(P->xm), 1.0, x64, 1.0, n, s));
@@ -1061,7 +1068,7 @@ int init_principal(rs_problem* P) {
         if (rel <= P->d.tol) break;
         CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
         const double rn = rel * P->bnorm;
-        RS(run_minres<T>(P, g, vp<T>(P->rT), false, std::max(0.5 * tol_abs, kInnerRho * rn), P->d.maxit, 0, false, &it, &eta, &bd));
+        RS(run_minres<T>(P, g, vp<T>(P->rT), false, std::max(0.5 * tol_abs, P->inner_rho * rn), P->d.maxit, 0, false, &it, &eta, &bd));
         P->mv_over += it;
         CU(axpby<T, double>(vp<T>(P->xm), 1.0, x64, 1.0, n, s));
       }
@@ -1257,7 +1264,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
     phase_end(P, 3, ph0);
     // sweeps: sweep 0 from r0; in mixed precision further sweeps from the FP64 residual
     CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
-    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * std::sqrt(r02)) : tol_abs;
+    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, P->inner_rho * std::sqrt(r02)) : tol_abs;
     const int max_sw = P->mixed ? kMaxSweeps : 1;
     int broke = 0;
     for (int sw = 0; sw < max_sw; ++sw) {
@@ -1284,7 +1291,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
       sl.matvecs += 1;
       if (!P->mixed || sl.relres_true <= P->d.tol || forced >= 0) break;
       CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
-      inner_tol = std::max(0.5 * tol_abs, kInnerRho * sl.relres_true * rnorm);
+      inner_tol = std::max(0.5 * tol_abs, P->inner_rho * sl.relres_true * rnorm);
       if (sw + 1 == max_sw) break;
     }
     gnz[l] = 1;
@@ -1327,7 +1334,7 @@ int solve_plain(rs_problem* P, double* X, rs_solve_stats* stats) {
     CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
     CU(convert<double, T>(P->b, vp<T>(P->rT), n, s));
     sl.relres0 = 1.0;
-    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * rnorm) : tol_abs;
+    double inner_tol = P->mixed ? std::max(0.5 * tol_abs, P->inner_rho * rnorm) : tol_abs;
     const int max_sw = P->mixed ? kMaxSweeps : 1;
     int broke = 0;
     for (int sw = 0; sw < max_sw; ++sw) {
@@ -1346,7 +1353,7 @@ int solve_plain(rs_problem* P, double* X, rs_solve_stats* stats) {
       sl.matvecs += 1;
       if (!P->mixed || sl.relres_true <= P->d.tol) break;
       CU(convert<double, T>(P->r64, vp<T>(P->rT), n, s));
-      inner_tol = std::max(0.5 * tol_abs, kInnerRho * sl.relres_true * rnorm);
+      inner_tol = std::max(0.5 * tol_abs, P->inner_rho * sl.relres_true * rnorm);
     }
     sl.status = (sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) &&
                  (sl.iters >= P->d.maxit || (broke && cg)))
@@ -1505,7 +1512,7 @@ int batch_prepare(BatchWork<T>& bw) {
   }
   phase_end(P, 3, ph0);
   for (int l : bw.run)
-    bw.inner[l] = P->mixed ? std::max(0.5 * tol_abs, kInnerRho * std::sqrt(bw.rnorm2[l])) : tol_abs;
+    bw.inner[l] = P->mixed ? std::max(0.5 * tol_abs, P->inner_rho * std::sqrt(bw.rnorm2[l])) : tol_abs;
   P->sys_host.assign((size_t)M * sizeof(MrBatchSys<T>), 0);
   MrBatchSys<T>* sh = reinterpret_cast<MrBatchSys<T>*>(P->sys_host.data());
   for (int l = 0; l < M; ++l) {
@@ -1720,7 +1727,7 @@ int batch_assemble(BatchWork<T>& bw, int sw) {
     bw.gnz[l] = 1;
     if (P->mixed && sl.relres_true > P->d.tol) {
       CU(cudaMemcpyAsync(P->R0B + (long)l * ld, P->r64, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      bw.inner[l] = std::max(0.5 * tol_abs, kInnerRho * sl.relres_true * P->bnorm);
+      bw.inner[l] = std::max(0.5 * tol_abs, P->inner_rho * sl.relres_true * P->bnorm);
       again.push_back(l);
     }
   }
@@ -1890,6 +1897,11 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // RS_STREAM_CTAS=N (N >= 1) runs every persistent solve in the streaming kernel on at
   // most N CTAs, so that small images exercise the multi-tile path (tests)
   if (const char* g = std::getenv("RS_STREAM_CTAS")) P->stream_ctas = std::max(0, std::atoi(g));
+  // RS_INNER_RHO overrides the relative reduction asked of each FP32 inner solve
+  if (const char* g = std::getenv("RS_INNER_RHO")) {
+    const double v = std::atof(g);
+    if (v > 0.0 && v < 1.0) P->inner_rho = v;
+  }
   // RS_PREFETCH=0 stages every tile synchronously in the persistent MINRES kernels
   if (const char* g = std::getenv("RS_PREFETCH")) P->use_prefetch = std::strcmp(g, "0") != 0;
   P->gprev_nz.assign(desc->M, 0);
@@ -2295,6 +2307,8 @@ rs_status rs_get_info(const rs_problem* P, rs_info* info) {
   info->kernel_launches = launch_count();
   info->minres_kernel = P->last_resident;
   info->stab_sweeps = P->stab_sweeps;
+  info->stab_candidates = P->ncand_stab;
+  info->stab_kept = P->nk_stab;
   return RS_OK;
 }
 

@@ -212,6 +212,7 @@ struct MinresState {
   int dir_pending;         // fused path: the direction update of the last step is due
   int next_j;              // batched kernel: the step a later launch resumes at (1 at start)
   int cg;                  // 1: projected CG recurrences instead of MINRES (same Lanczos process)
+  int min_iters;           // the tolerance may stop the solve only after this many steps
   double cg_eta, cg_zeta;  // CG: the last pivot eta_{j-1} and coefficient zeta_{j-1}
   unsigned int cnt_a, cnt_b;   // last-CTA tickets of the fused kernels (0 between launches)
   double h[kMaxLocal];     // K^T Op v_j
@@ -219,7 +220,7 @@ struct MinresState {
   double z[kMaxLocal];     // K^T r - sum_j tau_j hhat_j
 };
 cudaError_t minres_init(MinresState* st, const double* xi2, const double* Ktr, const int* s_dev,
-                        double tol_abs, int maxit, cudaStream_t s, int cg = 0);
+                        double tol_abs, int maxit, cudaStream_t s, int cg = 0, int min_iters = 0);
 
 // The CG scalar step (Lanczos form of CG: the LDL^T factorisation of T_m) on
 // column j of T_m in the arithmetic type S, from alpha_j, beta_j (st.beta) and

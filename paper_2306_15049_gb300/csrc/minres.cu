@@ -27,7 +27,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 __global__ void k_minres_init(MinresState* st, const double* xi2, const double* Ktr,
-                              const int* s_dev, double tol_abs, int maxit, int cg) {
+                              const int* s_dev, double tol_abs, int maxit, int cg, int min_iters) {
   if (threadIdx.x != 0) return;
   const int s = s_dev ? *s_dev : 0;
   const double xi = sqrt(xi2 ? *xi2 : 0.0);
@@ -44,6 +44,7 @@ __global__ void k_minres_init(MinresState* st, const double* xi2, const double* 
   st->dir_pending = 0;
   st->next_j = 1;
   st->cg = cg;
+  st->min_iters = min_iters;
   st->cg_eta = 1.0;
   st->cg_zeta = xi;
   st->cnt_a = 0;
@@ -111,7 +112,9 @@ __global__ void k_minres_step(MinresState* st, const double* __restrict__ hdots,
     st->iters = j + 1;
     st->performed = 1;
     st->beta = beta_next;
-    if (fabs(st->eta) <= st->tol_abs || beta_next == 0.0 || st->iters >= st->maxit) st->stop = 1;
+    if ((fabs(st->eta) <= st->tol_abs && st->iters >= st->min_iters) || beta_next == 0.0 ||
+        st->iters >= st->maxit)
+      st->stop = 1;
     return;
   }
   const double eps = st->sn2 * beta;
@@ -156,7 +159,9 @@ __global__ void k_minres_step(MinresState* st, const double* __restrict__ hdots,
   st->iters = j + 1;
   st->performed = 1;
   st->beta = beta_next;
-  if (fabs(st->eta) <= st->tol_abs || beta_next == 0.0 || st->iters >= st->maxit) st->stop = 1;
+  if ((fabs(st->eta) <= st->tol_abs && st->iters >= st->min_iters) || beta_next == 0.0 ||
+        st->iters >= st->maxit)
+      st->stop = 1;
 }
 
 template <typename T>
@@ -213,8 +218,8 @@ __global__ void k_poll(const MinresState* st, int* out) {
 }  // namespace
 
 cudaError_t minres_init(MinresState* st, const double* xi2, const double* Ktr, const int* s_dev,
-                        double tol_abs, int maxit, cudaStream_t s, int cg) {
-  k_minres_init<<<1, 32, 0, s>>>(st, xi2, Ktr, s_dev, tol_abs, maxit, cg);
+                        double tol_abs, int maxit, cudaStream_t s, int cg, int min_iters) {
+  k_minres_init<<<1, 32, 0, s>>>(st, xi2, Ktr, s_dev, tol_abs, maxit, cg, min_iters);
   return launched();
 }
 

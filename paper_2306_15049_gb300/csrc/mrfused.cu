@@ -263,7 +263,9 @@ k_mr_lanczos(MinresState* st, MrB<T> b, long n, double* alphas_rec, double* beta
         ss.iters = j + 1;
         ss.beta = beta_next;
         ss.dir_pending = 1;
-        if (fabs(ss.eta) <= ss.tol_abs || beta_next == 0.0 || ss.iters >= ss.maxit) ss.stop = 1;
+        if ((fabs(ss.eta) <= ss.tol_abs && ss.iters >= ss.min_iters) || beta_next == 0.0 ||
+            ss.iters >= ss.maxit)
+          ss.stop = 1;
       }
     } else {
     const double eps = ss.sn2 * beta_d;
@@ -302,7 +304,9 @@ k_mr_lanczos(MinresState* st, MrB<T> b, long n, double* alphas_rec, double* beta
       ss.iters = j + 1;
       ss.beta = beta_next;
       ss.dir_pending = 1;
-      if (fabs(ss.eta) <= ss.tol_abs || beta_next == 0.0 || ss.iters >= ss.maxit) ss.stop = 1;
+      if ((fabs(ss.eta) <= ss.tol_abs && ss.iters >= ss.min_iters) || beta_next == 0.0 ||
+            ss.iters >= ss.maxit)
+          ss.stop = 1;
     }
     }
   }

@@ -195,7 +195,9 @@ __device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T*
         ss.iters = it + 1;
         ss.beta = (double)beta_next;
         ss.dir_pending = 1;
-        if (fabs(ss.eta) <= ss.tol_abs || !(beta_next > S(0)) || ss.iters >= ss.maxit) ss.stop = 1;
+        if ((fabs(ss.eta) <= ss.tol_abs && ss.iters >= ss.min_iters) || !(beta_next > S(0)) ||
+            ss.iters >= ss.maxit)
+          ss.stop = 1;
         cf.delta = T(delta);
         cf.eps = T(eps);
         cf.inv_gamma = T(ig);
@@ -249,7 +251,9 @@ __device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T*
         ss.iters = it + 1;
         ss.beta = (double)beta_next;
         ss.dir_pending = 1;
-        if (fabs(ss.eta) <= ss.tol_abs || !(beta_next > S(0)) || ss.iters >= ss.maxit) ss.stop = 1;
+        if ((fabs(ss.eta) <= ss.tol_abs && ss.iters >= ss.min_iters) || !(beta_next > S(0)) ||
+            ss.iters >= ss.maxit)
+          ss.stop = 1;
         cf.delta = T(delta);
         cf.eps = T(eps);
         cf.inv_gamma = T(ig);
