@@ -96,12 +96,14 @@ def oracle_matvec_rate(wl, seconds):
     v = b.copy()
     count = 0
     t0 = time.perf_counter()
+    c0 = time.process_time()
     while True:
         v = op.apply(v, 1e-3, w)
-        v /= np.linalg.norm(v)
+        v /= np.abs(v).max()      # keeps the iterate scaled (a ufunc reduction: no BLAS threads)
         count += 1
         el = time.perf_counter() - t0
         if el >= seconds:
+            oracle_matvec_rate.cpu_per_wall = (time.process_time() - c0) / el
             return count / el, count, el
 
 
@@ -112,6 +114,7 @@ def cpu_baseline(wl, name, seconds):
     return {
         "value": solves_per_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
         "matvecs_per_s": rate,
+        "process_cpu_s_per_wall_s": round(getattr(oracle_matvec_rate, "cpu_per_wall", float("nan")), 2),
         "sample": (f"FP64 NumPy oracle: {count} matvecs of this workload's operator in {el:.1f} s "
                    f"(1 thread), scaled by the oracle's own count for the whole workload "
                    f"({oc['total_matvecs']} matvecs for {oc['total_solves']} solves, "
