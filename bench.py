@@ -35,8 +35,8 @@ METRIC = "shifted solves/sec & matvecs/sec at rel. residual 1e-8; HBM GB/s vs ro
 FP64_PEAK_GFLOPS = 152 * 2070e6 * 4 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2070 MHz (nominal 1.25 TF)
 # DRAM bytes (read + write) per MINRES step of k_mr_resident<float, 8> on a 512 x 512
 # image, from one ncu capture of 24-step launches (profiles/k_mr_resident_float_r8_512x512.md:
-# 15.79 MB + 0.05 MB per launch); scaled to a launch by its steps
-MR_RESIDENT_DRAM_BYTES_PER_STEP = {(512, 512, 8, "float"): (15.79e6 + 0.046e6) / 24}
+# 15.79 MB + 0.04 MB per launch); scaled to a launch by its steps
+MR_RESIDENT_DRAM_BYTES_PER_STEP = {(512, 512, 8, "float"): (15.795e6 + 0.042e6) / 24}
 
 
 def parse():
