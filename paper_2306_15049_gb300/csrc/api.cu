@@ -29,7 +29,6 @@ constexpr double kStabilizeRatio = 1e10;   // Algorithm "Stabilized U"
 constexpr double kStabDrop = 1e-12;        // numerically dependent candidate (CGS2)
 constexpr double kLocalDrop = 1e-10;       // local column drop rule
 constexpr double kAngleCos = 0.99;         // footnote of Section 5.3
-constexpr int kPoll = 8;                   // MINRES steps between stop-flag polls
 constexpr int kMaxSweeps = 12;             // FP64 refinement sweeps (mixed precision)
 constexpr double kInnerRho = 1e-4;         // inner relative reduction per sweep (mixed)
 constexpr int kDotStride = kMaxLocal + 1;
@@ -738,7 +737,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
   struct Chunk {
     int j0, graph, slot;
   };
-  Chunk inq[2];
+  Chunk inq[2] = {};
   int nq = 0, next_slot = 0, gnext = 0;
   bool stopped = false;
   auto retire = [&]() -> int {

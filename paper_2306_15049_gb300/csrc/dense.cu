@@ -15,7 +15,6 @@ namespace rk {
 namespace {
 
 constexpr int kDenseThreads = 256;
-constexpr int kWarps = kDenseThreads / 32;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -33,12 +33,6 @@ namespace {
 constexpr int kDots = kMaxLocal + 1;
 constexpr int kWarps = kThreads / 32;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum_w(T v) {
 #pragma unroll
