@@ -37,6 +37,9 @@ FP64_PEAK_GFLOPS = 152 * 2070e6 * 4 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2070 MH
 # image, from one ncu capture of 24-step launches (profiles/k_mr_resident_float_r8_512x512.md:
 # 15.79 MB + 0.04 MB per launch); scaled to a launch by its steps
 MR_RESIDENT_DRAM_BYTES_PER_STEP = {(512, 512, 8, "float"): (15.795e6 + 0.042e6) / 24}
+# The same for the streaming kernel k_mr_persist<float, 12> on a 2048 x 2048 image
+# (profiles/k_mr_persist_float_r12_2048x2048_dram.md: 10.46 GB + 2.10 GB per 24-step launch)
+MR_PERSIST_DRAM_BYTES_PER_STEP = {(2048, 2048, 12, "float"): (10.46e9 + 2.10e9) / 24}
 
 
 def parse():
@@ -538,8 +541,9 @@ def main():
         kname = ("k_mr_matvec<%s> (fused MINRES step: direction update, v_j, (A+gamma E) v_j, K^T y)"
                  % tname)
     traffic = None
-    per_step = MR_RESIDENT_DRAM_BYTES_PER_STEP.get((wl.height, wl.width, wl.radius, tname))
-    if cat == 0 and mk == 1 and per_step is not None:
+    per_step = (MR_RESIDENT_DRAM_BYTES_PER_STEP if mk == 1 else MR_PERSIST_DRAM_BYTES_PER_STEP if mk == 0
+                else {}).get((wl.height, wl.width, wl.radius, tname))
+    if cat == 0 and per_step is not None:
         traffic = per_step * tm["pixels"][0] / wl.n / launches
     if cat == 0 and args.precision == "mixed":
         achieved = tm["bytes"][cat] / (tm["ms"][cat] / 1000.0) / 1e9
