@@ -86,3 +86,30 @@ def test_joint_solve_sizes_and_argument_checks_need_no_gpu(lib):
     xs = (ctypes.c_void_p * 1)(None)
     st = lib.rs_solve_shifts_batched(probs, 1, xs, None, ctypes.c_void_p(256), 1 << 20)
     assert st == recyc.RS_EINVAL
+
+
+def test_desc_limits_need_no_gpu(lib):
+    """Sizes and fields at and beyond their limits are rejected before any work."""
+    import synth
+    from paper_2306_15049_gb300 import recyc
+    from paper_2306_15049_gb300.workloads import desc_for
+
+    def ok(mutate):
+        d, keep = desc_for(synth.C1)
+        mutate(d)
+        return recyc.rs_workspace_bytes(d) > 0
+
+    assert ok(lambda d: None)
+    assert not ok(lambda d: setattr(d, "height", 0))
+    assert not ok(lambda d: (setattr(d, "height", 1 << 15), setattr(d, "width", (1 << 13) + 1)))   # > 2^28 pixels
+    assert ok(lambda d: (setattr(d, "height", 1), setattr(d, "width", 1)))                          # one pixel
+    assert not ok(lambda d: setattr(d, "M", 0))
+    assert not ok(lambda d: setattr(d, "p_max", 0))
+    assert not ok(lambda d: setattr(d, "n_ritz_local", 15))                                         # |J| <= 14
+    assert ok(lambda d: setattr(d, "n_ritz_local", 14))
+    assert not ok(lambda d: setattr(d, "maxit", 0))
+    assert not ok(lambda d: setattr(d, "tol", -1.0))
+    assert not ok(lambda d: setattr(d, "inner", 2))
+    assert ok(lambda d: setattr(d, "inner", recyc.RS_CG))
+    assert not ok(lambda d: setattr(d, "precision", 2))
+    assert not ok(lambda d: setattr(d, "radon_angles", 3601))
