@@ -120,6 +120,24 @@ Taps make_taps(double sigma, int r) {
     sum += tp.g[a + r];
   }
   for (int k = 0; k <= 2 * r; ++k) tp.g[k] /= sum;
+  if (r <= kMaxR2) {
+    // c_t = sum_a g_a g_{a - t} (t = -2r..2r); lc[q][q'] = sum over the ghost rows
+    // k = -r..-1 of g_{k - q} g_{k - q'} (g symmetric, zero beyond r)
+    auto gv = [&](int a) { return (a >= -r && a <= r) ? tp.g[a + r] : 0.0; };
+    for (int t = -2 * r; t <= 2 * r; ++t) {
+      double c = 0.0;
+      for (int a = -r; a <= r; ++a) c += gv(a) * gv(a - t);
+      tp.c2[t + 2 * r] = c;
+      tp.c2f[t + 2 * r] = (float)c;
+    }
+    for (int q = 0; q < r; ++q)
+      for (int qq = 0; qq < r; ++qq) {
+        double v = 0.0;
+        for (int k = -r; k <= -1; ++k) v += gv(k - q) * gv(k - qq);
+        tp.lc[q * r + qq] = v;
+        tp.lcf[q * r + qq] = (float)v;
+      }
+  }
   return tp;
 }
 
@@ -1893,6 +1911,17 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   if (const char* g = std::getenv("RS_BATCH")) P->use_batch = std::strcmp(g, "0") != 0;
   // RS_COOP_CGS=0 runs CGS2 column by column (several launches per candidate)
   if (const char* g = std::getenv("RS_COOP_CGS")) P->use_coop_cgs = std::strcmp(g, "0") != 0;
+  // RS_STENCIL2 selects how the stand-alone operator kernel (true residuals, images
+  // of recycle spaces) applies A: unset or 0, four blur passes; "fp64", two
+  // autocorrelation passes for FP64 at radius >= 10 (measured 14-19 % faster there);
+  // 1, two passes for every precision and even radius <= 12.
+  P->tp.two_pass = 0;
+  if (const char* g = std::getenv("RS_STENCIL2")) {
+    if (desc->radon_angles == 0 && desc->radius <= kMaxR2) {
+      if (std::strcmp(g, "fp64") == 0) P->tp.two_pass = 1;
+      else if (std::strcmp(g, "0") != 0) P->tp.two_pass = 2;
+    }
+  }
   // RS_STREAM_CTAS=N (N >= 1) runs every persistent solve in the streaming kernel on at
   // most N CTAs, so that small images exercise the multi-tile path (tests)
   if (const char* g = std::getenv("RS_STREAM_CTAS")) P->stream_ctas = std::max(0, std::atoi(g));

@@ -26,11 +26,32 @@ struct RadonGeom {
 // The forward operator of a problem: the Gaussian blur taps (radon.nang == 0)
 // or the Radon geometry with a device sinogram buffer (nang * nb entries of
 // the vector type) for op_apply.
+constexpr int kMaxR2 = 12;           // largest radius of the two-pass stencil
 struct Taps {
   double g[kMaxTaps];
   int r;
   RadonGeom radon;
   void* sino;
+  // Two-pass form of A = H^T H (k_op_apply, when two_pass is set): with T the
+  // zero-boundary Toeplitz blur, T^T T = C - Lc - Uc, C the Toeplitz matrix of
+  // the autocorrelation c = g * g (4r + 1 taps, c2[2r] central) and Lc, Uc the
+  // terms of the truncated sum that fall outside the image at either edge, both
+  // equal to lc (r x r, row-major, indexed by the distances of row and column
+  // from that edge). two_pass: 0 never, 1 where measured faster (FP64, r >= 10),
+  // 2 always.
+  int two_pass;
+  double c2[4 * kMaxR2 + 1];
+  double lc[kMaxR2 * kMaxR2];
+  float c2f[4 * kMaxR2 + 1];   // the same in FP32 (constant operands of FP32 kernels)
+  float lcf[kMaxR2 * kMaxR2];
+  template <typename T>
+  __host__ __device__ T c2_at(int t) const {
+    if constexpr (sizeof(T) == 4) return c2f[t]; else return T(c2[t]);
+  }
+  template <typename T>
+  __host__ __device__ T lc_at(int i) const {
+    if constexpr (sizeof(T) == 4) return lcf[i]; else return T(lc[i]);
+  }
 };
 
 // Every kernel launch of the library goes through launched(): it returns the

@@ -35,7 +35,11 @@ k_op_apply(const T* __restrict__ x, long ldx, const T* __restrict__ w, T* __rest
   T* bufB = bufA + (kTileH + 4 * r) * (kTileW + 4 * r);
   T ax[kPPT], ex[kPPT], vc[kPPT];
   if (threadIdx.x <= 2 * r) sg[threadIdx.x] = T(tp.g[threadIdx.x]);
-  if constexpr (R > 0) {
+  if constexpr (R > 0 && R <= kMaxR2) {
+    const bool two = tp.two_pass == 2 || (tp.two_pass == 1 && sizeof(T) == 8 && R >= 10);
+    if (two && mode != 2) op_tile2<T, R>(x, w, H, W, tp, bufA, bufB, ax, ex, vc);
+    else op_tile_fast<T, R>(x, T(1), w, H, W, sg, bufA, bufB, mode != 2, ax, ex, vc);
+  } else if constexpr (R > 0) {
     op_tile_fast<T, R>(x, T(1), w, H, W, sg, bufA, bufB, mode != 2, ax, ex, vc);
   } else {
     op_tile<T>(x, T(1), w, H, W, sg, r, bufA, bufB, mode != 2, ax, ex, vc);

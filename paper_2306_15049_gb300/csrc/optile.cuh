@@ -348,6 +348,123 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
   }
 }
 
+// Same outputs as op_tile_fast (scale 1, the CTA's tile) with A applied as
+// two 1-D passes of the autocorrelation taps tp.c2 (4R + 1 of them) and the
+// edge corrections tp.lc (see Taps): pass 1 filters the rows of the staged tile
+// (32 + 4R rows, the tile's 32 columns) into s1, pass 2 the columns of s1 at the
+// owned pixels. Outputs outside the image are not meaningful (the caller masks
+// them). tp must be a kernel parameter, so that the taps with compile-time
+// indices are constant-bank operands.
+template <typename T, int R>
+__device__ __forceinline__ void op_tile2(const T* __restrict__ src, const T* __restrict__ w, int H,
+                                         int W, const Taps& tp, T* s0, T* s1, T* ax, T* ex, T* vc) {
+  static_assert(R % 2 == 0 && R >= 2 && R <= kMaxR2, "even radius within the tables");
+  constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
+  constexpr int NW = 4 + 4 * R;          // window of one 4-output group
+  const long n = (long)H * W;
+  const T* wx = w;
+  const T* wy = w + n;
+  const int i0 = (int)blockIdx.y * kTileH, j0 = (int)blockIdx.x * kTileW;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // stage src with a halo of 2R (zero outside the image)
+  {
+    constexpr int RPT = (AH + kThreads / 32 - 1) / (kThreads / 32);
+    constexpr int CPT = (AW + 31) / 32;
+    T st[RPT][CPT];
+#pragma unroll
+    for (int ri = 0; ri < RPT; ++ri) {
+      const int a = ty + ri * (kThreads / 32);
+      const int gi = i0 - 2 * R + a;
+      const bool rin = a < AH && gi >= 0 && gi < H;
+#pragma unroll
+      for (int ci = 0; ci < CPT; ++ci) {
+        const int c = tx + 32 * ci;
+        const int gj = j0 - 2 * R + c;
+        st[ri][ci] = (rin && c < AW && gj >= 0 && gj < W) ? src[(long)gi * W + gj] : T(0);
+      }
+    }
+#pragma unroll
+    for (int ri = 0; ri < RPT; ++ri) {
+      const int a = ty + ri * (kThreads / 32);
+#pragma unroll
+      for (int ci = 0; ci < CPT; ++ci) {
+        const int c = tx + 32 * ci;
+        if (a < AH && c < AW) s0[a * AW + c] = st[ri][ci];
+      }
+    }
+  }
+  __syncthreads();
+  // E v at the owned pixels (column tx, rows 4 ty .. 4 ty + 3)
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) {
+    const int ti = ty * kPPT + q, tj = tx;
+    const int gi = i0 + ti, gj = j0 + tj;
+    const bool in = gi < H && gj < W;
+    const long gidx = (long)gi * W + gj;
+    const T wl = (in && gj >= 1) ? wx[gidx - 1] : T(0);
+    const T wr = (in && gj < W - 1) ? wx[gidx] : T(0);
+    const T wu = (in && gi >= 1) ? wy[gidx - W] : T(0);
+    const T wd = (in && gi < H - 1) ? wy[gidx] : T(0);
+    const T* sp = s0 + (ti + 2 * R) * AW + (tj + 2 * R);
+    const T xc = sp[0];
+    ex[q] = wl * (xc - sp[-1]) - wr * (sp[1] - xc) + wu * (xc - sp[-AW]) - wd * (sp[AW] - xc);
+    vc[q] = xc;
+  }
+  // pass 1: rows of s0 -> s1 (AH x 32); output column c is image column j0 + c
+  const int nl = W < R ? W : R;        // columns (rows) near an edge that carry a correction
+  for (int item = threadIdx.x; item < AH * (kTileW / 4); item += kThreads) {
+    const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
+    const T* row = s0 + a * AW;
+    T win[NW], o[4];
+    load_row<T, NW>(row + c0, win);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T acc = T(0);
+#pragma unroll
+      for (int t = 0; t <= 4 * R; ++t) acc += tp.template c2_at<T>(t) * win[q + t];
+      o[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gj = j0 + c0 + q;
+      if (gj < W) {
+        if (gj < R)      // left edge: columns 0 .. nl-1, staged at 2R - j0 + q'
+          for (int qq = 0; qq < nl; ++qq) o[q] -= tp.template lc_at<T>(gj * R + qq) * row[qq - j0 + 2 * R];
+        if (gj >= W - R) {   // right edge: columns W-1-q', distance W-1-gj
+          const int d = W - 1 - gj;
+          for (int qq = 0; qq < nl; ++qq) o[q] -= tp.template lc_at<T>(d * R + qq) * row[(W - 1 - qq) - j0 + 2 * R];
+        }
+      }
+    }
+    store4<T>(s1 + a * kTileW + c0, o);
+  }
+  __syncthreads();
+  // pass 2: columns of s1 at the owned pixels; s1 row a is image row i0 - 2R + a
+  {
+    const int nlh = H < R ? H : R;
+    T win[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) win[k] = s1[(ty * kPPT + k) * kTileW + tx];
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      T acc = T(0);
+#pragma unroll
+      for (int t = 0; t <= 4 * R; ++t) acc += tp.template c2_at<T>(t) * win[q + t];
+      const int gi = i0 + ty * kPPT + q;
+      if (gi < H) {
+        if (gi < R)
+          for (int qq = 0; qq < nlh; ++qq) acc -= tp.template lc_at<T>(gi * R + qq) * s1[(qq - i0 + 2 * R) * kTileW + tx];
+        if (gi >= H - R) {
+          const int d = H - 1 - gi;
+          for (int qq = 0; qq < nlh; ++qq)
+            acc -= tp.template lc_at<T>(d * R + qq) * s1[((H - 1 - qq) - i0 + 2 * R) * kTileW + tx];
+        }
+      }
+      ax[q] = acc;
+    }
+  }
+}
+
 // Raise a kernel's dynamic shared-memory limit once per size (not per launch).
 template <typename K>
 inline cudaError_t ensure_smem(K kernel, size_t bytes, int* cached) {

@@ -72,3 +72,42 @@ def test_operator_at_full_workload_size():
     y = pr.torch.empty_like(xt)
     pr.P.rs_apply_operator(1e-3, xt, y)
     assert rel(pr.n(y), pr.op.apply(x, 1e-3, wts)) < 1e-13
+
+
+CASES2 = [
+    # even radii of the two-pass form: images smaller than the radius, one row or
+    # column, ragged tiles, and the workload radii
+    (8, 8, 1.0, 4), (9, 7, 3.0, 12), (1, 40, 1.0, 4), (33, 1, 1.0, 6), (37, 53, 1.5, 4),
+    (130, 70, 2.5, 8), (70, 130, 3.0, 10), (96, 100, 4.0, 12),
+]
+
+
+@pytest.mark.parametrize("h,w,sigma,r", CASES2)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_pass_operator_matches_oracle(h, w, sigma, r, precision):
+    """RS_STENCIL2=1: A as two autocorrelation passes with edge corrections."""
+    import os
+    old = os.environ.get("RS_STENCIL2")
+    os.environ["RS_STENCIL2"] = "1"
+    try:
+        wl = synth.tiny(h, w, sigma=sigma, radius=r, M=4, p=4, n_ritz_local=1, seed=h * 5 + w)
+        pr = Pair(wl, precision=precision, x_image=synth.random_vectors(h * w, 1, h + 2 * w)[:, 0])
+    finally:
+        if old is None:
+            del os.environ["RS_STENCIL2"]
+        else:
+            os.environ["RS_STENCIL2"] = old
+    n = h * w
+    wts = synth.random_weights(n, 4)
+    pr.P.rs_set_weights(pr.t(wts))
+    x = np.random.default_rng(h * w).standard_normal(n)
+    xt = pr.t(x)
+    y = pr.torch.empty_like(xt)
+    y2 = pr.torch.empty_like(xt)
+    for wp in ([False, True] if precision == 1 else [False]):
+        tol = 1e-13 if not wp else 2e-6
+        pr.P.rs_apply_operator(0.3, xt, y, mode=0, working_precision=wp)
+        assert rel(pr.n(y), pr.op.apply(x, 0.3, wts)) < tol
+        pr.P.rs_apply_operator(0.0, xt, y, y2, mode=1, working_precision=wp)
+        assert rel(pr.n(y), pr.op.apply_A(x)) < tol
+        assert rel(pr.n(y2), pr.op.apply_E(x, wts)) < tol
