@@ -21,7 +21,10 @@
  *    the caller's workspace of rs_workspace_bytes() bytes.
  *  - Work is queued on the problem's stream. Calls that report results to
  *    the host (stats, counts) synchronise that stream.
- *  - A problem is not thread-safe; use one problem per stream.
+ *  - A problem is not thread-safe; use one problem per stream. Launch shapes
+ *    (occupancy, shared-memory limits) are cached per process for the device
+ *    that first ran each kernel: use one CUDA device per process, and create
+ *    and drive problems from one host thread at a time.
  *  - Every call returns an rs_status; on failure rs_last_error() describes it.
  *    Inputs are validated before any work is queued (RS_EINVAL).
  */
