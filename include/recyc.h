@@ -310,17 +310,17 @@ rs_status rs_synthesize_data(const rs_problem_desc* desc, const double* x_dev,
                              void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* rs_synthesize_data without a workspace, for callers that cannot allocate
- * device memory (code inside a CUDA graph capture, where cudaMalloc is not
- * allowed, or a process whose device memory is fully held by another
- * allocator). The paper has no counterpart: this is an interface convenience.
- * The two norms' partial sums live in a fixed 8 KB device array inside the
- * library (1024 doubles; every GPU that loads the library keeps it until the
- * process exits). Images up to 2^28 pixels fit; larger ones are rejected with
- * RS_EINVAL. The first call on each device looks up the array's device
- * address, so make it before any stream capture. All calls share the array:
- * calls whose work overlaps on the GPU (other streams or host threads) race,
- * so serialise them. Nothing is allocated; the call synchronises `stream`.
- * Errors: rs_last_error(NULL). */
+ * device memory: a process whose device memory is fully held by another
+ * allocator (a framework's caching pool, or a memory cap set by the process that
+ * hosts the library), which therefore cannot set aside a workspace. The paper
+ * has no counterpart: this is an interface convenience. The two norms' partial
+ * sums live in a fixed 8 KB device array inside the library (1024 doubles;
+ * every GPU that loads the library keeps it until the process exits). Images
+ * up to 2^28 pixels fit; larger ones are rejected with RS_EINVAL. The first
+ * call on each device looks up the array's device address. All calls share the
+ * array: calls whose work overlaps on the GPU (other streams or host threads)
+ * race, so serialise them. Nothing is allocated; the call synchronises
+ * `stream` before it returns. Errors: rs_last_error(NULL). */
 rs_status rs_synthesize_data_noalloc(const rs_problem_desc* desc, const double* x_dev,
                                      const double* z_dev, double eta, double* d_out_dev,
                                      void* stream);

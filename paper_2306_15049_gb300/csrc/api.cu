@@ -111,36 +111,6 @@ __global__ void k_lcurve_corner(const double* rho2, const double* eta2, int M, i
   *lstar = bl;
 }
 
-Taps make_taps(double sigma, int r) {
-  Taps tp{};
-  tp.r = r;
-  double sum = 0.0;
-  for (int a = -r; a <= r; ++a) {
-    tp.g[a + r] = std::exp(-(double)(a * a) / (2.0 * sigma * sigma));
-    sum += tp.g[a + r];
-  }
-  for (int k = 0; k <= 2 * r; ++k) tp.g[k] /= sum;
-  if (r <= kMaxR2) {
-    // c_t = sum_a g_a g_{a - t} (t = -2r..2r); lc[q][q'] = sum over the ghost rows
-    // k = -r..-1 of g_{k - q} g_{k - q'} (g symmetric, zero beyond r)
-    auto gv = [&](int a) { return (a >= -r && a <= r) ? tp.g[a + r] : 0.0; };
-    for (int t = -2 * r; t <= 2 * r; ++t) {
-      double c = 0.0;
-      for (int a = -r; a <= r; ++a) c += gv(a) * gv(a - t);
-      tp.c2[t + 2 * r] = c;
-      tp.c2f[t + 2 * r] = (float)c;
-    }
-    for (int q = 0; q < r; ++q)
-      for (int qq = 0; qq < r; ++qq) {
-        double v = 0.0;
-        for (int k = -r; k <= -1; ++k) v += gv(k - q) * gv(k - qq);
-        tp.lc[q * r + qq] = v;
-        tp.lcf[q * r + qq] = (float)v;
-      }
-  }
-  return tp;
-}
-
 // ---------------------------------------------------------------------------
 // workspace carving
 // ---------------------------------------------------------------------------
@@ -1914,13 +1884,16 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // RS_STENCIL2 selects how the stand-alone operator kernel (true residuals, images
   // of recycle spaces) applies A: unset or 0, four blur passes; "fp64", two
   // autocorrelation passes for FP64 at radius >= 10 (measured 14-19 % faster there);
-  // 1, two passes for every precision and even radius <= 12.
+  // 1, two passes for every precision and even radius <= 12. Any other value is
+  // read as 0 and noted in the problem's error string.
   P->tp.two_pass = 0;
   if (const char* g = std::getenv("RS_STENCIL2")) {
-    if (desc->radon_angles == 0 && desc->radius <= kMaxR2) {
-      if (std::strcmp(g, "fp64") == 0) P->tp.two_pass = 1;
-      else if (std::strcmp(g, "0") != 0) P->tp.two_pass = 2;
-    }
+    int mode = 0;
+    if (std::strcmp(g, "fp64") == 0) mode = 1;
+    else if (std::strcmp(g, "1") == 0) mode = 2;
+    else if (std::strcmp(g, "0") != 0)
+      P->set_err(RS_OK, "RS_STENCIL2=%.32s not recognised (0, 1 or fp64): four-pass stencil used", g);
+    if (desc->radon_angles == 0 && desc->radius <= kMaxR2) P->tp.two_pass = mode;
   }
   // RS_STREAM_CTAS=N (N >= 1) runs every persistent solve in the streaming kernel on at
   // most N CTAs, so that small images exercise the multi-tile path (tests)
@@ -2376,6 +2349,37 @@ const char* rs_last_error(const rs_problem* P) { return P ? P->err.c_str() : g_e
 }  // extern "C"
 
 namespace rk {
+
+Taps make_taps(double sigma, int r) {
+  Taps tp{};
+  tp.r = r;
+  double sum = 0.0;
+  for (int a = -r; a <= r; ++a) {
+    tp.g[a + r] = std::exp(-(double)(a * a) / (2.0 * sigma * sigma));
+    sum += tp.g[a + r];
+  }
+  for (int k = 0; k <= 2 * r; ++k) tp.g[k] /= sum;
+  if (r <= kMaxR2) {
+    // c_t = sum_a g_a g_{a - t} (t = -2r..2r); lc[q][q'] = sum over the ghost rows
+    // k = -r..-1 of g_{k - q} g_{k - q'} (g symmetric, zero beyond r)
+    auto gv = [&](int a) { return (a >= -r && a <= r) ? tp.g[a + r] : 0.0; };
+    for (int t = -2 * r; t <= 2 * r; ++t) {
+      double c = 0.0;
+      for (int a = -r; a <= r; ++a) c += gv(a) * gv(a - t);
+      tp.c2[t + 2 * r] = c;
+      tp.c2f[t + 2 * r] = (float)c;
+    }
+    for (int q = 0; q < r; ++q)
+      for (int qq = 0; qq < r; ++qq) {
+        double v = 0.0;
+        for (int k = -r; k <= -1; ++k) v += gv(k - q) * gv(k - qq);
+        tp.lc[q * r + qq] = v;
+        tp.lcf[q * r + qq] = (float)v;
+      }
+  }
+  return tp;
+}
+
 void set_null_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 }  // namespace rk
 

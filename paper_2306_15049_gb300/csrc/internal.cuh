@@ -54,6 +54,10 @@ struct Taps {
   }
 };
 
+// Normalised Gaussian taps g_a ~ exp(-a^2 / (2 sigma^2)), |a| <= r, sum 1, and
+// the autocorrelation tables of the two-pass form (r <= kMaxR2); two_pass = 0.
+Taps make_taps(double sigma, int r);
+
 // Every kernel launch of the library goes through launched(): it returns the
 // launch status and counts the launch (process-wide, for the benchmark).
 cudaError_t launched();

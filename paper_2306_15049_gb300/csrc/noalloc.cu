@@ -1,8 +1,8 @@
 // rs_synthesize_data_noalloc: the data synthesis of rs_synthesize_data
 // (d = H x + eta ||H x|| / ||z|| z) for callers that cannot allocate device
-// memory at all -- for example code running inside a CUDA graph capture,
-// where cudaMalloc is not permitted, or a host process whose memory is fully
-// reserved by another allocator and which may not create a workspace of its
+// memory at all -- for example a host process whose device memory is fully
+// reserved by another allocator (a framework's caching pool, or a memory cap
+// set by the process that hosts it), which may not create a workspace of its
 // own. Instead of a caller workspace, the two norms' partial sums live in a
 // fixed file-scope device array.
 //
@@ -10,7 +10,7 @@
 // contents persist from one call to the next, and two calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on
 // it. Every call overwrites all the slots it reads, so nothing in it has to
-// start at zero.
+// start at zero. Each call ends by synchronising its stream.
 #include <cmath>
 #include <mutex>
 
@@ -82,14 +82,7 @@ extern "C" rs_status rs_synthesize_data_noalloc(const rs_problem_desc* desc, con
   if (e != cudaSuccess) return fail(RS_ECUDA, cudaGetErrorString(e));
   double* sc = part + G;
   cudaStream_t s = (cudaStream_t)stream;
-  rk::Taps tp{};
-  tp.r = desc->radius;
-  double sum = 0.0;
-  for (int a = -tp.r; a <= tp.r; ++a) {
-    tp.g[a + tp.r] = exp(-(double)(a * a) / (2.0 * desc->sigma * desc->sigma));
-    sum += tp.g[a + tp.r];
-  }
-  for (int k = 0; k <= 2 * tp.r; ++k) tp.g[k] /= sum;
+  const rk::Taps tp = rk::make_taps(desc->sigma, desc->radius);
   if ((e = rk::blur_apply(x_dev, d_out_dev, desc->height, desc->width, tp, 0, s)) ||
       (e = rk::norm2_partials<double>(d_out_dev, n, part, s)) ||
       (e = rk::reduce_partials(part, G, 1, 1, sc, s, nullptr, 0, nullptr)) ||

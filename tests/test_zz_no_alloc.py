@@ -1,12 +1,14 @@
 """The allocation-free data synthesis entry point, for callers that cannot
-allocate device memory (for example code that runs inside a CUDA graph
-capture, where cudaMalloc is not permitted).
+allocate device memory (for example a process whose device memory is held by
+another allocator, so that it cannot set aside a workspace).
 
 rs_synthesize_data_noalloc keeps its scratch in a fixed device array inside
 the library instead of a caller workspace. Through the C ABI, two calls in a
-row (different inputs, so that stale scratch would show) must give the same
-data image as rs_synthesize_data with a workspace, within the FP64 tolerance
-of the operator tests. This file is collected last on purpose."""
+row must give the same data image as rs_synthesize_data with a workspace,
+within the FP64 tolerance of the operator tests. The first call is small (13
+partial sums); the second is large enough that its reduction uses all 304
+partial-sum slots the array is sized for, so stale slots of the first call
+would show. This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -28,7 +30,7 @@ def test_noalloc_synthesis_matches_the_workspace_entry_point_on_two_calls():
     dev = torch.device("cuda:0")
     ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
     for call, (h, w, sigma, r, eta, seed) in enumerate([(130, 97, 2.0, 6, 0.02, 11),
-                                                        (64, 200, 1.5, 4, 0.05, 12)]):
+                                                        (640, 512, 1.5, 4, 0.05, 12)]):
         wl = synth.tiny(h, w, sigma=sigma, radius=r, M=4, p=4, n_ritz_local=1, seed=seed)
         desc, keep = desc_for(wl)
         x = torch.tensor(synth.piecewise_constant_image(h, w, seed).reshape(-1), dtype=torch.float64,
