@@ -290,16 +290,52 @@ def qr_with_drops(B: np.ndarray, rel: float = LOCAL_DROP):
 
 
 # ---------------------------------------------------------------------------
+# Algorithm "updatelocal": the corrections that join a local space
+# ---------------------------------------------------------------------------
+def local_corrections(l: int, k: int, G_prev: Optional[np.ndarray], G_cur: np.ndarray,
+                      batched: bool):
+    """The two correction vectors of shift l (0-based) in step k (Algorithm
+    updatelocal, last step; Figure "local"): g^(k-1,l) from the previous outer
+    step, and g^(k,l-1) of the previous shift of this step -- or, with
+    ``batched``, g^(k-1,l-1) so that the shifts of a step are independent.
+    A vector that does not exist (k = 0, l = 0) is None."""
+    g_old = G_prev[l] if (k >= 1 and G_prev is not None) else None
+    if batched:
+        g_new = G_prev[l - 1] if (k >= 1 and l >= 1 and G_prev is not None) else None
+    else:
+        g_new = G_cur[l - 1] if l >= 1 else None
+    return g_old, g_new
+
+
+def local_columns(g_old: Optional[np.ndarray], g_new: Optional[np.ndarray],
+                  cos_max: float = ANGLE_COS) -> List[np.ndarray]:
+    """The correction columns appended to W, in the order [g^(k-1,l), g^(k,l-1)]
+    (Algorithm updatelocal). Zero or missing vectors are left out; when both
+    exist and |cos angle(g_old, g_new)| > cos_max only g_new is kept (footnote of
+    Section 5.3)."""
+    gcols = [g for g in (g_old, g_new) if g is not None and np.linalg.norm(g) > 0]
+    if len(gcols) == 2:
+        c = abs(gcols[0] @ gcols[1]) / (np.linalg.norm(gcols[0]) * np.linalg.norm(gcols[1]))
+        if c > cos_max:
+            gcols = [gcols[1]]
+    return gcols
+
+
+# ---------------------------------------------------------------------------
 # One outer step of the "Shifted Recycling Algorithm"
 # ---------------------------------------------------------------------------
 def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
                S: State, prm: Params, Ut_given: Optional[np.ndarray] = None,
-               iters_override: Optional[List[int]] = None) -> StepResult:
+               iters_override: Optional[List[int]] = None,
+               record_local: bool = False) -> StepResult:
     """Solve all M shifted systems for the weights ``w`` (step k = S.k + 1).
 
     ``Ut_given`` replaces the principal-space construction (the basis is still
     stabilized); ``iters_override`` fixes the MINRES step count per shift
-    (tolerance ignored) for parity checks of iterates.
+    (tolerance ignored) for parity checks of iterates. With ``record_local``
+    the local basis U~_l of every shift (after drops; None where the initial
+    guess already met the tolerance) is returned in ``extra["local_cols"]``,
+    and the raw principal basis (before stabilize) in ``extra["Ut_raw"]``.
     """
     k = S.k + 1
     n = b.shape[0]
@@ -318,6 +354,7 @@ def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
         Ut_raw, mv = update_principal(op, b, gammas, w, S.w, S.V_i1, S.X_prev, prm)
         overhead += mv
     Ut = stabilize(Ut_raw, prm.p)
+    local_cols: List[Optional[np.ndarray]] = [None] * M_
     nc = Ut.shape[1]
     AU = np.stack([op.apply_A(Ut[:, j]) for j in range(nc)], axis=1) if nc else np.zeros((n, 0))
     EU = np.stack([op.apply_E(Ut[:, j], w) for j in range(nc)], axis=1) if nc else np.zeros((n, 0))
@@ -360,19 +397,8 @@ def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
         Wt = WtL if (l + 1) <= prm.I_split else WtR
         cols = [Ut @ Wt] if nc else []
         imgs = [AU @ Wt + gl * (EU @ Wt)] if nc else []
-        g_old = S.G_prev[l] if (k >= 1 and S.G_prev is not None) else None
-        if prm.batched_local:
-            g_new = S.G_prev[l - 1] if (k >= 1 and l >= 1 and S.G_prev is not None) else None
-        else:
-            g_new = G[l - 1] if l >= 1 else None
-        gcols = []
-        for g in (g_old, g_new):
-            if g is not None and np.linalg.norm(g) > 0:
-                gcols.append(g)
-        if len(gcols) == 2:
-            c = abs(gcols[0] @ gcols[1]) / (np.linalg.norm(gcols[0]) * np.linalg.norm(gcols[1]))
-            if c > ANGLE_COS:
-                gcols = [gcols[1]]
+        g_old, g_new = local_corrections(l, k, S.G_prev, G, prm.batched_local)
+        gcols = local_columns(g_old, g_new)
         for g in gcols:
             cols.append(g[:, None])
             imgs.append((op.apply_A(g) + gl * op.apply_E(g, w))[:, None])
@@ -382,6 +408,8 @@ def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
         Kl, Rl, kept = qr_with_drops(Bl)
         Ul_t = Ul_t[:, kept]
         local_dim[l] = Kl.shape[1]
+        if record_local:
+            local_cols[l] = Ul_t.copy()
 
         solver = recycled_cg if prm.inner == "cg" else recycled_minres
         if forced is not None:
@@ -404,9 +432,12 @@ def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
     S.w_prev, S.w = S.w, w.copy()
     S.X_prev = X.copy()
     S.G_prev = G.copy()
+    extra = {"C": C, "AU": AU, "EU": EU, "Ah": Ah, "Eh": Eh, "WtL": WtL, "WtR": WtR}
+    if record_local:
+        extra["local_cols"] = local_cols
+        extra["Ut_raw"] = Ut_raw
     return StepResult(X, X0, G, iters, matvecs, relres0, relres_est, relres_true, local_dim,
-                      nc, overhead, Ut, {"C": C, "AU": AU, "EU": EU, "Ah": Ah, "Eh": Eh,
-                                         "WtL": WtL, "WtR": WtR})
+                      nc, overhead, Ut, extra)
 
 
 def naive_minres(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray, tol: float,

@@ -176,3 +176,65 @@ def test_cg_without_the_sign_of_zeta_is_caught(monkeypatch):
         return res
     monkeypatch.setattr(tcg, "recycled_cg", wrong)
     _expect_fail(tcg.test_without_recycling_it_is_textbook_cg)
+
+
+def _mutated(module, fname, old, new):
+    """``module.fname`` with one fragment of its source replaced (a planted slip)."""
+    src = inspect.getsource(getattr(module, fname))
+    assert old in src, (fname, old)
+    ns = dict(vars(module))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    return ns[fname]
+
+
+@pytest.mark.parametrize("old,new", [
+    ("V_i2 = R2[:, :prm.b_ritz]", "V_i2 = R2[:, -prm.b_ritz:]"),      # largest Ritz values of i2
+    ("V_i1 = R1", "V_i1 = R2"),                                       # i2's Ritz vectors as V_i1
+    ("theta, S = np.linalg.eigh(T)", "theta, S = np.linalg.eigh(T[::-1, ::-1])"),  # reversed T_a
+])
+def test_planted_init_principal_mistakes_are_caught(monkeypatch, old, new):
+    import tests.test_oracle_principal as tp
+    monkeypatch.setattr(tp, "init_principal", _mutated(orc, "init_principal", old, new))
+    _expect_fail(tp.test_init_principal_takes_all_ritz_vectors_of_i1_and_the_smallest_of_i2)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("(w - w_prev) * op.grad(xc)", "(w_prev - w) * op.grad(xc)"),            # wrong sign of Eq. delta
+    ("lambda v: op.apply(v, g, w), rhs", "lambda v: op.apply(v, g, w_prev), rhs"),  # E_{k-1} for E_k
+    ("X_prev[prm.l_c - 1]", "X_prev[prm.l_c - 2]"),                           # wrong correction system
+    ("[V_i1, Vnew, X_prev.T]", "[Vnew, V_i1, X_prev.T]"),                     # blocks out of order
+])
+def test_planted_update_principal_mistakes_are_caught(monkeypatch, old, new):
+    import tests.test_oracle_principal as tp
+    monkeypatch.setattr(tp, "update_principal", _mutated(orc, "update_principal", old, new))
+    _expect_fail(tp.test_update_principal_solves_eq_delta_and_orders_the_blocks)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("for g in (g_old, g_new)", "for g in (g_new, g_old)"),      # g's swapped
+    ("gcols = [gcols[1]]", "gcols = [gcols[0]]"),                # the older g survives the angle rule
+    ("if c > cos_max", "if c > 0.999"),                          # a wrong threshold
+])
+def test_planted_angle_rule_mistakes_are_caught(monkeypatch, old, new):
+    import tests.test_oracle_principal as tp
+    monkeypatch.setattr(tp, "local_columns", _mutated(orc, "local_columns", old, new))
+    _expect_fail(tp.test_local_columns_angle_rule_just_below_and_just_above)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("g_old = G_prev[l] if", "g_old = G_prev[l - 1] if"),                       # index slip
+    ("g_new = G_prev[l - 1] if (k >= 1", "g_new = G_cur[l - 1] if (k >= 1"),    # batched reads this step
+    ("g_new = G_cur[l - 1] if l >= 1", "g_new = G_prev[l - 1] if l >= 1"),      # chain from the old step
+])
+def test_planted_local_correction_mistakes_are_caught(monkeypatch, old, new):
+    import tests.test_oracle_principal as tp
+    monkeypatch.setattr(tp, "local_corrections", _mutated(orc, "local_corrections", old, new))
+    _expect_fail(tp.test_local_corrections_pick_the_paper_vectors)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_planted_local_assembly_mistake_in_the_outer_step_is_caught(monkeypatch, batched):
+    import tests.test_oracle_principal as tp
+    bad = _mutated(orc, "outer_step", "local_columns(g_old, g_new)", "local_columns(g_new, g_old)")
+    monkeypatch.setattr(tp, "outer_step", bad)
+    _expect_fail(tp.test_outer_step_local_spaces_are_the_listed_columns, batched)
