@@ -195,16 +195,25 @@ rs_status rs_update_recycle(rs_problem* prob, int mode);
  * paper's own basis. */
 rs_status rs_set_recycle_basis(rs_problem* prob, const double* U_dev, int ncols);
 
-/* Solve all M shifted systems of the current step in order l = 1..M
- * (Section 4: initial guesses by Eq. orthupdate, local spaces by
- * Algorithms interior / updatelocalV2, recycled MINRES by Eq. minShift,
- * solutions by Eq. xFinal / upest). X_dev receives M x n doubles (shift l in
- * row l). stats_host (M entries) may be NULL. iters_override_host (M ints)
- * may be NULL; if given, shift l runs exactly that many MINRES steps and the
- * tolerance is ignored (for comparing iterates). Returns RS_ENOCONV if any
- * shift reached maxit. */
-rs_status rs_solve_shifts(rs_problem* prob, double* X_dev, rs_solve_stats* stats_host,
-                          const int* iters_override_host);
+/* Solve the shifted systems l0, l0+1, .., l0+count-1 (0-based) of the current
+ * step, in that order (Section 4: initial guesses by Eq. orthupdate, local spaces
+ * by Algorithms interior / updatelocalV2, recycled MINRES by Eq. minShift,
+ * solutions by Eq. xFinal / upest); l0 = 0, count = M solves the whole step.
+ * X_dev receives count x n doubles (shift l0 + i in row i). stats_host (count
+ * entries) may be NULL. iters_override_host (count ints) may be NULL; if given,
+ * shift l0 + i runs exactly that many MINRES steps and the tolerance is ignored
+ * (for comparing iterates). Sub-ranges of one step may come in several calls:
+ * the paper's chain g^(k,l-1) joins the local space of shift l when shift l-1
+ * was solved earlier in the same step (in order l0 = 0, 1, .. the result is
+ * that of one call over all shifts); with batched_local the shifts are
+ * independent. Solving a shift again in the same step replaces its solution.
+ * The next rs_set_weights hands x^(k,.) and g^(k,.) to step k+1 only if every
+ * shift of step k was solved (RS_UPDATE needs them). With batched_local and
+ * l0 = 0, count = M, all shifts advance in one cooperative launch where it
+ * fits. Errors: RS_EINVAL for l0 < 0, count < 1 or l0 + count > M; RS_ENOTREADY
+ * before rs_update_recycle; RS_ENOCONV if any of the shifts reached maxit. */
+rs_status rs_solve_shifts(rs_problem* prob, int l0, int count, double* X_dev,
+                          rs_solve_stats* stats_host, const int* iters_override_host);
 
 /* The comparison solver of the paper's experiments (Section 8): each shifted
  * system (A + gamma_l E_k) x = b of the current weights solved from x0 = 0 by

@@ -213,13 +213,14 @@ struct rs_problem {
   long long mv_total = 0, mv_over = 0;
   double bnorm = 0.0;
   std::string err = "no error";
-  std::vector<char> gprev_nz, gcur_nz;
+  // previous step: g^(k-1,l) != 0; this step: g^(k,l) != 0 and shift l solved
+  std::vector<char> gprev_nz, gcur_nz, solved_cur;
   int kept_init = 0;    // columns of V_i1
 
   // FP64 buffers
   double *b = nullptr, *dimg = nullptr, *r64 = nullptr, *y64 = nullptr, *t64 = nullptr;
   double *w64 = nullptr, *wprev64 = nullptr, *dw64 = nullptr;
-  double *Xprev = nullptr, *Ut_raw = nullptr, *Vi1 = nullptr;
+  double *Xprev = nullptr, *Xcur = nullptr, *Ut_raw = nullptr, *Vi1 = nullptr;
   // working-precision buffers (float or double)
   void *bT = nullptr, *wT = nullptr, *Ut = nullptr, *AU = nullptr, *EU = nullptr, *Kp = nullptr;
   void *WL = nullptr, *WR = nullptr, *AWL = nullptr, *EWL = nullptr, *AWR = nullptr, *EWR = nullptr;
@@ -340,6 +341,7 @@ void carve(rs_problem* P, Carver& cv) {
   P->wprev64 = cv.take<double>(z.ld2);
   P->dw64 = cv.take<double>(z.ld2);
   P->Xprev = cv.take<double>((size_t)z.M * z.ld);
+  P->Xcur = cv.take<double>((size_t)z.M * z.ld);
   P->Ut_raw = cv.take<double>((size_t)z.cmax * z.ld);
   P->Vi1 = cv.take<double>((size_t)std::max(z.a, 1) * z.ld);
   if (P->mixed) {
@@ -1135,7 +1137,7 @@ int update_principal(rs_problem* P) {
 // the same principal space and Ritz bases, chain their own corrections in the
 // local spaces [W, g_adj^(l-1)] and leave the forward state alone.
 template <typename T>
-int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
+int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats, const int* over,
               const double* G = nullptr, const double* gnorm = nullptr) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
@@ -1152,8 +1154,12 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
   const double* CEc = adj ? P->CEadj : P->CE;
   T* Gbuf = vp<T>(adj ? P->Gadj : P->Gcur);
   int any_noconv = 0;
-  std::vector<char> gnz(z.M, 0);
-  for (int l = 0; l < z.M; ++l) {
+  // the chain g^(k,l-1): forward solves keep it across calls of the same step
+  // (a sub-range continues it); adjoint solves chain only within the call
+  std::vector<char> gnz_adj(z.M, 0);
+  std::vector<char>& gnz = adj ? gnz_adj : P->gcur_nz;
+  for (int l = l0; l < l0 + count; ++l) {
+    const int i = l - l0;           // position in the caller's X, stats, overrides
     const double gl = P->gammas[l];
     const double* rhs = adj ? G + (long)l * n : P->b;
     const double rnorm = adj ? gnorm[l] : P->bnorm;
@@ -1161,13 +1167,13 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
     double ph0 = phase_begin(P);
     rs_solve_stats sl{};
     sl.sweeps = 0;
-    double* x = X + (long)l * n;    // caller's X is dense M x n
+    double* x = X + (long)i * n;    // caller's X is dense count x n
     T* gl_buf = Gbuf + (long)l * ld;
     if (adj && !(rnorm > 0.0)) {    // g_l = 0: lambda_l = 0
       CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
       CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
       phase_end(P, 3, ph0);
-      if (stats) stats[l] = sl;
+      if (stats) stats[i] = sl;
       continue;
     }
     // initial guess x0 = U~ c_l and r0 = rhs - A U~ c_l - gamma_l E U~ c_l
@@ -1180,7 +1186,7 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
     double r02 = 0.0;
     RS(read_back(P, &r02, P->scal + 10, sizeof r02));
     sl.relres0 = std::sqrt(r02) / rnorm;
-    const int forced = over ? over[l] : -1;
+    const int forced = over ? over[i] : -1;
     if (forced < 0 && sl.relres0 <= P->d.tol) {
       phase_end(P, 3, ph0);
       RS(true_residual(P, gl, x, &sl.relres_true, rhs, rnorm));
@@ -1190,9 +1196,14 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
       // residual decides; if it misses the tolerance the shift is solved from it.
       if (!P->mixed || sl.relres_true <= P->d.tol) {
         CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
+        gnz[l] = 0;
+        if (!adj) {
+          CU(cudaMemcpyAsync(P->Xcur + (long)l * ld, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+          P->solved_cur[l] = 1;
+        }
         sl.relres_est = sl.relres0;
         sl.sweeps = 0;
-        if (stats) stats[l] = sl;
+        if (stats) stats[i] = sl;
         continue;
       }
       sl.relres0 = sl.relres_true;
@@ -1282,22 +1293,39 @@ int solve_all(rs_problem* P, double* X, rs_solve_stats* stats, const int* over,
       if (sw + 1 == max_sw) break;
     }
     gnz[l] = 1;
+    if (!adj) {
+      CU(cudaMemcpyAsync(P->Xcur + (long)l * ld, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      P->solved_cur[l] = 1;
+    }
     // not converged: out of steps, or a CG pivot that vanished (MINRES breaks down only when
     // the Krylov space is invariant, where its iterate is exact)
     sl.status = (forced < 0 && sl.relres_true > P->d.tol * (P->mixed ? 1.0 : 1.0 + 1e-6) &&
                  (sl.iters >= P->d.maxit || (broke && P->d.inner == RS_CG)))
                     ? RS_ENOCONV : RS_OK;
     if (sl.status == RS_ENOCONV) any_noconv = 1;
-    if (stats) stats[l] = sl;
+    if (stats) stats[i] = sl;
   }
   if (adj) return any_noconv ? P->set_err(RS_ENOCONV, "an adjoint shift reached maxit") : RS_OK;
-  // hand over to the next outer step
-  CU(cudaMemcpy2DAsync(P->Xprev, ld * sizeof(double), X, n * sizeof(double), n * sizeof(double), z.M,
-                       cudaMemcpyDeviceToDevice, s));
-  std::swap(P->Gcur, P->Gprev);
-  P->gprev_nz = gnz;
-  P->have_prev = true;
+  // x^(k,l) and g^(k,l) of the solved shifts are in Xcur and Gcur; rs_set_weights
+  // hands them to the next outer step once every shift of this step is solved
   return any_noconv ? P->set_err(RS_ENOCONV, "a shift reached maxit") : RS_OK;
+}
+
+// Start of the next outer step: a step whose shifts were all solved hands its
+// solutions x^(k,.) and corrections g^(k,.) over (Eq. tildeUupdate and the
+// local spaces of Algorithm updatelocal read them); otherwise the next step
+// has no previous step to update from.
+void step_advance(rs_problem* P) {
+  bool all = P->k >= 0 && !P->solved_cur.empty();
+  for (char c : P->solved_cur) all = all && c;
+  if (all) {
+    std::swap(P->Xcur, P->Xprev);
+    std::swap(P->Gcur, P->Gprev);
+    P->gprev_nz = P->gcur_nz;
+  }
+  P->have_prev = all;
+  P->gcur_nz.assign(P->z.M, 0);
+  P->solved_cur.assign(P->z.M, 0);
 }
 
 // The comparison solver of the paper's experiments (Section 8): every shift of
@@ -1737,11 +1765,10 @@ int batch_finish(BatchWork<T>& bw, rs_solve_stats* stats) {
     if (sl.status == RS_ENOCONV) any_noconv = 1;
     if (stats) stats[l] = sl;
   }
-  CU(cudaMemcpy2DAsync(P->Xprev, ld * sizeof(double), bw.X, n * sizeof(double), n * sizeof(double), z.M,
+  CU(cudaMemcpy2DAsync(P->Xcur, ld * sizeof(double), bw.X, n * sizeof(double), n * sizeof(double), z.M,
                        cudaMemcpyDeviceToDevice, P->s));
-  std::swap(P->Gcur, P->Gprev);
-  P->gprev_nz = bw.gnz;
-  P->have_prev = true;
+  P->gcur_nz = bw.gnz;
+  P->solved_cur.assign(z.M, 1);
   return any_noconv ? P->set_err(RS_ENOCONV, "a shift reached maxit") : RS_OK;
 }
 
@@ -1825,7 +1852,7 @@ int adjoint_all(rs_problem* P, const double* G, double* Lam, rs_solve_stats* sta
   RS(read_back(P, stt.data(), P->status, M * sizeof(int)));
   for (int l = 0; l < M; ++l)
     if (stt[l]) return P->set_err(RS_EBREAKDOWN, "orthupdate matrix of shift %d is not SPD", l + 1);
-  return solve_all<T>(P, Lam, stats, nullptr, G, gn.data());
+  return solve_all<T>(P, 0, z.M, Lam, stats, nullptr, G, gn.data());
 }
 
 // ===========================================================================
@@ -1906,6 +1933,8 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // RS_PREFETCH=0 stages every tile synchronously in the persistent MINRES kernels
   if (const char* g = std::getenv("RS_PREFETCH")) P->use_prefetch = std::strcmp(g, "0") != 0;
   P->gprev_nz.assign(desc->M, 0);
+  P->gcur_nz.assign(desc->M, 0);
+  P->solved_cur.assign(desc->M, 0);
   Carver cv{(char*)workspace_dev};
   carve(P, cv);
   const long n = P->z.n;
@@ -1975,6 +2004,7 @@ rs_status rs_set_weights(rs_problem* P, const double* w_dev) {
   if (P->k >= 0) CU(cudaMemcpyAsync(P->wprev64, P->w64, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
   CU(cudaMemcpyAsync(P->w64, w_dev, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
   if (P->mixed) CU((convert<double, float>(P->w64, (float*)P->wT, 2 * n, P->s)));
+  step_advance(P);
   P->k += 1;
   P->have_recycle = false;
   return RS_OK;
@@ -2007,24 +2037,27 @@ rs_status rs_set_recycle_basis(rs_problem* P, const double* U_dev, int ncols) {
   return (rs_status)finish_principal<double>(P, ncols);
 }
 
-rs_status rs_solve_shifts(rs_problem* P, double* X_dev, rs_solve_stats* stats_host,
+rs_status rs_solve_shifts(rs_problem* P, int l0, int count, double* X_dev, rs_solve_stats* stats_host,
                           const int* iters_override_host) {
   if (!P) return RS_EINVAL;
   if (!P->have_recycle) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_update_recycle first");
+  if (l0 < 0 || count < 1 || l0 > P->z.M - count)
+    return (rs_status)P->set_err(RS_EINVAL, "need 0 <= l0 and 1 <= count <= M - l0 (M = %d)", P->z.M);
   if (!X_dev) return (rs_status)P->set_err(RS_EINVAL, "X_dev is NULL");
   if (iters_override_host)
-    for (int l = 0; l < P->z.M; ++l)
-      if (iters_override_host[l] < 0) return (rs_status)P->set_err(RS_EINVAL, "negative iteration override");
+    for (int i = 0; i < count; ++i)
+      if (iters_override_host[i] < 0) return (rs_status)P->set_err(RS_EINVAL, "negative iteration override");
   // batched local spaces: every shift in one cooperative launch where it fits
-  if (P->d.batched_local && P->use_batch && !iters_override_host && P->tp.radon.nang == 0) {
+  if (P->d.batched_local && P->use_batch && !iters_override_host && P->tp.radon.nang == 0 && l0 == 0 &&
+      count == P->z.M) {
     const int cap = mr_batch_capacity(P->d.radius, P->mixed ? 4 : 8);
     if (cap >= P->z.M) {
       if (P->mixed) return (rs_status)solve_batched<float>(P, X_dev, stats_host, cap);
       return (rs_status)solve_batched<double>(P, X_dev, stats_host, cap);
     }
   }
-  if (P->mixed) return (rs_status)solve_all<float>(P, X_dev, stats_host, iters_override_host);
-  return (rs_status)solve_all<double>(P, X_dev, stats_host, iters_override_host);
+  if (P->mixed) return (rs_status)solve_all<float>(P, l0, count, X_dev, stats_host, iters_override_host);
+  return (rs_status)solve_all<double>(P, l0, count, X_dev, stats_host, iters_override_host);
 }
 
 size_t rs_batch_scratch_bytes(int count, int total_shifts) {

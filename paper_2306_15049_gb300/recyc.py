@@ -75,7 +75,7 @@ _SIGS = {
     "rs_set_weights": (_I, [_P, _P]),
     "rs_update_recycle": (_I, [_P, _I]),
     "rs_set_recycle_basis": (_I, [_P, _P, _I]),
-    "rs_solve_shifts": (_I, [_P, _P, ctypes.POINTER(rs_solve_stats), ctypes.POINTER(_I)]),
+    "rs_solve_shifts": (_I, [_P, _I, _I, _P, ctypes.POINTER(rs_solve_stats), ctypes.POINTER(_I)]),
     "rs_initial_guesses": (_I, [_P, _P, _P]),
     "rs_solve_plain": (_I, [_P, _P, ctypes.POINTER(rs_solve_stats)]),
     "rs_solve_adjoint": (_I, [_P, _P, _P, ctypes.POINTER(rs_solve_stats)]),
@@ -246,14 +246,17 @@ class Problem:
     def rs_set_recycle_basis(self, U_dev, ncols: int):
         return self._check(self.lib.rs_set_recycle_basis(self.h, _ptr(U_dev), int(ncols)))
 
-    def rs_solve_shifts(self, X_dev, iters_override: Optional[List[int]] = None, allow_noconv=False):
-        stats = (rs_solve_stats * self.M)()
+    def rs_solve_shifts(self, X_dev, iters_override: Optional[List[int]] = None, allow_noconv=False,
+                        l0: int = 0, count: Optional[int] = None):
+        """Shifts l0 .. l0 + count - 1 (default: all M); X_dev holds count rows."""
+        count = self.M - l0 if count is None else int(count)
+        stats = (rs_solve_stats * max(count, 1))()
         ov = None
         if iters_override is not None:
-            ov = (ctypes.c_int * self.M)(*[int(v) for v in iters_override])
-        st = self.lib.rs_solve_shifts(self.h, _ptr(X_dev), stats, ov)
+            ov = (ctypes.c_int * len(iters_override))(*[int(v) for v in iters_override])
+        st = self.lib.rs_solve_shifts(self.h, int(l0), count, _ptr(X_dev), stats, ov)
         self._check(st, (RS_OK, RS_ENOCONV) if allow_noconv else (RS_OK,))
-        return [dict((f, getattr(s, f)) for f, _ in rs_solve_stats._fields_) for s in stats]
+        return [dict((f, getattr(s, f)) for f, _ in rs_solve_stats._fields_) for s in stats[:count]]
 
     def rs_solve_plain(self, X_dev, allow_noconv=False):
         stats = (rs_solve_stats * self.M)()
