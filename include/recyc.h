@@ -137,7 +137,8 @@ typedef struct {
   int minres_kernel;       /* kernel of the last persistent MINRES solve: 3 all shifts of a
                               batched_local step in one launch; 1 one CTA per tile, vectors in
                               registers; 0 tiles streamed through memory (not all co-resident);
-                              -1 none yet (step kernels only) */
+                              2 tiles streamed, every tile operand staged in shared memory by
+                              tensor copies (FP32); -1 none yet (step kernels only) */
   int stab_sweeps;         /* sweeps of the one-sided Jacobi SVD in the last stabilize
                               (Algorithm "Stabilized U"); 40 is its cap */
   int stab_candidates;     /* columns of U~ handed to the last stabilize */

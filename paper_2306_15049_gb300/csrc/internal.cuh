@@ -329,7 +329,8 @@ int mr_matvec_blocks(int H, int W);
 struct GridBar {
   unsigned long long count;   // arrivals so far (barrier b completes at b x CTAs)
   int err;                    // 1: a CTA's wait ran out of time; 2: local space wider
-                              // than the launch's shared memory (the solve is void)
+                              // than the launch's shared memory; 3: a tensor copy did not
+                              // complete in time (the solve is void in every case)
   int pad;
 };
 constexpr int kPersistMaxBlocks = 152 * 8;
@@ -357,6 +358,7 @@ struct MrP {
   int rec_cap;
   int j0;              // first step of this launch
   int prefetch;        // stage tiles with cp.async ahead of their use (where the layout allows)
+  int tma;             // FP32 images beyond the resident kernel: tensor-copy staged kernel (mrtma.cu)
 };
 // One system of a batched solve: its state, image (H x W, its own weights w
 // and blur taps: 2 kMaxTaps - 1 entries centred at kMaxTaps - 1, zero beyond
@@ -414,6 +416,13 @@ cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Tap
                        int s_alloc, cudaStream_t s, int* launched_blocks, int* resident,
                        int max_ctas = 0);
 bool mr_persist_supported(int radius);
+
+// ---------------------------------------------------------------- mrtma.cu
+// The streaming solve with every tile operand staged by tensor copies (FP32,
+// radius 4, 6, 8, 10 or 12, no kept Lanczos vectors, W a multiple of 4, 16-byte
+// aligned vectors). *done = false (nothing queued) where it does not apply.
+cudaError_t mr_stream_tma(MinresState* st, const MrP<float>& p, int H, int W, const Taps& tp, GridBar* bar,
+                          int s_alloc, cudaStream_t s, int max_ctas, int* launched_blocks, bool* done);
 
 // ---------------------------------------------------------------- cgs.cu
 struct CgsCtx {

@@ -398,6 +398,16 @@ cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const
       }
     }
   }
+  if constexpr (sizeof(T) == 4) {
+    if (p.tma) {
+      bool done = false;
+      RK_TRY(mr_stream_tma(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, &done));
+      if (done) {
+        *resident = 2;
+        return cudaSuccess;
+      }
+    }
+  }
   const size_t smem = persist_smem_elems<T>(R) * sizeof(T);
   static int cached = 0;
   static Occ occ;

@@ -1,0 +1,565 @@
+// Recycled MINRES (Section 2.3 / 4.2, Eq. minShift) for images with more
+// 32 x 32 tiles than co-resident CTAs, FP32 vectors: one persistent
+// cooperative launch per solve, one CTA per SM, every operand of a tile staged
+// in shared memory by the Tensor Memory Accelerator.
+//
+// The step is the one of k_mr_persist (mrpersist.cu): phase A over the tiles
+// (direction update of step j-1, v_j = u / beta_j, y = (A + gamma E) v_j,
+// partial dots [K^T y; v_j^T y]), a grid barrier, phase B over the pixels
+// (u = y - K h - alpha v_j - beta v_{j-1}, partial ||u||^2), a grid barrier and
+// the scalar Givens step on every CTA's copy of the state.
+//
+// What differs is how phase A is fed. Each CTA owns two stages of shared
+// memory; a stage holds one tile's operands:
+//   u with a halo of 2r (zero outside the image: the box's out-of-range fill),
+//   the weights w_x (one column to the left) and w_y (one row above),
+//   v_{j-1}, d_{j-2}, d_{j-3}, x_m of the tile (the direction update), and
+//   the s columns of the local space K on the tile (one 3-D box).
+// One thread issues the tensor copies of a tile (cp.async.bulk.tensor) on the
+// stage's mbarrier while the CTA computes the previous tile, so a tile never
+// waits for a memory round trip of its own: the copies of tile i+1 are in
+// flight during tile i. The first two tiles of a step are requested right
+// after the barrier that publishes u, before the scalar step.
+//
+// Memory ordering between the two proxies: every thread fences its generic
+// global stores (u, v_j, d, x_m) with fence.proxy.async.global before the grid
+// barrier that precedes their tensor-copy reads, the issuing thread fences
+// again after it, and the generic shared-memory accesses to a stage are fenced
+// (fence.proxy.async.shared::cta) before the CTA barrier after which the stage
+// is refilled. Every mbarrier wait is bounded in time: on a timeout the launch
+// raises an error flag and returns (the host reports the failure).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "mrcommon.cuh"
+
+namespace rk {
+
+namespace {
+
+constexpr unsigned long long kTmaTimeoutNs = 2000000000ull;   // 2 s, far beyond one tile
+constexpr int kWRow = 36;                  // staged weight rows: 4 columns left + 32
+constexpr int kWRows = 33;                 // 32 rows + 1 (w_x: one below; w_y: one above)
+constexpr int kWPlane = 1216;              // floats per staged weight plane (128-byte multiple)
+
+struct TmaMaps {
+  CUtensorMap u;       // {W, H}, box {32 + 4R, 32 + 4R}
+  CUtensorMap w;       // {W, 2H} ([w_x; w_y]), box {36, 33}
+  CUtensorMap v[3];    // Lanczos ring buffers, box {32, 32}
+  CUtensorMap d[3];    // direction ring buffers, box {32, 32}
+  CUtensorMap xm;      // box {32, 32}
+  CUtensorMap K;       // {W, H, s} with stride ldk between columns, box {32, 32, s}
+};
+
+template <int R>
+struct TapsF {
+  float g[2 * R + 1];
+};
+
+// Stage layout (floats, every tensor-copy destination 128-byte aligned).
+template <int R>
+struct StageLayout {
+  static constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
+  static constexpr int BW = kTileW + 2 * R, CH = kTileH + 2 * R;
+  static constexpr int kU = 0;
+  static constexpr int kW = AH * AW;                  // (32 + 4R)^2: a multiple of 64
+  static constexpr int kV = kW + 2 * kWPlane;
+  static constexpr int kK = kV + 4 * kTileH * kTileW;
+  __host__ __device__ static constexpr int stage_floats(int s) { return kK + s * kTileH * kTileW; }
+  static constexpr int kBufB = AH * BW;               // pass-1 output (and pass 3)
+  __host__ __device__ static constexpr size_t smem_bytes(int s) {
+    return (size_t)(2 * stage_floats(s) + kBufB) * sizeof(float) + 128;   // + alignment slack
+  }
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of the mbarrier to complete; false after kTmaTimeoutNs.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned spin = 1;; ++spin) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((spin & 255u) == 0 && global_ns() - t0 > kTmaTimeoutNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+        "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The tensor copies of tile t into stage `st` (one thread). with_v: the four
+// direction-update vectors of step j (not on the first step of a launch, where
+// no direction update is pending).
+template <int R>
+__device__ __forceinline__ void issue_tile(const TmaMaps& maps, float* stage, unsigned long long* bar,
+                                           int t, int tiles_x, int H, int j, bool with_v, int s) {
+  using L = StageLayout<R>;
+  const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
+  const int i0 = tyi * kTileH, j0 = txi * kTileW;
+  constexpr unsigned kTile = kTileH * kTileW * sizeof(float);
+  const unsigned bytes = (unsigned)(L::AH * L::AW * sizeof(float)) + 2u * kWRow * kWRows * sizeof(float) +
+                         (with_v ? 4u * kTile : 0u) + (unsigned)s * kTile;
+  mbar_expect_tx(bar, bytes);
+  tma_load_2d(stage + L::kU, &maps.u, j0 - 2 * R, i0 - 2 * R, bar);
+  tma_load_2d(stage + L::kW, &maps.w, j0 - 4, i0, bar);                       // w_x rows i0..
+  tma_load_2d(stage + L::kW + kWPlane, &maps.w, j0 - 4, H + i0 - 1, bar);     // w_y rows i0-1..
+  if (with_v) {
+    // v_{j-1} (never v_0 here: j - 1 >= 1 on every step after a launch's first)
+    tma_load_2d(stage + L::kV, &maps.v[(j - 1) % 3], j0, i0, bar);
+    tma_load_2d(stage + L::kV + 1024, &maps.d[((j - 2) % 3 + 3) % 3], j0, i0, bar);
+    tma_load_2d(stage + L::kV + 2048, &maps.d[((j - 3) % 3 + 3) % 3], j0, i0, bar);
+    tma_load_2d(stage + L::kV + 3072, &maps.xm, j0, i0, bar);
+  }
+  if (s > 0) tma_load_3d(stage + L::kK, &maps.K, j0, i0, 0, bar);
+}
+
+// Phase A of one tile from a filled stage: E v and the four blur passes of A v
+// on the staged (unscaled) u, outputs scaled by `scale` = 1 / beta_j (the
+// operator is linear). Same passes and rounding as op_tile_fast.
+template <int R>
+__device__ __forceinline__ void tile_operator(float* U, float* s1, const float* wxs, const float* wys,
+                                              const float* g, float scale, int i0, int j0, int H, int W,
+                                              float* ax, float* ex, float* vc) {
+  using L = StageLayout<R>;
+  constexpr int AH = L::AH, AW = L::AW, BW = L::BW, CH = L::CH;
+  constexpr int NW = 4 + 2 * R;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) {
+    const int ti = ty * kPPT + q, tj = tx;
+    const int gi = i0 + ti, gj = j0 + tj;
+    const bool in = gi < H && gj < W;
+    const float wl = (in && gj >= 1) ? wxs[ti * kWRow + tj + 3] : 0.f;
+    const float wr = (in && gj < W - 1) ? wxs[ti * kWRow + tj + 4] : 0.f;
+    const float wu = (in && gi >= 1) ? wys[ti * kWRow + tj + 4] : 0.f;
+    const float wd = (in && gi < H - 1) ? wys[(ti + 1) * kWRow + tj + 4] : 0.f;
+    const float* sp = U + (ti + 2 * R) * AW + (tj + 2 * R);
+    const float xc = sp[0];
+    ex[q] = (wl * (xc - sp[-1]) - wr * (sp[1] - xc) + wu * (xc - sp[-AW]) - wd * (sp[AW] - xc)) * scale;
+    vc[q] = xc * scale;
+  }
+  // pass 1: T_w along rows of U -> s1 (AH x BW); output column c is image column j0 - R + c
+  for (int item = threadIdx.x; item < AH * (BW / 4); item += kThreads) {
+    const int a = item / (BW / 4), c0 = 4 * (item % (BW / 4));
+    float win[NW], o[4];
+    load_row<float, NW>(U + a * AW + c0, win);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc += g[k] * win[q + k];
+      o[q] = acc;
+    }
+    store4<float>(s1 + a * BW + c0, o);
+  }
+  __syncthreads();
+  float* s2 = U;    // CH x BW
+  float* s3 = s1;   // CH x 32
+  // pass 2: T_h along columns -> H v on the tile plus a halo of R, zero outside the image
+  for (int item = threadIdx.x; item < BW * (CH / 4); item += kThreads) {
+    const int c = item % BW, a0 = 4 * (item / BW);
+    const int gj = j0 - R + c;
+    float win[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) win[k] = s1[(a0 + k) * BW + c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gi = i0 - R + a0 + q;
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc += g[k] * win[q + k];
+      s2[(a0 + q) * BW + c] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? acc : 0.f;
+    }
+  }
+  __syncthreads();
+  // pass 3: T_w^T along rows (reversed taps); output column c is j0 + c
+  for (int item = threadIdx.x; item < CH * (kTileW / 4); item += kThreads) {
+    const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
+    float win[NW], o[4];
+    load_row<float, NW>(s2 + a * BW + c0, win);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
+      o[q] = acc;
+    }
+    store4<float>(s3 + a * kTileW + c0, o);
+  }
+  __syncthreads();
+  // pass 4: T_h^T along columns -> A v at the owned pixels
+  {
+    float win[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) win[k] = s3[(ty * kPPT + k) * kTileW + tx];
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
+      ax[q] = acc * scale;
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads, 1)
+k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, TapsF<R> tf, int H, int W,
+         int s_alloc, GridBar* bar) {
+  using L = StageLayout<R>;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ MinresState ss;
+  __shared__ StepCoef<float> cf;
+  __shared__ float hd[kDots];
+  __shared__ float red[kWarps][kDots];
+  __shared__ double sc[5];
+  __shared__ int ok_s;
+  __shared__ __align__(8) unsigned long long mbar[2];
+  float* base = reinterpret_cast<float*>((reinterpret_cast<unsigned long long>(smem_raw) + 127ull) & ~127ull);
+  float* const stage0 = base;
+  float* const stage1 = base + L::stage_floats(s_alloc);
+  float* bufB = base + 2 * L::stage_floats(s_alloc);
+  const unsigned G = gridDim.x;
+  const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (H + kTileH - 1) / kTileH;
+  const int ntiles = tiles_x * tiles_y;
+  const long n = (long)H * W;
+  float* partA = reinterpret_cast<float*>(p.partA);
+  float* partB = reinterpret_cast<float*>(p.partB);
+  const Ptrs<float> ptr{p};
+  float g[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * R; ++k) g[k] = tf.g[k];
+  load_state(st, ss);
+  const float gam = float(__ldcg(p.gamma));
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) coef_from_state(ss, cf);
+  __syncthreads();
+  const int s = ss.s;
+  if (s > s_alloc) {   // the same decision in every CTA: nobody reaches a barrier
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&bar->err, 2);
+    return;
+  }
+  int j = p.j0;
+  // tiles of this CTA: t = blockIdx.x + i G, i = 0 .. mine - 1
+  const int mine = ((int)blockIdx.x < ntiles) ? (ntiles - (int)blockIdx.x + (int)G - 1) / (int)G : 0;
+  unsigned ph[2] = {0u, 0u};          // completed phases of each stage's mbarrier
+  bool issued[2] = {false, false};    // a copy into the stage not yet waited for (thread 0's view)
+  // the direction-update vectors are staged for every step with an update due:
+  // from the second step of the launch on (and on the first if a previous launch
+  // of the same solve left one pending)
+  bool withv = ss.dir_pending != 0;
+  if (threadIdx.x == 0) {
+    fence_proxy_async_global();
+    for (int i = 0; i < 2 && i < mine; ++i) {
+      issue_tile<R>(maps, i ? stage1 : stage0, &mbar[i], (int)blockIdx.x + i * (int)G, tiles_x, H, j, withv, s);
+      issued[i] = true;
+    }
+  }
+  unsigned long long nb = 0;
+  bool failed = false;
+  for (;;) {
+    const int pend = ss.dir_pending, stopped = ss.stop;
+    float acc[kDots];
+#pragma unroll
+    for (int k = 0; k < kDots; ++k) acc[k] = 0.f;
+    float* dout = ptr.d(j - 1);
+    float* vj = ptr.v(j);
+    const float scale = cf.inv_beta_next;
+    const float de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau;
+    // ---------------- phase A: tiles from the stages ----------------
+    for (int i = 0; i < mine; ++i) {
+      const int b = i & 1;
+      const int t = (int)blockIdx.x + i * (int)G;
+      const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
+      const int i0 = tyi * kTileH, j0 = txi * kTileW;
+      float* S = b ? stage1 : stage0;
+      const bool ok = mbar_wait_bounded(&mbar[b], ph[b] & 1u);
+      ph[b] += 1;
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          issued[b] = false;
+          atomicExch(&bar->err, 3);
+        }
+        failed = true;
+        break;
+      }
+      if (threadIdx.x == 0) issued[b] = false;
+      int gi[kPPT], pix[kPPT];
+      bool in[kPPT];
+      long gix[kPPT];
+#pragma unroll
+      for (int q = 0; q < kPPT; ++q) {
+        int ti, tj;
+        op_tile_pixel(q, ti, tj);
+        gi[q] = i0 + ti;
+        in[q] = gi[q] < H && (j0 + tj) < W;
+        gix[q] = in[q] ? (long)gi[q] * W + (j0 + tj) : 0;
+        pix[q] = ti * kTileW + tj;
+      }
+      if (pend) {   // d_{j-1} = (v_{j-1} - delta d_{j-2} - eps d_{j-3}) / gamma, x_m += tau d_{j-1}
+        const float* V = S + L::kV;
+#pragma unroll
+        for (int q = 0; q < kPPT; ++q) {
+          if (in[q]) {
+            const float dv = (V[pix[q]] - de * V[1024 + pix[q]] - ep * V[2048 + pix[q]]) * ig;
+            dout[gix[q]] = dv;
+            p.xm[gix[q]] = V[3072 + pix[q]] + tau * dv;
+          }
+        }
+      }
+      if (!stopped) {
+        float ax[kPPT], ex[kPPT], vc[kPPT], yk[kPPT];
+        tile_operator<R>(S + L::kU, bufB, S + L::kW, S + L::kW + kWPlane, g, scale, i0, j0, H, W, ax, ex,
+                         vc);
+        const float* Ks = S + L::kK;
+#pragma unroll
+        for (int q = 0; q < kPPT; ++q) {
+          yk[q] = in[q] ? ax[q] + gam * ex[q] : 0.f;
+          if (in[q]) {
+            p.y[gix[q]] = yk[q];
+            vj[gix[q]] = vc[q];
+            acc[kMaxLocal] += vc[q] * yk[q];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxLocal; ++k)
+          if (k < s)
+#pragma unroll
+            for (int q = 0; q < kPPT; ++q) acc[k] += Ks[k * 1024 + pix[q]] * yk[q];
+      }
+      // the stage is refilled after every generic access to it is fenced and done
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0 && i + 2 < mine) {
+        issue_tile<R>(maps, S, &mbar[b], t + 2 * (int)G, tiles_x, H, j, withv, s);
+        issued[b] = true;
+      }
+    }
+    if (failed || stopped) break;
+    store_dot_partials<float>(acc, s, red, partA);
+    if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    reduce_dot_partials<float>(partA, G, s, red, hd);
+    // ---------------- phase B: vectors ----------------
+    {
+      const float* vprev = ptr.v(j - 1);
+      float hk[kMaxLocal];
+#pragma unroll
+      for (int k = 0; k < kMaxLocal; ++k) hk[k] = (k < s) ? hd[k] : 0.f;
+      const float alpha = hd[s], beta = cf.beta;
+      float accb = 0.f;
+      const long nv = n / 4;
+      const long tid = blockIdx.x * (long)kThreads + threadIdx.x, nthr = (long)G * kThreads;
+      for (long iv = tid; iv < nv; iv += nthr) {
+        constexpr int KG = kMaxLocal / 2;
+        float4 kv[KG];
+#pragma unroll
+        for (int k = 0; k < KG; ++k)
+          if (k < s) kv[k] = reinterpret_cast<const float4*>(p.K + (long)k * p.ldk)[iv];
+        const float4 yv = __ldcg(reinterpret_cast<const float4*>(p.y) + iv);
+        const float4 vv = __ldcg(reinterpret_cast<const float4*>(vj) + iv);
+        const float4 pv = __ldcg(reinterpret_cast<const float4*>(vprev) + iv);
+        const float* ya = reinterpret_cast<const float*>(&yv);
+        const float* va = reinterpret_cast<const float*>(&vv);
+        const float* pa = reinterpret_cast<const float*>(&pv);
+        float4 uv;
+        float* ua = reinterpret_cast<float*>(&uv);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float val = ya[e] - alpha * va[e] - beta * pa[e];
+#pragma unroll
+          for (int k = 0; k < KG; ++k)
+            if (k < s) val -= hk[k] * reinterpret_cast<const float*>(&kv[k])[e];
+          ua[e] = val;
+        }
+        if (s > KG) {
+#pragma unroll
+          for (int k = 0; k < KG; ++k)
+            if (KG + k < s) kv[k] = reinterpret_cast<const float4*>(p.K + (long)(KG + k) * p.ldk)[iv];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+#pragma unroll
+            for (int k = 0; k < KG; ++k)
+              if (KG + k < s) ua[e] -= hk[KG + k] * reinterpret_cast<const float*>(&kv[k])[e];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) accb += ua[e] * ua[e];
+        reinterpret_cast<float4*>(p.u)[iv] = uv;
+      }
+      store_norm_partial<float>(accb, red, partB);
+    }
+    // u, v_j, d and x_m of this step are read by tensor copies after the barrier
+    fence_proxy_async_global();
+    if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
+    if (threadIdx.x == 0) {
+      fence_proxy_async_global();
+      for (int i = 0; i < 2 && i < mine; ++i) {
+        // the next step's direction update needs v_j, d_{j-1}, d_{j-2}, x_m (j >= 1)
+        issue_tile<R>(maps, i ? stage1 : stage0, &mbar[i], (int)blockIdx.x + i * (int)G, tiles_x, H, j + 1,
+                      true, s);
+        issued[i] = true;
+      }
+    }
+    scalar_step<float>(partB, G, hd, red, ss, cf, sc, p);
+    ++j;
+    withv = true;
+  }
+  // no copy may land after the CTA has left: wait (bounded) for any still in flight
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b)
+      if (issued[b]) {
+        mbar_wait_bounded(&mbar[b], ph[b] & 1u);
+        ph[b] += 1;
+      }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && !failed) store_state(st, ss);
+}
+
+// ---------------------------------------------------------------------------
+// host side: tensor maps and the launch
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t encode_fn() {
+  if (g_encode) return cudaSuccess;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return cudaSuccess;
+}
+
+// rank-2 FP32 map {w0, h0} (row stride w0 floats) or rank-3 with a column stride
+cudaError_t encode(CUtensorMap* m, const float* addr, int rank, unsigned long long w0, unsigned long long h0,
+                   unsigned long long d2, unsigned long long stride2_elems, unsigned bx, unsigned by,
+                   unsigned bz) {
+  const cuuint64_t dims[3] = {w0, h0, d2};
+  const cuuint64_t strides[2] = {w0 * sizeof(float), stride2_elems * sizeof(float)};
+  const cuuint32_t box[3] = {bx, by, bz};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(addr),
+                              dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; }
+
+template <int R>
+cudaError_t launch_tma(MinresState* st, const MrP<float>& p, int H, int W, const Taps& tp, GridBar* bar,
+                       int s_alloc, cudaStream_t s, int max_ctas, int* launched_blocks, bool* done) {
+  using L = StageLayout<R>;
+  *done = false;
+  const int sa = s_alloc < 1 ? 0 : s_alloc;
+  const size_t smem = L::smem_bytes(sa);
+  if (smem + 2048 > 227 * 1024) return cudaSuccess;   // with the kernel's static shared memory
+  RK_TRY(encode_fn());
+  static int cached = 0;
+  static Occ occ;
+  RK_TRY(ensure_smem(k_mr_tma<R>, smem, &cached));
+  RK_TRY(occupancy(k_mr_tma<R>, smem, &occ));
+  const int ntiles = mr_matvec_blocks(H, W);
+  int G = occ.per_sm * occ.sms;
+  if (G > ntiles) G = ntiles;
+  if (G > kPersistMaxBlocks) G = kPersistMaxBlocks;
+  if (max_ctas > 0 && G > max_ctas) G = max_ctas;
+  if (G < 1) return cudaSuccess;
+  TmaMaps maps{};
+  const unsigned long long w = (unsigned long long)W, h = (unsigned long long)H;
+  RK_TRY(encode(&maps.u, p.u, 2, w, h, 1, 0, L::AW, L::AH, 1));
+  RK_TRY(encode(&maps.w, p.w, 2, w, 2 * h, 1, 0, kWRow, kWRows, 1));
+  for (int i = 0; i < 3; ++i) {
+    RK_TRY(encode(&maps.v[i], p.vring[i], 2, w, h, 1, 0, kTileW, kTileH, 1));
+    RK_TRY(encode(&maps.d[i], p.dring[i], 2, w, h, 1, 0, kTileW, kTileH, 1));
+  }
+  RK_TRY(encode(&maps.xm, p.xm, 2, w, h, 1, 0, kTileW, kTileH, 1));
+  if (sa > 0) RK_TRY(encode(&maps.K, p.K, 3, w, h, (unsigned long long)sa, (unsigned long long)p.ldk, kTileW,
+                            kTileH, (unsigned)sa));
+  TapsF<R> tf{};
+  for (int k = 0; k <= 2 * R; ++k) tf.g[k] = (float)tp.g[k];
+  MinresState* a0 = st;
+  MrP<float> a1 = p;
+  int a4 = H, a5 = W, a6 = sa;
+  GridBar* a7 = bar;
+  void* args[] = {&a0, &a1, &maps, &tf, &a4, &a5, &a6, &a7};
+  RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_tma<R>, dim3(G), dim3(kThreads), args, smem, s));
+  *launched_blocks = G;
+  *done = true;
+  return launched();
+}
+
+}  // namespace
+
+cudaError_t mr_stream_tma(MinresState* st, const MrP<float>& p, int H, int W, const Taps& tp, GridBar* bar,
+                          int s_alloc, cudaStream_t s, int max_ctas, int* launched_blocks, bool* done) {
+  *done = false;
+  // the tensor maps need 16-byte row strides and addresses; kept Lanczos vectors
+  // (the seeding solves) stay with k_mr_persist
+  if (p.keep > 0 || (W % 4) != 0 || (p.ldk % 4) != 0 || !aligned16(p.u) || !aligned16(p.w) ||
+      !aligned16(p.vzero) ||
+      !aligned16(p.xm) || !aligned16(p.K) || !aligned16(p.y))
+    return cudaSuccess;
+  for (int i = 0; i < 3; ++i)
+    if (!aligned16(p.vring[i]) || !aligned16(p.dring[i])) return cudaSuccess;
+  switch (tp.r) {
+    case 4: return launch_tma<4>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 6: return launch_tma<6>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 8: return launch_tma<8>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 10: return launch_tma<10>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 12: return launch_tma<12>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    default: return cudaSuccess;
+  }
+}
+
+}  // namespace rk

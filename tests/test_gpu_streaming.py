@@ -16,15 +16,18 @@ pytestmark = pytest.mark.gpu
 
 
 def _pair(wl, precision, ctas):
-    old = os.environ.get("RS_STREAM_CTAS")
-    os.environ["RS_STREAM_CTAS"] = str(ctas)
+    # RS_TMA=0: this file covers k_mr_persist; the tensor-copy kernel has its own tests
+    env = {"RS_STREAM_CTAS": str(ctas), "RS_TMA": "0"}
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
     try:
         return Pair(wl, precision=precision)
     finally:
-        if old is None:
-            del os.environ["RS_STREAM_CTAS"]
-        else:
-            os.environ["RS_STREAM_CTAS"] = old
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
 
 
 @pytest.mark.parametrize("ctas", [1, 4])
