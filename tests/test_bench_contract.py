@@ -29,7 +29,7 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["impl"] == "reference"
     assert d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"].startswith("512x512")
+    assert d["config"]["workload"].startswith("2048x2048")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"]
