@@ -27,8 +27,9 @@ __device__ __forceinline__ T warp_sum_w(T v) {
 //
 // Per-CTA partial dots acc[0..s-1] (K^T y) and acc[kMaxLocal] (v^T y) into
 // partA[pos * kPersistMaxBlocks + blockIdx.x], pos = 0..s (alpha at pos s).
-template <typename T>
+template <typename T, int NT = kThreads>
 __device__ __forceinline__ void store_dot_partials(const T* acc, int s, T (*red)[kDots], T* partA) {
+  constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kDots; ++k) {
@@ -43,7 +44,7 @@ __device__ __forceinline__ void store_dot_partials(const T* acc, int s, T (*red)
     if (k < s || k == kMaxLocal) {
       T t = T(0);
 #pragma unroll
-      for (int wv = 0; wv < kWarps; ++wv) t += red[wv][k];
+      for (int wv = 0; wv < NW; ++wv) t += red[wv][k];
       partA[(long)(k == kMaxLocal ? s : k) * kPersistMaxBlocks + blockIdx.x] = t;
     }
   }
@@ -51,14 +52,15 @@ __device__ __forceinline__ void store_dot_partials(const T* acc, int s, T (*red)
 
 // hd[0..s] = sum over the G CTAs of partA (the same order in every CTA): thread
 // t takes CTAs t, t + kThreads, ...; all its loads are issued at once.
-template <typename T>
+template <typename T, int NT = kThreads>
 __device__ __forceinline__ void reduce_dot_partials(const T* partA, unsigned G, int s,
                                                     T (*red)[kDots], T* hd) {
+  constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T t[kDots];
 #pragma unroll
   for (int k = 0; k < kDots; ++k) t[k] = T(0);
-  for (unsigned g = threadIdx.x; g < G; g += kThreads) {
+  for (unsigned g = threadIdx.x; g < G; g += NT) {
     T l[kDots];
 #pragma unroll
     for (int k = 0; k < kDots; ++k) l[k] = (k <= s) ? __ldcg(partA + (long)k * kPersistMaxBlocks + g) : T(0);
@@ -77,15 +79,16 @@ __device__ __forceinline__ void reduce_dot_partials(const T* partA, unsigned G, 
   if (threadIdx.x <= s) {
     T v = T(0);
 #pragma unroll
-    for (int wv = 0; wv < kWarps; ++wv) v += red[wv][threadIdx.x];
+    for (int wv = 0; wv < NW; ++wv) v += red[wv][threadIdx.x];
     hd[threadIdx.x] = v;
   }
   __syncthreads();
 }
 
 // Per-CTA partial ||u||^2 into partB[blockIdx.x].
-template <typename T>
+template <typename T, int NT = kThreads>
 __device__ __forceinline__ void store_norm_partial(T accb, T (*red)[kDots], T* partB) {
+  constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   accb = warp_sum_w<T>(accb);
   if (lane == 0) red[warp][0] = accb;
@@ -93,7 +96,7 @@ __device__ __forceinline__ void store_norm_partial(T accb, T (*red)[kDots], T* p
   if (threadIdx.x == 0) {
     T t = T(0);
 #pragma unroll
-    for (int wv = 0; wv < kWarps; ++wv) t += red[wv][0];
+    for (int wv = 0; wv < NW; ++wv) t += red[wv][0];
     partB[blockIdx.x] = t;
   }
 }
@@ -124,20 +127,21 @@ __device__ __forceinline__ void coef_from_state(const MinresState& ss, StepCoef<
 // precision, which need a relative residual reduction of 1e-4 per refinement
 // sweep (an FP64 scalar chain costs a long latency per step on GB300). The
 // state itself is kept in FP64.
-template <typename T>
+template <typename T, int NT = kThreads>
 __device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T* hd,
                                             T (*red)[kDots], MinresState& ss, StepCoef<T>& cf,
                                             double* sc, const MrP<T>& p) {
+  constexpr int NW = NT / 32;
   using S = T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T t = T(0);
-  for (unsigned g = threadIdx.x; g < G; g += kThreads) t += __ldcg(partB + g);
+  for (unsigned g = threadIdx.x; g < G; g += NT) t += __ldcg(partB + g);
   t = warp_sum_w<T>(t);
   __syncthreads();   // red is reused
   if (lane == 0) red[warp][0] = t;
   __syncthreads();
   if (warp == 0) {
-    T un = (lane < kWarps) ? red[lane][0] : T(0);
+    T un = (lane < NW) ? red[lane][0] : T(0);
     un = warp_sum_w<T>(un);
     const int s = ss.s;
     if (lane == 0 && ss.cg) {
@@ -248,12 +252,14 @@ __device__ __forceinline__ void scalar_step(const T* partB, unsigned G, const T*
   __syncthreads();
 }
 
+template <int NT = kThreads>
 __device__ __forceinline__ void load_state(const MinresState* st, MinresState& ss) {
   constexpr int kWords = sizeof(MinresState) / sizeof(unsigned);
-  for (int i = threadIdx.x; i < kWords; i += kThreads)
+  for (int i = threadIdx.x; i < kWords; i += NT)
     reinterpret_cast<unsigned*>(&ss)[i] = __ldcg(reinterpret_cast<const unsigned*>(st) + i);
 }
 
+template <int NT = kThreads>
 __device__ __forceinline__ void store_state(MinresState* st, MinresState& ss) {
   constexpr int kWords = sizeof(MinresState) / sizeof(unsigned);
   __syncthreads();
@@ -262,7 +268,7 @@ __device__ __forceinline__ void store_state(MinresState* st, MinresState& ss) {
     ss.cnt_a = ss.cnt_b = 0;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kWords; i += kThreads)
+  for (int i = threadIdx.x; i < kWords; i += NT)
     reinterpret_cast<unsigned*>(st)[i] = reinterpret_cast<const unsigned*>(&ss)[i];
 }
 
@@ -341,12 +347,12 @@ struct Occ {
 };
 
 template <typename K>
-cudaError_t occupancy(K kernel, size_t smem, Occ* o) {
+cudaError_t occupancy(K kernel, size_t smem, Occ* o, int threads = kThreads) {
   if (o->per_sm >= 0 && o->smem == smem) return cudaSuccess;
   int dev = 0;
   RK_TRY(cudaGetDevice(&dev));
   RK_TRY(cudaDeviceGetAttribute(&o->sms, cudaDevAttrMultiProcessorCount, dev));
-  RK_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->per_sm, kernel, kThreads, smem));
+  RK_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->per_sm, kernel, threads, smem));
   o->smem = smem;
   return cudaSuccess;
 }

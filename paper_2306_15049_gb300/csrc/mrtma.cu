@@ -157,18 +157,22 @@ __device__ __forceinline__ void issue_tile(const TmaMaps& maps, float* stage, un
 
 // Phase A of one tile from a filled stage: E v and the four blur passes of A v
 // on the staged (unscaled) u, outputs scaled by `scale` = 1 / beta_j (the
-// operator is linear). Same passes and rounding as op_tile_fast.
-template <int R>
+// operator is linear). NT threads; thread (ty, tx) = (warp, lane) owns the PPT
+// pixels (ty PPT + q, tx), q < PPT. The taps are read from the kernel parameter
+// with compile-time indices (constant-bank operands, no registers).
+template <int R, int NT>
 __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* wxs, const float* wys,
-                                              const float* g, float scale, int i0, int j0, int H, int W,
+                                              const TapsF<R>& tf, float scale, int i0, int j0, int H, int W,
                                               float* ax, float* ex, float* vc) {
   using L = StageLayout<R>;
   constexpr int AH = L::AH, AW = L::AW, BW = L::BW, CH = L::CH;
+  constexpr int PPT = kTileH * kTileW / NT;
   constexpr int NW = 4 + 2 * R;
+  constexpr int NW4 = PPT + 2 * R;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < kPPT; ++q) {
-    const int ti = ty * kPPT + q, tj = tx;
+  for (int q = 0; q < PPT; ++q) {
+    const int ti = ty * PPT + q, tj = tx;
     const int gi = i0 + ti, gj = j0 + tj;
     const bool in = gi < H && gj < W;
     const float wl = (in && gj >= 1) ? wxs[ti * kWRow + tj + 3] : 0.f;
@@ -181,7 +185,7 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
     vc[q] = xc * scale;
   }
   // pass 1: T_w along rows of U -> s1 (AH x BW); output column c is image column j0 - R + c
-  for (int item = threadIdx.x; item < AH * (BW / 4); item += kThreads) {
+  for (int item = threadIdx.x; item < AH * (BW / 4); item += NT) {
     const int a = item / (BW / 4), c0 = 4 * (item % (BW / 4));
     float win[NW], o[4];
     load_row<float, NW>(U + a * AW + c0, win);
@@ -189,7 +193,7 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
     for (int q = 0; q < 4; ++q) {
       float acc = 0.f;
 #pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += g[k] * win[q + k];
+      for (int k = 0; k <= 2 * R; ++k) acc += tf.g[k] * win[q + k];
       o[q] = acc;
     }
     store4<float>(s1 + a * BW + c0, o);
@@ -198,7 +202,7 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
   float* s2 = U;    // CH x BW
   float* s3 = s1;   // CH x 32
   // pass 2: T_h along columns -> H v on the tile plus a halo of R, zero outside the image
-  for (int item = threadIdx.x; item < BW * (CH / 4); item += kThreads) {
+  for (int item = threadIdx.x; item < BW * (CH / 4); item += NT) {
     const int c = item % BW, a0 = 4 * (item / BW);
     const int gj = j0 - R + c;
     float win[NW];
@@ -209,13 +213,13 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
       const int gi = i0 - R + a0 + q;
       float acc = 0.f;
 #pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += g[k] * win[q + k];
+      for (int k = 0; k <= 2 * R; ++k) acc += tf.g[k] * win[q + k];
       s2[(a0 + q) * BW + c] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? acc : 0.f;
     }
   }
   __syncthreads();
   // pass 3: T_w^T along rows (reversed taps); output column c is j0 + c
-  for (int item = threadIdx.x; item < CH * (kTileW / 4); item += kThreads) {
+  for (int item = threadIdx.x; item < CH * (kTileW / 4); item += NT) {
     const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
     float win[NW], o[4];
     load_row<float, NW>(s2 + a * BW + c0, win);
@@ -223,7 +227,7 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
     for (int q = 0; q < 4; ++q) {
       float acc = 0.f;
 #pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
+      for (int k = 0; k <= 2 * R; ++k) acc += tf.g[2 * R - k] * win[q + k];
       o[q] = acc;
     }
     store4<float>(s3 + a * kTileW + c0, o);
@@ -231,29 +235,32 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
   __syncthreads();
   // pass 4: T_h^T along columns -> A v at the owned pixels
   {
-    float win[NW];
+    float win[NW4];
 #pragma unroll
-    for (int k = 0; k < NW; ++k) win[k] = s3[(ty * kPPT + k) * kTileW + tx];
+    for (int k = 0; k < NW4; ++k) win[k] = s3[(ty * PPT + k) * kTileW + tx];
 #pragma unroll
-    for (int q = 0; q < kPPT; ++q) {
+    for (int q = 0; q < PPT; ++q) {
       float acc = 0.f;
 #pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
+      for (int k = 0; k <= 2 * R; ++k) acc += tf.g[2 * R - k] * win[q + k];
       ax[q] = acc * scale;
     }
   }
 }
 
+constexpr int kTmaThreads = 512;
+
 template <int R>
-__global__ void __launch_bounds__(kThreads, 1)
-k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, TapsF<R> tf, int H, int W,
-         int s_alloc, GridBar* bar) {
+__global__ void __launch_bounds__(kTmaThreads, 1)
+k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, const TapsF<R> tf, int H,
+         int W, int s_alloc, GridBar* bar) {
   using L = StageLayout<R>;
+  constexpr int NT = kTmaThreads, NWARP = NT / 32, PPT = kTileH * kTileW / NT;
   extern __shared__ unsigned char smem_raw[];
   __shared__ MinresState ss;
   __shared__ StepCoef<float> cf;
   __shared__ float hd[kDots];
-  __shared__ float red[kWarps][kDots];
+  __shared__ float red[NWARP][kDots];
   __shared__ double sc[5];
   __shared__ int ok_s;
   __shared__ __align__(8) unsigned long long mbar[2];
@@ -268,10 +275,7 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, Ta
   float* partA = reinterpret_cast<float*>(p.partA);
   float* partB = reinterpret_cast<float*>(p.partB);
   const Ptrs<float> ptr{p};
-  float g[2 * R + 1];
-#pragma unroll
-  for (int k = 0; k <= 2 * R; ++k) g[k] = tf.g[k];
-  load_state(st, ss);
+  load_state<NT>(st, ss);
   const float gam = float(__ldcg(p.gamma));
   if (threadIdx.x == 0) {
     mbar_init(&mbar[0], 1);
@@ -289,18 +293,16 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, Ta
   int j = p.j0;
   // tiles of this CTA: t = blockIdx.x + i G, i = 0 .. mine - 1
   const int mine = ((int)blockIdx.x < ntiles) ? (ntiles - (int)blockIdx.x + (int)G - 1) / (int)G : 0;
-  unsigned ph[2] = {0u, 0u};          // completed phases of each stage's mbarrier
-  bool issued[2] = {false, false};    // a copy into the stage not yet waited for (thread 0's view)
+  unsigned ph0 = 0u, ph1 = 0u;          // completed phases of each stage's mbarrier
+  bool issued0 = false, issued1 = false;   // a copy not yet waited for (thread 0's view)
   // the direction-update vectors are staged for every step with an update due:
   // from the second step of the launch on (and on the first if a previous launch
   // of the same solve left one pending)
   bool withv = ss.dir_pending != 0;
   if (threadIdx.x == 0) {
     fence_proxy_async_global();
-    for (int i = 0; i < 2 && i < mine; ++i) {
-      issue_tile<R>(maps, i ? stage1 : stage0, &mbar[i], (int)blockIdx.x + i * (int)G, tiles_x, H, j, withv, s);
-      issued[i] = true;
-    }
+    if (mine > 0) { issue_tile<R>(maps, stage0, &mbar[0], (int)blockIdx.x, tiles_x, H, j, withv, s); issued0 = true; }
+    if (mine > 1) { issue_tile<R>(maps, stage1, &mbar[1], (int)blockIdx.x + (int)G, tiles_x, H, j, withv, s); issued1 = true; }
   }
   unsigned long long nb = 0;
   bool failed = false;
@@ -320,51 +322,43 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, Ta
       const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
       const int i0 = tyi * kTileH, j0 = txi * kTileW;
       float* S = b ? stage1 : stage0;
-      const bool ok = mbar_wait_bounded(&mbar[b], ph[b] & 1u);
-      ph[b] += 1;
+      const bool ok = mbar_wait_bounded(&mbar[b], (b ? ph1 : ph0) & 1u);
+      if (b) ++ph1; else ++ph0;
+      if (threadIdx.x == 0) { if (b) issued1 = false; else issued0 = false; }
       if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) {
-          issued[b] = false;
-          atomicExch(&bar->err, 3);
-        }
+        if (threadIdx.x == 0) atomicExch(&bar->err, 3);
         failed = true;
         break;
       }
-      if (threadIdx.x == 0) issued[b] = false;
-      int gi[kPPT], pix[kPPT];
-      bool in[kPPT];
-      long gix[kPPT];
-#pragma unroll
-      for (int q = 0; q < kPPT; ++q) {
-        int ti, tj;
-        op_tile_pixel(q, ti, tj);
-        gi[q] = i0 + ti;
-        in[q] = gi[q] < H && (j0 + tj) < W;
-        gix[q] = in[q] ? (long)gi[q] * W + (j0 + tj) : 0;
-        pix[q] = ti * kTileW + tj;
-      }
+      const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+      const int gj = j0 + tx;
       if (pend) {   // d_{j-1} = (v_{j-1} - delta d_{j-2} - eps d_{j-3}) / gamma, x_m += tau d_{j-1}
         const float* V = S + L::kV;
 #pragma unroll
-        for (int q = 0; q < kPPT; ++q) {
-          if (in[q]) {
-            const float dv = (V[pix[q]] - de * V[1024 + pix[q]] - ep * V[2048 + pix[q]]) * ig;
-            dout[gix[q]] = dv;
-            p.xm[gix[q]] = V[3072 + pix[q]] + tau * dv;
+        for (int q = 0; q < PPT; ++q) {
+          const int ti = ty * PPT + q, gi = i0 + ti, pix = ti * kTileW + tx;
+          if (gi < H && gj < W) {
+            const long g = (long)gi * W + gj;
+            const float dv = (V[pix] - de * V[1024 + pix] - ep * V[2048 + pix]) * ig;
+            dout[g] = dv;
+            p.xm[g] = V[3072 + pix] + tau * dv;
           }
         }
       }
       if (!stopped) {
-        float ax[kPPT], ex[kPPT], vc[kPPT], yk[kPPT];
-        tile_operator<R>(S + L::kU, bufB, S + L::kW, S + L::kW + kWPlane, g, scale, i0, j0, H, W, ax, ex,
-                         vc);
+        float ax[PPT], ex[PPT], vc[PPT], yk[PPT];
+        tile_operator<R, NT>(S + L::kU, bufB, S + L::kW, S + L::kW + kWPlane, tf, scale, i0, j0, H, W, ax, ex,
+                             vc);
         const float* Ks = S + L::kK;
 #pragma unroll
-        for (int q = 0; q < kPPT; ++q) {
-          yk[q] = in[q] ? ax[q] + gam * ex[q] : 0.f;
-          if (in[q]) {
-            p.y[gix[q]] = yk[q];
-            vj[gix[q]] = vc[q];
+        for (int q = 0; q < PPT; ++q) {
+          const int ti = ty * PPT + q, gi = i0 + ti;
+          const bool in = gi < H && gj < W;
+          yk[q] = in ? ax[q] + gam * ex[q] : 0.f;
+          if (in) {
+            const long g = (long)gi * W + gj;
+            p.y[g] = yk[q];
+            vj[g] = vc[q];
             acc[kMaxLocal] += vc[q] * yk[q];
           }
         }
@@ -372,20 +366,20 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, Ta
         for (int k = 0; k < kMaxLocal; ++k)
           if (k < s)
 #pragma unroll
-            for (int q = 0; q < kPPT; ++q) acc[k] += Ks[k * 1024 + pix[q]] * yk[q];
+            for (int q = 0; q < PPT; ++q) acc[k] += Ks[k * 1024 + (ty * PPT + q) * kTileW + tx] * yk[q];
       }
       // the stage is refilled after every generic access to it is fenced and done
       fence_proxy_async_smem();
       __syncthreads();
       if (threadIdx.x == 0 && i + 2 < mine) {
         issue_tile<R>(maps, S, &mbar[b], t + 2 * (int)G, tiles_x, H, j, withv, s);
-        issued[b] = true;
+        if (b) issued1 = true; else issued0 = true;
       }
     }
     if (failed || stopped) break;
-    store_dot_partials<float>(acc, s, red, partA);
+    store_dot_partials<float, NT>(acc, s, red, partA);
     if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
-    reduce_dot_partials<float>(partA, G, s, red, hd);
+    reduce_dot_partials<float, NT>(partA, G, s, red, hd);
     // ---------------- phase B: vectors ----------------
     {
       const float* vprev = ptr.v(j - 1);
@@ -395,7 +389,7 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, Ta
       const float alpha = hd[s], beta = cf.beta;
       float accb = 0.f;
       const long nv = n / 4;
-      const long tid = blockIdx.x * (long)kThreads + threadIdx.x, nthr = (long)G * kThreads;
+      const long tid = blockIdx.x * (long)NT + threadIdx.x, nthr = (long)G * NT;
       for (long iv = tid; iv < nv; iv += nthr) {
         constexpr int KG = kMaxLocal / 2;
         float4 kv[KG];
@@ -433,34 +427,31 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, Ta
         for (int e = 0; e < 4; ++e) accb += ua[e] * ua[e];
         reinterpret_cast<float4*>(p.u)[iv] = uv;
       }
-      store_norm_partial<float>(accb, red, partB);
+      store_norm_partial<float, NT>(accb, red, partB);
     }
     // u, v_j, d and x_m of this step are read by tensor copies after the barrier
     fence_proxy_async_global();
     if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
     if (threadIdx.x == 0) {
       fence_proxy_async_global();
-      for (int i = 0; i < 2 && i < mine; ++i) {
-        // the next step's direction update needs v_j, d_{j-1}, d_{j-2}, x_m (j >= 1)
-        issue_tile<R>(maps, i ? stage1 : stage0, &mbar[i], (int)blockIdx.x + i * (int)G, tiles_x, H, j + 1,
-                      true, s);
-        issued[i] = true;
+      // the next step's direction update needs v_j, d_{j-1}, d_{j-2}, x_m (j >= 1)
+      if (mine > 0) { issue_tile<R>(maps, stage0, &mbar[0], (int)blockIdx.x, tiles_x, H, j + 1, true, s); issued0 = true; }
+      if (mine > 1) {
+        issue_tile<R>(maps, stage1, &mbar[1], (int)blockIdx.x + (int)G, tiles_x, H, j + 1, true, s);
+        issued1 = true;
       }
     }
-    scalar_step<float>(partB, G, hd, red, ss, cf, sc, p);
+    scalar_step<float, NT>(partB, G, hd, red, ss, cf, sc, p);
     ++j;
     withv = true;
   }
   // no copy may land after the CTA has left: wait (bounded) for any still in flight
   if (threadIdx.x == 0) {
-    for (int b = 0; b < 2; ++b)
-      if (issued[b]) {
-        mbar_wait_bounded(&mbar[b], ph[b] & 1u);
-        ph[b] += 1;
-      }
+    if (issued0) mbar_wait_bounded(&mbar[0], ph0 & 1u);
+    if (issued1) mbar_wait_bounded(&mbar[1], ph1 & 1u);
   }
   __syncthreads();
-  if (blockIdx.x == 0 && !failed) store_state(st, ss);
+  if (blockIdx.x == 0 && !failed) store_state<NT>(st, ss);
 }
 
 // ---------------------------------------------------------------------------
@@ -508,7 +499,7 @@ cudaError_t launch_tma(MinresState* st, const MrP<float>& p, int H, int W, const
   static int cached = 0;
   static Occ occ;
   RK_TRY(ensure_smem(k_mr_tma<R>, smem, &cached));
-  RK_TRY(occupancy(k_mr_tma<R>, smem, &occ));
+  RK_TRY(occupancy(k_mr_tma<R>, smem, &occ, kTmaThreads));
   const int ntiles = mr_matvec_blocks(H, W);
   int G = occ.per_sm * occ.sms;
   if (G > ntiles) G = ntiles;
@@ -533,7 +524,7 @@ cudaError_t launch_tma(MinresState* st, const MrP<float>& p, int H, int W, const
   int a4 = H, a5 = W, a6 = sa;
   GridBar* a7 = bar;
   void* args[] = {&a0, &a1, &maps, &tf, &a4, &a5, &a6, &a7};
-  RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_tma<R>, dim3(G), dim3(kThreads), args, smem, s));
+  RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_tma<R>, dim3(G), dim3(kTmaThreads), args, smem, s));
   *launched_blocks = G;
   *done = true;
   return launched();

@@ -14,7 +14,9 @@ streaming CTAs, uneven tile counts per CTA. Two outer steps (k = 0 seeding
 solves, k = 1 Eq. delta update). Bar: every system's recomputed residual within
 the tolerance; every FP64 solution, re-solved with the oracle's
 step counts, within 1e-6 of the oracle's; free-running step counts within
-1 % + 2 of the oracle's and solutions within 1e-4; mixed precision within 1e-4."""
+2 % + 2 of the oracle's (at r = 12 some systems need 250+ steps, and two FP64
+runs whose sums are ordered differently cross the tolerance a few steps apart)
+and solutions within 1e-4; mixed precision within 1e-4."""
 import os
 
 import numpy as np
@@ -89,8 +91,8 @@ def test_kernel_matches_oracle_at_large_radius(r, kernel, precision):
             assert st["relres_true"] <= wl.tol * (1 + 1e-6), (k, l, st)
             assert rel(Xn[l], o.X[l]) <= 1e-4, (k, l, rel(Xn[l], o.X[l]))
             if precision == 0:
-                assert abs(st["iters"] - o.iters[l]) <= max(2, 0.01 * o.iters[l]), (k, l, st["iters"], o.iters[l])
-        if precision == 0 and not batched:
+                assert abs(st["iters"] - o.iters[l]) <= 2 + 0.02 * o.iters[l], (k, l, st["iters"], o.iters[l])
+        if precision == 0:
             # the same step with the oracle's MINRES step counts: the iterates themselves
             # (a free-running solve may stop one step earlier or later than the oracle's,
             # where rounding moves |eta_j| across the tolerance)
