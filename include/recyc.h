@@ -202,8 +202,10 @@ rs_status rs_set_recycle_basis(rs_problem* prob, const double* U_dev, int ncols)
  * solutions by Eq. xFinal / upest); l0 = 0, count = M solves the whole step.
  * X_dev receives count x n doubles (shift l0 + i in row i). stats_host (count
  * entries) may be NULL. iters_override_host (count ints) may be NULL; if given,
- * shift l0 + i runs exactly that many MINRES steps and the tolerance is ignored
- * (for comparing iterates). Sub-ranges of one step may come in several calls:
+ * shift l0 + i runs exactly iters_override_host[i] MINRES steps with the
+ * tolerance ignored (for comparing iterates; 0 still applies the local space's
+ * projected correction), or, for a negative entry, is solved as without the
+ * override (the tolerance decides, and an initial guess that meets it is kept). Sub-ranges of one step may come in several calls:
  * the paper's chain g^(k,l-1) joins the local space of shift l when shift l-1
  * was solved earlier in the same step (in order l0 = 0, 1, .. the result is
  * that of one call over all shifts); with batched_local the shifts are

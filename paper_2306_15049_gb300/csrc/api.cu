@@ -2051,9 +2051,6 @@ rs_status rs_solve_shifts(rs_problem* P, int l0, int count, double* X_dev, rs_so
   if (l0 < 0 || count < 1 || l0 > P->z.M - count)
     return (rs_status)P->set_err(RS_EINVAL, "need 0 <= l0 and 1 <= count <= M - l0 (M = %d)", P->z.M);
   if (!X_dev) return (rs_status)P->set_err(RS_EINVAL, "X_dev is NULL");
-  if (iters_override_host)
-    for (int i = 0; i < count; ++i)
-      if (iters_override_host[i] < 0) return (rs_status)P->set_err(RS_EINVAL, "negative iteration override");
   // batched local spaces: every shift in one cooperative launch where it fits
   if (P->d.batched_local && P->use_batch && !iters_override_host && P->tp.radon.nang == 0 && l0 == 0 &&
       count == P->z.M) {
