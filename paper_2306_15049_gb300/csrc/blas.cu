@@ -174,6 +174,57 @@ k_gemm_ts(const TX* __restrict__ X, long ldx, int nx, const double* __restrict__
   }
 }
 
+// Y[:, l] for l in blocks of NB output columns: each thread keeps one row's NB
+// sums in registers and reads X once per block (the one-column kernel above
+// reads X once per output column). A: accumulation type. With an FP32 result the
+// products are summed in FP32 with compensation (Kahan), so the result keeps
+// about the accuracy of its own rounding; an FP64 result sums in FP64 in the
+// same order as k_gemm_ts.
+template <typename TX, typename TY, typename A, int NB>
+__global__ void __launch_bounds__(kThreads)
+k_gemm_ts_blk(const TX* __restrict__ X, long ldx, int nx, const double* __restrict__ C, int ldc,
+              int ny, double beta, TY* __restrict__ Y, long ldy, long n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A* Cs = reinterpret_cast<A*>(smem_raw);   // nx x NB: Cs[j * NB + c] = C[j, l0 + c]
+  constexpr bool kKahan = sizeof(A) == 4;
+  for (int l0 = 0; l0 < ny; l0 += NB) {
+    const int nb = (ny - l0 < NB) ? ny - l0 : NB;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nx * NB; idx += kThreads) {
+      const int j = idx / NB, c = idx - j * NB;
+      Cs[idx] = (c < nb) ? A(C[j + (long)(l0 + c) * ldc]) : A(0);
+    }
+    __syncthreads();
+    for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
+      A acc[NB], cmp[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) acc[c] = cmp[c] = A(0);
+      for (int j = 0; j < nx; ++j) {
+        const A x = A(X[(long)j * ldx + i]);
+        const A* cj = Cs + j * NB;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          if constexpr (kKahan) {
+            const A y = x * cj[c] - cmp[c];
+            const A t = __fadd_rn(acc[c], y);
+            cmp[c] = __fsub_rn(__fsub_rn(t, acc[c]), y);
+            acc[c] = t;
+          } else {
+            acc[c] = fma(x, cj[c], acc[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        if (c < nb) {
+          TY* yp = Y + (long)(l0 + c) * ldy + i;
+          *yp = (beta == 0.0) ? TY(acc[c]) : TY(beta * (double)(*yp) + (double)acc[c]);
+        }
+      }
+    }
+  }
+}
+
 constexpr int kGramRows = 16;
 constexpr int kGramAcc = 32;   // outputs per thread: nx * ny <= kThreads * kGramAcc
 
@@ -211,6 +262,67 @@ k_gram(const T* __restrict__ X, long ldx, int nx, const T* __restrict__ Y, long 
 #pragma unroll
         for (int rr = 0; rr < kGramRows; ++rr) a = fma(Xs[rr * nx + i], Ys[rr * ny + j], a);
         acc[q] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kGramAcc; ++q) {
+    const int o = threadIdx.x + q * kThreads;
+    if (o < nout) partials[(long)blockIdx.x * nout + o] = acc[q];
+  }
+}
+
+// The same Gram for FP32 data at FP64 accuracy without an FP64 multiply per
+// term: over each block of kGramRows rows a thread sums its products in two-float
+// arithmetic (the exact product x y = p + e from an FMA, then Knuth's two-sum of
+// the running high part with p, the rounding errors and e collected in a low
+// part), and adds the block's hi + lo to an FP64 accumulator. GB300 runs FP32
+// operations at many times its FP64 rate; the FP64 work is two additions per
+// block of kGramRows products instead of one FMA per product.
+__global__ void __launch_bounds__(kThreads)
+k_gram_f32(const float* __restrict__ X, long ldx, int nx, const float* __restrict__ Y, long ldy, int ny,
+           long n, long rows_per_cta, double* partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Xs = reinterpret_cast<float*>(smem_raw);
+  float* Ys = Xs + kGramRows * nx;
+  const int nout = nx * ny;
+  double acc[kGramAcc];
+#pragma unroll
+  for (int q = 0; q < kGramAcc; ++q) acc[q] = 0.0;
+  const long r0 = blockIdx.x * rows_per_cta;
+  const long r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
+  for (long rb = r0; rb < r1; rb += kGramRows) {
+    for (int idx = threadIdx.x; idx < kGramRows * nx; idx += kThreads) {
+      const int k = idx / kGramRows, rr = idx - k * kGramRows;
+      const long row = rb + rr;
+      Xs[rr * nx + k] = (row < r1) ? X[(long)k * ldx + row] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < kGramRows * ny; idx += kThreads) {
+      const int k = idx / kGramRows, rr = idx - k * kGramRows;
+      const long row = rb + rr;
+      Ys[rr * ny + k] = (row < r1) ? Y[(long)k * ldy + row] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kGramAcc; ++q) {
+      const int o = threadIdx.x + q * kThreads;
+      if (o < nout) {
+        const int i = o % nx, j = o / nx;
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int rr = 0; rr < kGramRows; ++rr) {
+          const float x = Xs[rr * nx + i], y = Ys[rr * ny + j];
+          // rounded-as-written operations (never contracted into an FMA)
+          const float p = __fmul_rn(x, y);
+          const float e = fmaf(x, y, -p);                          // x y - p exactly
+          const float t = __fadd_rn(hi, p);                        // two-sum: hi + p = t + d
+          const float bb = __fsub_rn(t, hi);
+          const float d = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+          hi = t;
+          lo = __fadd_rn(lo, __fadd_rn(d, e));
+        }
+        acc[q] += (double)hi + (double)lo;
       }
     }
     __syncthreads();
@@ -319,6 +431,40 @@ template <typename TX, typename TY>
 cudaError_t gemm_ts(const TX* X, long ldx, int nx, const double* C, int ldc, int ny, double beta,
                     TY* Y, long ldy, long n, cudaStream_t s) {
   if (ny <= 0) return cudaSuccess;
+  if (ny >= 4 && nx >= 1) {
+    // several outputs: X read once per block of output columns. An FP32 result
+    // (TY float) accumulates in FP32 with compensation, an FP64 one in FP64.
+    if constexpr (sizeof(TY) == 4) {
+      constexpr int NB = 32;
+      const size_t smem = (size_t)nx * NB * sizeof(float);
+      if (smem <= 96 * 1024) {
+        static size_t attr = 0;
+        if (smem > attr) {
+          RK_TRY(cudaFuncSetAttribute(k_gemm_ts_blk<TX, TY, float, NB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          attr = smem;
+        }
+        k_gemm_ts_blk<TX, TY, float, NB><<<ew_grid(n), kThreads, smem, s>>>(X, ldx, nx, C, ldc, ny, beta, Y,
+                                                                            ldy, n);
+        return launched();
+      }
+    } else {
+      constexpr int NB = 16;
+      using A = typename GemmAcc<TX>::type;
+      const size_t smem = (size_t)nx * NB * sizeof(A);
+      if (smem <= 96 * 1024) {
+        static size_t attr = 0;
+        if (smem > attr) {
+          RK_TRY(cudaFuncSetAttribute(k_gemm_ts_blk<TX, TY, A, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+          attr = smem;
+        }
+        k_gemm_ts_blk<TX, TY, A, NB><<<ew_grid(n), kThreads, smem, s>>>(X, ldx, nx, C, ldc, ny, beta, Y, ldy,
+                                                                        n);
+        return launched();
+      }
+    }
+  }
   k_gemm_ts<TX, TY><<<ew_grid(n), kThreads, 0, s>>>(X, ldx, nx, C, ldc, ny, beta, Y, ldy, n);
   return launched();
 }
@@ -336,9 +482,15 @@ cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, lon
   if (chunk > 1500 - nx) chunk = 1500 - nx;   // shared memory: 16 (nx + chunk) doubles <= 192 KB
   for (int j0 = 0; j0 < ny; j0 += chunk) {
     const int nyc = (ny - j0 < chunk) ? ny - j0 : chunk;
-    const size_t smem = (size_t)kGramRows * (nx + nyc) * sizeof(double);
-    RK_TRY(cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_gram<T><<<G, kThreads, smem, s>>>(X, ldx, nx, Y + (long)j0 * ldy, ldy, nyc, n, rows, partials);
+    if constexpr (sizeof(T) == 4) {
+      const size_t smem = (size_t)kGramRows * (nx + nyc) * sizeof(float);
+      RK_TRY(cudaFuncSetAttribute(k_gram_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_gram_f32<<<G, kThreads, smem, s>>>(X, ldx, nx, Y + (long)j0 * ldy, ldy, nyc, n, rows, partials);
+    } else {
+      const size_t smem = (size_t)kGramRows * (nx + nyc) * sizeof(double);
+      RK_TRY(cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_gram<T><<<G, kThreads, smem, s>>>(X, ldx, nx, Y + (long)j0 * ldy, ldy, nyc, n, rows, partials);
+    }
     RK_TRY(launched());
     RK_TRY(reduce_partials(partials, G, nx * nyc, nx * nyc, out + (long)j0 * nx, s, nullptr, 0,
                            nullptr));
