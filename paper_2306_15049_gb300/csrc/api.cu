@@ -299,7 +299,7 @@ struct rs_problem {
   bool use_coop_cgs = true; // CGS2 blocks as one cooperative launch
   int stream_ctas = 0;       // > 0: persistent solves stream tiles on at most this many CTAs
   bool use_prefetch = true;  // persistent MINRES kernels stage tiles ahead with cp.async
-  bool use_tma = true;       // FP32 streaming solves stage tile operands with tensor copies
+  int use_tma = 1;           // FP32 streaming solves stage tile operands with tensor copies (2: two-pass A)
   double* partials_p = nullptr;
   GridBar* gbar = nullptr;
 
@@ -757,7 +757,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     mp.rec_cap = keep;
     mp.j0 = n_unfused + 1;
     mp.prefetch = P->use_prefetch ? 1 : 0;
-    mp.tma = P->use_tma ? 1 : 0;
+    mp.tma = P->use_tma;
     CU(cudaMemsetAsync(P->gbar, 0, sizeof(GridBar), s));
     const int slot = timed_begin(P);
     int G = 0, resident = 0;
@@ -1937,8 +1937,13 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // RS_PREFETCH=0 stages every tile synchronously in the persistent MINRES kernels
   if (const char* g = std::getenv("RS_PREFETCH")) P->use_prefetch = std::strcmp(g, "0") != 0;
   // RS_TMA=0 runs the FP32 streaming solves in k_mr_persist instead of the kernel whose
-  // tile operands are staged by tensor copies (mrtma.cu)
-  if (const char* g = std::getenv("RS_TMA")) P->use_tma = std::strcmp(g, "0") != 0;
+  // tile operands are staged by tensor copies (mrtma.cu); RS_TMA=2 applies A there as
+  // two autocorrelation passes (RS_TMA=1: four blur passes)
+  if (const char* g = std::getenv("RS_TMA")) {
+    if (std::strcmp(g, "0") == 0) P->use_tma = 0;
+    else if (std::strcmp(g, "2") == 0) P->use_tma = 2;
+    else P->use_tma = 1;
+  }
   P->gprev_nz.assign(desc->M, 0);
   P->gcur_nz.assign(desc->M, 0);
   P->solved_cur.assign(desc->M, 0);

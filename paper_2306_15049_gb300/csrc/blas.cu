@@ -279,27 +279,29 @@ k_gram(const T* __restrict__ X, long ldx, int nx, const T* __restrict__ Y, long 
 // the running high part with p, the rounding errors and e collected in a low
 // part), and adds the block's hi + lo to an FP64 accumulator. GB300 runs FP32
 // operations at many times its FP64 rate; the FP64 work is two additions per
-// block of kGramRows products instead of one FMA per product.
+// block of kGramRowsF products instead of one FMA per product (GB300 issues FP64
+// at 2 lanes per clock and SM).
+constexpr int kGramRowsF = 64;
 __global__ void __launch_bounds__(kThreads)
 k_gram_f32(const float* __restrict__ X, long ldx, int nx, const float* __restrict__ Y, long ldy, int ny,
            long n, long rows_per_cta, double* partials) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Xs = reinterpret_cast<float*>(smem_raw);
-  float* Ys = Xs + kGramRows * nx;
+  float* Ys = Xs + kGramRowsF * nx;
   const int nout = nx * ny;
   double acc[kGramAcc];
 #pragma unroll
   for (int q = 0; q < kGramAcc; ++q) acc[q] = 0.0;
   const long r0 = blockIdx.x * rows_per_cta;
   const long r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
-  for (long rb = r0; rb < r1; rb += kGramRows) {
-    for (int idx = threadIdx.x; idx < kGramRows * nx; idx += kThreads) {
-      const int k = idx / kGramRows, rr = idx - k * kGramRows;
+  for (long rb = r0; rb < r1; rb += kGramRowsF) {
+    for (int idx = threadIdx.x; idx < kGramRowsF * nx; idx += kThreads) {
+      const int k = idx / kGramRowsF, rr = idx - k * kGramRowsF;
       const long row = rb + rr;
       Xs[rr * nx + k] = (row < r1) ? X[(long)k * ldx + row] : 0.f;
     }
-    for (int idx = threadIdx.x; idx < kGramRows * ny; idx += kThreads) {
-      const int k = idx / kGramRows, rr = idx - k * kGramRows;
+    for (int idx = threadIdx.x; idx < kGramRowsF * ny; idx += kThreads) {
+      const int k = idx / kGramRowsF, rr = idx - k * kGramRowsF;
       const long row = rb + rr;
       Ys[rr * ny + k] = (row < r1) ? Y[(long)k * ldy + row] : 0.f;
     }
@@ -311,7 +313,7 @@ k_gram_f32(const float* __restrict__ X, long ldx, int nx, const float* __restric
         const int i = o % nx, j = o / nx;
         float hi = 0.f, lo = 0.f;
 #pragma unroll
-        for (int rr = 0; rr < kGramRows; ++rr) {
+        for (int rr = 0; rr < kGramRowsF; ++rr) {
           const float x = Xs[rr * nx + i], y = Ys[rr * ny + j];
           // rounded-as-written operations (never contracted into an FMA)
           const float p = __fmul_rn(x, y);
@@ -480,10 +482,11 @@ cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, lon
   const long rows = (n + G - 1) / G;
   int chunk = (kThreads * kGramAcc) / nx;
   if (chunk > 1500 - nx) chunk = 1500 - nx;   // shared memory: 16 (nx + chunk) doubles <= 192 KB
+  if (sizeof(T) == 4 && chunk > 700 - nx) chunk = 700 - nx;   // 64 (nx + chunk) floats <= 175 KB
   for (int j0 = 0; j0 < ny; j0 += chunk) {
     const int nyc = (ny - j0 < chunk) ? ny - j0 : chunk;
     if constexpr (sizeof(T) == 4) {
-      const size_t smem = (size_t)kGramRows * (nx + nyc) * sizeof(float);
+      const size_t smem = (size_t)kGramRowsF * (nx + nyc) * sizeof(float);
       RK_TRY(cudaFuncSetAttribute(k_gram_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_gram_f32<<<G, kThreads, smem, s>>>(X, ldx, nx, Y + (long)j0 * ldy, ldy, nyc, n, rows, partials);
     } else {

@@ -51,9 +51,15 @@ struct TmaMaps {
   CUtensorMap K;       // {W, H, s} with stride ldk between columns, box {32, 32, s}
 };
 
+// Taps of the kernel (a kernel parameter, so that loops with compile-time
+// indices read them as constant-bank operands): g (2R + 1) for the four blur
+// passes; for the two-pass form of A = H^T H the autocorrelation c2 = g * g
+// (4R + 1) and the r x r edge corrections lc (see Taps in internal.cuh).
 template <int R>
 struct TapsF {
   float g[2 * R + 1];
+  float c2[4 * R + 1];
+  float lc[R * R];
 };
 
 // Stage layout (floats, every tensor-copy destination 128-byte aligned).
@@ -248,9 +254,98 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
   }
 }
 
+// The same outputs as tile_operator with A applied as two 1-D passes of the
+// autocorrelation taps c2 with the edge corrections lc (the form that
+// optile.cuh's op_tile2 uses): pass 1 filters the rows of the staged tile (its
+// 32 + 4R rows, the tile's 32 columns) into s1, pass 2 the columns of s1 at the
+// owned pixels; one CTA barrier instead of three and a third fewer FMAs than
+// the four blur passes. Outputs outside the image are not meaningful (the
+// caller masks them).
+template <int R, int NT>
+__device__ __forceinline__ void tile_operator2(const float* U, float* s1, const float* wxs, const float* wys,
+                                               const TapsF<R>& tf, float scale, int i0, int j0, int H, int W,
+                                               float* ax, float* ex, float* vc) {
+  using L = StageLayout<R>;
+  constexpr int AH = L::AH, AW = L::AW;
+  constexpr int PPT = kTileH * kTileW / NT;
+  constexpr int NW = 4 + 4 * R;
+  constexpr int NW2 = PPT + 4 * R;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int ti = ty * PPT + q, tj = tx;
+    const int gi = i0 + ti, gj = j0 + tj;
+    const bool in = gi < H && gj < W;
+    const float wl = (in && gj >= 1) ? wxs[ti * kWRow + tj + 3] : 0.f;
+    const float wr = (in && gj < W - 1) ? wxs[ti * kWRow + tj + 4] : 0.f;
+    const float wu = (in && gi >= 1) ? wys[ti * kWRow + tj + 4] : 0.f;
+    const float wd = (in && gi < H - 1) ? wys[(ti + 1) * kWRow + tj + 4] : 0.f;
+    const float* sp = U + (ti + 2 * R) * AW + (tj + 2 * R);
+    const float xc = sp[0];
+    ex[q] = (wl * (xc - sp[-1]) - wr * (sp[1] - xc) + wu * (xc - sp[-AW]) - wd * (sp[AW] - xc)) * scale;
+    vc[q] = xc * scale;
+  }
+  // pass 1: rows of U -> s1 (AH x 32); output column c is image column j0 + c
+  const int nl = W < R ? W : R;   // columns (rows) near an edge that carry a correction
+  const bool edge_x = j0 < R || j0 + kTileW > W - R;
+  for (int item = threadIdx.x; item < AH * (kTileW / 4); item += NT) {
+    const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
+    const float* row = U + a * AW;
+    float win[NW], o[4];
+    load_row<float, NW>(row + c0, win);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t <= 4 * R; ++t) acc += tf.c2[t] * win[q + t];
+      o[q] = acc;
+    }
+    if (edge_x) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gj = j0 + c0 + q;
+        if (gj < W) {
+          if (gj < R)          // left edge: image columns 0 .. nl-1, staged at qq - j0 + 2R
+            for (int qq = 0; qq < nl; ++qq) o[q] -= tf.lc[gj * R + qq] * row[qq - j0 + 2 * R];
+          if (gj >= W - R) {   // right edge: image columns W-1-qq, at the distance W-1-gj
+            const int d = W - 1 - gj;
+            for (int qq = 0; qq < nl; ++qq) o[q] -= tf.lc[d * R + qq] * row[(W - 1 - qq) - j0 + 2 * R];
+          }
+        }
+      }
+    }
+    store4<float>(s1 + a * kTileW + c0, o);
+  }
+  __syncthreads();
+  // pass 2: columns of s1 at the owned pixels; s1 row a is image row i0 - 2R + a
+  {
+    const int nlh = H < R ? H : R;
+    float win[NW2];
+#pragma unroll
+    for (int k = 0; k < NW2; ++k) win[k] = s1[(ty * PPT + k) * kTileW + tx];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t <= 4 * R; ++t) acc += tf.c2[t] * win[q + t];
+      const int gi = i0 + ty * PPT + q;
+      if (gi < H) {
+        if (gi < R)
+          for (int qq = 0; qq < nlh; ++qq) acc -= tf.lc[gi * R + qq] * s1[(qq - i0 + 2 * R) * kTileW + tx];
+        if (gi >= H - R) {
+          const int d = H - 1 - gi;
+          for (int qq = 0; qq < nlh; ++qq)
+            acc -= tf.lc[d * R + qq] * s1[((H - 1 - qq) - i0 + 2 * R) * kTileW + tx];
+        }
+      }
+      ax[q] = acc * scale;
+    }
+  }
+}
+
 constexpr int kTmaThreads = 512;
 
-template <int R>
+template <int R, bool TWO>
 __global__ void __launch_bounds__(kTmaThreads, 1)
 k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, const TapsF<R> tf, int H,
          int W, int s_alloc, GridBar* bar) {
@@ -347,8 +442,12 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
       }
       if (!stopped) {
         float ax[PPT], ex[PPT], vc[PPT], yk[PPT];
-        tile_operator<R, NT>(S + L::kU, bufB, S + L::kW, S + L::kW + kWPlane, tf, scale, i0, j0, H, W, ax, ex,
-                             vc);
+        if constexpr (TWO)
+          tile_operator2<R, NT>(S + L::kU, bufB, S + L::kW, S + L::kW + kWPlane, tf, scale, i0, j0, H, W, ax,
+                                ex, vc);
+        else
+          tile_operator<R, NT>(S + L::kU, bufB, S + L::kW, S + L::kW + kWPlane, tf, scale, i0, j0, H, W, ax,
+                               ex, vc);
         const float* Ks = S + L::kK;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
@@ -487,7 +586,7 @@ cudaError_t encode(CUtensorMap* m, const float* addr, int rank, unsigned long lo
 
 bool aligned16(const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; }
 
-template <int R>
+template <int R, bool TWO>
 cudaError_t launch_tma(MinresState* st, const MrP<float>& p, int H, int W, const Taps& tp, GridBar* bar,
                        int s_alloc, cudaStream_t s, int max_ctas, int* launched_blocks, bool* done) {
   using L = StageLayout<R>;
@@ -498,8 +597,8 @@ cudaError_t launch_tma(MinresState* st, const MrP<float>& p, int H, int W, const
   RK_TRY(encode_fn());
   static int cached = 0;
   static Occ occ;
-  RK_TRY(ensure_smem(k_mr_tma<R>, smem, &cached));
-  RK_TRY(occupancy(k_mr_tma<R>, smem, &occ, kTmaThreads));
+  RK_TRY(ensure_smem(k_mr_tma<R, TWO>, smem, &cached));
+  RK_TRY(occupancy(k_mr_tma<R, TWO>, smem, &occ, kTmaThreads));
   const int ntiles = mr_matvec_blocks(H, W);
   int G = occ.per_sm * occ.sms;
   if (G > ntiles) G = ntiles;
@@ -519,12 +618,14 @@ cudaError_t launch_tma(MinresState* st, const MrP<float>& p, int H, int W, const
                             kTileH, (unsigned)sa));
   TapsF<R> tf{};
   for (int k = 0; k <= 2 * R; ++k) tf.g[k] = (float)tp.g[k];
+  for (int k = 0; k <= 4 * R; ++k) tf.c2[k] = tp.c2f[k];
+  for (int k = 0; k < R * R; ++k) tf.lc[k] = tp.lcf[k];
   MinresState* a0 = st;
   MrP<float> a1 = p;
   int a4 = H, a5 = W, a6 = sa;
   GridBar* a7 = bar;
   void* args[] = {&a0, &a1, &maps, &tf, &a4, &a5, &a6, &a7};
-  RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_tma<R>, dim3(G), dim3(kTmaThreads), args, smem, s));
+  RK_TRY(cudaLaunchCooperativeKernel((const void*)k_mr_tma<R, TWO>, dim3(G), dim3(kTmaThreads), args, smem, s));
   *launched_blocks = G;
   *done = true;
   return launched();
@@ -543,12 +644,19 @@ cudaError_t mr_stream_tma(MinresState* st, const MrP<float>& p, int H, int W, co
     return cudaSuccess;
   for (int i = 0; i < 3; ++i)
     if (!aligned16(p.vring[i]) || !aligned16(p.dring[i])) return cudaSuccess;
+  // p.tma: 1 the four blur passes, 2 the two autocorrelation passes (radius <= kMaxR2)
+  const bool two = p.tma == 2 && tp.r <= kMaxR2;
   switch (tp.r) {
-    case 4: return launch_tma<4>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
-    case 6: return launch_tma<6>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
-    case 8: return launch_tma<8>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
-    case 10: return launch_tma<10>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
-    case 12: return launch_tma<12>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 4: return two ? launch_tma<4, true>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done)
+                       : launch_tma<4, false>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 6: return two ? launch_tma<6, true>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done)
+                       : launch_tma<6, false>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 8: return two ? launch_tma<8, true>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done)
+                       : launch_tma<8, false>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 10: return two ? launch_tma<10, true>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done)
+                        : launch_tma<10, false>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
+    case 12: return two ? launch_tma<12, true>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done)
+                        : launch_tma<12, false>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
     default: return cudaSuccess;
   }
 }
