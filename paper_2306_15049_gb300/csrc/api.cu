@@ -34,6 +34,7 @@ constexpr double kInnerRho = 1e-4;         // inner relative reduction per sweep
 constexpr int kDotStride = kMaxLocal + 1;
 constexpr int kBatchTail = 2;               // batched solves: the last shifts run one by one
 constexpr int kChunk = 6;                  // MINRES steps per CUDA-graph replay (a multiple of 3)
+constexpr int kStabPanel = 16;             // candidates per panel of the blocked stabilize CGS2
 
 long round_up(long x, long a) { return (x + a - 1) / a * a; }
 
@@ -235,6 +236,7 @@ struct rs_problem {
   double *Rfull = nullptr, *XT = nullptr, *Vsv = nullptr, *sig = nullptr, *hdots = nullptr;
   double *coef = nullptr, *scal = nullptr, *Ktr = nullptr, *Rk = nullptr, *zc = nullptr;
   double *arec = nullptr, *brec = nullptr, *lc = nullptr;
+  double *nbin = nullptr, *cblk = nullptr;   // stabilize by panels: candidate norms, panel coefficients
   // oblique guesses with two anchors (Eq. updates): per anchor R_a, K_a^T E U_a, K_a^T b
   void* Kan = nullptr;
   // batched solves (batched_local = 1): every shift's local space, MINRES vectors
@@ -385,6 +387,8 @@ void carve(rs_problem* P, Carver& cv) {
   P->WtL = cv.take<double>((size_t)z.p * std::max(z.J, 1));
   P->WtR = cv.take<double>((size_t)z.p * std::max(z.J, 1));
   P->Rfull = cv.take<double>((size_t)z.cmax * z.cmax);
+  P->nbin = cv.take<double>((size_t)z.cmax);
+  P->cblk = cv.take<double>((size_t)3 * z.cmax * kStabPanel);
   P->XT = cv.take<double>((size_t)z.cmax * z.cmax);
   P->Vsv = cv.take<double>((size_t)z.cmax * z.cmax);
   P->sig = cv.take<double>(z.cmax);

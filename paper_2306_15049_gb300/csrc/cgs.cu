@@ -19,7 +19,7 @@ namespace {
 __global__ void k_cgs_finalize(CgsCtx c, int cand, const double* coef1, const double* coef2,
                                const double* nb2, const double* np2) {
   const int s = c.count[0];
-  const double nb = sqrt(*nb2), np = sqrt(*np2);
+  const double nb = sqrt(c.nb_in ? c.nb_in[cand] : *nb2), np = sqrt(*np2);
   const int keep = (nb > 0.0 && np > c.drop_rel * nb) ? 1 : 0;
   if (c.Rk && keep) {
     for (int k = threadIdx.x; k < c.ldr; k += blockDim.x)
@@ -28,7 +28,8 @@ __global__ void k_cgs_finalize(CgsCtx c, int cand, const double* coef1, const do
   if (c.Rfull) {
     const double inv = nb > 0.0 ? 1.0 / nb : 0.0;
     double* col = c.Rfull + (long)cand * c.ldrf;
-    for (int k = threadIdx.x; k < c.ldrf; k += blockDim.x) {
+    const int rrows = c.rrows > 0 ? c.rrows : c.ldrf;
+    for (int k = threadIdx.x; k < rrows; k += blockDim.x) {
       double v = 0.0;
       if (nb > 0.0) v = (k < s) ? (coef1[k] + coef2[k]) * inv : ((k == s && keep) ? np * inv : 0.0);
       col[k] = v;

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_block(CgsB<T> a, GridBar* bar
     cta_dots<T>(a.Q, a.ldq, s, bs, c0, len, part, G);
     if (!grid_sync(bar, (++nb) * G, &ok_s)) return;
     reduce_rows<T>(part, G, s + 1, c1);
-    const double nb2 = (double)c1[s];
+    const double nb2 = c.nb_in ? c.nb_in[j] : (double)c1[s];
     // ---- S2: b -= Q c1, c2 = Q^T b
     part = part0 + (long)(nb & 1) * region;
     cta_axpy<T>(a.Q, a.ldq, s, c1, bs, c0, len);
@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_block(CgsB<T> a, GridBar* bar
       }
       if (c.Rfull) {
         double* col = c.Rfull + (long)j * c.ldrf;
-        for (int k = threadIdx.x; k < c.ldrf; k += kThreads) {
+        const int rrows = c.rrows > 0 ? c.rrows : c.ldrf;
+        for (int k = threadIdx.x; k < rrows; k += kThreads) {
           double v = 0.0;
           if (inb > 0.0) v = (k < s) ? ((double)c1[k] + (double)c2[k]) * inb : ((k == s && keep) ? np * inb : 0.0);
           col[k] = v;

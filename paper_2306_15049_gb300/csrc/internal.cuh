@@ -437,6 +437,12 @@ struct CgsCtx {
   double* partials;        // scratch red_grid(n) * ldr
   double* scal;            // scratch 4
   double drop_rel;
+  // Optional (0 / nullptr: off). nb_in[j]: the squared norm of candidate j before
+  // any projection (the keep rule and the Rfull scaling refer to it; set when the
+  // candidates were already projected against an earlier block of Q). rrows: rows
+  // of an Rfull column written (default ldrf).
+  const double* nb_in;
+  int rrows;
 };
 cudaError_t cgs_reset(const CgsCtx& c, cudaStream_t s);
 template <typename T>
