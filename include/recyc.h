@@ -337,6 +337,26 @@ rs_status rs_synthesize_data_noalloc(const rs_problem_desc* desc, const double* 
                                      const double* z_dev, double eta, double* d_out_dev,
                                      void* stream);
 
+/* Self-test of the bounded grid-barrier wait of the library's persistent
+ * cooperative kernels (no counterpart in the paper: it checks the failure path of
+ * this implementation). Launches two CTAs of which one never arrives at the
+ * barrier; the other's wait gives up after the barrier's time limit (2 s), sets
+ * the barrier's error flag and returns, as a persistent solve does when a CTA
+ * stalls. scratch_dev: at least 64 bytes of 16-byte aligned device memory;
+ * *err_host receives the flag (1: the wait ran out). Returns RS_OK when the wait
+ * gave up as it must; the context stays usable. Synchronises `stream`. Errors:
+ * rs_last_error(NULL). */
+rs_status rs_selftest_grid_barrier(void* scratch_dev, size_t scratch_bytes, void* stream, int* err_host);
+
+/* Measurement helper (no counterpart in the paper): the FP64 FMA rate of the
+ * GPU's CUDA cores, which bounds the library's FP64 kernels (the FP64 stencil,
+ * the FP64 Grams and CGS2). Runs 8 CTAs of 256 threads per SM, each thread eight
+ * independent FMA chains of 16384 steps, timed with CUDA events on `stream`
+ * after a short warm-up launch. scratch_dev: at least 8 * SMs * 256 doubles of
+ * device memory (overwritten); *gflops_host receives GFLOP/s (2 per FMA).
+ * Synchronises `stream`. Errors: rs_last_error(NULL). */
+rs_status rs_measure_fp64_fma(void* scratch_dev, size_t scratch_bytes, void* stream, double* gflops_host);
+
 rs_status rs_get_info(const rs_problem* prob, rs_info* info_host);
 
 /* Turn per-kernel event timing on (1) or off (0); either call resets the

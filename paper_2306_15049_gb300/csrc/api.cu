@@ -50,6 +50,22 @@ __global__ void k_coef_neg(const double* C, const double* gammas, int nc, int M,
   }
 }
 
+// dst = -src (cnt entries)
+__global__ void k_negate(const double* src, double* dst, int cnt) {
+  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < cnt; i += blockDim.x * gridDim.x) dst[i] = -src[i];
+}
+
+// Rows 0..s0-1 of the normalised R columns of a panel of b candidates j0.. that
+// were projected against the first s0 kept columns: (C1 + C2) / ||b_in||.
+__global__ void k_panel_rows(const double* C1, const double* C2, int s0, int b, const double* nb2,
+                             double* Rfull, int ldrf, int j0) {
+  for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < s0 * b; idx += blockDim.x * gridDim.x) {
+    const int k = idx % s0, jj = idx / s0;
+    const double nb = sqrt(nb2[jj]);
+    Rfull[k + (long)(j0 + jj) * ldrf] = nb > 0.0 ? (C1[idx] + C2[idx]) / nb : 0.0;
+  }
+}
+
 // H = sym(Ah) + gamma sym(Eh)
 __global__ void k_form_h(const double* Ah, const double* Eh, int nc, double gamma, double* Hs) {
   for (int idx = threadIdx.x; idx < nc * nc; idx += blockDim.x) {
@@ -302,6 +318,7 @@ struct rs_problem {
   int stream_ctas = 0;       // > 0: persistent solves stream tiles on at most this many CTAs
   bool use_prefetch = true;  // persistent MINRES kernels stage tiles ahead with cp.async
   int use_tma = 1;           // FP32 streaming solves stage tile operands with tensor copies (2: two-pass A)
+  bool stab_panels = true;   // stabilize CGS2 by panels of candidates (column by column when false)
   double* partials_p = nullptr;
   GridBar* gbar = nullptr;
 
@@ -901,6 +918,71 @@ int coop_check(rs_problem* P) {
   return RS_OK;
 }
 
+// Algorithm "Stabilized U", first part: the CGS2 factorisation (with the drop
+// rule of kStabDrop and one R column per candidate, normalised by the
+// candidate's norm) of the ncand candidates in Ut_raw, in place, by panels of
+// kStabPanel candidates. A panel is first projected twice against every column
+// kept so far (two FP64 Gram products Q^T P and two updates P -= Q C: Q is read
+// four times per panel instead of four times per candidate), then its columns
+// are orthogonalised among themselves in order by the cooperative CGS2 kernel,
+// whose keep rule and R scaling refer to each candidate's norm before the
+// panel's projection. The same R, kept columns and drops as the column-by-column
+// CGS2 up to rounding. Returns the kept count in *nk; *used = false (nothing
+// queued) where the cooperative kernel does not fit, and the caller runs the
+// column-by-column path.
+int stabilize_cgs2_panels(rs_problem* P, int ncand, int* nk, bool* used) {
+  const Dims& z = P->z;
+  const long n = z.n, ld = z.ld;
+  cudaStream_t s = P->s;
+  *used = false;
+  double* U = P->Ut_raw;
+  // every candidate's squared norm, before any of them is modified
+  for (int j = 0; j < ncand; ++j) {
+    CU(norm2_partials<double>(U + (long)j * ld, n, P->partials, s));
+    CU(reduce_partials(P->partials, z.G, 1, 1, P->nbin + j, s, nullptr, 0, nullptr));
+  }
+  double* C1 = P->cblk;
+  double* C2 = C1 + (long)z.cmax * kStabPanel;
+  double* Cn = C2 + (long)z.cmax * kStabPanel;
+  int s0 = 0;
+  for (int j0 = 0; j0 < ncand; j0 += kStabPanel) {
+    const int b = std::min(kStabPanel, ncand - j0);
+    double* Pn = U + (long)j0 * ld;
+    if (s0 > 0) {
+      CU(gram<double>(U, ld, s0, Pn, ld, b, n, P->partials, C1, s));
+      k_negate<<<8, 256, 0, s>>>(C1, Cn, s0 * b);
+      CU(launched());
+      CU(gemm_ts<double, double>(U, ld, s0, Cn, s0, b, 1.0, Pn, ld, n, s));
+      CU(gram<double>(U, ld, s0, Pn, ld, b, n, P->partials, C2, s));
+      k_negate<<<8, 256, 0, s>>>(C2, Cn, s0 * b);
+      CU(launched());
+      CU(gemm_ts<double, double>(U, ld, s0, Cn, s0, b, 1.0, Pn, ld, n, s));
+      k_panel_rows<<<8, 256, 0, s>>>(C1, C2, s0, b, P->nbin + j0, P->Rfull, z.cmax, j0);
+      CU(launched());
+    }
+    CgsCtx c = cgs_ctx(P, z.cmax, nullptr, P->Rfull + (long)j0 * z.cmax + s0, z.cmax, kStabDrop);
+    c.nb_in = P->nbin + j0;
+    c.rrows = z.cmax - s0;
+    c.kept_idx = P->kept + s0;
+    bool done = false;
+    CU(cgs2_block<double>(c, U + (long)s0 * ld, ld, Pn, ld, b, 1, n, P->gbar, s, &done));
+    if (!done) {
+      if (j0 == 0) return RS_OK;   // nothing modified yet: the column path takes over
+      return P->set_err(RS_ECUDA, "stabilize: the cooperative CGS2 kernel stopped fitting");
+    }
+    RS(coop_check(P));
+    int kp = 0;
+    RS(read_back(P, &kp, P->cnt, sizeof kp));
+    s0 += kp;
+  }
+  // the kept count where the caller and the column path expect it
+  CU(cudaMemcpyAsync(P->cnt, &s0, sizeof(int), cudaMemcpyHostToDevice, s));
+  CU(cudaStreamSynchronize(s));
+  *nk = s0;
+  *used = true;
+  return RS_OK;
+}
+
 // Algorithm "Stabilized U" on the ncand columns of Ut_raw (FP64), then the
 // images, K, R, the matrices of Eq. orthupdate and Eq. hq, and the Ritz
 // vectors of Algorithm "interior" at gamma_{J_L}, gamma_{J_R}.
@@ -910,11 +992,15 @@ int finish_principal_body(rs_problem* P, int ncand) {
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
   // stabilize: CGS2 (in place, normalised R per candidate), SVD of R
-  CgsCtx c = cgs_ctx(P, z.cmax, nullptr, P->Rfull, z.cmax, kStabDrop);
-  RS(cgs2_all<double>(P, c, P->Ut_raw, P->Ut_raw, ncand, true));
   int nk = 0;
-  RS(read_back(P, &nk, P->cnt, sizeof nk));
-  RS(coop_check(P));
+  bool panels = false;
+  if (P->use_coop_cgs && P->stab_panels) RS(stabilize_cgs2_panels(P, ncand, &nk, &panels));
+  if (!panels) {
+    CgsCtx c = cgs_ctx(P, z.cmax, nullptr, P->Rfull, z.cmax, kStabDrop);
+    RS(cgs2_all<double>(P, c, P->Ut_raw, P->Ut_raw, ncand, true));
+    RS(read_back(P, &nk, P->cnt, sizeof nk));
+    RS(coop_check(P));
+  }
   int ncn = 0;
   if (nk > 0) {
     k_transpose_r<<<32, 256, 0, s>>>(P->Rfull, z.cmax, nk, ncand, P->XT);
@@ -1940,6 +2026,8 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   }
   // RS_PREFETCH=0 stages every tile synchronously in the persistent MINRES kernels
   if (const char* g = std::getenv("RS_PREFETCH")) P->use_prefetch = std::strcmp(g, "0") != 0;
+  // RS_STAB_PANELS=0 runs the stabilize CGS2 column by column instead of by panels
+  if (const char* g = std::getenv("RS_STAB_PANELS")) P->stab_panels = std::strcmp(g, "0") != 0;
   // RS_TMA=0 runs the FP32 streaming solves in k_mr_persist instead of the kernel whose
   // tile operands are staged by tensor copies (mrtma.cu); RS_TMA=2 applies A there as
   // two autocorrelation passes (RS_TMA=1: four blur passes)

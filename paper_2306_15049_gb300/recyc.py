@@ -91,6 +91,8 @@ _SIGS = {
     "rs_synthesize_data": (_I, [ctypes.POINTER(rs_problem_desc), _P, _P, _D, _P, _P,
                                 ctypes.c_size_t, _P]),
     "rs_synthesize_data_noalloc": (_I, [ctypes.POINTER(rs_problem_desc), _P, _P, _D, _P, _P]),
+    "rs_selftest_grid_barrier": (_I, [_P, ctypes.c_size_t, _P, ctypes.POINTER(_I)]),
+    "rs_measure_fp64_fma": (_I, [_P, ctypes.c_size_t, _P, ctypes.POINTER(_D)]),
     "rs_get_info": (_I, [_P, ctypes.POINTER(rs_info)]),
     "rs_set_timing": (_I, [_P, _I]),
     "rs_get_timing": (_I, [_P, ctypes.POINTER(rs_timing)]),

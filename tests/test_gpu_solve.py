@@ -259,3 +259,37 @@ def test_c2_full_size_first_step_every_shift_meets_tolerance(precision):
         rr = np.linalg.norm(r) / np.linalg.norm(pr.b)
         assert rr <= wl.tol * (1 + 1e-4), (l, rr, stats[l])
         assert abs(rr - stats[l]["relres_true"]) <= 1e-3 * wl.tol
+
+
+def test_stabilize_by_panels_matches_column_by_column():
+    """Algorithm "Stabilized U" by panels of 16 candidates (the default) against
+    the column-by-column CGS2 (RS_STAB_PANELS=0): the same n_c and the same
+    principal space, on steps whose candidates span several panels."""
+    import os
+    wl = synth.tiny(48, 44, sigma=1.5, radius=4, M=10, p=16, n_ritz_local=3, seed=77, tol=1e-9)
+    bases = {}
+    for flag in ("1", "0"):
+        old = os.environ.get("RS_STAB_PANELS")
+        os.environ["RS_STAB_PANELS"] = flag
+        try:
+            pr = Pair(wl)
+        finally:
+            if old is None:
+                del os.environ["RS_STAB_PANELS"]
+            else:
+                os.environ["RS_STAB_PANELS"] = old
+        out = []
+        for k, w in enumerate([np.ones(2 * wl.n), synth.random_weights(wl.n, 5, lo=1.0, hi=300.0)]):
+            pr.P.rs_set_weights(pr.t(w))
+            pr.P.rs_update_recycle(0 if k == 0 else 1)
+            info = pr.P.rs_get_info()
+            U = pr.torch.empty(wl.p, wl.n, dtype=pr.torch.float64, device=pr.dev)
+            nc = pr.P.rs_get_principal_basis(U)
+            out.append((info["stab_candidates"], info["stab_kept"], nc, pr.n(U)[:nc].T.copy()))
+            X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
+            pr.P.rs_solve_shifts(X)
+        bases[flag] = out
+    assert bases["1"][1][0] > 16          # the update step's candidates fill more than one panel
+    for (c1, k1, n1, U1), (c0, k0, n0, U0) in zip(bases["1"], bases["0"]):
+        assert (c1, k1, n1) == (c0, k0, n0)
+        assert _proj_dist(U1, U0) < 1e-6     # rounding, amplified for directions with sigma near 1e-10 sigma_1
