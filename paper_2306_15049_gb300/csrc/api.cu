@@ -317,7 +317,7 @@ struct rs_problem {
   bool use_coop_cgs = true; // CGS2 blocks as one cooperative launch
   int stream_ctas = 0;       // > 0: persistent solves stream tiles on at most this many CTAs
   bool use_prefetch = true;  // persistent MINRES kernels stage tiles ahead with cp.async
-  int use_tma = 1;           // FP32 streaming solves stage tile operands with tensor copies (2: two-pass A)
+  int use_tma = 2;           // FP32 streaming solves stage tile operands with tensor copies (2: two-pass A)
   bool stab_panels = true;   // stabilize CGS2 by panels of candidates (column by column when false)
   double* partials_p = nullptr;
   GridBar* gbar = nullptr;
@@ -922,8 +922,9 @@ int coop_check(rs_problem* P) {
 // rule of kStabDrop and one R column per candidate, normalised by the
 // candidate's norm) of the ncand candidates in Ut_raw, in place, by panels of
 // kStabPanel candidates. A panel is first projected twice against every column
-// kept so far (two FP64 Gram products Q^T P and two updates P -= Q C: Q is read
-// four times per panel instead of four times per candidate), then its columns
+// kept so far (two Gram products Q^T P and two updates P -= Q C of FP64 data,
+// computed in two-float arithmetic: GB300's FP64 rate bounded the column-by-column
+// CGS2), then its columns
 // are orthogonalised among themselves in order by the cooperative CGS2 kernel,
 // whose keep rule and R scaling refer to each candidate's norm before the
 // panel's projection. The same R, kept columns and drops as the column-by-column
@@ -948,7 +949,16 @@ int stabilize_cgs2_panels(rs_problem* P, int ncand, int* nk, bool* used) {
   for (int j0 = 0; j0 < ncand; j0 += kStabPanel) {
     const int b = std::min(kStabPanel, ncand - j0);
     double* Pn = U + (long)j0 * ld;
-    if (s0 > 0) {
+    if (s0 > 0 && s0 <= kThreads) {
+      // the products in two-float arithmetic (about 2^-46 relative, far below the
+      // 1e-10 singular-value threshold, at FP32 rates); the panel itself stays FP64
+      CU(gram_d2f(U, ld, s0, Pn, ld, b, n, P->partials, C1, s));
+      CU(gemm_sub_d2f(U, ld, s0, C1, s0, b, Pn, ld, n, s));
+      CU(gram_d2f(U, ld, s0, Pn, ld, b, n, P->partials, C2, s));
+      CU(gemm_sub_d2f(U, ld, s0, C2, s0, b, Pn, ld, n, s));
+      k_panel_rows<<<8, 256, 0, s>>>(C1, C2, s0, b, P->nbin + j0, P->Rfull, z.cmax, j0);
+      CU(launched());
+    } else if (s0 > 0) {
       CU(gram<double>(U, ld, s0, Pn, ld, b, n, P->partials, C1, s));
       k_negate<<<8, 256, 0, s>>>(C1, Cn, s0 * b);
       CU(launched());
@@ -2029,8 +2039,9 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // RS_STAB_PANELS=0 runs the stabilize CGS2 column by column instead of by panels
   if (const char* g = std::getenv("RS_STAB_PANELS")) P->stab_panels = std::strcmp(g, "0") != 0;
   // RS_TMA=0 runs the FP32 streaming solves in k_mr_persist instead of the kernel whose
-  // tile operands are staged by tensor copies (mrtma.cu); RS_TMA=2 applies A there as
-  // two autocorrelation passes (RS_TMA=1: four blur passes)
+  // tile operands are staged by tensor copies (mrtma.cu); that kernel applies A as two
+  // autocorrelation passes (RS_TMA=2, the default: measured 150 against 157 us per step
+  // on the 2048 x 2048 workload) or, RS_TMA=1, as four blur passes
   if (const char* g = std::getenv("RS_TMA")) {
     if (std::strcmp(g, "0") == 0) P->use_tma = 0;
     else if (std::strcmp(g, "2") == 0) P->use_tma = 2;

@@ -336,6 +336,140 @@ k_gram_f32(const float* __restrict__ X, long ldx, int nx, const float* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 data in two-float arithmetic (the stabilize's panel products)
+// ---------------------------------------------------------------------------
+// x = h + l with h = fl32(x), l = fl32(x - h): about 48 significant bits. A
+// product x y is h_x h_y (split exactly into p + e by an FMA) plus the cross
+// terms h_x l_y + l_x h_y (their FP32 rounding is about 2^-48 of p); sums run
+// in two-float (Knuth's two-sum) and are flushed into FP64 every kD2fRows
+// rows. Relative accuracy about 2^-46, at FP32 rates instead of GB300's FP64
+// rate; every operation below is rounded as written (no FMA contraction).
+constexpr int kD2fRows = 32;
+constexpr int kD2fCols = 16;   // right-hand columns of one launch
+
+__device__ __forceinline__ void split_d2f(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+
+// hi + lo += (xh + xl)(yh + yl)
+__device__ __forceinline__ void d2f_madd(float xh, float xl, float yh, float yl, float& hi, float& lo) {
+  const float p = __fmul_rn(xh, yh);
+  const float e = fmaf(xh, yh, -p);
+  const float c = fmaf(xh, yl, __fmul_rn(xl, yh));
+  const float t = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(t, hi);
+  const float d = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  hi = t;
+  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(d, e), c));
+}
+
+// partials[blockIdx.x * nx * ny + i + j nx] = CTA's share of (X^T Y)[i, j] for FP64
+// X (nx columns) and Y (ny <= kD2fCols columns): thread i of the CTA owns output
+// row i (nx <= kThreads) and all ny columns.
+__global__ void __launch_bounds__(kThreads)
+k_gram_d2f(const double* __restrict__ X, long ldx, int nx, const double* __restrict__ Y, long ldy, int ny,
+           long n, long rows_per_cta, double* partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Xh = reinterpret_cast<float*>(smem_raw);         // kD2fRows x nx
+  float* Xl = Xh + kD2fRows * nx;
+  float* Yh = Xl + kD2fRows * nx;                           // kD2fRows x kD2fCols
+  float* Yl = Yh + kD2fRows * kD2fCols;
+  const int i = threadIdx.x;
+  double acc[kD2fCols];
+#pragma unroll
+  for (int j = 0; j < kD2fCols; ++j) acc[j] = 0.0;
+  const long r0 = blockIdx.x * rows_per_cta;
+  const long r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
+  for (long rb = r0; rb < r1; rb += kD2fRows) {
+    for (int idx = threadIdx.x; idx < kD2fRows * nx; idx += kThreads) {
+      const int k = idx / kD2fRows, rr = idx - k * kD2fRows;
+      const long row = rb + rr;
+      float h = 0.f, l = 0.f;
+      if (row < r1) split_d2f(X[(long)k * ldx + row], h, l);
+      Xh[rr * nx + k] = h;
+      Xl[rr * nx + k] = l;
+    }
+    for (int idx = threadIdx.x; idx < kD2fRows * kD2fCols; idx += kThreads) {
+      const int k = idx / kD2fRows, rr = idx - k * kD2fRows;
+      const long row = rb + rr;
+      float h = 0.f, l = 0.f;
+      if (row < r1 && k < ny) split_d2f(Y[(long)k * ldy + row], h, l);
+      Yh[rr * kD2fCols + k] = h;
+      Yl[rr * kD2fCols + k] = l;
+    }
+    __syncthreads();
+    if (i < nx) {
+      float hi[kD2fCols], lo[kD2fCols];
+#pragma unroll
+      for (int j = 0; j < kD2fCols; ++j) hi[j] = lo[j] = 0.f;
+      for (int rr = 0; rr < kD2fRows; ++rr) {
+        const float xh = Xh[rr * nx + i], xl = Xl[rr * nx + i];
+        const float4* yh4 = reinterpret_cast<const float4*>(Yh + rr * kD2fCols);
+        const float4* yl4 = reinterpret_cast<const float4*>(Yl + rr * kD2fCols);
+#pragma unroll
+        for (int v = 0; v < kD2fCols / 4; ++v) {
+          const float4 a = yh4[v], c = yl4[v];
+          d2f_madd(xh, xl, a.x, c.x, hi[4 * v], lo[4 * v]);
+          d2f_madd(xh, xl, a.y, c.y, hi[4 * v + 1], lo[4 * v + 1]);
+          d2f_madd(xh, xl, a.z, c.z, hi[4 * v + 2], lo[4 * v + 2]);
+          d2f_madd(xh, xl, a.w, c.w, hi[4 * v + 3], lo[4 * v + 3]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kD2fCols; ++j) acc[j] += (double)hi[j] + (double)lo[j];
+    }
+    __syncthreads();
+  }
+  if (i < nx) {
+    const int nout = nx * ny;
+#pragma unroll
+    for (int j = 0; j < kD2fCols; ++j)
+      if (j < ny) partials[(long)blockIdx.x * nout + i + (long)j * nx] = acc[j];
+  }
+}
+
+// Y[:, j] -= X C[:, j] (j < ny <= kD2fCols) for FP64 X (nx columns), Y and C, the
+// products summed in two-float arithmetic and subtracted in FP64.
+__global__ void __launch_bounds__(kThreads)
+k_gemm_sub_d2f(const double* __restrict__ X, long ldx, int nx, const double* __restrict__ C, int ldc, int ny,
+               double* __restrict__ Y, long ldy, long n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ch = reinterpret_cast<float*>(smem_raw);   // nx x kD2fCols
+  float* Cl = Ch + nx * kD2fCols;
+  for (int idx = threadIdx.x; idx < nx * kD2fCols; idx += kThreads) {
+    const int k = idx / kD2fCols, j = idx - k * kD2fCols;
+    float h = 0.f, l = 0.f;
+    if (j < ny) split_d2f(C[k + (long)j * ldc], h, l);
+    Ch[idx] = h;
+    Cl[idx] = l;
+  }
+  __syncthreads();
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < n; i += (long)gridDim.x * kThreads) {
+    float hi[kD2fCols], lo[kD2fCols];
+#pragma unroll
+    for (int j = 0; j < kD2fCols; ++j) hi[j] = lo[j] = 0.f;
+    for (int k = 0; k < nx; ++k) {
+      float xh, xl;
+      split_d2f(X[(long)k * ldx + i], xh, xl);
+      const float4* ch4 = reinterpret_cast<const float4*>(Ch + k * kD2fCols);
+      const float4* cl4 = reinterpret_cast<const float4*>(Cl + k * kD2fCols);
+#pragma unroll
+      for (int v = 0; v < kD2fCols / 4; ++v) {
+        const float4 a = ch4[v], c = cl4[v];
+        d2f_madd(xh, xl, a.x, c.x, hi[4 * v], lo[4 * v]);
+        d2f_madd(xh, xl, a.y, c.y, hi[4 * v + 1], lo[4 * v + 1]);
+        d2f_madd(xh, xl, a.z, c.z, hi[4 * v + 2], lo[4 * v + 2]);
+        d2f_madd(xh, xl, a.w, c.w, hi[4 * v + 3], lo[4 * v + 3]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kD2fCols; ++j)
+      if (j < ny) Y[(long)j * ldy + i] -= (double)hi[j] + (double)lo[j];
+  }
+}
+
 template <typename TX, typename TY>
 __global__ void k_axpby(const TX* __restrict__ x, double a, TY* __restrict__ y, double b, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
@@ -499,6 +633,38 @@ cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, lon
                            nullptr));
   }
   return cudaSuccess;
+}
+
+cudaError_t gram_d2f(const double* X, long ldx, int nx, const double* Y, long ldy, int ny, long n,
+                     double* partials, double* out, cudaStream_t s) {
+  if (nx <= 0 || ny <= 0) return cudaSuccess;
+  if (nx > kThreads || ny > kD2fCols) return cudaErrorInvalidValue;
+  const int G = 152;
+  const long rows = ((n + G - 1) / G + kD2fRows - 1) / kD2fRows * kD2fRows;
+  const size_t smem = (size_t)kD2fRows * (2 * nx + 2 * kD2fCols) * sizeof(float);
+  static size_t attr = 0;
+  if (smem > attr) {
+    RK_TRY(cudaFuncSetAttribute(k_gram_d2f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  k_gram_d2f<<<G, kThreads, smem, s>>>(X, ldx, nx, Y, ldy, ny, n, rows, partials);
+  RK_TRY(launched());
+  return reduce_partials(partials, G, nx * ny, nx * ny, out, s, nullptr, 0, nullptr);
+}
+
+cudaError_t gemm_sub_d2f(const double* X, long ldx, int nx, const double* C, int ldc, int ny, double* Y,
+                         long ldy, long n, cudaStream_t s) {
+  if (nx <= 0 || ny <= 0) return cudaSuccess;
+  if (ny > kD2fCols) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)2 * nx * kD2fCols * sizeof(float);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static size_t attr = 0;
+  if (smem > attr) {
+    RK_TRY(cudaFuncSetAttribute(k_gemm_sub_d2f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  k_gemm_sub_d2f<<<ew_grid(n), kThreads, smem, s>>>(X, ldx, nx, C, ldc, ny, Y, ldy, n);
+  return launched();
 }
 
 template <typename TX, typename TY>

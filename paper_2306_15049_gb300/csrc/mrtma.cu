@@ -9,18 +9,17 @@
 // (u = y - K h - alpha v_j - beta v_{j-1}, partial ||u||^2), a grid barrier and
 // the scalar Givens step on every CTA's copy of the state.
 //
-// What differs is how phase A is fed. Each CTA owns a ring of three stages of
-// shared memory; a stage holds one tile's
+// What differs is how phase A is fed. Each CTA owns two stages of shared
+// memory; a stage holds one tile's operands:
 //   u with a halo of 2r (zero outside the image: the box's out-of-range fill),
-//   weights w_x (one column to the left) and w_y (one row above), and
-//   v_{j-1}, d_{j-2}, d_{j-3}, x_m (the direction update),
-// and one more buffer holds the tile's s columns of the local space K (one 3-D
-// box), which the tile needs only after its stencil. One thread issues the
-// tensor copies (cp.async.bulk.tensor) on each buffer's mbarrier: a tile's
-// stage two tiles ahead of its use, its K columns one tile ahead, so the
-// copies of the next three tiles are in flight while one computes. The first
-// tiles of a step are requested right after the barrier that publishes u,
-// before the scalar step.
+//   the weights w_x (one column to the left) and w_y (one row above),
+//   v_{j-1}, d_{j-2}, d_{j-3}, x_m of the tile (the direction update), and
+//   the s columns of the local space K on the tile (one 3-D box).
+// One thread issues the tensor copies of a tile (cp.async.bulk.tensor) on the
+// stage's mbarrier while the CTA computes the previous tile, so a tile never
+// waits for a memory round trip of its own: the copies of tile i+1 are in
+// flight during tile i. The first two tiles of a step are requested right
+// after the barrier that publishes u, before the scalar step.
 //
 // Memory ordering between the two proxies: every thread fences its generic
 // global stores (u, v_j, d, x_m) with fence.proxy.async.global before the grid
@@ -63,10 +62,7 @@ struct TapsF {
   float lc[R * R];
 };
 
-// Shared-memory layout (floats, every tensor-copy destination 128-byte aligned):
-// kStages ring stages [u halo | w_x, w_y | v_{j-1}, d_{j-2}, d_{j-3}, x_m], the
-// K buffer (s columns of 32 x 32), and the stencil's work buffer.
-constexpr int kStages = 3;
+// Stage layout (floats, every tensor-copy destination 128-byte aligned).
 template <int R>
 struct StageLayout {
   static constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
@@ -74,12 +70,11 @@ struct StageLayout {
   static constexpr int kU = 0;
   static constexpr int kW = AH * AW;                  // (32 + 4R)^2: a multiple of 64
   static constexpr int kV = kW + 2 * kWPlane;
-  static constexpr int kStage = kV + 4 * kTileH * kTileW;
-  static constexpr int kK = kStages * kStage;         // K buffer
-  __host__ __device__ static constexpr int buf_b(int s) { return kK + s * kTileH * kTileW; }
+  static constexpr int kK = kV + 4 * kTileH * kTileW;
+  __host__ __device__ static constexpr int stage_floats(int s) { return kK + s * kTileH * kTileW; }
   static constexpr int kBufB = AH * BW;               // pass-1 output (and pass 3)
   __host__ __device__ static constexpr size_t smem_bytes(int s) {
-    return (size_t)(buf_b(s) + kBufB) * sizeof(float) + 128;   // + alignment slack
+    return (size_t)(2 * stage_floats(s) + kBufB) * sizeof(float) + 128;   // + alignment slack
   }
 };
 
@@ -140,18 +135,18 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// The tensor copies of tile t's stage (one thread): u with its halo, the two
-// weight planes and, with_v, the four direction-update vectors of step j (not on
-// the first step of a launch, where no direction update is pending).
+// The tensor copies of tile t into stage `st` (one thread). with_v: the four
+// direction-update vectors of step j (not on the first step of a launch, where
+// no direction update is pending).
 template <int R>
-__device__ __forceinline__ void issue_stage(const TmaMaps& maps, float* stage, unsigned long long* bar,
-                                            int t, int tiles_x, int H, int j, bool with_v) {
+__device__ __forceinline__ void issue_tile(const TmaMaps& maps, float* stage, unsigned long long* bar,
+                                           int t, int tiles_x, int H, int j, bool with_v, int s) {
   using L = StageLayout<R>;
   const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
   const int i0 = tyi * kTileH, j0 = txi * kTileW;
   constexpr unsigned kTile = kTileH * kTileW * sizeof(float);
   const unsigned bytes = (unsigned)(L::AH * L::AW * sizeof(float)) + 2u * kWRow * kWRows * sizeof(float) +
-                         (with_v ? 4u * kTile : 0u);
+                         (with_v ? 4u * kTile : 0u) + (unsigned)s * kTile;
   mbar_expect_tx(bar, bytes);
   tma_load_2d(stage + L::kU, &maps.u, j0 - 2 * R, i0 - 2 * R, bar);
   tma_load_2d(stage + L::kW, &maps.w, j0 - 4, i0, bar);                       // w_x rows i0..
@@ -163,14 +158,7 @@ __device__ __forceinline__ void issue_stage(const TmaMaps& maps, float* stage, u
     tma_load_2d(stage + L::kV + 2048, &maps.d[((j - 3) % 3 + 3) % 3], j0, i0, bar);
     tma_load_2d(stage + L::kV + 3072, &maps.xm, j0, i0, bar);
   }
-}
-
-// The s columns of the local space K on tile t into the K buffer (one thread).
-__device__ __forceinline__ void issue_k(const TmaMaps& maps, float* kbuf, unsigned long long* bar, int t,
-                                        int tiles_x, int s) {
-  const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
-  mbar_expect_tx(bar, (unsigned)s * kTileH * kTileW * sizeof(float));
-  tma_load_3d(kbuf, &maps.K, txi * kTileW, tyi * kTileH, 0, bar);
+  if (s > 0) tma_load_3d(stage + L::kK, &maps.K, j0, i0, 0, bar);
 }
 
 // Phase A of one tile from a filled stage: E v and the four blur passes of A v
@@ -370,10 +358,11 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
   __shared__ float red[NWARP][kDots];
   __shared__ double sc[5];
   __shared__ int ok_s;
-  __shared__ __align__(8) unsigned long long mbar[kStages + 1];   // ring stages, then the K buffer
+  __shared__ __align__(8) unsigned long long mbar[2];
   float* base = reinterpret_cast<float*>((reinterpret_cast<unsigned long long>(smem_raw) + 127ull) & ~127ull);
-  float* const kbuf = base + L::kK;
-  float* const bufB = base + L::buf_b(s_alloc);
+  float* const stage0 = base;
+  float* const stage1 = base + L::stage_floats(s_alloc);
+  float* bufB = base + 2 * L::stage_floats(s_alloc);
   const unsigned G = gridDim.x;
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (H + kTileH - 1) / kTileH;
   const int ntiles = tiles_x * tiles_y;
@@ -384,7 +373,8 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
   load_state<NT>(st, ss);
   const float gam = float(__ldcg(p.gamma));
   if (threadIdx.x == 0) {
-    for (int b = 0; b <= kStages; ++b) mbar_init(&mbar[b], 1);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -398,29 +388,17 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
   int j = p.j0;
   // tiles of this CTA: t = blockIdx.x + i G, i = 0 .. mine - 1
   const int mine = ((int)blockIdx.x < ntiles) ? (ntiles - (int)blockIdx.x + (int)G - 1) / (int)G : 0;
-  // Tiles go through the ring in order: the CTA's q-th tile (counted over all
-  // steps) uses stage q % kStages, whose mbarrier completes its phase q / kStages
-  // then; the q-th K copy completes phase q of the K buffer's mbarrier. Every
-  // thread keeps the counts of tiles and K copies consumed (q, kq); thread 0 also
-  // the counts issued (qi, ki), for the bounded drain at exit.
-  unsigned q = 0, kq = 0, qi = 0, ki = 0;
+  unsigned ph0 = 0u, ph1 = 0u;          // completed phases of each stage's mbarrier
+  bool issued0 = false, issued1 = false;   // a copy not yet waited for (thread 0's view)
   // the direction-update vectors are staged for every step with an update due:
   // from the second step of the launch on (and on the first if a previous launch
   // of the same solve left one pending)
   bool withv = ss.dir_pending != 0;
-  auto issue_step_start = [&](int jj, bool wv) {   // thread 0
+  if (threadIdx.x == 0) {
     fence_proxy_async_global();
-    for (int i = 0; i < kStages && i < mine; ++i) {
-      const unsigned sq = qi++;
-      issue_stage<R>(maps, base + (sq % kStages) * L::kStage, &mbar[sq % kStages], (int)blockIdx.x + i * (int)G,
-                     tiles_x, H, jj, wv);
-    }
-    if (mine > 0 && s > 0) {
-      issue_k(maps, kbuf, &mbar[kStages], (int)blockIdx.x, tiles_x, s);
-      ++ki;
-    }
-  };
-  if (threadIdx.x == 0) issue_step_start(j, withv);
+    if (mine > 0) { issue_tile<R>(maps, stage0, &mbar[0], (int)blockIdx.x, tiles_x, H, j, withv, s); issued0 = true; }
+    if (mine > 1) { issue_tile<R>(maps, stage1, &mbar[1], (int)blockIdx.x + (int)G, tiles_x, H, j, withv, s); issued1 = true; }
+  }
   unsigned long long nb = 0;
   bool failed = false;
   for (;;) {
@@ -432,14 +410,16 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
     float* vj = ptr.v(j);
     const float scale = cf.inv_beta_next;
     const float de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau;
-    // ---------------- phase A: tiles from the ring ----------------
-    for (int i = 0; i < mine; ++i, ++q) {
-      const int b = (int)(q % kStages);
+    // ---------------- phase A: tiles from the stages ----------------
+    for (int i = 0; i < mine; ++i) {
+      const int b = i & 1;
       const int t = (int)blockIdx.x + i * (int)G;
       const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
       const int i0 = tyi * kTileH, j0 = txi * kTileW;
-      float* S = base + b * L::kStage;
-      const bool ok = mbar_wait_bounded(&mbar[b], (q / kStages) & 1u);
+      float* S = b ? stage1 : stage0;
+      const bool ok = mbar_wait_bounded(&mbar[b], (b ? ph1 : ph0) & 1u);
+      if (b) ++ph1; else ++ph0;
+      if (threadIdx.x == 0) { if (b) issued1 = false; else issued0 = false; }
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) atomicExch(&bar->err, 3);
         failed = true;
@@ -450,8 +430,8 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
       if (pend) {   // d_{j-1} = (v_{j-1} - delta d_{j-2} - eps d_{j-3}) / gamma, x_m += tau d_{j-1}
         const float* V = S + L::kV;
 #pragma unroll
-        for (int qq = 0; qq < PPT; ++qq) {
-          const int ti = ty * PPT + qq, gi = i0 + ti, pix = ti * kTileW + tx;
+        for (int q = 0; q < PPT; ++q) {
+          const int ti = ty * PPT + q, gi = i0 + ti, pix = ti * kTileW + tx;
           if (gi < H && gj < W) {
             const long g = (long)gi * W + gj;
             const float dv = (V[pix] - de * V[1024 + pix] - ep * V[2048 + pix]) * ig;
@@ -468,47 +448,31 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
         else
           tile_operator<R, NT>(S + L::kU, bufB, S + L::kW, S + L::kW + kWPlane, tf, scale, i0, j0, H, W, ax,
                                ex, vc);
+        const float* Ks = S + L::kK;
 #pragma unroll
-        for (int qq = 0; qq < PPT; ++qq) {
-          const int ti = ty * PPT + qq, gi = i0 + ti;
+        for (int q = 0; q < PPT; ++q) {
+          const int ti = ty * PPT + q, gi = i0 + ti;
           const bool in = gi < H && gj < W;
-          yk[qq] = in ? ax[qq] + gam * ex[qq] : 0.f;
+          yk[q] = in ? ax[q] + gam * ex[q] : 0.f;
           if (in) {
             const long g = (long)gi * W + gj;
-            p.y[g] = yk[qq];
-            vj[g] = vc[qq];
-            acc[kMaxLocal] += vc[qq] * yk[qq];
+            p.y[g] = yk[q];
+            vj[g] = vc[q];
+            acc[kMaxLocal] += vc[q] * yk[q];
           }
         }
-        if (s > 0) {
-          const bool okk = mbar_wait_bounded(&mbar[kStages], kq & 1u);
-          ++kq;
-          if (__syncthreads_or(!okk)) {
-            if (threadIdx.x == 0) atomicExch(&bar->err, 3);
-            failed = true;
-            break;
-          }
 #pragma unroll
-          for (int k = 0; k < kMaxLocal; ++k)
-            if (k < s)
+        for (int k = 0; k < kMaxLocal; ++k)
+          if (k < s)
 #pragma unroll
-              for (int qq = 0; qq < PPT; ++qq) acc[k] += kbuf[k * 1024 + (ty * PPT + qq) * kTileW + tx] * yk[qq];
-        }
+            for (int q = 0; q < PPT; ++q) acc[k] += Ks[k * 1024 + (ty * PPT + q) * kTileW + tx] * yk[q];
       }
-      // the stage and the K buffer are refilled after every generic access to them
-      // is fenced and done
+      // the stage is refilled after every generic access to it is fenced and done
       fence_proxy_async_smem();
       __syncthreads();
-      if (threadIdx.x == 0) {
-        if (!stopped && s > 0 && i + 1 < mine) {
-          issue_k(maps, kbuf, &mbar[kStages], t + (int)G, tiles_x, s);
-          ++ki;
-        }
-        if (i + kStages < mine) {
-          const unsigned sq = qi++;
-          issue_stage<R>(maps, base + (sq % kStages) * L::kStage, &mbar[sq % kStages], t + kStages * (int)G,
-                         tiles_x, H, j, withv);
-        }
+      if (threadIdx.x == 0 && i + 2 < mine) {
+        issue_tile<R>(maps, S, &mbar[b], t + 2 * (int)G, tiles_x, H, j, withv, s);
+        if (b) issued1 = true; else issued0 = true;
       }
     }
     if (failed || stopped) break;
@@ -567,16 +531,23 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
     // u, v_j, d and x_m of this step are read by tensor copies after the barrier
     fence_proxy_async_global();
     if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
-    // the next step's direction update needs v_j, d_{j-1}, d_{j-2}, x_m (j >= 1)
-    if (threadIdx.x == 0) issue_step_start(j + 1, true);
+    if (threadIdx.x == 0) {
+      fence_proxy_async_global();
+      // the next step's direction update needs v_j, d_{j-1}, d_{j-2}, x_m (j >= 1)
+      if (mine > 0) { issue_tile<R>(maps, stage0, &mbar[0], (int)blockIdx.x, tiles_x, H, j + 1, true, s); issued0 = true; }
+      if (mine > 1) {
+        issue_tile<R>(maps, stage1, &mbar[1], (int)blockIdx.x + (int)G, tiles_x, H, j + 1, true, s);
+        issued1 = true;
+      }
+    }
     scalar_step<float, NT>(partB, G, hd, red, ss, cf, sc, p);
     ++j;
     withv = true;
   }
   // no copy may land after the CTA has left: wait (bounded) for any still in flight
   if (threadIdx.x == 0) {
-    for (unsigned sq = q; sq < qi; ++sq) mbar_wait_bounded(&mbar[sq % kStages], (sq / kStages) & 1u);
-    if (ki > kq) mbar_wait_bounded(&mbar[kStages], kq & 1u);
+    if (issued0) mbar_wait_bounded(&mbar[0], ph0 & 1u);
+    if (issued1) mbar_wait_bounded(&mbar[1], ph1 & 1u);
   }
   __syncthreads();
   if (blockIdx.x == 0 && !failed) store_state<NT>(st, ss);
