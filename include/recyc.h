@@ -143,6 +143,12 @@ typedef struct {
                               (Algorithm "Stabilized U"); 40 is its cap */
   int stab_candidates;     /* columns of U~ handed to the last stabilize */
   int stab_kept;           /* of those, kept by its CGS2 (before the singular-value cut) */
+  int tuned_variant;       /* FP32 streaming solves (images with more tiles than co-resident
+                              CTAs): the variant the last one ran, picked by the library's
+                              autotuner on the first solve of each image shape (timed trials
+                              of 24 steps) unless RS_TMA pins it: 2 tensor-copy kernel with A as
+                              two autocorrelation passes, 1 the same with four blur passes, 0
+                              the cp.async streaming kernel; -1 no streaming FP32 solve */
 } rs_info;
 
 /* Per-kernel device time, gathered with CUDA events around every launch of

@@ -7,7 +7,10 @@
 // caller's workspace, and reads back the few integers that decide what to
 // launch next (n_c after stabilize, convergence flags, skip decisions).
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -35,6 +38,7 @@ constexpr int kDotStride = kMaxLocal + 1;
 constexpr int kBatchTail = 2;               // batched solves: the last shifts run one by one
 constexpr int kChunk = 6;                  // MINRES steps per CUDA-graph replay (a multiple of 3)
 constexpr int kStabPanel = 16;             // candidates per panel of the blocked stabilize CGS2
+constexpr int kTuneSteps = 24;             // MINRES steps of one autotuning trial
 
 long round_up(long x, long a) { return (x + a - 1) / a * a; }
 
@@ -319,6 +323,9 @@ struct rs_problem {
   bool use_prefetch = true;  // persistent MINRES kernels stage tiles ahead with cp.async
   int use_tma = 2;           // FP32 streaming solves stage tile operands with tensor copies (2: two-pass A)
   bool stab_panels = true;   // stabilize CGS2 by panels of candidates (column by column when false)
+  bool autotune = true;      // pick the streaming-solve variant by timed trials (off when RS_TMA is set)
+  bool in_tune = false;      // inside a trial
+  int tuned_variant = -1;    // the variant the last streaming solve ran (-1: not tuned)
   double* partials_p = nullptr;
   GridBar* gbar = nullptr;
 
@@ -649,13 +656,107 @@ void graph_timing_flush(rs_problem* P, int gi, int j0, int iters_done, double by
 // local space (Kl, count on the device, may be 0) and optional kept Lanczos
 // vectors (keep, reorth). On exit xm holds V_m y and st->z the coupling part.
 // s_host is the local dimension (for the work accounting of the timing).
+// Launch-configuration autotuner of the FP32 streaming MINRES solve. Where the
+// image has more tiles than co-resident CTAs (so the resident kernel does not
+// apply), three variants can run the solve: the tensor-copy kernel with A as
+// two autocorrelation passes (variant 2) or four blur passes (1), and the
+// cp.async streaming kernel (0). The first solve of a (device, image, radius,
+// local dimension) runs a trial of kTuneSteps steps of each variant on its own
+// right-hand side (twice; the second round is timed with CUDA events), and the
+// fastest is kept for every later solve of that shape in the process. Trials
+// change no result: each solve starts from its right-hand side, and their
+// operator applications and timing records are not counted.
+struct TuneCache {
+  std::mutex mu;
+  std::map<std::array<int, 5>, int> best;
+};
+TuneCache& tune_cache() {
+  static TuneCache c;
+  return c;
+}
+
 template <typename T>
 int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_abs, int maxit,
                int keep, bool reorth, int* iters_out, double* eta_out, int* breakdown_out,
-               int s_host = 0, int cg = 0, int min_iters = 0) {
+               int s_host = 0, int cg = 0, int min_iters = 0);
+
+template <typename T>
+int tuned_variant(rs_problem* P, double gamma, const T* r, bool use_K, int s_host, int cg, int* variant) {
+  *variant = P->use_tma;
+  if constexpr (sizeof(T) != 4) return RS_OK;
+  if (!P->autotune || P->in_tune || P->stream_ctas > 0 || !P->use_persist || (P->d.width % 4) != 0 ||
+      P->tp.radon.nang > 0)
+    return RS_OK;
+  const int s_alloc = use_K ? std::max(s_host, 1) : 1;
+  if (mr_resident_applies<T>(P->d.height, P->d.width, P->tp.r, s_alloc)) return RS_OK;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  const std::array<int, 5> key{dev, P->d.height, P->d.width, P->tp.r, s_alloc};
+  {
+    std::lock_guard<std::mutex> lock(tune_cache().mu);
+    auto it = tune_cache().best.find(key);
+    if (it != tune_cache().best.end()) {
+      *variant = it->second;
+      return RS_OK;
+    }
+  }
+  P->in_tune = true;
+  const bool timing_was = P->timing;
+  P->timing = false;
+  const long long mv0 = P->mv_total;
+  const int saved = P->use_tma;
+  const int cands[3] = {2, 1, 0};
+  float best_ms = 0.f;
+  int best = saved;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = RS_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = RS_ECUDA;
+  for (int round = 0; round < 2 && rc == RS_OK; ++round) {
+    for (int v : cands) {
+      P->use_tma = v;
+      int it = 0, bd = 0;
+      double eta = 0.0;
+      cudaEventRecord(e0, P->s);
+      rc = run_minres<T>(P, gamma, r, use_K, 0.0, kTuneSteps, 0, false, &it, &eta, &bd, s_host, cg, 0);
+      if (rc != RS_OK) break;
+      cudaEventRecord(e1, P->s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = RS_ECUDA;
+        break;
+      }
+      if (round == 1 && (best_ms == 0.f || ms < best_ms)) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  P->use_tma = saved;
+  P->mv_total = mv0;
+  P->timing = timing_was;
+  P->in_tune = false;
+  if (rc != RS_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lock(tune_cache().mu);
+    tune_cache().best[key] = best;
+  }
+  *variant = best;
+  return RS_OK;
+}
+
+template <typename T>
+int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_abs, int maxit,
+               int keep, bool reorth, int* iters_out, double* eta_out, int* breakdown_out,
+               int s_host, int cg, int min_iters) {
   const Dims& z = P->z;
   const long n = z.n, ld = z.ld;
   cudaStream_t s = P->s;
+  // the streaming variant (autotuned on the first solve of this shape) before
+  // anything of this solve is queued: the trials reuse the solve's buffers
+  int variant = P->use_tma;
+  if (P->use_persist && keep == 0 && !reorth) RS(tuned_variant<T>(P, gamma, r, use_K, s_host, cg, &variant));
   T* Kl = vp<T>(P->Kl);
   const int* cntK = P->cnt;   // local count lives in cnt[0] (CGS context)
   T* u = vp<T>(P->u);
@@ -778,7 +879,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     mp.rec_cap = keep;
     mp.j0 = n_unfused + 1;
     mp.prefetch = P->use_prefetch ? 1 : 0;
-    mp.tma = P->use_tma;
+    mp.tma = variant;
     CU(cudaMemsetAsync(P->gbar, 0, sizeof(GridBar), s));
     const int slot = timed_begin(P);
     int G = 0, resident = 0;
@@ -786,6 +887,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
                                          use_K ? std::max(s_host, 1) : 1, s, &G, &resident,
                                          P->stream_ctas);
     P->last_resident = resident;
+    if (!P->in_tune) P->tuned_variant = resident == 2 || resident == 0 ? variant : -1;
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
       // not co-resident on this device: the step kernels below take over
       (void)cudaGetLastError();
@@ -2042,7 +2144,9 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   // tile operands are staged by tensor copies (mrtma.cu); that kernel applies A as two
   // autocorrelation passes (RS_TMA=2, the default: measured 150 against 157 us per step
   // on the 2048 x 2048 workload) or, RS_TMA=1, as four blur passes
+  if (const char* g = std::getenv("RS_AUTOTUNE")) P->autotune = std::strcmp(g, "0") != 0;
   if (const char* g = std::getenv("RS_TMA")) {
+    P->autotune = false;   // a pinned variant
     if (std::strcmp(g, "0") == 0) P->use_tma = 0;
     else if (std::strcmp(g, "2") == 0) P->use_tma = 2;
     else P->use_tma = 1;
@@ -2452,6 +2556,7 @@ rs_status rs_get_info(const rs_problem* P, rs_info* info) {
   info->ld = (int)P->z.ld;
   info->kernel_launches = launch_count();
   info->minres_kernel = P->last_resident;
+  info->tuned_variant = P->tuned_variant;
   info->stab_sweeps = P->stab_sweeps;
   info->stab_candidates = P->ncand_stab;
   info->stab_kept = P->nk_stab;

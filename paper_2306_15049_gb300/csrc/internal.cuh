@@ -423,6 +423,9 @@ cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Tap
                        int s_alloc, cudaStream_t s, int* launched_blocks, int* resident,
                        int max_ctas = 0);
 bool mr_persist_supported(int radius);
+// Whether mr_persist would run the one-CTA-per-tile kernel (every tile co-resident).
+template <typename T>
+bool mr_resident_applies(int H, int W, int radius, int s_alloc);
 
 // ---------------------------------------------------------------- mrtma.cu
 // The streaming solve with every tile operand staged by tensor copies (FP32,

@@ -441,6 +441,33 @@ cudaError_t mr_persist(MinresState* st, const MrP<T>& p, int H, int W, const Tap
   }
 }
 
+template <typename T, int R>
+bool resident_fits(int H, int W, int s_alloc) {
+  const int ntiles = mr_matvec_blocks(H, W);
+  const int sa = s_alloc < 1 ? 1 : s_alloc;
+  const size_t smem = ((size_t)op_tile_smem_elems(R) + (size_t)sa * kTileH * kTileW) * sizeof(T);
+  if (smem > 227 * 1024 || ntiles > kPersistMaxBlocks) return false;
+  static int cached = 0;
+  static Occ occ;
+  if (ensure_smem(k_mr_resident<T, R>, smem, &cached) != cudaSuccess) return false;
+  if (occupancy(k_mr_resident<T, R>, smem, &occ) != cudaSuccess) return false;
+  return ntiles <= occ.per_sm * occ.sms;
+}
+
+template <typename T>
+bool mr_resident_applies(int H, int W, int radius, int s_alloc) {
+  switch (radius) {
+    case 4: return resident_fits<T, 4>(H, W, s_alloc);
+    case 6: return resident_fits<T, 6>(H, W, s_alloc);
+    case 8: return resident_fits<T, 8>(H, W, s_alloc);
+    case 10: return resident_fits<T, 10>(H, W, s_alloc);
+    case 12: return resident_fits<T, 12>(H, W, s_alloc);
+    default: return false;
+  }
+}
+template bool mr_resident_applies<float>(int, int, int, int);
+template bool mr_resident_applies<double>(int, int, int, int);
+
 bool mr_persist_supported(int radius) {
   return radius == 4 || radius == 6 || radius == 8 || radius == 10 || radius == 12;
 }

@@ -53,6 +53,7 @@ class rs_info(ctypes.Structure):
         ("matvecs_total", ctypes.c_longlong), ("matvecs_overhead", ctypes.c_longlong),
         ("ld", ctypes.c_int), ("kernel_launches", ctypes.c_longlong), ("minres_kernel", ctypes.c_int),
         ("stab_sweeps", ctypes.c_int), ("stab_candidates", ctypes.c_int), ("stab_kept", ctypes.c_int),
+        ("tuned_variant", ctypes.c_int),
     ]
 
 
