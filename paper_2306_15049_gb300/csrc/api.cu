@@ -257,6 +257,7 @@ struct rs_problem {
   double *coef = nullptr, *scal = nullptr, *Ktr = nullptr, *Rk = nullptr, *zc = nullptr;
   double *arec = nullptr, *brec = nullptr, *lc = nullptr;
   double *nbin = nullptr, *cblk = nullptr;   // stabilize by panels: candidate norms, panel coefficients
+  float *Qh = nullptr, *Ql = nullptr;        // stabilize by panels: the kept columns split into two floats
   // oblique guesses with two anchors (Eq. updates): per anchor R_a, K_a^T E U_a, K_a^T b
   void* Kan = nullptr;
   // batched solves (batched_local = 1): every shift's local space, MINRES vectors
@@ -413,6 +414,8 @@ void carve(rs_problem* P, Carver& cv) {
   P->Rfull = cv.take<double>((size_t)z.cmax * z.cmax);
   P->nbin = cv.take<double>((size_t)z.cmax);
   P->cblk = cv.take<double>((size_t)3 * z.cmax * kStabPanel);
+  P->Qh = cv.take<float>((size_t)z.cmax * z.ld);
+  P->Ql = cv.take<float>((size_t)z.cmax * z.ld);
   P->XT = cv.take<double>((size_t)z.cmax * z.cmax);
   P->Vsv = cv.take<double>((size_t)z.cmax * z.cmax);
   P->sig = cv.take<double>(z.cmax);
@@ -1054,10 +1057,10 @@ int stabilize_cgs2_panels(rs_problem* P, int ncand, int* nk, bool* used) {
     if (s0 > 0 && s0 <= kThreads) {
       // the products in two-float arithmetic (about 2^-46 relative, far below the
       // 1e-10 singular-value threshold, at FP32 rates); the panel itself stays FP64
-      CU(gram_d2f(U, ld, s0, Pn, ld, b, n, P->partials, C1, s));
-      CU(gemm_sub_d2f(U, ld, s0, C1, s0, b, Pn, ld, n, s));
-      CU(gram_d2f(U, ld, s0, Pn, ld, b, n, P->partials, C2, s));
-      CU(gemm_sub_d2f(U, ld, s0, C2, s0, b, Pn, ld, n, s));
+      CU(gram_d2f(P->Qh, P->Ql, ld, s0, Pn, ld, b, n, P->partials, C1, s));
+      CU(gemm_sub_d2f(P->Qh, P->Ql, ld, s0, C1, s0, b, Pn, ld, n, s));
+      CU(gram_d2f(P->Qh, P->Ql, ld, s0, Pn, ld, b, n, P->partials, C2, s));
+      CU(gemm_sub_d2f(P->Qh, P->Ql, ld, s0, C2, s0, b, Pn, ld, n, s));
       k_panel_rows<<<8, 256, 0, s>>>(C1, C2, s0, b, P->nbin + j0, P->Rfull, z.cmax, j0);
       CU(launched());
     } else if (s0 > 0) {
@@ -1085,6 +1088,8 @@ int stabilize_cgs2_panels(rs_problem* P, int ncand, int* nk, bool* used) {
     RS(coop_check(P));
     int kp = 0;
     RS(read_back(P, &kp, P->cnt, sizeof kp));
+    // the panel's kept columns, split once for the later panels' products
+    CU(split_d2f_cols(U + (long)s0 * ld, ld, kp, n, P->Qh + (long)s0 * ld, P->Ql + (long)s0 * ld, s));
     s0 += kp;
   }
   // the kept count where the caller and the column path expect it

@@ -365,12 +365,13 @@ __device__ __forceinline__ void d2f_madd(float xh, float xl, float yh, float yl,
   lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(d, e), c));
 }
 
-// partials[blockIdx.x * nx * ny + i + j nx] = CTA's share of (X^T Y)[i, j] for FP64
-// X (nx columns) and Y (ny <= kD2fCols columns): thread i of the CTA owns output
-// row i (nx <= kThreads) and all ny columns.
+// partials[blockIdx.x * nx * ny + i + j nx] = CTA's share of (X^T Y)[i, j] for X
+// given as its two-float split (Xh, Xl: nx columns of floats, x = h + l) and FP64
+// Y (ny <= kD2fCols columns): thread i of the CTA owns output row i (nx <=
+// kThreads) and all ny columns.
 __global__ void __launch_bounds__(kThreads)
-k_gram_d2f(const double* __restrict__ X, long ldx, int nx, const double* __restrict__ Y, long ldy, int ny,
-           long n, long rows_per_cta, double* partials) {
+k_gram_d2f(const float* __restrict__ XH, const float* __restrict__ XL, long ldx, int nx,
+           const double* __restrict__ Y, long ldy, int ny, long n, long rows_per_cta, double* partials) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Xh = reinterpret_cast<float*>(smem_raw);         // kD2fRows x nx
   float* Xl = Xh + kD2fRows * nx;
@@ -386,10 +387,9 @@ k_gram_d2f(const double* __restrict__ X, long ldx, int nx, const double* __restr
     for (int idx = threadIdx.x; idx < kD2fRows * nx; idx += kThreads) {
       const int k = idx / kD2fRows, rr = idx - k * kD2fRows;
       const long row = rb + rr;
-      float h = 0.f, l = 0.f;
-      if (row < r1) split_d2f(X[(long)k * ldx + row], h, l);
-      Xh[rr * nx + k] = h;
-      Xl[rr * nx + k] = l;
+      const bool in = row < r1;
+      Xh[rr * nx + k] = in ? XH[(long)k * ldx + row] : 0.f;
+      Xl[rr * nx + k] = in ? XL[(long)k * ldx + row] : 0.f;
     }
     for (int idx = threadIdx.x; idx < kD2fRows * kD2fCols; idx += kThreads) {
       const int k = idx / kD2fRows, rr = idx - k * kD2fRows;
@@ -430,11 +430,12 @@ k_gram_d2f(const double* __restrict__ X, long ldx, int nx, const double* __restr
   }
 }
 
-// Y[:, j] -= X C[:, j] (j < ny <= kD2fCols) for FP64 X (nx columns), Y and C, the
-// products summed in two-float arithmetic and subtracted in FP64.
+// Y[:, j] -= X C[:, j] (j < ny <= kD2fCols) for X given as its two-float split
+// (nx columns) and FP64 Y and C, the products summed in two-float arithmetic
+// and subtracted in FP64.
 __global__ void __launch_bounds__(kThreads)
-k_gemm_sub_d2f(const double* __restrict__ X, long ldx, int nx, const double* __restrict__ C, int ldc, int ny,
-               double* __restrict__ Y, long ldy, long n) {
+k_gemm_sub_d2f(const float* __restrict__ XH, const float* __restrict__ XL, long ldx, int nx,
+               const double* __restrict__ C, int ldc, int ny, double* __restrict__ Y, long ldy, long n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Ch = reinterpret_cast<float*>(smem_raw);   // nx x kD2fCols
   float* Cl = Ch + nx * kD2fCols;
@@ -451,8 +452,7 @@ k_gemm_sub_d2f(const double* __restrict__ X, long ldx, int nx, const double* __r
 #pragma unroll
     for (int j = 0; j < kD2fCols; ++j) hi[j] = lo[j] = 0.f;
     for (int k = 0; k < nx; ++k) {
-      float xh, xl;
-      split_d2f(X[(long)k * ldx + i], xh, xl);
+      const float xh = XH[(long)k * ldx + i], xl = XL[(long)k * ldx + i];
       const float4* ch4 = reinterpret_cast<const float4*>(Ch + k * kD2fCols);
       const float4* cl4 = reinterpret_cast<const float4*>(Cl + k * kD2fCols);
 #pragma unroll
@@ -467,6 +467,19 @@ k_gemm_sub_d2f(const double* __restrict__ X, long ldx, int nx, const double* __r
 #pragma unroll
     for (int j = 0; j < kD2fCols; ++j)
       if (j < ny) Y[(long)j * ldy + i] -= (double)hi[j] + (double)lo[j];
+  }
+}
+
+// H[:, k] + L[:, k] = X[:, k] to two-float precision, k < ncols
+__global__ void k_split_d2f(const double* __restrict__ X, long ldx, int ncols, long n, float* __restrict__ H,
+                            float* __restrict__ L) {
+  const long total = (long)ncols * n;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const long k = idx / n, i = idx - k * n;
+    float h, l;
+    split_d2f(X[k * ldx + i], h, l);
+    H[k * ldx + i] = h;
+    L[k * ldx + i] = l;
   }
 }
 
@@ -635,8 +648,8 @@ cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, lon
   return cudaSuccess;
 }
 
-cudaError_t gram_d2f(const double* X, long ldx, int nx, const double* Y, long ldy, int ny, long n,
-                     double* partials, double* out, cudaStream_t s) {
+cudaError_t gram_d2f(const float* XH, const float* XL, long ldx, int nx, const double* Y, long ldy, int ny,
+                     long n, double* partials, double* out, cudaStream_t s) {
   if (nx <= 0 || ny <= 0) return cudaSuccess;
   if (nx > kThreads || ny > kD2fCols) return cudaErrorInvalidValue;
   const int G = 152;
@@ -647,13 +660,13 @@ cudaError_t gram_d2f(const double* X, long ldx, int nx, const double* Y, long ld
     RK_TRY(cudaFuncSetAttribute(k_gram_d2f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
-  k_gram_d2f<<<G, kThreads, smem, s>>>(X, ldx, nx, Y, ldy, ny, n, rows, partials);
+  k_gram_d2f<<<G, kThreads, smem, s>>>(XH, XL, ldx, nx, Y, ldy, ny, n, rows, partials);
   RK_TRY(launched());
   return reduce_partials(partials, G, nx * ny, nx * ny, out, s, nullptr, 0, nullptr);
 }
 
-cudaError_t gemm_sub_d2f(const double* X, long ldx, int nx, const double* C, int ldc, int ny, double* Y,
-                         long ldy, long n, cudaStream_t s) {
+cudaError_t gemm_sub_d2f(const float* XH, const float* XL, long ldx, int nx, const double* C, int ldc, int ny,
+                         double* Y, long ldy, long n, cudaStream_t s) {
   if (nx <= 0 || ny <= 0) return cudaSuccess;
   if (ny > kD2fCols) return cudaErrorInvalidValue;
   const size_t smem = (size_t)2 * nx * kD2fCols * sizeof(float);
@@ -663,7 +676,13 @@ cudaError_t gemm_sub_d2f(const double* X, long ldx, int nx, const double* C, int
     RK_TRY(cudaFuncSetAttribute(k_gemm_sub_d2f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
-  k_gemm_sub_d2f<<<ew_grid(n), kThreads, smem, s>>>(X, ldx, nx, C, ldc, ny, Y, ldy, n);
+  k_gemm_sub_d2f<<<ew_grid(n), kThreads, smem, s>>>(XH, XL, ldx, nx, C, ldc, ny, Y, ldy, n);
+  return launched();
+}
+
+cudaError_t split_d2f_cols(const double* X, long ldx, int ncols, long n, float* H, float* L, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  k_split_d2f<<<ew_grid((long)ncols * n), kThreads, 0, s>>>(X, ldx, ncols, n, H, L);
   return launched();
 }
 

@@ -145,12 +145,15 @@ template <typename T>
 cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,
                  double* partials, double* out, cudaStream_t s);
 // The same two products for FP64 data at about 2^-46 relative accuracy in
-// two-float arithmetic (FP32 rates): out (nx x ny, column-major) = X^T Y with
-// nx <= 256, ny <= 16 (partials: 152 nx ny doubles); Y[:, j] -= X C[:, j], ny <= 16.
-cudaError_t gram_d2f(const double* X, long ldx, int nx, const double* Y, long ldy, int ny, long n,
-                     double* partials, double* out, cudaStream_t s);
-cudaError_t gemm_sub_d2f(const double* X, long ldx, int nx, const double* C, int ldc, int ny, double* Y,
-                         long ldy, long n, cudaStream_t s);
+// two-float arithmetic (FP32 rates), X given as its split (XH + XL, floats,
+// leading dimension ldx; split_d2f_cols makes it): out (nx x ny, column-major) =
+// X^T Y with nx <= 256, ny <= 16 (partials: 152 nx ny doubles); Y[:, j] -= X C[:, j],
+// ny <= 16.
+cudaError_t gram_d2f(const float* XH, const float* XL, long ldx, int nx, const double* Y, long ldy, int ny,
+                     long n, double* partials, double* out, cudaStream_t s);
+cudaError_t gemm_sub_d2f(const float* XH, const float* XL, long ldx, int nx, const double* C, int ldc, int ny,
+                         double* Y, long ldy, long n, cudaStream_t s);
+cudaError_t split_d2f_cols(const double* X, long ldx, int ncols, long n, float* H, float* L, cudaStream_t s);
 // y = a*x + b*y (host scalars).
 template <typename TX, typename TY>
 cudaError_t axpby(const TX* x, double a, TY* y, double b, long n, cudaStream_t s);
