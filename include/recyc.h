@@ -272,7 +272,12 @@ size_t rs_batch_scratch_bytes(int count, int total_shifts);
  * finish; the last two continue one at a time), then each problem's solutions,
  * refinement sweeps (RS_MIXED) and hand-over to its next step are as in
  * rs_solve_shifts. X_dev[i]: problem i's M x n solutions; stats_host[i] may be
- * NULL (or stats_host itself). Errors: rs_last_error(NULL). */
+ * NULL (or stats_host itself). The joint launch is what this call measures
+ * against one batched launch per problem (rs_solve_shifts on each): the first
+ * call for a batch shape (the problems' sizes, radii, shift counts, precision)
+ * times the joint launch, the second the per-problem launches, and later calls
+ * of that shape in the process take the faster (RS_BATCH_JOINT=1 or 0 pins the
+ * choice). Errors: rs_last_error(NULL). */
 rs_status rs_solve_shifts_batched(rs_problem* const* probs, int count, double* const* X_dev,
                                   rs_solve_stats* const* stats_host, void* scratch_dev,
                                   size_t scratch_bytes);

@@ -33,7 +33,7 @@ constexpr double kStabDrop = 1e-12;        // numerically dependent candidate (C
 constexpr double kLocalDrop = 1e-10;       // local column drop rule
 constexpr double kAngleCos = 0.99;         // footnote of Section 5.3
 constexpr int kMaxSweeps = 12;             // FP64 refinement sweeps (mixed precision)
-constexpr double kInnerRho = 1e-4;         // inner relative reduction per sweep (mixed)
+constexpr double kInnerRho = 1e-2;         // inner relative reduction per sweep (mixed)
 constexpr int kDotStride = kMaxLocal + 1;
 constexpr int kBatchTail = 2;               // batched solves: the last shifts run one by one
 constexpr int kChunk = 6;                  // MINRES steps per CUDA-graph replay (a multiple of 3)
@@ -2320,6 +2320,65 @@ rs_status rs_solve_shifts_batched(rs_problem* const* probs, int count, double* c
   }
   const int cap = mr_batch_capacity(R, probs[0]->mixed ? 4 : 8);
   if (cap < total) return bad("more shifts than co-resident CTAs of the batched kernel");
+  // One launch for every shift of every problem, or one batched launch per
+  // problem: pinned by RS_BATCH_JOINT (1 / 0), else the faster for this batch shape
+  // (the problems' sizes, radii, shift counts, precision) -- the first call of a
+  // shape runs and times the joint launch, the second the per-problem launches
+  // (CUDA events on the common stream), later calls the faster of the two.
+  static std::mutex tune_mu;
+  static std::map<std::vector<int>, std::array<float, 2>> tune_ms;   // [joint, per problem], < 0 unknown
+  std::vector<int> key;
+  for (int i = 0; i < count; ++i)
+    key.insert(key.end(), {probs[i]->d.height, probs[i]->d.width, probs[i]->d.radius, probs[i]->z.M,
+                           probs[i]->mixed ? 1 : 0});
+  int joint = -1;
+  bool record = false;
+  if (const char* g = std::getenv("RS_BATCH_JOINT")) joint = std::strcmp(g, "0") != 0 ? 1 : 0;
+  if (joint < 0) {
+    std::lock_guard<std::mutex> lock(tune_mu);
+    auto it = tune_ms.find(key);
+    if (it == tune_ms.end()) it = tune_ms.emplace(key, std::array<float, 2>{-1.f, -1.f}).first;
+    const auto& t = it->second;
+    if (t[0] < 0.f) { joint = 1; record = true; }
+    else if (t[1] < 0.f) { joint = 0; record = true; }
+    else joint = t[0] <= t[1] ? 1 : 0;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (record && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+                 cudaEventRecord(e0, probs[0]->s) != cudaSuccess)) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    e0 = e1 = nullptr;
+    record = false;
+  }
+  auto finish_timing = [&](int rc_in) {
+    if (record) {
+      float ms = -1.f;
+      if (rc_in == RS_OK && cudaEventRecord(e1, probs[0]->s) == cudaSuccess &&
+          cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(tune_mu);
+        tune_ms[key][joint ? 0 : 1] = ms;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    return (rs_status)rc_in;
+  };
+  if (!joint) {
+    int rc = RS_OK;
+    for (int i = 0; i < count; ++i) {
+      const rs_status st = rs_solve_shifts(probs[i], 0, probs[i]->z.M, X_dev[i],
+                                           stats_host ? stats_host[i] : nullptr, nullptr);
+      if (st == RS_ENOCONV) {
+        rc = RS_ENOCONV;
+      } else if (st != RS_OK) {
+        set_null_error(probs[i]->err.c_str());
+        return finish_timing(st);
+      }
+    }
+    if (rc == RS_ENOCONV) set_null_error("a shift reached maxit");
+    return finish_timing(rc);
+  }
   Carver cv{(char*)scratch_dev};
   BatchScratch sc{};
   sc.sys = cv.take<MrBatchSys<double>>((size_t)total);
@@ -2343,7 +2402,7 @@ rs_status rs_solve_shifts_batched(rs_problem* const* probs, int count, double* c
     for (int i = 0; i < count; ++i)
       if (probs[i]->err != "no error") { set_null_error(probs[i]->err.c_str()); break; }
   }
-  return (rs_status)rc;
+  return finish_timing(rc);
 }
 
 rs_status rs_solve_plain(rs_problem* P, double* X_dev, rs_solve_stats* stats_host) {

@@ -91,7 +91,8 @@ def test_batched_launch_agrees_with_shift_by_shift_solves_at_512():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_several_images_of_uneven_size_in_one_launch(precision):
+def test_several_images_of_uneven_size_in_one_launch(precision, monkeypatch):
+    monkeypatch.setenv("RS_BATCH_JOINT", "1")       # the joint kernel, not the per-problem choice
     """Three images of different sizes, blurs and shift counts: two outer steps
     solved jointly (rs_solve_shifts_batched: all their shifts in one persistent
     launch) against each image solved on its own, and against the oracle."""
@@ -141,3 +142,24 @@ def test_joint_solve_rejects_mismatched_problems():
         recyc.rs_solve_shifts_batched([a.P, b.P], X)
     with pytest.raises(recyc.RecycError):
         recyc.rs_solve_shifts_batched([a.P, a.P], [X[0], X[0]])
+
+
+def test_joint_call_picks_the_faster_way_and_solves_every_shift():
+    """Without RS_BATCH_JOINT the call times the joint launch on its first call
+    for a batch shape and the per-problem launches on its second, then keeps the
+    faster; every call solves every shift to its tolerance."""
+    from paper_2306_15049_gb300 import recyc
+    specs = [(96, 80, 1.5, 4, 4), (64, 64, 2.5, 8, 5)]
+    wls = [synth.tiny(h, w, sigma=sg, radius=r, M=M, p=6, n_ritz_local=2, seed=95 + i, tol=1e-9)
+           for i, (h, w, sg, r, M) in enumerate(specs)]
+    prs = [_pair(wl, 1, True) for wl in wls]
+    for call in range(3):
+        Xs = []
+        for pr in prs:
+            pr.P.rs_set_weights(pr.t(np.ones(2 * pr.wl.n)))
+            pr.P.rs_update_recycle(0)
+            Xs.append(pr.torch.empty(pr.wl.M, pr.wl.n, dtype=pr.torch.float64, device=pr.dev))
+        stats = recyc.rs_solve_shifts_batched([pr.P for pr in prs], Xs)
+        for st, pr in zip(stats, prs):
+            assert len(st) == pr.wl.M
+            assert all(s_["relres_true"] <= pr.wl.tol * (1 + 1e-6) for s_ in st), (call, st)
