@@ -53,7 +53,11 @@ CSRC = os.path.join(ROOT, "paper_2306_15049_gb300", "csrc")
 # basis, 24 steps each: about 1.3 GB on the device); scaled to a launch of the timed
 # workload by its algorithmic bytes. `src` is the SHA-256 (first 16 hex digits) of the
 # kernel's sources at the capture: a kernel changed since reports traffic null.
-TRAFFIC = {}
+TRAFFIC = {
+    # 2048 x 2048, radius 12, mixed, two-pass stencil (RS_TMA=2): two 24-step launches read
+    # 10.70 + 11.53 GB and wrote 2.14 + 2.13 GB against 12.48 + 13.29 GB algorithmic (s = 8, 9)
+    "k_mr_tma<float,12>": {"dram_per_alg": 1.029, "src": "9235b07c48c97149"},
+}
 
 OUTER_KEYS = ("init_solves", "update_vnew", "principal_setup", "shift_setup", "shift_minres",
               "fp64_residuals")
