@@ -327,7 +327,7 @@ def local_columns(g_old: Optional[np.ndarray], g_new: Optional[np.ndarray],
 def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
                S: State, prm: Params, Ut_given: Optional[np.ndarray] = None,
                iters_override: Optional[List[int]] = None,
-               record_local: bool = False) -> StepResult:
+               record_local: bool = False, shifts: Optional[List[int]] = None) -> StepResult:
     """Solve all M shifted systems for the weights ``w`` (step k = S.k + 1).
 
     ``Ut_given`` replaces the principal-space construction (the basis is still
@@ -335,8 +335,12 @@ def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
     (tolerance ignored) for parity checks of iterates. With ``record_local``
     the local basis U~_l of every shift (after drops; None where the initial
     guess already met the tolerance) is returned in ``extra["local_cols"]``,
-    and the raw principal basis (before stabilize) in ``extra["Ut_raw"]``.
+    and the raw principal basis (before stabilize) in ``extra["Ut_raw"]``. With
+    ``shifts`` (0-based, batched local spaces only: their shifts are independent)
+    only those shifts are solved; the others are left at zero.
     """
+    if shifts is not None and not prm.batched_local:
+        raise ValueError("a subset of shifts needs batched local spaces")
     k = S.k + 1
     n = b.shape[0]
     M_ = len(gammas)
@@ -381,6 +385,8 @@ def outer_step(op: Operator, b: np.ndarray, gammas: np.ndarray, w: np.ndarray,
     local_dim = np.zeros(M_, dtype=int)
 
     for l in range(M_):
+        if shifts is not None and l not in shifts:
+            continue
         gl = gammas[l]
         apply_l = (lambda v, gl=gl: op.apply(v, gl, w))
         x0, r0 = X0[l], R0[l]
