@@ -54,9 +54,6 @@ CSRC = os.path.join(ROOT, "paper_2306_15049_gb300", "csrc")
 # workload by its algorithmic bytes. `src` is the SHA-256 (first 16 hex digits) of the
 # kernel's sources at the capture: a kernel changed since reports traffic null.
 TRAFFIC = {
-    # 2048 x 2048, radius 12, mixed, two-pass stencil (RS_TMA=2): two 24-step launches read
-    # 10.70 + 11.53 GB and wrote 2.14 + 2.13 GB against 12.48 + 13.29 GB algorithmic (s = 8, 9)
-    "k_mr_tma<float,12>": {"dram_per_alg": 1.029, "src": "9235b07c48c97149"},
 }
 
 OUTER_KEYS = ("init_solves", "update_vnew", "principal_setup", "shift_setup", "shift_minres",
@@ -101,7 +98,7 @@ def workload_config(wl, precision):
 
 def kernel_src_sha():
     h = hashlib.sha256()
-    for f in ("mrtma.cu", "mrpersist.cu", "mrcommon.cuh", "optile.cuh", "gridsync.cuh"):
+    for f in ("mrtma.cu", "mrtmaok.cu", "tma.cuh", "mrpersist.cu", "mrcommon.cuh", "optile.cuh", "gridsync.cuh"):
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -492,7 +489,8 @@ def roofline_entry(job, ms_total, minres_kernel, wl, precision, fp64_peak):
     cat = 0 if tm["ms"][0] >= tm["ms"][1] else 1
     launches = max(1, tm["launches"][cat])
     tname = "float" if precision == "mixed" else "double"
-    names = {3: f"k_mr_batch<{tname},{wl.radius}>", 2: f"k_mr_tma<{tname},{wl.radius}>",
+    names = {4: f"k_mr_tmaok<{tname},{wl.radius}>", 3: f"k_mr_batch<{tname},{wl.radius}>",
+             2: f"k_mr_tma<{tname},{wl.radius}>",
              1: f"k_mr_resident<{tname},{wl.radius}>", 0: f"k_mr_persist<{tname},{wl.radius}>"}
     kname = names.get(minres_kernel, f"k_mr_matvec<{tname}>") if cat == 0 else \
         "k_op_apply<double> (FP64 true / refinement residual matvec)"
@@ -517,7 +515,8 @@ def roofline_entry(job, ms_total, minres_kernel, wl, precision, fp64_peak):
                       "peak_source": f"{peak_kind} hbm_gbs",
                       "algorithmic_bytes_per_launch": bytes_per_launch,
                       "us_per_minres_step": tm["ms"][cat] * 1000.0 / max(1.0, steps),
-                      "bytes_per_step": "(15 + 2 s) n 4 (s = local dimension)"})
+                      "bytes_per_step": "(12 + 2 s) n 4 (one recycled-MINRES iteration, s = local "
+                                        "dimension: K_l read twice, 12 vectors of n floats)"})
     elif cat == 0 and minres_kernel == 1:
         # vectors of one solve fit in L2: bound by the grid barriers, reported per step
         entry.update({"bound": "latency", "us_per_minres_step": tm["ms"][cat] * 1000.0 / max(1.0, steps),

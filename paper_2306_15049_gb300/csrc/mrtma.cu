@@ -28,19 +28,11 @@
 // (fence.proxy.async.shared::cta) before the CTA barrier after which the stage
 // is refilled. Every mbarrier wait is bounded in time: on a timeout the launch
 // raises an error flag and returns (the host reports the failure).
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include "mrcommon.cuh"
+#include "tma.cuh"
 
 namespace rk {
 
 namespace {
-
-constexpr unsigned long long kTmaTimeoutNs = 2000000000ull;   // 2 s, far beyond one tile
-constexpr int kWRow = 36;                  // staged weight rows: 4 columns left + 32
-constexpr int kWRows = 33;                 // 32 rows + 1 (w_x: one below; w_y: one above)
-constexpr int kWPlane = 1216;              // floats per staged weight plane (128-byte multiple)
 
 struct TmaMaps {
   CUtensorMap u;       // {W, H}, box {32 + 4R, 32 + 4R}
@@ -49,17 +41,6 @@ struct TmaMaps {
   CUtensorMap d[3];    // direction ring buffers, box {32, 32}
   CUtensorMap xm;      // box {32, 32}
   CUtensorMap K;       // {W, H, s} with stride ldk between columns, box {32, 32, s}
-};
-
-// Taps of the kernel (a kernel parameter, so that loops with compile-time
-// indices read them as constant-bank operands): g (2R + 1) for the four blur
-// passes; for the two-pass form of A = H^T H the autocorrelation c2 = g * g
-// (4R + 1) and the r x r edge corrections lc (see Taps in internal.cuh).
-template <int R>
-struct TapsF {
-  float g[2 * R + 1];
-  float c2[4 * R + 1];
-  float lc[R * R];
 };
 
 // Stage layout (floats, every tensor-copy destination 128-byte aligned).
@@ -77,63 +58,6 @@ struct StageLayout {
     return (size_t)(2 * stage_floats(s) + kBufB) * sizeof(float) + 128;   // + alignment slack
   }
 };
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for phase `parity` of the mbarrier to complete; false after kTmaTimeoutNs.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (unsigned spin = 1;; ++spin) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((spin & 255u) == 0 && global_ns() - t0 > kTmaTimeoutNs) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
-        "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 // The tensor copies of tile t into stage `st` (one thread). with_v: the four
 // direction-update vectors of step j (not on the first step of a launch, where
@@ -249,95 +173,6 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
       float acc = 0.f;
 #pragma unroll
       for (int k = 0; k <= 2 * R; ++k) acc += tf.g[2 * R - k] * win[q + k];
-      ax[q] = acc * scale;
-    }
-  }
-}
-
-// The same outputs as tile_operator with A applied as two 1-D passes of the
-// autocorrelation taps c2 with the edge corrections lc (the form that
-// optile.cuh's op_tile2 uses): pass 1 filters the rows of the staged tile (its
-// 32 + 4R rows, the tile's 32 columns) into s1, pass 2 the columns of s1 at the
-// owned pixels; one CTA barrier instead of three and a third fewer FMAs than
-// the four blur passes. Outputs outside the image are not meaningful (the
-// caller masks them).
-template <int R, int NT>
-__device__ __forceinline__ void tile_operator2(const float* U, float* s1, const float* wxs, const float* wys,
-                                               const TapsF<R>& tf, float scale, int i0, int j0, int H, int W,
-                                               float* ax, float* ex, float* vc) {
-  using L = StageLayout<R>;
-  constexpr int AH = L::AH, AW = L::AW;
-  constexpr int PPT = kTileH * kTileW / NT;
-  constexpr int NW = 4 + 4 * R;
-  constexpr int NW2 = PPT + 4 * R;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    const int ti = ty * PPT + q, tj = tx;
-    const int gi = i0 + ti, gj = j0 + tj;
-    const bool in = gi < H && gj < W;
-    const float wl = (in && gj >= 1) ? wxs[ti * kWRow + tj + 3] : 0.f;
-    const float wr = (in && gj < W - 1) ? wxs[ti * kWRow + tj + 4] : 0.f;
-    const float wu = (in && gi >= 1) ? wys[ti * kWRow + tj + 4] : 0.f;
-    const float wd = (in && gi < H - 1) ? wys[(ti + 1) * kWRow + tj + 4] : 0.f;
-    const float* sp = U + (ti + 2 * R) * AW + (tj + 2 * R);
-    const float xc = sp[0];
-    ex[q] = (wl * (xc - sp[-1]) - wr * (sp[1] - xc) + wu * (xc - sp[-AW]) - wd * (sp[AW] - xc)) * scale;
-    vc[q] = xc * scale;
-  }
-  // pass 1: rows of U -> s1 (AH x 32); output column c is image column j0 + c
-  const int nl = W < R ? W : R;   // columns (rows) near an edge that carry a correction
-  const bool edge_x = j0 < R || j0 + kTileW > W - R;
-  for (int item = threadIdx.x; item < AH * (kTileW / 4); item += NT) {
-    const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
-    const float* row = U + a * AW;
-    float win[NW], o[4];
-    load_row<float, NW>(row + c0, win);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int t = 0; t <= 4 * R; ++t) acc += tf.c2[t] * win[q + t];
-      o[q] = acc;
-    }
-    if (edge_x) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int gj = j0 + c0 + q;
-        if (gj < W) {
-          if (gj < R)          // left edge: image columns 0 .. nl-1, staged at qq - j0 + 2R
-            for (int qq = 0; qq < nl; ++qq) o[q] -= tf.lc[gj * R + qq] * row[qq - j0 + 2 * R];
-          if (gj >= W - R) {   // right edge: image columns W-1-qq, at the distance W-1-gj
-            const int d = W - 1 - gj;
-            for (int qq = 0; qq < nl; ++qq) o[q] -= tf.lc[d * R + qq] * row[(W - 1 - qq) - j0 + 2 * R];
-          }
-        }
-      }
-    }
-    store4<float>(s1 + a * kTileW + c0, o);
-  }
-  __syncthreads();
-  // pass 2: columns of s1 at the owned pixels; s1 row a is image row i0 - 2R + a
-  {
-    const int nlh = H < R ? H : R;
-    float win[NW2];
-#pragma unroll
-    for (int k = 0; k < NW2; ++k) win[k] = s1[(ty * PPT + k) * kTileW + tx];
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int t = 0; t <= 4 * R; ++t) acc += tf.c2[t] * win[q + t];
-      const int gi = i0 + ty * PPT + q;
-      if (gi < H) {
-        if (gi < R)
-          for (int qq = 0; qq < nlh; ++qq) acc -= tf.lc[gi * R + qq] * s1[(qq - i0 + 2 * R) * kTileW + tx];
-        if (gi >= H - R) {
-          const int d = H - 1 - gi;
-          for (int qq = 0; qq < nlh; ++qq)
-            acc -= tf.lc[d * R + qq] * s1[((H - 1 - qq) - i0 + 2 * R) * kTileW + tx];
-        }
-      }
       ax[q] = acc * scale;
     }
   }
@@ -556,36 +391,6 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
 // ---------------------------------------------------------------------------
 // host side: tensor maps and the launch
 // ---------------------------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-cudaError_t encode_fn() {
-  if (g_encode) return cudaSuccess;
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q{};
-  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess) return e;
-  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return cudaSuccess;
-}
-
-// rank-2 FP32 map {w0, h0} (row stride w0 floats) or rank-3 with a column stride
-cudaError_t encode(CUtensorMap* m, const float* addr, int rank, unsigned long long w0, unsigned long long h0,
-                   unsigned long long d2, unsigned long long stride2_elems, unsigned bx, unsigned by,
-                   unsigned bz) {
-  const cuuint64_t dims[3] = {w0, h0, d2};
-  const cuuint64_t strides[2] = {w0 * sizeof(float), stride2_elems * sizeof(float)};
-  const cuuint32_t box[3] = {bx, by, bz};
-  const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(addr),
-                              dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-bool aligned16(const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; }
-
 template <int R, bool TWO>
 cudaError_t launch_tma(MinresState* st, const MrP<float>& p, int H, int W, const Taps& tp, GridBar* bar,
                        int s_alloc, cudaStream_t s, int max_ctas, int* launched_blocks, bool* done) {
@@ -644,8 +449,9 @@ cudaError_t mr_stream_tma(MinresState* st, const MrP<float>& p, int H, int W, co
     return cudaSuccess;
   for (int i = 0; i < 3; ++i)
     if (!aligned16(p.vring[i]) || !aligned16(p.dring[i])) return cudaSuccess;
-  // p.tma: 1 the four blur passes, 2 the two autocorrelation passes (radius <= kMaxR2)
-  const bool two = p.tma == 2 && tp.r <= kMaxR2;
+  // p.tma: 1 the four blur passes, 2 (or 3 where mrtmaok.cu did not apply) the two
+  // autocorrelation passes (radius <= kMaxR2)
+  const bool two = p.tma >= 2 && tp.r <= kMaxR2;
   switch (tp.r) {
     case 4: return two ? launch_tma<4, true>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done)
                        : launch_tma<4, false>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);
