@@ -98,7 +98,7 @@ def workload_config(wl, precision):
 
 def kernel_src_sha():
     h = hashlib.sha256()
-    for f in ("mrtma.cu", "mrtmaok.cu", "tma.cuh", "mrpersist.cu", "mrcommon.cuh", "optile.cuh", "gridsync.cuh"):
+    for f in ("mrtma.cu", "tma.cuh", "mrpersist.cu", "mrcommon.cuh", "optile.cuh", "gridsync.cuh"):
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -489,8 +489,7 @@ def roofline_entry(job, ms_total, minres_kernel, wl, precision, fp64_peak):
     cat = 0 if tm["ms"][0] >= tm["ms"][1] else 1
     launches = max(1, tm["launches"][cat])
     tname = "float" if precision == "mixed" else "double"
-    names = {4: f"k_mr_tmaok<{tname},{wl.radius}>", 3: f"k_mr_batch<{tname},{wl.radius}>",
-             2: f"k_mr_tma<{tname},{wl.radius}>",
+    names = {3: f"k_mr_batch<{tname},{wl.radius}>", 2: f"k_mr_tma<{tname},{wl.radius}>",
              1: f"k_mr_resident<{tname},{wl.radius}>", 0: f"k_mr_persist<{tname},{wl.radius}>"}
     kname = names.get(minres_kernel, f"k_mr_matvec<{tname}>") if cat == 0 else \
         "k_op_apply<double> (FP64 true / refinement residual matvec)"

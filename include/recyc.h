@@ -138,10 +138,7 @@ typedef struct {
                               batched_local step in one launch; 1 one CTA per tile, vectors in
                               registers; 0 tiles streamed through memory (not all co-resident);
                               2 tiles streamed, every tile operand staged in shared memory by
-                              tensor copies (FP32); 4 tiles streamed, tensor copies of the
-                              vector and weights only, the projection's dots taken from the
-                              images (A + gamma E) K_l in the pixel phase (FP32); -1 none yet
-                              (step kernels only) */
+                              tensor copies (FP32); -1 none yet (step kernels only) */
   int stab_sweeps;         /* sweeps of the one-sided Jacobi SVD in the last stabilize
                               (Algorithm "Stabilized U"); 40 is its cap */
   int stab_candidates;     /* columns of U~ handed to the last stabilize */
@@ -149,12 +146,9 @@ typedef struct {
   int tuned_variant;       /* FP32 streaming solves (images with more tiles than co-resident
                               CTAs): the variant the last one ran, picked by the library's
                               autotuner on the first solve of each image shape (timed trials
-                              of 24 steps) unless RS_TMA pins it: 3 the kernel of
-                              minres_kernel 4 (the images (A + gamma E) K_l cost s operator
-                              applications per shift, counted in its matvecs), 2 tensor-copy
-                              kernel with A as two autocorrelation passes, 1 the same with four
-                              blur passes, 0 the cp.async streaming kernel; -1 no streaming FP32
-                              solve */
+                              of 24 steps) unless RS_TMA pins it: 2 tensor-copy kernel with A as
+                              two autocorrelation passes, 1 the same with four blur passes, 0
+                              the cp.async streaming kernel; -1 no streaming FP32 solve */
 } rs_info;
 
 /* Per-kernel device time, gathered with CUDA events around every launch of

@@ -246,7 +246,6 @@ struct rs_problem {
   void *bT = nullptr, *wT = nullptr, *Ut = nullptr, *AU = nullptr, *EU = nullptr, *Kp = nullptr;
   void *WL = nullptr, *WR = nullptr, *AWL = nullptr, *EWL = nullptr, *AWR = nullptr, *EWR = nullptr;
   void *Bc = nullptr, *Kl = nullptr, *Gcur = nullptr, *Gprev = nullptr, *Vkeep = nullptr;
-  void* OKl = nullptr;   // (A + gamma E) K_l for the FP32 streaming solve (mixed precision)
   void *vring[3] = {nullptr, nullptr, nullptr}, *dring[3] = {nullptr, nullptr, nullptr};
   void *vzero = nullptr, *u = nullptr, *y = nullptr, *xm = nullptr, *rT = nullptr;
   // small device arrays
@@ -328,12 +327,6 @@ struct rs_problem {
   bool autotune = true;      // pick the streaming-solve variant by timed trials (off when RS_TMA is set)
   bool in_tune = false;      // inside a trial
   int tuned_variant = -1;    // the variant the last streaming solve ran (-1: not tuned)
-  // OKl holds (A + ok_gamma E_k) K_l for K_l as of generation ok_have (ok_s columns);
-  // ok_gen advances whenever K_l or the weights change
-  long long ok_gen = 0, ok_have = -1;
-  double ok_gamma = 0.0;
-  int ok_s = 0;
-  int extra_mv = 0;          // operator applications of the last solve besides its steps
   double* partials_p = nullptr;
   GridBar* gbar = nullptr;
 
@@ -391,7 +384,6 @@ void carve(rs_problem* P, Carver& cv) {
   P->WL = vec(jn); P->WR = vec(jn); P->AWL = vec(jn); P->EWL = vec(jn); P->AWR = vec(jn); P->EWR = vec(jn);
   P->Bc = vec((long)z.smax * z.ld);
   P->Kl = vec((long)z.smax * z.ld);
-  if (P->mixed) P->OKl = vec((long)z.smax * z.ld);
   P->Gcur = vec((long)z.M * z.ld);
   P->Gprev = vec((long)z.M * z.ld);
   P->Vkeep = vec((long)std::max(z.keep, 1) * z.ld);
@@ -715,9 +707,8 @@ int tuned_variant(rs_problem* P, double gamma, const T* r, bool use_K, int s_hos
   const bool timing_was = P->timing;
   P->timing = false;
   const long long mv0 = P->mv_total;
-  const int xmv0 = P->extra_mv;
   const int saved = P->use_tma;
-  const int cands[4] = {3, 2, 1, 0};
+  const int cands[3] = {2, 1, 0};
   float best_ms = 0.f;
   int best = saved;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -747,8 +738,6 @@ int tuned_variant(rs_problem* P, double gamma, const T* r, bool use_K, int s_hos
   if (e1) cudaEventDestroy(e1);
   P->use_tma = saved;
   P->mv_total = mv0;
-  P->extra_mv = xmv0;
-  P->ok_have = -1;   // the solve itself computes (and counts) the images of K_l
   P->timing = timing_was;
   P->in_tune = false;
   if (rc != RS_OK) return rc;
@@ -894,25 +883,6 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
     mp.j0 = n_unfused + 1;
     mp.prefetch = P->use_prefetch ? 1 : 0;
     mp.tma = variant;
-    mp.OK = nullptr;
-    if constexpr (sizeof(T) == 4) {
-      // the streaming kernel of variant 3 takes K^T (A + gamma E) v_j as Q^T v_j,
-      // Q = (A + gamma E) K: s operator applications per shift, kept for its sweeps
-      const int sa = use_K ? std::max(s_host, 1) : 1;
-      if (variant == 3 && use_K && s_host > 0 && P->OKl &&
-          (P->stream_ctas > 0 || !mr_resident_applies<T>(P->d.height, P->d.width, P->tp.r, sa))) {
-        if (P->ok_have != P->ok_gen || P->ok_gamma != gamma || P->ok_s != s_host) {
-          CU(op_apply<T>(Kl, ld, s_host, wT, vp<T>(P->OKl), nullptr, ld, P->d.height, P->d.width, P->tp, gamma,
-                         0, s));
-          P->ok_have = P->ok_gen;
-          P->ok_gamma = gamma;
-          P->ok_s = s_host;
-          P->mv_total += s_host;
-          P->extra_mv += s_host;
-        }
-        mp.OK = vp<T>(P->OKl);
-      }
-    }
     CU(cudaMemsetAsync(P->gbar, 0, sizeof(GridBar), s));
     const int slot = timed_begin(P);
     int G = 0, resident = 0;
@@ -920,8 +890,8 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
                                          use_K ? std::max(s_host, 1) : 1, s, &G, &resident,
                                          P->stream_ctas);
     P->last_resident = resident;
-    // the variant that ran (3 and 2 fall back to 2 and 0 where their layout does not apply)
-    if (!P->in_tune) P->tuned_variant = resident == 4 ? 3 : (resident == 2 ? std::min(variant, 2) : (resident == 0 ? 0 : -1));
+    // the variant that ran (1 and 2 fall back to 0 where their layout does not apply)
+    if (!P->in_tune) P->tuned_variant = resident == 2 ? variant : (resident == 0 ? 0 : -1);
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
       // not co-resident on this device: the step kernels below take over
       (void)cudaGetLastError();
@@ -1497,7 +1467,6 @@ int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats
     CgsCtx c = cgs_ctx(P, kMaxLocal, P->Rk, nullptr, 0, kLocalDrop);
     // candidate j's image is in Bc[:, j]; kept columns are compacted into Kl
     RS(cgs2_all<T>(P, c, Kl, Bc, ncand, false));
-    ++P->ok_gen;
     int sdim = 0;
     RS(read_back(P, &sdim, P->cnt, sizeof sdim));
     RS(coop_check(P));
@@ -1513,11 +1482,10 @@ int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats
       double eta = 0.0;
       const int mi = forced >= 0 ? forced : P->d.maxit;
       const double ph1 = phase_begin(P);
-      P->extra_mv = 0;
       RS(run_minres<T>(P, gl, vp<T>(P->rT), sdim > 0, forced >= 0 ? 0.0 : inner_tol, mi, 0, false, &it, &eta, &bd,
                        sdim, P->d.inner == RS_CG ? 1 : 0));
       sl.iters += it;
-      sl.matvecs += it + P->extra_mv;
+      sl.matvecs += it;
       sl.relres_est = eta / rnorm;
       sl.sweeps = sw + 1;
       broke |= bd;
@@ -2180,14 +2148,12 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   if (const char* g = std::getenv("RS_STAB_PANELS")) P->stab_panels = std::strcmp(g, "0") != 0;
   // RS_TMA pins the FP32 streaming solve: 0 k_mr_persist; 1 or 2 the kernel whose tile
   // operands are staged by tensor copies (mrtma.cu) with A as four blur passes (1) or two
-  // autocorrelation passes (2); 3 the kernel whose tile phase applies the operator alone
-  // (mrtmaok.cu). Unset, the autotuner picks one per image shape.
+  // autocorrelation passes (2). Unset, the autotuner picks one per image shape.
   if (const char* g = std::getenv("RS_AUTOTUNE")) P->autotune = std::strcmp(g, "0") != 0;
   if (const char* g = std::getenv("RS_TMA")) {
     P->autotune = false;   // a pinned variant
     if (std::strcmp(g, "0") == 0) P->use_tma = 0;
     else if (std::strcmp(g, "2") == 0) P->use_tma = 2;
-    else if (std::strcmp(g, "3") == 0) P->use_tma = 3;
     else P->use_tma = 1;
   }
   P->gprev_nz.assign(desc->M, 0);
@@ -2262,7 +2228,6 @@ rs_status rs_set_weights(rs_problem* P, const double* w_dev) {
   if (P->k >= 0) CU(cudaMemcpyAsync(P->wprev64, P->w64, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
   CU(cudaMemcpyAsync(P->w64, w_dev, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
   if (P->mixed) CU((convert<double, float>(P->w64, (float*)P->wT, 2 * n, P->s)));
-  ++P->ok_gen;
   step_advance(P);
   P->k += 1;
   P->have_recycle = false;

@@ -368,9 +368,7 @@ struct MrP {
   int rec_cap;
   int j0;              // first step of this launch
   int prefetch;        // stage tiles with cp.async ahead of their use (where the layout allows)
-  int tma;             // FP32 images beyond the resident kernel: tensor-copy staged kernel (mrtma.cu;
-                       // 3: mrtmaok.cu, which needs OK)
-  const T* OK;         // (A + gamma E) K (s columns of stride ldk) or nullptr
+  int tma;             // FP32 images beyond the resident kernel: tensor-copy staged kernel (mrtma.cu)
 };
 // One system of a batched solve: its state, image (H x W, its own weights w
 // and blur taps: 2 kMaxTaps - 1 entries centred at kMaxTaps - 1, zero beyond
@@ -438,14 +436,6 @@ bool mr_resident_applies(int H, int W, int radius, int s_alloc);
 // aligned vectors). *done = false (nothing queued) where it does not apply.
 cudaError_t mr_stream_tma(MinresState* st, const MrP<float>& p, int H, int W, const Taps& tp, GridBar* bar,
                           int s_alloc, cudaStream_t s, int max_ctas, int* launched_blocks, bool* done);
-// The FP32 streaming solve whose tile phase applies the operator alone
-// (mrtmaok.cu): the projection's dots K^T (A + gamma E) v_j are taken as
-// p.OK^T v_j in the pixel phase. The start of a solve only (p.j0 = 1, no kept
-// Lanczos vectors), radius 4, 6, 8, 10 or 12, W a multiple of 4, 16-byte
-// aligned vectors, p.OK given when s_alloc > 0. *done = false (nothing queued)
-// where it does not apply.
-cudaError_t mr_stream_tmaok(MinresState* st, const MrP<float>& p, int H, int W, const Taps& tp, GridBar* bar,
-                            int s_alloc, cudaStream_t s, int max_ctas, int* launched_blocks, bool* done);
 
 // ---------------------------------------------------------------- cgs.cu
 struct CgsCtx {

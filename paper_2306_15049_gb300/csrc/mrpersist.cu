@@ -399,14 +399,6 @@ cudaError_t launch_persist(MinresState* st, const MrP<T>& p, int H, int W, const
     }
   }
   if constexpr (sizeof(T) == 4) {
-    if (p.tma == 3) {
-      bool done = false;
-      RK_TRY(mr_stream_tmaok(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, &done));
-      if (done) {
-        *resident = 4;
-        return cudaSuccess;
-      }
-    }
     if (p.tma) {
       bool done = false;
       RK_TRY(mr_stream_tma(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, &done));

@@ -97,8 +97,6 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
   using L = StageLayout<R>;
   constexpr int AH = L::AH, AW = L::AW, BW = L::BW, CH = L::CH;
   constexpr int PPT = kTileH * kTileW / NT;
-  constexpr int NW = 4 + 2 * R;
-  constexpr int NW4 = PPT + 2 * R;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
@@ -117,15 +115,8 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
   // pass 1: T_w along rows of U -> s1 (AH x BW); output column c is image column j0 - R + c
   for (int item = threadIdx.x; item < AH * (BW / 4); item += NT) {
     const int a = item / (BW / 4), c0 = 4 * (item % (BW / 4));
-    float win[NW], o[4];
-    load_row<float, NW>(U + a * AW + c0, win);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += tf.g[k] * win[q + k];
-      o[q] = acc;
-    }
+    float o[4];
+    slide_row4<float, 2 * R + 1>(U + a * AW + c0, [&](int k) { return tf.g[k]; }, o);
     store4<float>(s1 + a * BW + c0, o);
   }
   __syncthreads();
@@ -135,46 +126,29 @@ __device__ __forceinline__ void tile_operator(float* U, float* s1, const float* 
   for (int item = threadIdx.x; item < BW * (CH / 4); item += NT) {
     const int c = item % BW, a0 = 4 * (item / BW);
     const int gj = j0 - R + c;
-    float win[NW];
-#pragma unroll
-    for (int k = 0; k < NW; ++k) win[k] = s1[(a0 + k) * BW + c];
+    float o[4];
+    slide_col<float, 4, 2 * R + 1>(s1 + a0 * BW + c, BW, [&](int k) { return tf.g[k]; }, o);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int gi = i0 - R + a0 + q;
-      float acc = 0.f;
-#pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += tf.g[k] * win[q + k];
-      s2[(a0 + q) * BW + c] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? acc : 0.f;
+      s2[(a0 + q) * BW + c] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? o[q] : 0.f;
     }
   }
   __syncthreads();
   // pass 3: T_w^T along rows (reversed taps); output column c is j0 + c
   for (int item = threadIdx.x; item < CH * (kTileW / 4); item += NT) {
     const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
-    float win[NW], o[4];
-    load_row<float, NW>(s2 + a * BW + c0, win);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += tf.g[2 * R - k] * win[q + k];
-      o[q] = acc;
-    }
+    float o[4];
+    slide_row4<float, 2 * R + 1>(s2 + a * BW + c0, [&](int k) { return tf.g[2 * R - k]; }, o);
     store4<float>(s3 + a * kTileW + c0, o);
   }
   __syncthreads();
   // pass 4: T_h^T along columns -> A v at the owned pixels
   {
-    float win[NW4];
+    float o[PPT];
+    slide_col<float, PPT, 2 * R + 1>(s3 + (ty * PPT) * kTileW + tx, kTileW, [&](int k) { return tf.g[2 * R - k]; }, o);
 #pragma unroll
-    for (int k = 0; k < NW4; ++k) win[k] = s3[(ty * PPT + k) * kTileW + tx];
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += tf.g[2 * R - k] * win[q + k];
-      ax[q] = acc * scale;
-    }
+    for (int q = 0; q < PPT; ++q) ax[q] = o[q] * scale;
   }
 }
 
@@ -449,9 +423,8 @@ cudaError_t mr_stream_tma(MinresState* st, const MrP<float>& p, int H, int W, co
     return cudaSuccess;
   for (int i = 0; i < 3; ++i)
     if (!aligned16(p.vring[i]) || !aligned16(p.dring[i])) return cudaSuccess;
-  // p.tma: 1 the four blur passes, 2 (or 3 where mrtmaok.cu did not apply) the two
-  // autocorrelation passes (radius <= kMaxR2)
-  const bool two = p.tma >= 2 && tp.r <= kMaxR2;
+  // p.tma: 1 the four blur passes, 2 the two autocorrelation passes (radius <= kMaxR2)
+  const bool two = p.tma == 2 && tp.r <= kMaxR2;
   switch (tp.r) {
     case 4: return two ? launch_tma<4, true>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done)
                        : launch_tma<4, false>(st, p, H, W, tp, bar, s_alloc, s, max_ctas, launched_blocks, done);

@@ -151,6 +151,53 @@ __device__ __forceinline__ void store4(T* p, const T* o) {
   }
 }
 
+// Sliding-window 1-D filters. o[q] = sum_{k < NTAP} tap(k) x[q + k], each sum
+// taken in increasing k (the order of a plain loop over the taps), with the
+// window x read as it is consumed instead of held in registers all at once:
+// slide_row4 reads x = p[0 ..] as 16-byte vectors (4 outputs), slide_col reads
+// x[e] = p[e * stride] (NQ outputs). tap(k) is called with compile-time k.
+template <typename T, int NTAP, typename Tap>
+__device__ __forceinline__ void slide_row4(const T* p, Tap tap, T* o) {
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::n;
+  constexpr int NWIN = NTAP + 3;
+  static_assert(NWIN % VW == 0, "window must be a whole number of 16-byte vectors");
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q] = T(0);
+#pragma unroll
+  for (int v = 0; v < NWIN / VW; ++v) {
+    const V t = reinterpret_cast<const V*>(p)[v];
+    T xe[VW];
+    if constexpr (VW == 4) {
+      xe[0] = t.x; xe[1] = t.y; xe[2] = t.z; xe[3] = t.w;
+    } else {
+      xe[0] = t.x; xe[1] = t.y;
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = v * VW + e - q;
+        if (k >= 0 && k < NTAP) o[q] += tap(k) * xe[e];
+      }
+  }
+}
+
+template <typename T, int NQ, int NTAP, typename Tap>
+__device__ __forceinline__ void slide_col(const T* p, int stride, Tap tap, T* o) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) o[q] = T(0);
+#pragma unroll
+  for (int e = 0; e < NQ + NTAP - 1; ++e) {
+    const T x = p[e * stride];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int k = e - q;
+      if (k >= 0 && k < NTAP) o[q] += tap(k) * x;
+    }
+  }
+}
+
 // Loads of data that other CTAs of the same (persistent) kernel may have
 // written: L2 only, never a stale L1 line.
 template <bool CG, typename T>
@@ -197,9 +244,9 @@ __device__ __forceinline__ void cp_async_wait_group() {
 }
 
 // Same contract as op_tile, for a compile-time even radius R: every 1-D pass
-// keeps a register window of 4 + 2R inputs per thread and produces 4 outputs
-// from it (row passes read the window with 16-byte shared loads; column
-// passes walk down one column), and no index needs a runtime division.
+// produces 4 outputs per thread from a sliding window of 4 + 2R inputs (row
+// passes read it with 16-byte shared loads; column passes walk down one
+// column), and no index needs a runtime division.
 // CG: stage with L2-only loads; tile_y / tile_x: the tile (default: the CTA's).
 // taps: 2R+1 values, read after the staging barrier (so a caller may fill a
 // shared-memory copy just before the call). PRE: s0 already holds the unscaled
@@ -214,7 +261,6 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
   static_assert(R % 2 == 0 && R >= 2, "even radius");
   constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
   constexpr int BW = kTileW + 2 * R, CH = kTileH + 2 * R;
-  constexpr int NW = 4 + 2 * R;          // window of one 4-output group
   const long n = (long)H * W;
   const T* wx = w;
   const T* wy = w + n;
@@ -286,15 +332,8 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
   // pass 1: T_w along rows of s0 -> s1 (AH x BW); output column c is image column j0 - R + c
   for (int item = threadIdx.x; item < AH * (BW / 4); item += kThreads) {
     const int a = item / (BW / 4), c0 = 4 * (item % (BW / 4));
-    T win[NW], o[4];
-    load_row<T, NW>(s0 + a * AW + c0, win);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      T acc = T(0);
-#pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += g[k] * win[q + k];
-      o[q] = acc;
-    }
+    T o[4];
+    slide_row4<T, 2 * R + 1>(s0 + a * AW + c0, [&](int k) { return g[k]; }, o);
     store4<T>(s1 + a * BW + c0, o);
   }
   __syncthreads();
@@ -305,46 +344,29 @@ __device__ __forceinline__ void op_tile_fast(const T* __restrict__ src, T scale,
   for (int item = threadIdx.x; item < BW * (CH / 4); item += kThreads) {
     const int c = item % BW, a0 = 4 * (item / BW);
     const int gj = j0 - R + c;
-    T win[NW];
-#pragma unroll
-    for (int k = 0; k < NW; ++k) win[k] = s1[(a0 + k) * BW + c];
+    T o[4];
+    slide_col<T, 4, 2 * R + 1>(s1 + a0 * BW + c, BW, [&](int k) { return g[k]; }, o);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int gi = i0 - R + a0 + q;
-      T acc = T(0);
-#pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += g[k] * win[q + k];
-      s2[(a0 + q) * BW + c] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? acc : T(0);
+      s2[(a0 + q) * BW + c] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? o[q] : T(0);
     }
   }
   __syncthreads();
   // pass 3: T_w^T along rows of s2 -> s3 (reversed taps); output column c is j0 + c
   for (int item = threadIdx.x; item < CH * (kTileW / 4); item += kThreads) {
     const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
-    T win[NW], o[4];
-    load_row<T, NW>(s2 + a * BW + c0, win);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      T acc = T(0);
-#pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
-      o[q] = acc;
-    }
+    T o[4];
+    slide_row4<T, 2 * R + 1>(s2 + a * BW + c0, [&](int k) { return g[2 * R - k]; }, o);
     store4<T>(s3 + a * kTileW + c0, o);
   }
   __syncthreads();
   // pass 4: T_h^T along columns of s3 -> A v at the owned pixels
   {
-    T win[NW];
+    T o[kPPT];
+    slide_col<T, kPPT, 2 * R + 1>(s3 + (ty * kPPT) * kTileW + tx, kTileW, [&](int k) { return g[2 * R - k]; }, o);
 #pragma unroll
-    for (int k = 0; k < NW; ++k) win[k] = s3[(ty * kPPT + k) * kTileW + tx];
-#pragma unroll
-    for (int q = 0; q < kPPT; ++q) {
-      T acc = T(0);
-#pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc += g[2 * R - k] * win[q + k];
-      ax[q] = PRE ? acc * scale : acc;
-    }
+    for (int q = 0; q < kPPT; ++q) ax[q] = PRE ? o[q] * scale : o[q];
   }
 }
 
@@ -360,7 +382,6 @@ __device__ __forceinline__ void op_tile2(const T* __restrict__ src, const T* __r
                                          int W, const Taps& tp, T* s0, T* s1, T* ax, T* ex, T* vc) {
   static_assert(R % 2 == 0 && R >= 2 && R <= kMaxR2, "even radius within the tables");
   constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
-  constexpr int NW = 4 + 4 * R;          // window of one 4-output group
   const long n = (long)H * W;
   const T* wx = w;
   const T* wy = w + n;
@@ -415,15 +436,8 @@ __device__ __forceinline__ void op_tile2(const T* __restrict__ src, const T* __r
   for (int item = threadIdx.x; item < AH * (kTileW / 4); item += kThreads) {
     const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
     const T* row = s0 + a * AW;
-    T win[NW], o[4];
-    load_row<T, NW>(row + c0, win);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      T acc = T(0);
-#pragma unroll
-      for (int t = 0; t <= 4 * R; ++t) acc += tp.template c2_at<T>(t) * win[q + t];
-      o[q] = acc;
-    }
+    T o[4];
+    slide_row4<T, 4 * R + 1>(row + c0, [&](int t) { return tp.template c2_at<T>(t); }, o);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int gj = j0 + c0 + q;
@@ -442,14 +456,12 @@ __device__ __forceinline__ void op_tile2(const T* __restrict__ src, const T* __r
   // pass 2: columns of s1 at the owned pixels; s1 row a is image row i0 - 2R + a
   {
     const int nlh = H < R ? H : R;
-    T win[NW];
-#pragma unroll
-    for (int k = 0; k < NW; ++k) win[k] = s1[(ty * kPPT + k) * kTileW + tx];
+    T o[kPPT];
+    slide_col<T, kPPT, 4 * R + 1>(s1 + (ty * kPPT) * kTileW + tx, kTileW,
+                                  [&](int t) { return tp.template c2_at<T>(t); }, o);
 #pragma unroll
     for (int q = 0; q < kPPT; ++q) {
-      T acc = T(0);
-#pragma unroll
-      for (int t = 0; t <= 4 * R; ++t) acc += tp.template c2_at<T>(t) * win[q + t];
+      T acc = o[q];
       const int gi = i0 + ty * kPPT + q;
       if (gi < H) {
         if (gi < R)

@@ -1,5 +1,5 @@
-// Tensor-copy (TMA) helpers shared by the streaming FP32 MINRES kernels
-// (mrtma.cu, mrtmaok.cu): mbarrier waits bounded in time, tiled bulk tensor
+// Tensor-copy (TMA) helpers of the streaming FP32 MINRES kernel (mrtma.cu):
+// mbarrier waits bounded in time, tiled bulk tensor
 // copies into shared memory, the proxy fences, the taps as a kernel parameter,
 // the two-pass tile operator on a staged tile, and the host-side encoding of
 // tensor maps (cuTensorMapEncodeTiled through the runtime's driver entry point).
@@ -102,8 +102,6 @@ __device__ __forceinline__ void tile_operator2(const float* U, float* s1, const 
                                                float* ax, float* ex, float* vc) {
   constexpr int AH = kTileH + 4 * R, AW = kTileW + 4 * R;
   constexpr int PPT = kTileH * kTileW / NT;
-  constexpr int NW = 4 + 4 * R;
-  constexpr int NW2 = PPT + 4 * R;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
@@ -125,21 +123,8 @@ __device__ __forceinline__ void tile_operator2(const float* U, float* s1, const 
   for (int item = threadIdx.x; item < AH * (kTileW / 4); item += NT) {
     const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
     const float* row = U + a * AW;
-    // o[q] = sum_t c2[t] row[c0 + q + t] in increasing t, the window read one 16-byte
-    // vector at a time (few registers live: no window array)
-    float o[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int v = 0; v < NW / 4; ++v) {
-      const float4 x4 = reinterpret_cast<const float4*>(row + c0)[v];
-      const float xe[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int t = 4 * v + e - q;
-          if (t >= 0 && t <= 4 * R) o[q] += tf.c2[t] * xe[e];
-        }
-    }
+    float o[4];
+    slide_row4<float, 4 * R + 1>(row + c0, [&](int t) { return tf.c2[t]; }, o);
     if (edge_x) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -160,19 +145,8 @@ __device__ __forceinline__ void tile_operator2(const float* U, float* s1, const 
   // pass 2: columns of s1 at the owned pixels; s1 row a is image row i0 - 2R + a
   {
     const int nlh = H < R ? H : R;
-    // acc[q] = sum_t c2[t] s1[ty PPT + q + t][tx] in increasing t, one value at a time
     float acc2[PPT];
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) acc2[q] = 0.f;
-#pragma unroll
-    for (int e = 0; e < NW2; ++e) {
-      const float x = s1[(ty * PPT + e) * kTileW + tx];
-#pragma unroll
-      for (int q = 0; q < PPT; ++q) {
-        const int t = e - q;
-        if (t >= 0 && t <= 4 * R) acc2[q] += tf.c2[t] * x;
-      }
-    }
+    slide_col<float, PPT, 4 * R + 1>(s1 + (ty * PPT) * kTileW + tx, kTileW, [&](int t) { return tf.c2[t]; }, acc2);
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       float acc = acc2[q];

@@ -8,9 +8,6 @@ persistent MINRES kernel those workloads run, through the C ABI:
 * k_mr_tma       (the FP32 streaming kernel whose tile operands are staged by
                   tensor copies, with A as four blur passes or, RS_TMA=2, as two
                   autocorrelation passes with edge corrections; RS_STREAM_CTAS),
-* k_mr_tmaok     (the FP32 streaming kernel whose tile phase applies the
-                  operator alone, the projection's dots taken from the images
-                  (A + gamma E) K in the pixel phase; RS_TMA=3, RS_STREAM_CTAS),
 * k_mr_batch     (every shift of a step in one launch, batched local spaces).
 
 The 128 x 124 image has a ragged last tile column (28 pixels) and, on three
@@ -33,7 +30,7 @@ from tests.gpu_util import Pair, rel
 pytestmark = pytest.mark.gpu
 
 SIGMA = {10: 3.0, 12: 4.0}
-KERNEL = {"resident": 1, "persist": 0, "tma": 2, "tma2": 2, "tmaok": 4, "batch": 3}
+KERNEL = {"resident": 1, "persist": 0, "tma": 2, "tma2": 2, "batch": 3}
 
 
 def _workload(r):
@@ -69,7 +66,7 @@ def _pair(wl, precision, batched, env):
 
 
 CASES = [("resident", 0), ("resident", 1), ("persist", 0), ("persist", 1), ("tma", 1), ("tma2", 1),
-         ("tmaok", 1), ("batch", 0), ("batch", 1)]
+         ("batch", 0), ("batch", 1)]
 
 
 @pytest.mark.parametrize("r", [10, 12])
@@ -77,8 +74,8 @@ CASES = [("resident", 0), ("resident", 1), ("persist", 0), ("persist", 1), ("tma
 def test_kernel_matches_oracle_at_large_radius(r, kernel, precision):
     wl = _workload(r)
     batched = kernel == "batch"
-    env = {"RS_TMA": {"tma": "1", "tma2": "2", "tmaok": "3"}.get(kernel, "0")}
-    if kernel in ("persist", "tma", "tma2", "tmaok"):
+    env = {"RS_TMA": {"tma": "1", "tma2": "2"}.get(kernel, "0")}
+    if kernel in ("persist", "tma", "tma2"):
         env["RS_STREAM_CTAS"] = "3"
     weights, steps = _oracle(r, batched)
     pr = _pair(wl, precision, batched, env)

@@ -15,10 +15,9 @@ from tests.gpu_util import Pair, rel
 pytestmark = pytest.mark.gpu
 
 
-def _pair(wl, precision, ctas, variant="0"):
-    # RS_TMA=0: k_mr_persist; RS_TMA=3: k_mr_tmaok (tensor copies of the vector and
-    # weights only, the projection's dots from the images of K in the pixel phase)
-    env = {"RS_STREAM_CTAS": str(ctas), "RS_TMA": variant}
+def _pair(wl, precision, ctas):
+    # RS_TMA=0: this file covers k_mr_persist; the tensor-copy kernel has its own tests
+    env = {"RS_STREAM_CTAS": str(ctas), "RS_TMA": "0"}
     old = {k: os.environ.get(k) for k in env}
     os.environ.update(env)
     try:
@@ -64,28 +63,3 @@ def test_streaming_kernel_matches_oracle(precision, ctas):
     if precision == 0:
         assert n_eq >= 0.75 * n_tot
 
-
-@pytest.mark.parametrize("ctas", [1, 4])
-def test_operator_only_tile_phase_kernel_matches_oracle(ctas):
-    """k_mr_tmaok (FP32) on the same ragged 96 x 80 image, one and four CTAs
-    (9 tiles: uneven counts per CTA and, on one CTA, more tiles than stages)."""
-    wl = synth.tiny(96, 80, sigma=1.5, radius=4, M=6, p=8, n_ritz_local=3, seed=41, tol=1e-9)
-    pr = _pair(wl, 1, ctas, variant="3")
-    S = State()
-    for k, w in enumerate([np.ones(2 * wl.n), synth.random_weights(wl.n, 43, lo=1.0, hi=300.0)]):
-        o = outer_step(pr.op, pr.b, pr.gammas, w, S, pr.prm)
-        pr.P.rs_set_weights(pr.t(w))
-        pr.P.rs_update_recycle(0 if k == 0 else 1)
-        X = pr.torch.empty(wl.M, wl.n, dtype=pr.torch.float64, device=pr.dev)
-        stats = pr.P.rs_solve_shifts(X)
-        info = pr.P.rs_get_info()
-        assert info["minres_kernel"] == 4 and info["tuned_variant"] == 3, info
-        Xn = pr.n(X)
-        for l in range(wl.M):
-            st = stats[l]
-            assert st["relres_true"] <= wl.tol * (1 + 1e-6), (k, l, st)
-            assert rel(Xn[l], o.X[l]) <= 1e-4, (k, l, rel(Xn[l], o.X[l]))
-            # matvecs = MINRES steps + one FP64 residual per sweep + the images of the
-            # (at most two) correction candidates + the s images (A + gamma E) K_l
-            extra = st["matvecs"] - st["iters"] - st["sweeps"] - st["local_dim"]
-            assert 0 <= extra <= 2, (k, l, st)
