@@ -79,8 +79,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (512x512, four images, differentiation, 64x64 oracle parity)")
-    ap.add_argument("--profile-case", nargs="?", const="step", choices=["step", "small"],
+    ap.add_argument("--profile-case", nargs="?", const="step", choices=["step", "job", "small"],
                     help="run once for a profiler and exit (step: the first two outer steps of the workload; "
+                         "job: all its outer steps; "
                          "small: four shifts of the same image on a random 12-column principal basis, "
                          "24 MINRES steps each)")
     return ap.parse_args()
@@ -760,12 +761,12 @@ def profile_case(args, wl, dev):
 
     import synth
     from paper_2306_15049_gb300 import recyc
-    if args.profile_case == "step":
-        # the first two outer steps: k = 0 (seeding solves) and k = 1 (Eq. delta update)
+    if args.profile_case in ("step", "job"):
+        # the first two outer steps (k = 0: seeding solves; k = 1: Eq. delta update), or all K
         job = Job(wl, args.precision, dev)
-        rs = [job.step(), job.step()]
+        rs = [job.step() for _ in range(2 if args.profile_case == "step" else wl.K)]
         torch.cuda.synchronize(dev)
-        print(json.dumps({"profile_case": "step", "workload": wl.name, "precision": args.precision,
+        print(json.dumps({"profile_case": args.profile_case, "workload": wl.name, "precision": args.precision,
                           "steps": rs}), flush=True)
         return
     small = synth.tiny(wl.height, wl.width, sigma=wl.sigma, radius=wl.radius, M=4, p=12,
