@@ -292,10 +292,14 @@ rs_status rs_get_principal_basis(rs_problem* prob, double* U_dev, int* nc_host);
 
 /* y = (A + gamma E_k) x  (mode 0), or y = A x and y2 = E_k x (mode 1), or
  * y = E_k x (mode 2), or y = C x (mode 3: the blur H, or the Radon transform with
- * y of m doubles), or y = C^T x (mode 4: x of m doubles). Otherwise x, y, y2 are
+ * y of m doubles), or y = C^T x (mode 4: x of m doubles), or y = (A + gamma E_k) x
+ * in two-float arithmetic (mode 5: each FP64 value carried as a pair of floats,
+ * every product and sum with its rounding error kept, about 2^-44 relative; blur
+ * operator with an even radius 4..12, else RS_EINVAL; the true residuals of
+ * mixed-precision problems are computed this way). Otherwise x, y, y2 are
  * n doubles on the device, computed in the problem's working precision for modes
  * 0-2 when use_working_precision is 1, else in FP64. Counts as one matvec
- * (modes 0-2). */
+ * (modes 0-2, 5). */
 rs_status rs_apply_operator(rs_problem* prob, double gamma, const double* x_dev,
                             double* y_dev, double* y2_dev, int mode,
                             int use_working_precision);

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "librecyc.so")
-SOURCES = ["matvec.cu", "blas.cu", "dense.cu", "minres.cu", "mrfused.cu", "mrpersist.cu", "mrtma.cu", "mrbatch.cu",
+SOURCES = ["matvec.cu", "matvec_df.cu", "blas.cu", "dense.cu", "minres.cu", "mrfused.cu", "mrpersist.cu", "mrtma.cu", "mrbatch.cu",
            "cgs.cu", "cgsblock.cu", "api.cu", "noalloc.cu", "radon.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

@@ -38,6 +38,7 @@ constexpr int kDotStride = kMaxLocal + 1;
 constexpr int kBatchTail = 2;               // batched solves: the last shifts run one by one
 constexpr int kChunk = 6;                  // MINRES steps per CUDA-graph replay (a multiple of 3)
 constexpr int kStabPanel = 16;             // candidates per panel of the blocked stabilize CGS2
+constexpr int kGuessBatch = 16;            // shifts whose initial guesses one pass over U~ computes
 constexpr int kTuneSteps = 24;             // MINRES steps of one autotuning trial
 
 long round_up(long x, long a) { return (x + a - 1) / a * a; }
@@ -242,6 +243,8 @@ struct rs_problem {
   double *b = nullptr, *dimg = nullptr, *r64 = nullptr, *y64 = nullptr, *t64 = nullptr;
   double *w64 = nullptr, *wprev64 = nullptr, *dw64 = nullptr;
   double *Xprev = nullptr, *Xcur = nullptr, *Ut_raw = nullptr, *Vi1 = nullptr;
+  double* R0blk = nullptr;   // initial residuals of a batch of kGuessBatch shifts
+  float *xdh = nullptr, *xdl = nullptr, *wdh = nullptr, *wdl = nullptr;   // two-float splits of x and w
   // working-precision buffers (float or double)
   void *bT = nullptr, *wT = nullptr, *Ut = nullptr, *AU = nullptr, *EU = nullptr, *Kp = nullptr;
   void *WL = nullptr, *WR = nullptr, *AWL = nullptr, *EWL = nullptr, *AWR = nullptr, *EWR = nullptr;
@@ -324,6 +327,7 @@ struct rs_problem {
   bool use_prefetch = true;  // persistent MINRES kernels stage tiles ahead with cp.async
   int use_tma = 2;           // FP32 streaming solves stage tile operands with tensor copies (2: two-pass A)
   bool stab_panels = true;   // stabilize CGS2 by panels of candidates (column by column when false)
+  bool use_df = true;        // mixed precision: true residuals in two-float arithmetic
   bool autotune = true;      // pick the streaming-solve variant by timed trials (off when RS_TMA is set)
   bool in_tune = false;      // inside a trial
   int tuned_variant = -1;    // the variant the last streaming solve ran (-1: not tuned)
@@ -370,6 +374,11 @@ void carve(rs_problem* P, Carver& cv) {
   P->dw64 = cv.take<double>(z.ld2);
   P->Xprev = cv.take<double>((size_t)z.M * z.ld);
   P->Xcur = cv.take<double>((size_t)z.M * z.ld);
+  P->R0blk = cv.take<double>((size_t)kGuessBatch * z.ld);
+  P->xdh = cv.take<float>(z.ld);
+  P->xdl = cv.take<float>(z.ld);
+  P->wdh = cv.take<float>(z.ld2);
+  P->wdl = cv.take<float>(z.ld2);
   P->Ut_raw = cv.take<double>((size_t)z.cmax * z.ld);
   P->Vi1 = cv.take<double>((size_t)std::max(z.a, 1) * z.ld);
   if (P->mixed) {
@@ -599,8 +608,14 @@ int true_residual(rs_problem* P, double gamma, const double* x64, double* relres
   }
   const double t0 = phase_begin(P);
   const int slot = timed_begin(P);
-  CU(op_apply<double>(x64, P->z.ld, 1, P->w64, P->y64, nullptr, P->z.ld, P->d.height, P->d.width,
-                      P->tp, gamma, 0, P->s));
+  if (P->mixed && P->use_df && P->tp.radon.nang == 0 && op_apply_df_supported(P->tp.r)) {
+    // mixed precision: the residual in two-float arithmetic (FP64-level accuracy at FP32 rates)
+    CU(split_df(x64, P->xdh, P->xdl, P->z.n, P->s));
+    CU(op_apply_df(P->xdh, P->xdl, P->wdh, P->wdl, P->y64, P->d.height, P->d.width, P->tp, gamma, P->s));
+  } else {
+    CU(op_apply<double>(x64, P->z.ld, 1, P->w64, P->y64, nullptr, P->z.ld, P->d.height, P->d.width,
+                        P->tp, gamma, 0, P->s));
+  }
   timed_end(P, slot, 1, -1, P->z.n, 32.0 * P->z.n, (8.0 * (2 * P->tp.r + 1) + 10.0) * P->z.n);
   CU(residual64(rhs, P->y64, P->r64, P->z.n, P->partials, P->s));
   CU(reduce_partials(P->partials, P->z.G, 1, 1, P->scal + 8, P->s, nullptr, 0, nullptr));
@@ -1381,6 +1396,18 @@ int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats
     sl.sweeps = 0;
     double* x = X + (long)i * n;    // caller's X is dense count x n
     T* gl_buf = Gbuf + (long)l * ld;
+    // initial guesses x0 = U~ c_l (into the caller's rows) and r0 = rhs - A U~ c_l -
+    // gamma_l E U~ c_l (into R0blk) for the next kGuessBatch shifts at once: U~, A U~
+    // and E U~ are read once per batch; a shift's arithmetic does not depend on the batch
+    if (i % kGuessBatch == 0) {
+      const int nb = std::min(kGuessBatch, count - i);
+      CU(gemm_ts_cols<T, double>(Ut, ld, nc, Cc + (long)l * nc, nc, nb, 0.0, X + (long)i * n, n, n, s));
+      for (int q = 0; q < nb; ++q)
+        CU(cudaMemcpyAsync(P->R0blk + (long)q * ld, adj ? G + (long)(l + q) * n : P->b, n * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+      CU(gemm_ts_cols<T, double>(vp<T>(P->AU), ld, nc, CAc + (long)l * nc, nc, nb, 1.0, P->R0blk, ld, n, s));
+      CU(gemm_ts_cols<T, double>(vp<T>(P->EU), ld, nc, CEc + (long)l * nc, nc, nb, 1.0, P->R0blk, ld, n, s));
+    }
     if (adj && !(rnorm > 0.0)) {    // g_l = 0: lambda_l = 0
       CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
       CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
@@ -1388,11 +1415,8 @@ int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats
       if (stats) stats[i] = sl;
       continue;
     }
-    // initial guess x0 = U~ c_l and r0 = rhs - A U~ c_l - gamma_l E U~ c_l
-    CU(gemm_ts<T, double>(Ut, ld, nc, Cc + (long)l * nc, nc, 1, 0.0, x, n, n, s));
-    CU(cudaMemcpyAsync(P->r64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CU(gemm_ts<T, double>(vp<T>(P->AU), ld, nc, CAc + (long)l * nc, nc, 1, 1.0, P->r64, ld, n, s));
-    CU(gemm_ts<T, double>(vp<T>(P->EU), ld, nc, CEc + (long)l * nc, nc, 1, 1.0, P->r64, ld, n, s));
+    CU(cudaMemcpyAsync(P->r64, P->R0blk + (long)(i % kGuessBatch) * ld, n * sizeof(double),
+                       cudaMemcpyDeviceToDevice, s));
     CU(norm2_partials<double>(P->r64, n, P->partials, s));
     CU(reduce_partials(P->partials, z.G, 1, 1, P->scal + 10, s, nullptr, 0, nullptr));
     double r02 = 0.0;
@@ -2144,6 +2168,9 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   }
   // RS_PREFETCH=0 stages every tile synchronously in the persistent MINRES kernels
   if (const char* g = std::getenv("RS_PREFETCH")) P->use_prefetch = std::strcmp(g, "0") != 0;
+  // RS_RESID_DF=0 computes the true residuals of mixed precision in FP64 instead of
+  // two-float arithmetic
+  if (const char* g = std::getenv("RS_RESID_DF")) P->use_df = std::strcmp(g, "0") != 0;
   // RS_STAB_PANELS=0 runs the stabilize CGS2 column by column instead of by panels
   if (const char* g = std::getenv("RS_STAB_PANELS")) P->stab_panels = std::strcmp(g, "0") != 0;
   // RS_TMA pins the FP32 streaming solve: 0 k_mr_persist; 1 or 2 the kernel whose tile
@@ -2228,6 +2255,7 @@ rs_status rs_set_weights(rs_problem* P, const double* w_dev) {
   if (P->k >= 0) CU(cudaMemcpyAsync(P->wprev64, P->w64, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
   CU(cudaMemcpyAsync(P->w64, w_dev, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, P->s));
   if (P->mixed) CU((convert<double, float>(P->w64, (float*)P->wT, 2 * n, P->s)));
+  if (P->tp.radon.nang == 0) CU(split_df(P->w64, P->wdh, P->wdl, 2 * n, P->s));
   step_advance(P);
   P->k += 1;
   P->have_recycle = false;
@@ -2478,14 +2506,20 @@ rs_status rs_apply_operator(rs_problem* P, double gamma, const double* x_dev, do
                             double* y2_dev, int mode, int use_working_precision) {
   if (!P) return RS_EINVAL;
   if (!x_dev || !y_dev || (mode == 1 && !y2_dev)) return (rs_status)P->set_err(RS_EINVAL, "NULL vector");
-  if (mode < 0 || mode > 4) return (rs_status)P->set_err(RS_EINVAL, "mode must be 0..4");
-  if (mode < 3 && P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  if (mode < 0 || mode > 5) return (rs_status)P->set_err(RS_EINVAL, "mode must be 0..5");
+  if ((mode < 3 || mode == 5) && P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
+  if (mode == 5 && (P->tp.radon.nang > 0 || !op_apply_df_supported(P->tp.r)))
+    return (rs_status)P->set_err(RS_EINVAL, "mode 5 needs the blur operator with an even radius 4..12");
   const long n = P->z.n, ld = P->z.ld;
   const int H = P->d.height, W = P->d.width;
   if (mode == 3) {
     CU(forward_apply(P, x_dev, y_dev));
   } else if (mode == 4) {
     CU(adjoint_apply(P, x_dev, y_dev));
+  } else if (mode == 5) {
+    CU(split_df(x_dev, P->xdh, P->xdl, n, P->s));
+    CU(op_apply_df(P->xdh, P->xdl, P->wdh, P->wdl, y_dev, H, W, P->tp, gamma, P->s));
+    P->mv_total += 1;
   } else if (P->mixed && use_working_precision) {
     float* xf = (float*)P->u;
     float* yf = (float*)P->y;

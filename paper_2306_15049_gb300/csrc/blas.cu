@@ -98,6 +98,109 @@ k_multidot(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host,
   }
 }
 
+// The same dots from 16-byte vector loads, four columns per pass over y (y is
+// read once per group of four columns, and each thread has five loads in flight
+// instead of one scalar pair). Needs n and ldx multiples of the vector width and
+// 16-byte aligned vectors (the host checks; k_multidot takes the rest).
+template <typename T> struct V16;
+template <> struct V16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct V16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ void vdot_acc(const typename V16<T>::type& a, const typename V16<T>::type& b,
+                                         Acc<T>& acc) {
+  if constexpr (V16<T>::n == 4) {
+    acc.add(a.x, b.x); acc.add(a.y, b.y); acc.add(a.z, b.z); acc.add(a.w, b.w);
+  } else {
+    acc.add(a.x, b.x); acc.add(a.y, b.y);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_multidot_v(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host,
+             const T* __restrict__ extra, const T* __restrict__ y, long n, double* partials,
+             int stride, const int* stop) {
+  if (stop && *stop) return;
+  using V = typename V16<T>::type;
+  constexpr int VW = V16<T>::n;
+  __shared__ double sh[kThreads / 32];
+  const int cnt = cnt_dev ? *cnt_dev : cnt_host;
+  const int nd = cnt + (extra ? 1 : 0);
+  const long nv = n / VW;
+  const V* y4 = reinterpret_cast<const V*>(y);
+  for (int k0 = 0; k0 < nd; k0 += 4) {
+    const V* xs[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = k0 + c;
+      xs[c] = reinterpret_cast<const V*>(k < cnt ? X + (long)k * ldx : extra);
+    }
+    Acc<T> acc[4];
+    for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < nv; i += (long)gridDim.x * kThreads) {
+      const V b = y4[i];
+      V a[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (k0 + c < nd) a[c] = xs[c][i];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (k0 + c < nd) vdot_acc<T>(a[c], b, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (k0 + c < nd) {
+        const double t = block_sum_t<T>(acc[c].get(), sh);
+        if (threadIdx.x == 0) partials[(long)blockIdx.x * stride + k0 + c] = t;
+      }
+    }
+  }
+}
+
+// y += sign sum_k c_k X[:, k] with 16-byte vectors, every column in one pass
+// (the layout conditions of k_multidot_v); optional ||y||^2 partials.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_multi_axpy_v(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host,
+               const double* __restrict__ c, double sign, T* __restrict__ y, long n,
+               double* norm_partials, const int* stop) {
+  if (stop && *stop) return;
+  using V = typename V16<T>::type;
+  constexpr int VW = V16<T>::n;
+  __shared__ double sh[kThreads / 32];
+  __shared__ T sc[kMaxDots];
+  const int cnt = cnt_dev ? *cnt_dev : cnt_host;
+  for (int k = threadIdx.x; k < cnt; k += kThreads) sc[k] = T(sign * c[k]);
+  __syncthreads();
+  const long nv = n / VW;
+  V* y4 = reinterpret_cast<V*>(y);
+  Acc<T> acc;
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < nv; i += (long)gridDim.x * kThreads) {
+    V v = y4[i];
+    T* va = reinterpret_cast<T*>(&v);
+    for (int k0 = 0; k0 < cnt; k0 += 4) {
+      V a[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (k0 + q < cnt) a[q] = reinterpret_cast<const V*>(X + (long)(k0 + q) * ldx)[i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (k0 + q < cnt) {
+          const T* aa = reinterpret_cast<const T*>(&a[q]);
+#pragma unroll
+          for (int e = 0; e < VW; ++e) va[e] += sc[k0 + q] * aa[e];
+        }
+    }
+    y4[i] = v;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) acc.add(va[e], va[e]);
+  }
+  if (norm_partials) {
+    const double t = block_sum_t<T>(acc.get(), sh);
+    if (threadIdx.x == 0) norm_partials[blockIdx.x] = t;
+  }
+}
+
 // One warp per output; lanes add partials g = lane, lane + 32, ... then a
 // fixed shuffle tree.
 __global__ void k_reduce(const double* __restrict__ partials, int G, int nd, int stride,
@@ -336,6 +439,106 @@ k_gram_f32(const float* __restrict__ X, long ldx, int nx, const float* __restric
   }
 }
 
+// The same Gram register-blocked: thread b owns the 4 x 2 output block (rows
+// 4 bi .. 4 bi + 3 of X^T, columns 2 bj, 2 bj + 1 of Y) and sums its eight
+// products over a staged block of kGbRows rows in two-float registers (one
+// 16-byte and one 8-byte shared load per row for eight products, instead of two
+// scalar loads per product); each block's sums are then added, again in
+// two-float (Knuth's two-sum), into a per-CTA two-float accumulator in shared
+// memory, and the CTA's totals leave as FP64 partial sums. Every product is
+// exact (an FMA recovers its rounding error) and every addition keeps its
+// error: about 2^-46 of the sum of |x y|, at FP32 rates.
+constexpr int kGbRows = 64;
+
+__device__ __forceinline__ void tf_madd(float x, float y, float& hi, float& lo) {
+  const float p = __fmul_rn(x, y);
+  const float e = fmaf(x, y, -p);                          // x y - p exactly
+  const float t = __fadd_rn(hi, p);                        // two-sum: hi + p = t + d
+  const float bb = __fsub_rn(t, hi);
+  const float d = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  hi = t;
+  lo = __fadd_rn(lo, __fadd_rn(d, e));
+}
+
+// (H, L) += (h, l) in two-float
+__device__ __forceinline__ void tf_add(float& H, float& L, float h, float l) {
+  const float t = __fadd_rn(H, h);
+  const float bb = __fsub_rn(t, H);
+  const float d = __fadd_rn(__fsub_rn(H, __fsub_rn(t, bb)), __fsub_rn(h, bb));
+  H = t;
+  L = __fadd_rn(L, __fadd_rn(d, l));
+}
+
+__host__ __device__ constexpr size_t gram_blk_smem(int nxp, int nyp) {
+  return ((size_t)kGbRows * (nxp + nyp) + 2 * (size_t)nxp * nyp) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_gram_f32_blk(const float* __restrict__ X, long ldx, int nx, const float* __restrict__ Y, long ldy, int ny,
+               long n, long rows_per_cta, double* partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nxp = (nx + 3) & ~3, nyp = (ny + 1) & ~1;
+  float* Xs = reinterpret_cast<float*>(smem_raw);   // kGbRows x nxp
+  float* Ys = Xs + kGbRows * nxp;                    // kGbRows x nyp
+  float* Hs = Ys + kGbRows * nyp;                    // output column j at Hs + j nxp
+  float* Ls = Hs + (long)nyp * nxp;
+  const int nbi = nxp / 4, nblk = nbi * (nyp / 2);
+  for (int idx = threadIdx.x; idx < nyp * nxp; idx += kThreads) Hs[idx] = Ls[idx] = 0.f;
+  const long r0 = blockIdx.x * rows_per_cta;
+  const long r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
+  for (long rb = r0; rb < r1; rb += kGbRows) {
+    __syncthreads();   // the previous block's reads are done
+    for (int idx = threadIdx.x; idx < kGbRows * nxp; idx += kThreads) {
+      const int k = idx / kGbRows, rr = idx - k * kGbRows;
+      const long row = rb + rr;
+      Xs[rr * nxp + k] = (k < nx && row < r1) ? X[(long)k * ldx + row] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < kGbRows * nyp; idx += kThreads) {
+      const int k = idx / kGbRows, rr = idx - k * kGbRows;
+      const long row = rb + rr;
+      Ys[rr * nyp + k] = (k < ny && row < r1) ? Y[(long)k * ldy + row] : 0.f;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nblk; b += kThreads) {
+      const int bi = b % nbi, bj = b / nbi;
+      float hi[8], lo[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0.f;
+#pragma unroll 4
+      for (int rr = 0; rr < kGbRows; ++rr) {
+        const float4 x = *reinterpret_cast<const float4*>(Xs + rr * nxp + 4 * bi);
+        const float2 y = *reinterpret_cast<const float2*>(Ys + rr * nyp + 2 * bj);
+        tf_madd(x.x, y.x, hi[0], lo[0]);
+        tf_madd(x.y, y.x, hi[1], lo[1]);
+        tf_madd(x.z, y.x, hi[2], lo[2]);
+        tf_madd(x.w, y.x, hi[3], lo[3]);
+        tf_madd(x.x, y.y, hi[4], lo[4]);
+        tf_madd(x.y, y.y, hi[5], lo[5]);
+        tf_madd(x.z, y.y, hi[6], lo[6]);
+        tf_madd(x.w, y.y, hi[7], lo[7]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        float4* H4 = reinterpret_cast<float4*>(Hs + (long)(2 * bj + jj) * nxp + 4 * bi);
+        float4* L4 = reinterpret_cast<float4*>(Ls + (long)(2 * bj + jj) * nxp + 4 * bi);
+        float4 h = *H4, l = *L4;
+        tf_add(h.x, l.x, hi[4 * jj], lo[4 * jj]);
+        tf_add(h.y, l.y, hi[4 * jj + 1], lo[4 * jj + 1]);
+        tf_add(h.z, l.z, hi[4 * jj + 2], lo[4 * jj + 2]);
+        tf_add(h.w, l.w, hi[4 * jj + 3], lo[4 * jj + 3]);
+        *H4 = h;
+        *L4 = l;
+      }
+    }
+  }
+  __syncthreads();
+  const int nout = nx * ny;
+  for (int o = threadIdx.x; o < nout; o += kThreads) {
+    const int i = o % nx, j = o / nx;
+    partials[(long)blockIdx.x * nout + o] = (double)Hs[(long)j * nxp + i] + (double)Ls[(long)j * nxp + i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 data in two-float arithmetic (the stabilize's panel products)
 // ---------------------------------------------------------------------------
@@ -553,8 +756,14 @@ template <typename T>
 cudaError_t multidot(const T* X, long ldx, const int* cnt_dev, int cnt_host, const T* extra,
                      const T* y, long n, double* partials, int stride, cudaStream_t s,
                      const int* stop) {
-  k_multidot<T><<<red_grid(n), kThreads, 0, s>>>(X, ldx, cnt_dev, cnt_host, extra, y, n, partials,
-                                                 stride, stop);
+  constexpr int VW = V16<T>::n;
+  auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; };
+  if (n % VW == 0 && ldx % VW == 0 && al(X) && al(extra) && al(y))
+    k_multidot_v<T><<<red_grid(n), kThreads, 0, s>>>(X, ldx, cnt_dev, cnt_host, extra, y, n, partials, stride,
+                                                     stop);
+  else
+    k_multidot<T><<<red_grid(n), kThreads, 0, s>>>(X, ldx, cnt_dev, cnt_host, extra, y, n, partials,
+                                                   stride, stop);
   return launched();
 }
 
@@ -571,8 +780,14 @@ template <typename T>
 cudaError_t multi_axpy(const T* X, long ldx, const int* cnt_dev, int cnt_host, const double* c,
                        double sign, T* y, long n, double* norm_partials, cudaStream_t s,
                        const int* stop) {
-  k_multi_axpy<T><<<red_grid(n), kThreads, 0, s>>>(X, ldx, cnt_dev, cnt_host, c, sign, y, n,
-                                                   norm_partials, stop);
+  constexpr int VW = V16<T>::n;
+  auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; };
+  if (n % VW == 0 && ldx % VW == 0 && al(X) && al(y))
+    k_multi_axpy_v<T><<<red_grid(n), kThreads, 0, s>>>(X, ldx, cnt_dev, cnt_host, c, sign, y, n, norm_partials,
+                                                       stop);
+  else
+    k_multi_axpy<T><<<red_grid(n), kThreads, 0, s>>>(X, ldx, cnt_dev, cnt_host, c, sign, y, n,
+                                                     norm_partials, stop);
   return launched();
 }
 
@@ -618,6 +833,28 @@ cudaError_t gemm_ts(const TX* X, long ldx, int nx, const double* C, int ldc, int
   return launched();
 }
 
+template <typename TX, typename TY>
+cudaError_t gemm_ts_cols(const TX* X, long ldx, int nx, const double* C, int ldc, int ny, double beta,
+                         TY* Y, long ldy, long n, cudaStream_t s) {
+  if (ny <= 0) return cudaSuccess;
+  constexpr int NB = 16;
+  using A = typename GemmAcc<TX>::type;
+  const size_t smem = (size_t)nx * NB * sizeof(A);
+  if (smem > 96 * 1024) return cudaErrorInvalidValue;
+  static size_t attr = 0;
+  if (smem > attr) {
+    RK_TRY(cudaFuncSetAttribute(k_gemm_ts_blk<TX, TY, A, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+    attr = smem;
+  }
+  k_gemm_ts_blk<TX, TY, A, NB><<<ew_grid(n), kThreads, smem, s>>>(X, ldx, nx, C, ldc, ny, beta, Y, ldy, n);
+  return launched();
+}
+template cudaError_t gemm_ts_cols<float, double>(const float*, long, int, const double*, int, int, double,
+                                                 double*, long, long, cudaStream_t);
+template cudaError_t gemm_ts_cols<double, double>(const double*, long, int, const double*, int, int, double,
+                                                  double*, long, long, cudaStream_t);
+
 template <typename T>
 cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,
                  double* partials, double* out, cudaStream_t s) {
@@ -630,6 +867,30 @@ cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, lon
   int chunk = (kThreads * kGramAcc) / nx;
   if (chunk > 1500 - nx) chunk = 1500 - nx;   // shared memory: 16 (nx + chunk) doubles <= 192 KB
   if (sizeof(T) == 4 && chunk > 700 - nx) chunk = 700 - nx;   // 64 (nx + chunk) floats <= 175 KB
+  if constexpr (sizeof(T) == 4) {
+    // register-blocked two-float kernel: Y in chunks whose accumulators fit in shared memory
+    const int nxp = (nx + 3) & ~3;
+    int cb = (kThreads * kGramAcc) / nx;   // the partials hold kThreads * kGramAcc outputs per CTA
+    while (cb > 2 && gram_blk_smem(nxp, (cb + 1) & ~1) > 200 * 1024) --cb;
+    if (nx <= 256 && cb >= 2 && gram_blk_smem(nxp, (cb + 1) & ~1) <= 200 * 1024) {
+      const long rows_b = (rows + kGbRows - 1) / kGbRows * kGbRows;
+      static size_t attr = 0;
+      for (int j0 = 0; j0 < ny; j0 += cb) {
+        const int nyc = (ny - j0 < cb) ? ny - j0 : cb;
+        const size_t smem = gram_blk_smem(nxp, (nyc + 1) & ~1);
+        if (smem > attr) {
+          RK_TRY(cudaFuncSetAttribute(k_gram_f32_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          attr = smem;
+        }
+        k_gram_f32_blk<<<G, kThreads, smem, s>>>(reinterpret_cast<const float*>(X), ldx, nx,
+                                                 reinterpret_cast<const float*>(Y) + (long)j0 * ldy, ldy, nyc, n,
+                                                 rows_b, partials);
+        RK_TRY(launched());
+        RK_TRY(reduce_partials(partials, G, nx * nyc, nx * nyc, out + (long)j0 * nx, s, nullptr, 0, nullptr));
+      }
+      return cudaSuccess;
+    }
+  }
   for (int j0 = 0; j0 < ny; j0 += chunk) {
     const int nyc = (ny - j0 < chunk) ? ny - j0 : chunk;
     if constexpr (sizeof(T) == 4) {

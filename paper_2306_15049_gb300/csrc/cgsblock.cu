@@ -35,6 +35,7 @@ struct CgsB {
   int reset;       // 1: start from an empty Q (count 0)
   long n;
   int chunk;
+  int vec;         // 1: Q columns 16-byte aligned with ldq a multiple of the vector width
 };
 
 template <typename T>
@@ -120,6 +121,94 @@ __device__ __forceinline__ T cta_axpy(const T* Q, long ldq, int s, const T* cf, 
   return nrm;
 }
 
+// 16-byte vector forms of cta_dots and cta_axpy (Q aligned, ldq a multiple of the
+// vector width; chunk starts c0 are multiples of 4): four vector loads in flight
+// per lane or thread instead of scalar pairs. The rows past the last whole vector
+// of the CTA's range are taken one by one.
+template <typename T> struct VecC;
+template <> struct VecC<float> { using type = float4; static constexpr int n = 4; };
+template <> struct VecC<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ T vdot(const typename VecC<T>::type& q, const typename VecC<T>::type& b, T a) {
+  if constexpr (VecC<T>::n == 4) {
+    a += q.x * b.x; a += q.y * b.y; a += q.z * b.z; a += q.w * b.w;
+  } else {
+    a += q.x * b.x; a += q.y * b.y;
+  }
+  return a;
+}
+
+template <typename T>
+__device__ __forceinline__ void cta_dots_v(const T* Q, long ldq, int s, const T* bs, long c0, int len,
+                                           T* part, int G) {
+  using V = typename VecC<T>::type;
+  constexpr int VW = VecC<T>::n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nvec = len / VW;
+  const V* bv = reinterpret_cast<const V*>(bs);
+  for (int k = warp; k < s; k += kW) {
+    const T* qs = Q + (long)k * ldq + c0;
+    const V* q = reinterpret_cast<const V*>(qs);
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int e = lane;
+    for (; e + 96 < nvec; e += 128) {
+      const V q0 = q[e], q1 = q[e + 32], q2 = q[e + 64], q3 = q[e + 96];
+      a0 = vdot<T>(q0, bv[e], a0);
+      a1 = vdot<T>(q1, bv[e + 32], a1);
+      a2 = vdot<T>(q2, bv[e + 64], a2);
+      a3 = vdot<T>(q3, bv[e + 96], a3);
+    }
+    for (; e < nvec; e += 32) a0 = vdot<T>(q[e], bv[e], a0);
+    for (int i = nvec * VW + lane; i < len; i += 32) a1 += qs[i] * bs[i];
+    const T t = warp_sum_v<T>((a0 + a1) + (a2 + a3));
+    if (lane == 0) part[(long)k * G + blockIdx.x] = t;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T cta_axpy_v(const T* Q, long ldq, int s, const T* cf, T* bs, long c0, int len) {
+  using V = typename VecC<T>::type;
+  constexpr int VW = VecC<T>::n;
+  const int nvec = len / VW;
+  V* bv = reinterpret_cast<V*>(bs);
+  const T* q0p = Q + c0;
+  T nrm = T(0);
+  for (int e = threadIdx.x; e < nvec; e += kThreads) {
+    V v = bv[e];
+    T* va = reinterpret_cast<T*>(&v);
+    int k = 0;
+    for (; k + 3 < s; k += 4) {
+      const V x0 = reinterpret_cast<const V*>(q0p + (long)k * ldq)[e];
+      const V x1 = reinterpret_cast<const V*>(q0p + (long)(k + 1) * ldq)[e];
+      const V x2 = reinterpret_cast<const V*>(q0p + (long)(k + 2) * ldq)[e];
+      const V x3 = reinterpret_cast<const V*>(q0p + (long)(k + 3) * ldq)[e];
+      const T* a = reinterpret_cast<const T*>(&x0);
+      const T* b = reinterpret_cast<const T*>(&x1);
+      const T* c = reinterpret_cast<const T*>(&x2);
+      const T* d = reinterpret_cast<const T*>(&x3);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) va[i] -= (cf[k] * a[i] + cf[k + 1] * b[i]) + (cf[k + 2] * c[i] + cf[k + 3] * d[i]);
+    }
+    for (; k < s; ++k) {
+      const V x0 = reinterpret_cast<const V*>(q0p + (long)k * ldq)[e];
+      const T* a = reinterpret_cast<const T*>(&x0);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) va[i] -= cf[k] * a[i];
+    }
+    bv[e] = v;
+#pragma unroll
+    for (int i = 0; i < VW; ++i) nrm += va[i] * va[i];
+  }
+  for (int i = nvec * VW + threadIdx.x; i < len; i += kThreads) {
+    T v = bs[i];
+    for (int k = 0; k < s; ++k) v -= cf[k] * q0p[(long)k * ldq + i];
+    bs[i] = v;
+    nrm += v * v;
+  }
+  return nrm;
+}
+
 // thread 0 gets the CTA sum of v
 template <typename T>
 __device__ __forceinline__ T cta_sum(T v, T* red) {
@@ -168,20 +257,23 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_block(CgsB<T> a, GridBar* bar
     }
     t = cta_sum<T>(t, red);   // ends with bs visible to the CTA
     if (threadIdx.x == 0) part[(long)s * G + blockIdx.x] = t;
-    cta_dots<T>(a.Q, a.ldq, s, bs, c0, len, part, G);
+    if (a.vec) cta_dots_v<T>(a.Q, a.ldq, s, bs, c0, len, part, G);
+    else cta_dots<T>(a.Q, a.ldq, s, bs, c0, len, part, G);
     if (!grid_sync(bar, (++nb) * G, &ok_s)) return;
     reduce_rows<T>(part, G, s + 1, c1);
     const double nb2 = c.nb_in ? c.nb_in[j] : (double)c1[s];
     // ---- S2: b -= Q c1, c2 = Q^T b
     part = part0 + (long)(nb & 1) * region;
-    cta_axpy<T>(a.Q, a.ldq, s, c1, bs, c0, len);
+    if (a.vec) cta_axpy_v<T>(a.Q, a.ldq, s, c1, bs, c0, len);
+    else cta_axpy<T>(a.Q, a.ldq, s, c1, bs, c0, len);
     __syncthreads();
-    cta_dots<T>(a.Q, a.ldq, s, bs, c0, len, part, G);
+    if (a.vec) cta_dots_v<T>(a.Q, a.ldq, s, bs, c0, len, part, G);
+    else cta_dots<T>(a.Q, a.ldq, s, bs, c0, len, part, G);
     if (!grid_sync(bar, (++nb) * G, &ok_s)) return;
     reduce_rows<T>(part, G, s, c2);
     // ---- S3: b -= Q c2, ||b||^2
     part = part0 + (long)(nb & 1) * region;
-    t = cta_axpy<T>(a.Q, a.ldq, s, c2, bs, c0, len);
+    t = a.vec ? cta_axpy_v<T>(a.Q, a.ldq, s, c2, bs, c0, len) : cta_axpy<T>(a.Q, a.ldq, s, c2, bs, c0, len);
     t = cta_sum<T>(t, red);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
     if (!grid_sync(bar, (++nb) * G, &ok_s)) return;
@@ -270,7 +362,8 @@ cudaError_t cgs2_block(const CgsCtx& c, T* Q, long ldq, T* B, long ldb, int ncan
   RK_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs2_block<T>, kThreads, smem));
   if ((long)per_sm * sms < G) return cudaSuccess;
   RK_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBar), s));
-  CgsB<T> a{c, Q, ldq, B, ldb, ncand, reset, n, (int)chunk};
+  const int vec = (ldq % VecC<T>::n) == 0 && (reinterpret_cast<unsigned long long>(Q) & 15ull) == 0;
+  CgsB<T> a{c, Q, ldq, B, ldb, ncand, reset, n, (int)chunk, vec};
   GridBar* b = bar;
   void* args[] = {&a, &b};
   RK_TRY(cudaLaunchCooperativeKernel((const void*)k_cgs2_block<T>, dim3((unsigned)G), dim3(kThreads),

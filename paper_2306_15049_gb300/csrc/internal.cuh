@@ -79,6 +79,13 @@ template <typename T>
 cudaError_t op_apply(const T* x, long ldx, int ncols, const T* w, T* y, T* y2, long ldy,
                      int H, int W, const Taps& tp, double gamma, int mode, cudaStream_t s,
                      const int* stop = nullptr);
+// matvec_df.cu: xh + xl = x (h = fl32(x), l = fl32(x - h)), n values.
+cudaError_t split_df(const double* x, float* xh, float* xl, long n, cudaStream_t s);
+// y = (A + gamma E) x (mode 0) in two-float arithmetic from the split x and w (2n),
+// FP64 out; radius 4, 6, 8, 10 or 12 (op_apply_df_supported), blur operator only.
+bool op_apply_df_supported(int radius);
+cudaError_t op_apply_df(const float* xh, const float* xl, const float* wh, const float* wl, double* y, int H,
+                        int W, const Taps& tp, double gamma, cudaStream_t s);
 // y = H x (adjoint = 0) or y = H^T x (adjoint = 1), FP64.
 cudaError_t blur_apply(const double* x, double* y, int H, int W, const Taps& tp, int adjoint,
                        cudaStream_t s);
@@ -140,6 +147,12 @@ cudaError_t multi_axpy(const T* X, long ldx, const int* cnt_dev, int cnt_host, c
 template <typename TX, typename TY>
 cudaError_t gemm_ts(const TX* X, long ldx, int nx, const double* C, int ldc, int ny, double beta,
                     TY* Y, long ldy, long n, cudaStream_t s);
+// The same product with every output column taken by the blocked kernel (X read
+// once per 16 columns): a column's arithmetic does not depend on how many
+// columns one call computes. nx <= 1536 (FP64) or 6144 (FP32).
+template <typename TX, typename TY>
+cudaError_t gemm_ts_cols(const TX* X, long ldx, int nx, const double* C, int ldc, int ny, double beta,
+                         TY* Y, long ldy, long n, cudaStream_t s);
 // out (nx x ny, column-major, FP64) = X^T Y; partials needs 152 * min(nx*ny, 8192) doubles.
 template <typename T>
 cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,

@@ -82,11 +82,20 @@ def test_batched_launch_agrees_with_shift_by_shift_solves_at_512():
         pr = _pair(wl, 1, batch)
         outs.append(_steps(pr, w))
         assert (pr.P.rs_get_info()["minres_kernel"] == 3) == batch
+    bnorm = np.linalg.norm(pr.b)
     for k in range(2):
         (Xb, sb), (Xs, ss) = outs[0][k], outs[1][k]
         for l in range(wl.M):
             assert sb[l]["relres_true"] <= wl.tol, (k, l, sb[l])
-            assert rel(Xb[l], Xs[l]) <= 1e-4, (k, l, rel(Xb[l], Xs[l]))
+            assert ss[l]["relres_true"] <= wl.tol, (k, l, ss[l])
+            e = rel(Xb[l], Xs[l])
+            if e > 1e-4:
+                # two solutions to a relative residual of 1e-8 differ by at most 2e-8 |b| in
+                # the residual norm; the forward difference of the smallest shifts is that
+                # times the condition number of (A + gamma E) (gamma = 1e-5 here)
+                dr = pr.op.apply(Xb[l] - Xs[l], pr.gammas[l], w[k])
+                assert np.linalg.norm(dr) <= 2 * wl.tol * bnorm * (1 + 1e-6), (k, l, e)
+                assert e <= 1e-3, (k, l, e)
             assert sb[l]["iters"] <= 1.2 * ss[l]["iters"] + 10, (k, l, sb[l]["iters"], ss[l]["iters"])
 
 

@@ -111,3 +111,54 @@ def test_two_pass_operator_matches_oracle(h, w, sigma, r, precision):
         pr.P.rs_apply_operator(0.0, xt, y, y2, mode=1, working_precision=wp)
         assert rel(pr.n(y), pr.op.apply_A(x)) < tol
         assert rel(pr.n(y2), pr.op.apply_E(x, wts)) < tol
+
+
+@pytest.mark.parametrize("h,w,sigma,r", CASES2)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_float_operator_matches_oracle(h, w, sigma, r, precision):
+    """Mode 5: (A + gamma E) x in two-float arithmetic (the true residuals of mixed
+    precision) within 1e-12 of the FP64 oracle, for every even radius of the
+    two-pass form and images smaller than the radius."""
+    wl = synth.tiny(h, w, sigma=sigma, radius=r, M=4, p=4, n_ritz_local=1, seed=h * 3 + w)
+    pr = Pair(wl, precision=precision, x_image=synth.random_vectors(h * w, 1, 2 * h + w)[:, 0])
+    n = h * w
+    wts = synth.random_weights(n, 5, lo=1.0, hi=300.0)
+    pr.P.rs_set_weights(pr.t(wts))
+    x = np.random.default_rng(h * w + 1).standard_normal(n)
+    xt = pr.t(x)
+    y = pr.torch.empty_like(xt)
+    for gamma in [1e-6, 0.3, 7.0]:
+        pr.P.rs_apply_operator(gamma, xt, y, mode=5)
+        assert rel(pr.n(y), pr.op.apply(x, gamma, wts)) < 1e-12, gamma
+
+
+def test_two_float_residual_at_full_workload_size():
+    """512 x 512, radius 8: a residual b - (A + gamma E) x a billion times smaller
+    than (A + gamma E) x keeps its leading digits when the product is taken in
+    two-float arithmetic (what the refinement of mixed precision needs)."""
+    wl = synth.C2
+    pr = Pair(wl, precision=1)
+    n = wl.n
+    wts = synth.random_weights(n, 11, lo=1.0, hi=1000.0)
+    pr.P.rs_set_weights(pr.t(wts))
+    x = synth.piecewise_constant_image(wl.height, wl.width, 78).reshape(-1)
+    gamma = 1e-4
+    ax = pr.op.apply(x, gamma, wts)
+    delta = 1e-9 * np.linalg.norm(ax) / np.sqrt(n) * np.random.default_rng(3).standard_normal(n)
+    b = ax + delta
+    y = pr.torch.empty(n, dtype=pr.torch.float64, device=pr.dev)
+    pr.P.rs_apply_operator(gamma, pr.t(x), y, mode=5)
+    r_gpu = b - pr.n(y)
+    assert rel(pr.n(y), ax) < 1e-13
+    assert rel(r_gpu, delta) < 1e-3
+
+
+def test_two_float_mode_rejects_the_radon_operator():
+    from paper_2306_15049_gb300.recyc import RecycError
+    wl = synth.tiny(24, 24, M=4, p=4, n_ritz_local=1, radon_angles=12)
+    pr = Pair(wl)
+    pr.P.rs_set_weights(pr.t(np.ones(2 * wl.n)))
+    xt = pr.t(np.ones(wl.n))
+    y = pr.torch.empty_like(xt)
+    with pytest.raises(RecycError):
+        pr.P.rs_apply_operator(0.1, xt, y, mode=5)
