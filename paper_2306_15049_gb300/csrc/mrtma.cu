@@ -167,6 +167,7 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
   __shared__ float red[NWARP][kDots];
   __shared__ double sc[5];
   __shared__ int ok_s;
+  __shared__ int tma_bad;   // a tensor copy of this CTA did not complete in time
   __shared__ __align__(8) unsigned long long mbar[2];
   float* base = reinterpret_cast<float*>((reinterpret_cast<unsigned long long>(smem_raw) + 127ull) & ~127ull);
   float* const stage0 = base;
@@ -182,6 +183,7 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
   load_state<NT>(st, ss);
   const float gam = float(__ldcg(p.gamma));
   if (threadIdx.x == 0) {
+    tma_bad = 0;
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -226,13 +228,16 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
       const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
       const int i0 = tyi * kTileH, j0 = txi * kTileW;
       float* S = b ? stage1 : stage0;
-      const bool ok = mbar_wait_bounded(&mbar[b], (b ? ph1 : ph0) & 1u);
-      if (b) ++ph1; else ++ph0;
-      if (threadIdx.x == 0) { if (b) issued1 = false; else issued0 = false; }
-      if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicExch(&bar->err, 3);
-        failed = true;
-        break;
+      // every thread waits for the stage itself (observing the completed phase makes
+      // the copied data visible to it); a copy that timed out marks the CTA, which
+      // finishes the tile on whatever the stage holds and leaves after its barrier
+      volatile int* bad = &tma_bad;
+      const bool ok = *bad == 0 && mbar_wait_bounded(&mbar[b], (b ? ph1 : ph0) & 1u);
+      if (ok) {
+        if (b) ++ph1; else ++ph0;
+        if (threadIdx.x == 0) { if (b) issued1 = false; else issued0 = false; }
+      } else {
+        *bad = 1;
       }
       const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
       const int gj = j0 + tx;
@@ -279,6 +284,11 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
       // the stage is refilled after every generic access to it is fenced and done
       fence_proxy_async_smem();
       __syncthreads();
+      if (*bad) {   // the same value in every thread after the barrier
+        if (threadIdx.x == 0) atomicExch(&bar->err, 3);
+        failed = true;
+        break;
+      }
       if (threadIdx.x == 0 && i + 2 < mine) {
         issue_tile<R>(maps, S, &mbar[b], t + 2 * (int)G, tiles_x, H, j, withv, s);
         if (b) issued1 = true; else issued0 = true;
