@@ -98,8 +98,8 @@ k_multidot(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host,
   }
 }
 
-// The same dots from 16-byte vector loads, four columns per pass over y (y is
-// read once per group of four columns, and each thread has five loads in flight
+// The same dots from 16-byte vector loads, eight columns per pass over y (y is
+// read once per group of eight columns, and each thread has nine loads in flight
 // instead of one scalar pair). Needs n and ldx multiples of the vector width and
 // 16-byte aligned vectors (the host checks; k_multidot takes the rest).
 template <typename T> struct V16;
@@ -124,31 +124,32 @@ k_multidot_v(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host
   if (stop && *stop) return;
   using V = typename V16<T>::type;
   constexpr int VW = V16<T>::n;
+  constexpr int CG = 8;   // columns per pass: nine 16-byte loads in flight per thread
   __shared__ double sh[kThreads / 32];
   const int cnt = cnt_dev ? *cnt_dev : cnt_host;
   const int nd = cnt + (extra ? 1 : 0);
   const long nv = n / VW;
   const V* y4 = reinterpret_cast<const V*>(y);
-  for (int k0 = 0; k0 < nd; k0 += 4) {
-    const V* xs[4];
+  for (int k0 = 0; k0 < nd; k0 += CG) {
+    const V* xs[CG];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < CG; ++c) {
       const int k = k0 + c;
       xs[c] = reinterpret_cast<const V*>(k < cnt ? X + (long)k * ldx : extra);
     }
-    Acc<T> acc[4];
+    Acc<T> acc[CG];
     for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < nv; i += (long)gridDim.x * kThreads) {
       const V b = y4[i];
-      V a[4];
+      V a[CG];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < CG; ++c)
         if (k0 + c < nd) a[c] = xs[c][i];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < CG; ++c)
         if (k0 + c < nd) vdot_acc<T>(a[c], b, acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < CG; ++c) {
       if (k0 + c < nd) {
         const double t = block_sum_t<T>(acc[c].get(), sh);
         if (threadIdx.x == 0) partials[(long)blockIdx.x * stride + k0 + c] = t;
@@ -178,13 +179,13 @@ k_multi_axpy_v(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_ho
   for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < nv; i += (long)gridDim.x * kThreads) {
     V v = y4[i];
     T* va = reinterpret_cast<T*>(&v);
-    for (int k0 = 0; k0 < cnt; k0 += 4) {
-      V a[4];
+    for (int k0 = 0; k0 < cnt; k0 += 8) {
+      V a[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 8; ++q)
         if (k0 + q < cnt) a[q] = reinterpret_cast<const V*>(X + (long)(k0 + q) * ldx)[i];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 8; ++q)
         if (k0 + q < cnt) {
           const T* aa = reinterpret_cast<const T*>(&a[q]);
 #pragma unroll

@@ -59,30 +59,52 @@ struct StageLayout {
   }
 };
 
-// The tensor copies of tile t into stage `st` (one thread). with_v: the four
-// direction-update vectors of step j (not on the first step of a launch, where
-// no direction update is pending).
+constexpr int kIssueParts = 8;   // tensor copies per tile, one per issuing warp
+
+// Copy `part` of tile t into a stage (0: u with its 2R halo; 1, 2: the w_x and w_y
+// rows; 3-6: v_{j-1}, d_{j-2}, d_{j-3}, x_m when with_v, the direction update of step
+// j being due; 7: the s columns of K as one 3-D box), issued by lane 0 of warp
+// `part`. The stage's mbarrier expects kIssueParts arrivals: each issuing lane posts
+// its own byte count with its arrival before its copy, so the phase completes only
+// once all parts have arrived and every byte has landed. Spreading the copies over
+// eight warps keeps any one warp (and the CTA barrier that waits for it) from
+// holding for the time the tensor-copy unit takes to accept all of them.
 template <int R>
-__device__ __forceinline__ void issue_tile(const TmaMaps& maps, float* stage, unsigned long long* bar,
+__device__ __forceinline__ void issue_part(int part, const TmaMaps& maps, float* stage, unsigned long long* bar,
                                            int t, int tiles_x, int H, int j, bool with_v, int s) {
   using L = StageLayout<R>;
   const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
   const int i0 = tyi * kTileH, j0 = txi * kTileW;
   constexpr unsigned kTile = kTileH * kTileW * sizeof(float);
-  const unsigned bytes = (unsigned)(L::AH * L::AW * sizeof(float)) + 2u * kWRow * kWRows * sizeof(float) +
-                         (with_v ? 4u * kTile : 0u) + (unsigned)s * kTile;
-  mbar_expect_tx(bar, bytes);
-  tma_load_2d(stage + L::kU, &maps.u, j0 - 2 * R, i0 - 2 * R, bar);
-  tma_load_2d(stage + L::kW, &maps.w, j0 - 4, i0, bar);                       // w_x rows i0..
-  tma_load_2d(stage + L::kW + kWPlane, &maps.w, j0 - 4, H + i0 - 1, bar);     // w_y rows i0-1..
-  if (with_v) {
-    // v_{j-1} (never v_0 here: j - 1 >= 1 on every step after a launch's first)
-    tma_load_2d(stage + L::kV, &maps.v[(j - 1) % 3], j0, i0, bar);
-    tma_load_2d(stage + L::kV + 1024, &maps.d[((j - 2) % 3 + 3) % 3], j0, i0, bar);
-    tma_load_2d(stage + L::kV + 2048, &maps.d[((j - 3) % 3 + 3) % 3], j0, i0, bar);
-    tma_load_2d(stage + L::kV + 3072, &maps.xm, j0, i0, bar);
+  constexpr unsigned kWBox = kWRow * kWRows * sizeof(float);
+  if (part == 0) {
+    mbar_expect_tx(bar, (unsigned)(L::AH * L::AW * sizeof(float)));
+    tma_load_2d(stage + L::kU, &maps.u, j0 - 2 * R, i0 - 2 * R, bar);
+  } else if (part == 1) {
+    mbar_expect_tx(bar, kWBox);
+    tma_load_2d(stage + L::kW, &maps.w, j0 - 4, i0, bar);                       // w_x rows i0..
+  } else if (part == 2) {
+    mbar_expect_tx(bar, kWBox);
+    tma_load_2d(stage + L::kW + kWPlane, &maps.w, j0 - 4, H + i0 - 1, bar);     // w_y rows i0-1..
+  } else if (part <= 6) {
+    if (!with_v) {
+      mbar_arrive(bar);
+    } else {
+      // v_{j-1} (never v_0 here: j - 1 >= 1 on every step after a launch's first)
+      mbar_expect_tx(bar, kTile);
+      const CUtensorMap* m = part == 3 ? &maps.v[(j - 1) % 3]
+                           : part == 4 ? &maps.d[((j - 2) % 3 + 3) % 3]
+                           : part == 5 ? &maps.d[((j - 3) % 3 + 3) % 3] : &maps.xm;
+      tma_load_2d(stage + L::kV + 1024 * (part - 3), m, j0, i0, bar);
+    }
+  } else {
+    if (s > 0) {
+      mbar_expect_tx(bar, (unsigned)s * kTile);
+      tma_load_3d(stage + L::kK, &maps.K, j0, i0, 0, bar);
+    } else {
+      mbar_arrive(bar);
+    }
   }
-  if (s > 0) tma_load_3d(stage + L::kK, &maps.K, j0, i0, 0, bar);
 }
 
 // Phase A of one tile from a filled stage: E v and the four blur passes of A v
@@ -184,8 +206,8 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
   const float gam = float(__ldcg(p.gamma));
   if (threadIdx.x == 0) {
     tma_bad = 0;
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    mbar_init(&mbar[0], kIssueParts);
+    mbar_init(&mbar[1], kIssueParts);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -205,10 +227,15 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
   // from the second step of the launch on (and on the first if a previous launch
   // of the same solve left one pending)
   bool withv = ss.dir_pending != 0;
-  if (threadIdx.x == 0) {
+  const int ipart = (threadIdx.x & 31) == 0 && (threadIdx.x >> 5) < kIssueParts ? (int)(threadIdx.x >> 5) : -1;
+  if (ipart >= 0) {
     fence_proxy_async_global();
-    if (mine > 0) { issue_tile<R>(maps, stage0, &mbar[0], (int)blockIdx.x, tiles_x, H, j, withv, s); issued0 = true; }
-    if (mine > 1) { issue_tile<R>(maps, stage1, &mbar[1], (int)blockIdx.x + (int)G, tiles_x, H, j, withv, s); issued1 = true; }
+    if (mine > 0) issue_part<R>(ipart, maps, stage0, &mbar[0], (int)blockIdx.x, tiles_x, H, j, withv, s);
+    if (mine > 1) issue_part<R>(ipart, maps, stage1, &mbar[1], (int)blockIdx.x + (int)G, tiles_x, H, j, withv, s);
+  }
+  if (threadIdx.x == 0) {
+    issued0 = mine > 0;
+    issued1 = mine > 1;
   }
   unsigned long long nb = 0;
   bool failed = false;
@@ -220,7 +247,7 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
     float* dout = ptr.d(j - 1);
     float* vj = ptr.v(j);
     const float scale = cf.inv_beta_next;
-    const float de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau;
+    const float de = cf.delta, ep = cf.eps, ig = cf.inv_gamma, tau = cf.tau, cbeta = cf.beta;
     // ---------------- phase A: tiles from the stages ----------------
     for (int i = 0; i < mine; ++i) {
       const int b = i & 1;
@@ -263,6 +290,7 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
           tile_operator<R, NT>(S + L::kU, bufB, S + L::kW, S + L::kW + kWPlane, tf, scale, i0, j0, H, W, ax,
                                ex, vc);
         const float* Ks = S + L::kK;
+        const float* Vp = S + L::kV;   // v_{j-1} where the direction-update vectors are staged
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
           const int ti = ty * PPT + q, gi = i0 + ti;
@@ -270,7 +298,8 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
           yk[q] = in ? ax[q] + gam * ex[q] : 0.f;
           if (in) {
             const long g = (long)gi * W + gj;
-            p.y[g] = yk[q];
+            // y - beta_j v_{j-1} when v_{j-1} is at hand: phase B then skips reading it
+            p.y[g] = withv ? yk[q] - cbeta * Vp[ti * kTileW + tx] : yk[q];
             vj[g] = vc[q];
             acc[kMaxLocal] += vc[q] * yk[q];
           }
@@ -289,9 +318,9 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
         failed = true;
         break;
       }
-      if (threadIdx.x == 0 && i + 2 < mine) {
-        issue_tile<R>(maps, S, &mbar[b], t + 2 * (int)G, tiles_x, H, j, withv, s);
-        if (b) issued1 = true; else issued0 = true;
+      if (i + 2 < mine) {
+        if (ipart >= 0) issue_part<R>(ipart, maps, S, &mbar[b], t + 2 * (int)G, tiles_x, H, j, withv, s);
+        if (threadIdx.x == 0) { if (b) issued1 = true; else issued0 = true; }
       }
     }
     if (failed || stopped) break;
@@ -316,7 +345,8 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
           if (k < s) kv[k] = reinterpret_cast<const float4*>(p.K + (long)k * p.ldk)[iv];
         const float4 yv = __ldcg(reinterpret_cast<const float4*>(p.y) + iv);
         const float4 vv = __ldcg(reinterpret_cast<const float4*>(vj) + iv);
-        const float4 pv = __ldcg(reinterpret_cast<const float4*>(vprev) + iv);
+        // phase A stored y - beta v_{j-1} whenever it had v_{j-1} staged
+        const float4 pv = withv ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcg(reinterpret_cast<const float4*>(vprev) + iv);
         const float* ya = reinterpret_cast<const float*>(&yv);
         const float* va = reinterpret_cast<const float*>(&vv);
         const float* pa = reinterpret_cast<const float*>(&pv);
@@ -350,14 +380,15 @@ k_mr_tma(MinresState* st, MrP<float> p, const __grid_constant__ TmaMaps maps, co
     // u, v_j, d and x_m of this step are read by tensor copies after the barrier
     fence_proxy_async_global();
     if (!grid_sync(bar, (++nb) * G, &ok_s)) { failed = true; break; }
-    if (threadIdx.x == 0) {
+    if (ipart >= 0) {
       fence_proxy_async_global();
       // the next step's direction update needs v_j, d_{j-1}, d_{j-2}, x_m (j >= 1)
-      if (mine > 0) { issue_tile<R>(maps, stage0, &mbar[0], (int)blockIdx.x, tiles_x, H, j + 1, true, s); issued0 = true; }
-      if (mine > 1) {
-        issue_tile<R>(maps, stage1, &mbar[1], (int)blockIdx.x + (int)G, tiles_x, H, j + 1, true, s);
-        issued1 = true;
-      }
+      if (mine > 0) issue_part<R>(ipart, maps, stage0, &mbar[0], (int)blockIdx.x, tiles_x, H, j + 1, true, s);
+      if (mine > 1) issue_part<R>(ipart, maps, stage1, &mbar[1], (int)blockIdx.x + (int)G, tiles_x, H, j + 1, true, s);
+    }
+    if (threadIdx.x == 0) {
+      issued0 = mine > 0;
+      issued1 = mine > 1;
     }
     scalar_step<float, NT>(partB, G, hd, red, ss, cf, sc, p);
     ++j;
