@@ -570,9 +570,13 @@ __device__ __forceinline__ void d2f_madd(float xh, float xl, float yh, float yl,
 }
 
 // partials[blockIdx.x * nx * ny + i + j nx] = CTA's share of (X^T Y)[i, j] for X
-// given as its two-float split (Xh, Xl: nx columns of floats, x = h + l) and FP64
-// Y (ny <= kD2fCols columns): thread i of the CTA owns output row i (nx <=
-// kThreads) and all ny columns.
+// given as its two-float split (Xh, Xl: nx <= kThreads columns of floats, x = h + l)
+// and FP64 Y (ny <= kD2fCols columns). A thread owns one row i of the output and
+// four of its columns (consecutive threads: the four column groups of one row, so
+// every thread has work once nx >= kThreads / 4), up to four such blocks; it sums
+// each staged block of kD2fRows rows in two-float registers and adds the block
+// sums, again in two-float, into accumulators kept in registers across the CTA's
+// rows (FP64 only for the final partial sums).
 __global__ void __launch_bounds__(kThreads)
 k_gram_d2f(const float* __restrict__ XH, const float* __restrict__ XL, long ldx, int nx,
            const double* __restrict__ Y, long ldy, int ny, long n, long rows_per_cta, double* partials) {
@@ -581,10 +585,12 @@ k_gram_d2f(const float* __restrict__ XH, const float* __restrict__ XL, long ldx,
   float* Xl = Xh + kD2fRows * nx;
   float* Yh = Xl + kD2fRows * nx;                           // kD2fRows x kD2fCols
   float* Yl = Yh + kD2fRows * kD2fCols;
-  const int i = threadIdx.x;
-  double acc[kD2fCols];
+  constexpr int NG = 4;                                     // output blocks per thread
+  float H[NG][4], L[NG][4];
 #pragma unroll
-  for (int j = 0; j < kD2fCols; ++j) acc[j] = 0.0;
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) H[g][c] = L[g][c] = 0.f;
   const long r0 = blockIdx.x * rows_per_cta;
   const long r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
   for (long rb = r0; rb < r1; rb += kD2fRows) {
@@ -604,33 +610,37 @@ k_gram_d2f(const float* __restrict__ XH, const float* __restrict__ XL, long ldx,
       Yl[rr * kD2fCols + k] = l;
     }
     __syncthreads();
-    if (i < nx) {
-      float hi[kD2fCols], lo[kD2fCols];
 #pragma unroll
-      for (int j = 0; j < kD2fCols; ++j) hi[j] = lo[j] = 0.f;
-      for (int rr = 0; rr < kD2fRows; ++rr) {
-        const float xh = Xh[rr * nx + i], xl = Xl[rr * nx + i];
-        const float4* yh4 = reinterpret_cast<const float4*>(Yh + rr * kD2fCols);
-        const float4* yl4 = reinterpret_cast<const float4*>(Yl + rr * kD2fCols);
-#pragma unroll
-        for (int v = 0; v < kD2fCols / 4; ++v) {
-          const float4 a = yh4[v], c = yl4[v];
-          d2f_madd(xh, xl, a.x, c.x, hi[4 * v], lo[4 * v]);
-          d2f_madd(xh, xl, a.y, c.y, hi[4 * v + 1], lo[4 * v + 1]);
-          d2f_madd(xh, xl, a.z, c.z, hi[4 * v + 2], lo[4 * v + 2]);
-          d2f_madd(xh, xl, a.w, c.w, hi[4 * v + 3], lo[4 * v + 3]);
+    for (int g = 0; g < NG; ++g) {
+      const int o = threadIdx.x + g * kThreads, i = o >> 2, j4 = o & 3;
+      if (i < nx) {
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int rr = 0; rr < kD2fRows; ++rr) {
+          const float xh = Xh[rr * nx + i], xl = Xl[rr * nx + i];
+          const float4 a = reinterpret_cast<const float4*>(Yh + rr * kD2fCols)[j4];
+          const float4 c = reinterpret_cast<const float4*>(Yl + rr * kD2fCols)[j4];
+          d2f_madd(xh, xl, a.x, c.x, hi[0], lo[0]);
+          d2f_madd(xh, xl, a.y, c.y, hi[1], lo[1]);
+          d2f_madd(xh, xl, a.z, c.z, hi[2], lo[2]);
+          d2f_madd(xh, xl, a.w, c.w, hi[3], lo[3]);
         }
-      }
 #pragma unroll
-      for (int j = 0; j < kD2fCols; ++j) acc[j] += (double)hi[j] + (double)lo[j];
+        for (int c = 0; c < 4; ++c) tf_add(H[g][c], L[g][c], hi[c], lo[c]);
+      }
     }
     __syncthreads();
   }
-  if (i < nx) {
-    const int nout = nx * ny;
+  const int nout = nx * ny;
 #pragma unroll
-    for (int j = 0; j < kD2fCols; ++j)
-      if (j < ny) partials[(long)blockIdx.x * nout + i + (long)j * nx] = acc[j];
+  for (int g = 0; g < NG; ++g) {
+    const int o = threadIdx.x + g * kThreads, i = o >> 2, j4 = o & 3;
+    if (i < nx) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = 4 * j4 + c;
+        if (j < ny) partials[(long)blockIdx.x * nout + i + (long)j * nx] = (double)H[g][c] + (double)L[g][c];
+      }
+    }
   }
 }
 
