@@ -686,7 +686,7 @@ void graph_timing_flush(rs_problem* P, int gi, int j0, int iters_done, double by
 // operator applications and timing records are not counted.
 struct TuneCache {
   std::mutex mu;
-  std::map<std::array<int, 5>, int> best;
+  std::map<std::array<int, 4>, int> best;
 };
 TuneCache& tune_cache() {
   static TuneCache c;
@@ -709,7 +709,9 @@ int tuned_variant(rs_problem* P, double gamma, const T* r, bool use_K, int s_hos
   if (mr_resident_applies<T>(P->d.height, P->d.width, P->tp.r, s_alloc)) return RS_OK;
   int dev = 0;
   CU(cudaGetDevice(&dev));
-  const std::array<int, 5> key{dev, P->d.height, P->d.width, P->tp.r, s_alloc};
+  // one pick per image shape: every streaming solve of the shape runs the same variant
+  // whatever its local dimension (the trials use the first such solve's)
+  const std::array<int, 4> key{dev, P->d.height, P->d.width, P->tp.r};
   {
     std::lock_guard<std::mutex> lock(tune_cache().mu);
     auto it = tune_cache().best.find(key);
