@@ -1175,11 +1175,11 @@ int finish_principal_body(rs_problem* P, int ncand) {
   // Gram blocks
   const T* bT = vp<T>(P->mixed ? P->bT : (void*)P->b);
   CU(gram<T>(Kp, ld, ncn, EU, ld, ncn, n, P->partials, P->G_KE, s));
-  CU(gram<T>(EU, ld, ncn, EU, ld, ncn, n, P->partials, P->G_EE, s));
+  CU(gram_sym<T>(EU, ld, EU, ld, ncn, n, P->partials, P->G_EE, s));
   CU(gram<T>(EU, ld, ncn, bT, ld, 1, n, P->partials, P->G_Eb, s));
   CU(gram<T>(Kp, ld, ncn, bT, ld, 1, n, P->partials, P->Ktb, s));
-  CU(gram<T>(Ut, ld, ncn, AU, ld, ncn, n, P->partials, P->Ah, s));
-  CU(gram<T>(Ut, ld, ncn, EU, ld, ncn, n, P->partials, P->Eh, s));
+  CU(gram_sym<T>(Ut, ld, AU, ld, ncn, n, P->partials, P->Ah, s));   // U~^T A U~
+  CU(gram_sym<T>(Ut, ld, EU, ld, ncn, n, P->partials, P->Eh, s));   // U~^T E U~
   PrincipalSmall ps{P->Rp, P->G_KE, P->G_EE, P->G_Eb, P->Mm, P->Nm, P->UtEb};
   CU(principal_small(ps, ncn, P->T1, s));
   if (P->d.guess == RS_GUESS_ORTHOGONAL) {

@@ -476,7 +476,7 @@ __host__ __device__ constexpr size_t gram_blk_smem(int nxp, int nyp) {
 
 __global__ void __launch_bounds__(kThreads)
 k_gram_f32_blk(const float* __restrict__ X, long ldx, int nx, const float* __restrict__ Y, long ldy, int ny,
-               long n, long rows_per_cta, double* partials) {
+               long n, long rows_per_cta, double* partials, int sym_j0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nxp = (nx + 3) & ~3, nyp = (ny + 1) & ~1;
   float* Xs = reinterpret_cast<float*>(smem_raw);   // kGbRows x nxp
@@ -502,6 +502,9 @@ k_gram_f32_blk(const float* __restrict__ X, long ldx, int nx, const float* __res
     __syncthreads();
     for (int b = threadIdx.x; b < nblk; b += kThreads) {
       const int bi = b % nbi, bj = b / nbi;
+      // a symmetric product (sym_j0 >= 0: output column j is column sym_j0 + j of the
+      // whole): blocks wholly below the diagonal are left to the mirror
+      if (sym_j0 >= 0 && 4 * bi > sym_j0 + 2 * bj + 1) continue;
       float hi[8], lo[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0.f;
@@ -866,9 +869,33 @@ template cudaError_t gemm_ts_cols<float, double>(const float*, long, int, const 
 template cudaError_t gemm_ts_cols<double, double>(const double*, long, int, const double*, int, int, double,
                                                   double*, long, long, cudaStream_t);
 
+// out[i + j nx] = out[j + i nx] for i > j (the lower triangle from the upper)
+__global__ void k_mirror_upper(double* out, int nx) {
+  for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < nx * nx; idx += blockDim.x * gridDim.x) {
+    const int i = idx % nx, j = idx / nx;
+    if (i > j) out[idx] = out[j + (long)i * nx];
+  }
+}
+
+template <typename T>
+cudaError_t gram_impl(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,
+                      double* partials, double* out, cudaStream_t s, bool sym);
+
 template <typename T>
 cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,
                  double* partials, double* out, cudaStream_t s) {
+  return gram_impl<T>(X, ldx, nx, Y, ldy, ny, n, partials, out, s, false);
+}
+
+template <typename T>
+cudaError_t gram_sym(const T* X, long ldx, const T* Y, long ldy, int nx, long n, double* partials, double* out,
+                     cudaStream_t s) {
+  return gram_impl<T>(X, ldx, nx, Y, ldy, nx, n, partials, out, s, true);
+}
+
+template <typename T>
+cudaError_t gram_impl(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,
+                      double* partials, double* out, cudaStream_t s, bool sym) {
   // out (nx x ny, column-major) = X^T Y; Y is split into column chunks so that
   // one CTA holds at most kThreads * kGramAcc outputs.
   if (nx <= 0 || ny <= 0) return cudaSuccess;
@@ -895,9 +922,13 @@ cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, lon
         }
         k_gram_f32_blk<<<G, kThreads, smem, s>>>(reinterpret_cast<const float*>(X), ldx, nx,
                                                  reinterpret_cast<const float*>(Y) + (long)j0 * ldy, ldy, nyc, n,
-                                                 rows_b, partials);
+                                                 rows_b, partials, sym ? j0 : -1);
         RK_TRY(launched());
         RK_TRY(reduce_partials(partials, G, nx * nyc, nx * nyc, out + (long)j0 * nx, s, nullptr, 0, nullptr));
+      }
+      if (sym) {
+        k_mirror_upper<<<8, 256, 0, s>>>(out, nx);
+        RK_TRY(launched());
       }
       return cudaSuccess;
     }
@@ -1003,6 +1034,8 @@ cudaError_t check_finite(const double* x, long n, int sign, int* ok_dev, cudaStr
                                      long, double*, cudaStream_t, const int*);                   \
   template cudaError_t gram<T>(const T*, long, int, const T*, long, int, long, double*, double*,  \
                                cudaStream_t);                                                     \
+  template cudaError_t gram_sym<T>(const T*, long, const T*, long, int, long, double*, double*,   \
+                                   cudaStream_t);                                                 \
   template cudaError_t scale_dev<T>(const T*, T*, long, const double*, int, const int*,           \
                                     cudaStream_t);                                                \
   template cudaError_t norm2_partials<T>(const T*, long, double*, cudaStream_t);

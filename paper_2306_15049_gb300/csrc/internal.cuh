@@ -153,6 +153,12 @@ cudaError_t gemm_ts(const TX* X, long ldx, int nx, const double* C, int ldc, int
 template <typename TX, typename TY>
 cudaError_t gemm_ts_cols(const TX* X, long ldx, int nx, const double* C, int ldc, int ny, double beta,
                          TY* Y, long ldy, long n, cudaStream_t s);
+// out (nx x nx) = X^T Y for a product known to be symmetric in exact arithmetic
+// (X^T A X with Y = A X, A symmetric): FP32 data computes the upper triangle and
+// mirrors it; FP64 data computes every entry.
+template <typename T>
+cudaError_t gram_sym(const T* X, long ldx, const T* Y, long ldy, int nx, long n, double* partials, double* out,
+                     cudaStream_t s);
 // out (nx x ny, column-major, FP64) = X^T Y; partials needs 152 * min(nx*ny, 8192) doubles.
 template <typename T>
 cudaError_t gram(const T* X, long ldx, int nx, const T* Y, long ldy, int ny, long n,
