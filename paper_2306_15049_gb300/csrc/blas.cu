@@ -106,14 +106,15 @@ template <typename T> struct V16;
 template <> struct V16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct V16<double> { using type = double2; static constexpr int n = 2; };
 
+// sum_e q_e b_e added to p in element order (one FMA each)
 template <typename T>
-__device__ __forceinline__ void vdot_acc(const typename V16<T>::type& a, const typename V16<T>::type& b,
-                                         Acc<T>& acc) {
+__device__ __forceinline__ T vdot_part(const typename V16<T>::type& a, const typename V16<T>::type& b, T p) {
   if constexpr (V16<T>::n == 4) {
-    acc.add(a.x, b.x); acc.add(a.y, b.y); acc.add(a.z, b.z); acc.add(a.w, b.w);
+    p = fma(a.x, b.x, p); p = fma(a.y, b.y, p); p = fma(a.z, b.z, p); p = fma(a.w, b.w, p);
   } else {
-    acc.add(a.x, b.x); acc.add(a.y, b.y);
+    p = fma(a.x, b.x, p); p = fma(a.y, b.y, p);
   }
+  return p;
 }
 
 template <typename T>
@@ -137,7 +138,14 @@ k_multidot_v(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host
       const int k = k0 + c;
       xs[c] = reinterpret_cast<const V*>(k < cnt ? X + (long)k * ldx : extra);
     }
-    Acc<T> acc[CG];
+    // per column a running sum in T flushed into FP64 every 8 products (the cadence
+    // of Acc<float>, one decision per pair of vectors instead of one per product;
+    // FP64 data keeps a single FMA chain, as Acc<double>)
+    T part[CG];
+    double tot[CG];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) { part[c] = T(0); tot[c] = 0.0; }
+    int it = 0;
     for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < nv; i += (long)gridDim.x * kThreads) {
       const V b = y4[i];
       V a[CG];
@@ -146,12 +154,16 @@ k_multidot_v(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_host
         if (k0 + c < nd) a[c] = xs[c][i];
 #pragma unroll
       for (int c = 0; c < CG; ++c)
-        if (k0 + c < nd) vdot_acc<T>(a[c], b, acc[c]);
+        if (k0 + c < nd) part[c] = vdot_part<T>(a[c], b, part[c]);
+      if (sizeof(T) == 4 && ((++it) * VW) % 8 == 0) {   // FP64 data: one FMA chain, as Acc<double>
+#pragma unroll
+        for (int c = 0; c < CG; ++c) { tot[c] += (double)part[c]; part[c] = T(0); }
+      }
     }
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
       if (k0 + c < nd) {
-        const double t = block_sum_t<T>(acc[c].get(), sh);
+        const double t = block_sum_t<T>(tot[c] + (double)part[c], sh);
         if (threadIdx.x == 0) partials[(long)blockIdx.x * stride + k0 + c] = t;
       }
     }
@@ -179,13 +191,13 @@ k_multi_axpy_v(const T* __restrict__ X, long ldx, const int* cnt_dev, int cnt_ho
   for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < nv; i += (long)gridDim.x * kThreads) {
     V v = y4[i];
     T* va = reinterpret_cast<T*>(&v);
-    for (int k0 = 0; k0 < cnt; k0 += 8) {
-      V a[8];
+    for (int k0 = 0; k0 < cnt; k0 += 4) {
+      V a[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < 4; ++q)
         if (k0 + q < cnt) a[q] = reinterpret_cast<const V*>(X + (long)(k0 + q) * ldx)[i];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < 4; ++q)
         if (k0 + q < cnt) {
           const T* aa = reinterpret_cast<const T*>(&a[q]);
 #pragma unroll
