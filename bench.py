@@ -482,7 +482,8 @@ class Job:
         return {"k": k, "solves": wl.M, "matvecs": info["matvecs_total"] - info0["matvecs_total"],
                 "iters": sum(s["iters"] for s in stats),
                 "worst_relres": max(s["relres_true"] for s in stats), "nc": info["nc"],
-                "minres_kernel": info["minres_kernel"], "kernel_launches": info["kernel_launches"],
+                "minres_kernel": info["minres_kernel"], "tuned_variant": info["tuned_variant"],
+                "kernel_launches": info["kernel_launches"],
                 "launches_before": info0["kernel_launches"], "lstar": ls}
 
 
@@ -514,7 +515,7 @@ def per_k(step_ms, res):
     return {str(k): round(sum(v) / len(v), 3) for k, v in sorted(out.items())}
 
 
-def roofline_entry(job, ms_total, minres_kernel, wl, precision, fp64_peak):
+def roofline_entry(job, ms_total, minres_kernel, wl, precision, fp64_peak, tuned_variant=-1):
     peaks, peak_kind = measured_peaks()
     tm = job.timing
     cat = 0 if tm["ms"][0] >= tm["ms"][1] else 1
@@ -527,6 +528,8 @@ def roofline_entry(job, ms_total, minres_kernel, wl, precision, fp64_peak):
     entry = {"kernel": kname, "launches": tm["launches"][cat],
              "avg_launch_us": tm["ms"][cat] * 1000.0 / launches,
              "kernel_time_share_of_step": tm["ms"][cat] / ms_total if ms_total > 0 else None}
+    if cat == 0 and minres_kernel == 2 and tuned_variant in (1, 2):
+        entry["stencil"] = "A as two autocorrelation passes" if tuned_variant == 2 else "A as four blur passes"
     steps = tm["pixels"][cat] / wl.n
     if cat == 0 and precision == "mixed" and minres_kernel != 1:
         achieved = tm["bytes"][cat] / (tm["ms"][cat] / 1000.0) / 1e9
@@ -923,16 +926,18 @@ def main():
                 "matvecs_per_solve": mvs / max(1, solves),
                 "minres_iters_per_solve": sum(r["iters"] for r in res) / max(1, solves),
                 "worst_true_relres": max(r["worst_relres"] for r in res), "n_c": res[-1]["nc"],
+                "tuned_variant": res[-1]["tuned_variant"],
                 "phases_ms_per_step": {k: v / args.steps for k, v in job.timing["phase_ms"].items()}},
         "gpu_launches": int(launches_timed), "clocks": clocks,
-        "roofline": roofline_entry(job, ms, res[-1]["minres_kernel"], wl, args.precision, fp64_peak),
+        "roofline": roofline_entry(job, ms, res[-1]["minres_kernel"], wl, args.precision, fp64_peak,
+                                   res[-1]["tuned_variant"]),
         "fp64_fma_peak": {"value": fp64_peak[0] / 1e3, "unit": "TFLOP/s", "source": fp64_peak[1]},
     }
 
     if not args.no_e2e:
         job.prepare_e2e()
         job.h2d = job.d2h = 0
-        e_ms, _, e_res, _ = run_steps(job, args.steps, e2e=True)
+        e_ms, e_step_ms, e_res, _ = run_steps(job, args.steps, e2e=True)
         e_solves = sum(r["solves"] for r in e_res)
         if dist:
             e_ms, (e_solves,) = reduce_over_ranks(dist, e_ms, [e_solves], dev)
@@ -941,7 +946,10 @@ def main():
                        "what": "data image (at k = 0) and weights w_k copied in from pinned host memory, all "
                                "solutions x^(k,.) and w_{k+1} copied back into pinned host memory, every step; "
                                "the solutions of each block of 16 shifts on a copy stream while the next block "
-                               "solves, the step ending when every copy has landed"}
+                               "solves, the step ending when every copy has landed",
+                       "ms_per_outer_step_by_k": per_k(e_step_ms, e_res),
+                       "matvecs_per_solve": sum(r["matvecs"] for r in e_res) /
+                       max(1, sum(r["solves"] for r in e_res))}
     job.restart()
 
     if world == 1 and rank == 0:

@@ -296,10 +296,11 @@ rs_status rs_get_principal_basis(rs_problem* prob, double* U_dev, int* nc_host);
  * in two-float arithmetic (mode 5: each FP64 value carried as a pair of floats,
  * every product and sum with its rounding error kept, about 2^-44 relative; blur
  * operator with an even radius 4..12, else RS_EINVAL; the true residuals of
- * mixed-precision problems are computed this way). Otherwise x, y, y2 are
- * n doubles on the device, computed in the problem's working precision for modes
- * 0-2 when use_working_precision is 1, else in FP64. Counts as one matvec
- * (modes 0-2, 5). */
+ * mixed-precision problems are computed this way), or y = H x in the same
+ * two-float arithmetic (mode 6: the blur, same radii; the misfit of the L-curve
+ * of mixed-precision problems). Otherwise x, y, y2 are n doubles on the device,
+ * computed in the problem's working precision for modes 0-2 when
+ * use_working_precision is 1, else in FP64. Counts as one matvec (modes 0-2, 5). */
 rs_status rs_apply_operator(rs_problem* prob, double gamma, const double* x_dev,
                             double* y_dev, double* y2_dev, int mode,
                             int use_working_precision);

@@ -2508,10 +2508,10 @@ rs_status rs_apply_operator(rs_problem* P, double gamma, const double* x_dev, do
                             double* y2_dev, int mode, int use_working_precision) {
   if (!P) return RS_EINVAL;
   if (!x_dev || !y_dev || (mode == 1 && !y2_dev)) return (rs_status)P->set_err(RS_EINVAL, "NULL vector");
-  if (mode < 0 || mode > 5) return (rs_status)P->set_err(RS_EINVAL, "mode must be 0..5");
+  if (mode < 0 || mode > 6) return (rs_status)P->set_err(RS_EINVAL, "mode must be 0..6");
   if ((mode < 3 || mode == 5) && P->k < 0) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_set_weights first");
-  if (mode == 5 && (P->tp.radon.nang > 0 || !op_apply_df_supported(P->tp.r)))
-    return (rs_status)P->set_err(RS_EINVAL, "mode 5 needs the blur operator with an even radius 4..12");
+  if (mode >= 5 && (P->tp.radon.nang > 0 || !op_apply_df_supported(P->tp.r)))
+    return (rs_status)P->set_err(RS_EINVAL, "modes 5 and 6 need the blur operator with an even radius 4..12");
   const long n = P->z.n, ld = P->z.ld;
   const int H = P->d.height, W = P->d.width;
   if (mode == 3) {
@@ -2522,6 +2522,9 @@ rs_status rs_apply_operator(rs_problem* P, double gamma, const double* x_dev, do
     CU(split_df(x_dev, P->xdh, P->xdl, n, P->s));
     CU(op_apply_df(P->xdh, P->xdl, P->wdh, P->wdl, y_dev, H, W, P->tp, gamma, P->s));
     P->mv_total += 1;
+  } else if (mode == 6) {
+    CU(split_df(x_dev, P->xdh, P->xdl, n, P->s));
+    CU(blur_apply_df(P->xdh, P->xdl, y_dev, H, W, P->tp, P->s));
   } else if (P->mixed && use_working_precision) {
     float* xf = (float*)P->u;
     float* yf = (float*)P->y;
@@ -2568,7 +2571,13 @@ rs_status rs_lcurve(rs_problem* P, const double* X_dev, int count, double* rho_h
   const long n = P->z.n;
   for (int l = 0; l < count; ++l) {
     const double* x = X_dev + (long)l * n;
-    CU(forward_apply(P, x, P->t64));
+    if (P->mixed && P->use_df && P->tp.radon.nang == 0 && op_apply_df_supported(P->tp.r)) {
+      // mixed precision: H x in two-float arithmetic (FP64-level accuracy at FP32 rates)
+      CU(split_df(x, P->xdh, P->xdl, n, P->s));
+      CU(blur_apply_df(P->xdh, P->xdl, P->t64, P->d.height, P->d.width, P->tp, P->s));
+    } else {
+      CU(forward_apply(P, x, P->t64));
+    }
     CU(residual64(P->dimg, P->t64, nullptr, P->z.m, P->partials, P->s));
     CU(reduce_partials(P->partials, P->z.G, 1, 1, P->lc + l, P->s, nullptr, 0, nullptr));
     CU(wgrad_norm2_partials(x, P->w64, P->d.height, P->d.width, P->partials, P->z.G, P->s));

@@ -86,6 +86,9 @@ cudaError_t split_df(const double* x, float* xh, float* xl, long n, cudaStream_t
 bool op_apply_df_supported(int radius);
 cudaError_t op_apply_df(const float* xh, const float* xl, const float* wh, const float* wl, double* y, int H,
                         int W, const Taps& tp, double gamma, cudaStream_t s);
+// y = H x (the blur) in the same two-float arithmetic from the split x; the same radii.
+cudaError_t blur_apply_df(const float* xh, const float* xl, double* y, int H, int W, const Taps& tp,
+                          cudaStream_t s);
 // y = H x (adjoint = 0) or y = H^T x (adjoint = 1), FP64.
 cudaError_t blur_apply(const double* x, double* y, int H, int W, const Taps& tp, int adjoint,
                        cudaStream_t s);

@@ -237,6 +237,97 @@ cudaError_t launch_df(const float* xh, const float* xl, const float* wh, const f
   return launched();
 }
 
+// The blur y = H x (FP64 out) in the same two-float arithmetic: H = T_h (x) T_w as
+// two 1-D passes of the taps g (2R + 1) over the tile and a halo of R (the
+// misfit ||H x - d|| of the L-curve).
+template <int R>
+struct TapsG {
+  float gh[2 * R + 1], gl[2 * R + 1];
+};
+
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_blur_df(const float* __restrict__ xh, const float* __restrict__ xl, double* __restrict__ y, int H, int W,
+          const TapsG<R> tp) {
+  constexpr int AH = kTileH + 2 * R, AW = kTileW + 2 * R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Sh = reinterpret_cast<float*>(smem_raw);   // AH x AW
+  float* Sl = Sh + AH * AW;
+  float* Ph = Sl + AH * AW;                          // AH x 32
+  float* Pl = Ph + AH * kTileW;
+  const int i0 = blockIdx.y * kTileH, j0 = blockIdx.x * kTileW;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int idx = threadIdx.x; idx < AH * AW; idx += kThreads) {
+    const int a = idx / AW, c = idx - a * AW;
+    const int gi = i0 - R + a, gj = j0 - R + c;
+    const bool in = gi >= 0 && gi < H && gj >= 0 && gj < W;
+    const long g = in ? (long)gi * W + gj : 0;
+    Sh[idx] = in ? xh[g] : 0.f;
+    Sl[idx] = in ? xl[g] : 0.f;
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < AH * (kTileW / 4); item += kThreads) {
+    const int a = item / (kTileW / 4), c0 = 4 * (item % (kTileW / 4));
+    float oh[4] = {0.f, 0.f, 0.f, 0.f}, ol[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int v = 0; v < (2 * R + 4) / 4; ++v) {
+      const float4 h4 = reinterpret_cast<const float4*>(Sh + a * AW + c0)[v];
+      const float4 l4 = reinterpret_cast<const float4*>(Sl + a * AW + c0)[v];
+      const float xe[4] = {h4.x, h4.y, h4.z, h4.w}, le[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int t = 4 * v + e - q;
+          if (t >= 0 && t <= 2 * R) df_madd(tp.gh[t], tp.gl[t], xe[e], le[e], oh[q], ol[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) df_norm(oh[q], ol[q]);
+    *reinterpret_cast<float4*>(Ph + a * kTileW + c0) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+    *reinterpret_cast<float4*>(Pl + a * kTileW + c0) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+  }
+  __syncthreads();
+  float ah[kPPT], al[kPPT];
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) ah[q] = al[q] = 0.f;
+#pragma unroll
+  for (int e = 0; e < kPPT + 2 * R; ++e) {
+    const int a = ty * kPPT + e;
+    const float vh = Ph[a * kTileW + tx], vl = Pl[a * kTileW + tx];
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      const int t = e - q;
+      if (t >= 0 && t <= 2 * R) df_madd(tp.gh[t], tp.gl[t], vh, vl, ah[q], al[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) {
+    const int gi = i0 + ty * kPPT + q, gj = j0 + tx;
+    if (gi < H && gj < W) {
+      df_norm(ah[q], al[q]);
+      y[(long)gi * W + gj] = (double)ah[q] + (double)al[q];
+    }
+  }
+}
+
+template <int R>
+cudaError_t launch_blur_df(const float* xh, const float* xl, double* y, int H, int W, const Taps& tp,
+                           cudaStream_t s) {
+  constexpr int AH = kTileH + 2 * R, AW = kTileW + 2 * R;
+  const size_t smem = (2 * (size_t)AH * AW + 2 * (size_t)AH * kTileW) * sizeof(float);
+  static int cached = 0;
+  RK_TRY(ensure_smem(k_blur_df<R>, smem, &cached));
+  TapsG<R> t{};
+  for (int k = 0; k <= 2 * R; ++k) {
+    t.gh[k] = (float)tp.g[k];
+    t.gl[k] = (float)(tp.g[k] - (double)t.gh[k]);
+  }
+  const dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
+  k_blur_df<R><<<grid, kThreads, smem, s>>>(xh, xl, y, H, W, t);
+  return launched();
+}
+
 }  // namespace
 
 bool op_apply_df_supported(int radius) {
@@ -249,6 +340,18 @@ cudaError_t split_df(const double* x, float* xh, float* xl, long n, cudaStream_t
   if (g < 1) g = 1;
   k_split_df<<<(unsigned)g, kThreads, 0, s>>>(x, xh, xl, n);
   return launched();
+}
+
+cudaError_t blur_apply_df(const float* xh, const float* xl, double* y, int H, int W, const Taps& tp,
+                          cudaStream_t s) {
+  switch (tp.r) {
+    case 4: return launch_blur_df<4>(xh, xl, y, H, W, tp, s);
+    case 6: return launch_blur_df<6>(xh, xl, y, H, W, tp, s);
+    case 8: return launch_blur_df<8>(xh, xl, y, H, W, tp, s);
+    case 10: return launch_blur_df<10>(xh, xl, y, H, W, tp, s);
+    case 12: return launch_blur_df<12>(xh, xl, y, H, W, tp, s);
+    default: return cudaErrorNotSupported;
+  }
 }
 
 cudaError_t op_apply_df(const float* xh, const float* xl, const float* wh, const float* wl, double* y, int H,

@@ -117,8 +117,9 @@ def test_two_pass_operator_matches_oracle(h, w, sigma, r, precision):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_two_float_operator_matches_oracle(h, w, sigma, r, precision):
     """Mode 5: (A + gamma E) x in two-float arithmetic (the true residuals of mixed
-    precision) within 1e-12 of the FP64 oracle, for every even radius of the
-    two-pass form and images smaller than the radius."""
+    precision), and mode 6: H x alone (the L-curve misfit), within 1e-12 of the
+    FP64 oracle, for every even radius of the two-pass form and images smaller
+    than the radius."""
     wl = synth.tiny(h, w, sigma=sigma, radius=r, M=4, p=4, n_ritz_local=1, seed=h * 3 + w)
     pr = Pair(wl, precision=precision, x_image=synth.random_vectors(h * w, 1, 2 * h + w)[:, 0])
     n = h * w
@@ -130,6 +131,9 @@ def test_two_float_operator_matches_oracle(h, w, sigma, r, precision):
     for gamma in [1e-6, 0.3, 7.0]:
         pr.P.rs_apply_operator(gamma, xt, y, mode=5)
         assert rel(pr.n(y), pr.op.apply(x, gamma, wts)) < 1e-12, gamma
+    # mode 6: the blur H x alone (the misfit of the L-curve)
+    pr.P.rs_apply_operator(0.0, xt, y, mode=6)
+    assert rel(pr.n(y), pr.op.blur(x)) < 1e-12
 
 
 def test_two_float_residual_at_full_workload_size():
@@ -160,5 +164,28 @@ def test_two_float_mode_rejects_the_radon_operator():
     pr.P.rs_set_weights(pr.t(np.ones(2 * wl.n)))
     xt = pr.t(np.ones(wl.n))
     y = pr.torch.empty_like(xt)
-    with pytest.raises(RecycError):
-        pr.P.rs_apply_operator(0.1, xt, y, mode=5)
+    for mode in (5, 6):
+        with pytest.raises(RecycError):
+            pr.P.rs_apply_operator(0.1, xt, y, mode=mode)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lcurve_points_match_oracle_in_both_precisions(precision):
+    """Section 2.2's L-curve of given solutions: rho_l = ||H x_l - d|| (the blur in
+    two-float arithmetic under mixed precision, in FP64 otherwise) and eta_l =
+    ||w^(1/2) .* L x_l|| match the oracle, and so does the corner. The misfit is
+    about 1e-2 of ||H x||, so the two-float product (about 2^-44 of ||H x||)
+    leaves it about 1e-11 relative; FP32 would leave 1e-5."""
+    from oracle.outer import lcurve_corner, lcurve_points
+    wl = synth.tiny(70, 130, sigma=3.0, radius=10, M=6, p=4, n_ritz_local=1, seed=5)
+    pr = Pair(wl, precision=precision)
+    wts = synth.random_weights(wl.n, 9, lo=0.5, hi=50.0)
+    pr.P.rs_set_weights(pr.t(wts))
+    # solutions near the data at a range of distances: points along an L-shape
+    rng = np.random.default_rng(17)
+    X = np.stack([pr.x_true + s * rng.standard_normal(wl.n) for s in np.geomspace(1e-3, 1.0, wl.M)])
+    rho, eta, ls = pr.P.rs_lcurve(pr.t(X), wl.M)
+    rho_o, eta_o = lcurve_points(pr.op, X, pr.d, wts)
+    np.testing.assert_allclose(rho, rho_o, rtol=1e-10)
+    np.testing.assert_allclose(eta, eta_o, rtol=1e-12)
+    assert ls == lcurve_corner(rho_o, eta_o)
