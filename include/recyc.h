@@ -18,7 +18,11 @@
  *    workspace and the stream, and keeps them valid until the call returns
  *    (device buffers: until the work queued on the stream has finished).
  *  - The library never allocates device memory: all device state lives in
- *    the caller's workspace of rs_workspace_bytes() bytes.
+ *    the caller's workspace of rs_workspace_bytes() bytes. Each problem holds
+ *    64 KB of host-mapped pinned memory through which the library's own
+ *    synchronous reads of scalars and small arrays come back, written by a
+ *    kernel rather than copied, so they do not wait behind a caller's bulk
+ *    device-to-host copies on another stream.
  *  - Work is queued on the problem's stream. Calls that report results to
  *    the host (stats, counts) synchronise that stream.
  *  - A problem is not thread-safe; use one problem per stream. Launch shapes

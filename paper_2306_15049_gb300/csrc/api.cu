@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstddef>
 #include <map>
 #include <mutex>
 #include <cstdarg>
@@ -38,6 +39,7 @@ constexpr int kDotStride = kMaxLocal + 1;
 constexpr int kBatchTail = 2;               // batched solves: the last shifts run one by one
 constexpr int kChunk = 6;                  // MINRES steps per CUDA-graph replay (a multiple of 3)
 constexpr int kStabPanel = 16;             // candidates per panel of the blocked stabilize CGS2
+constexpr size_t kStageBytes = 64 * 1024;  // host-mapped staging of synchronous reads
 constexpr int kGuessBatch = 16;            // shifts whose initial guesses one pass over U~ computes
 constexpr int kTuneSteps = 24;             // MINRES steps of one autotuning trial
 
@@ -289,7 +291,7 @@ struct rs_problem {
   double *Ran[2] = {nullptr, nullptr}, *Man[2] = {nullptr, nullptr}, *Kban[2] = {nullptr, nullptr};
   double *G_KEan = nullptr, *Nscr = nullptr, *UtEbscr = nullptr;
   int *cnt = nullptr, *flag = nullptr, *kept = nullptr, *perm = nullptr, *status = nullptr;
-  int *poll = nullptr, *ok = nullptr, *lstar = nullptr;
+  int *ok = nullptr, *lstar = nullptr;
   MinresState* st = nullptr;
   size_t need = 0;
 
@@ -312,8 +314,14 @@ struct rs_problem {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // two instances: one runs while one is read
   cudaEvent_t gev[2][2 * kChunk] = {};
-  // pipelined stop-flag polls: pinned host slots and their events
+  // pipelined stop-flag polls: host-mapped pinned slots (written by the poll kernel
+  // through dpoll) and their events
   int* hpoll_pinned = nullptr;
+  int* dpoll = nullptr;
+  // host-mapped pinned staging of the library's synchronous reads (hstage on the
+  // host, dstage its device address): kernel stores, no copy engine
+  unsigned char* hstage = nullptr;
+  unsigned char* dstage = nullptr;
   cudaEvent_t pev[2] = {nullptr, nullptr};
   double* gcur = nullptr;
   double* partials_a = nullptr;
@@ -344,6 +352,7 @@ struct rs_problem {
     for (cudaEvent_t e : pev)
       if (e) cudaEventDestroy(e);
     if (hpoll_pinned) cudaFreeHost(hpoll_pinned);
+    if (hstage) cudaFreeHost(hstage);
     if (cap) cudaStreamDestroy(cap);
   }
 
@@ -442,7 +451,6 @@ void carve(rs_problem* P, Carver& cv) {
   P->kept = cv.take<int>(z.cmax + kMaxLocal);
   P->perm = cv.take<int>(z.cmax + 4);
   P->status = cv.take<int>(z.M);
-  P->poll = cv.take<int>(4);
   P->ok = cv.take<int>(4);
   P->lstar = cv.take<int>(4);
   P->st = cv.take<MinresState>(1);
@@ -515,7 +523,17 @@ void carve(rs_problem* P, Carver& cv) {
 template <typename T> T* vp(void* p) { return reinterpret_cast<T*>(p); }
 template <typename T> T* col(void* p, long j, long ld) { return reinterpret_cast<T*>(p) + j * ld; }
 
+// Synchronous read of device bytes: through the host-mapped staging buffer (a
+// kernel's stores) up to kStageBytes, so that it never waits behind bulk
+// device-to-host copies a caller runs on another stream (a copy engine serves its
+// copies in order: a read queued behind a copy of solutions waited for all of it).
 int read_back(rs_problem* P, void* host, const void* dev, size_t bytes) {
+  if (bytes <= kStageBytes) {
+    CU(stage_copy(P->dstage, dev, bytes, P->s));
+    CU(cudaStreamSynchronize(P->s));
+    std::memcpy(host, P->hstage, bytes);
+    return RS_OK;
+  }
   CU(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, P->s));
   CU(cudaStreamSynchronize(P->s));
   return RS_OK;
@@ -923,9 +941,11 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
       MinresState st;
       GridBar bar;
     } hs;
-    CU(cudaMemcpyAsync(&hs.st, P->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(&hs.bar, P->gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+    static_assert(sizeof hs <= kStageBytes, "staging buffer too small");
+    CU(stage_copy(P->dstage, P->st, sizeof(MinresState), s));
+    CU(stage_copy(P->dstage + offsetof(decltype(hs), bar), P->gbar, sizeof(GridBar), s));
     CU(cudaStreamSynchronize(s));
+    std::memcpy(&hs, P->hstage, sizeof hs);
     if (hs.bar.err == 2)
       return (rs_status)P->set_err(RS_ECUDA, "persistent MINRES kernel: local space wider than %d", s_host);
     if (hs.bar.err == 3)
@@ -968,8 +988,7 @@ int run_minres(rs_problem* P, double gamma, const T* r, bool use_K, double tol_a
         }
       }
     }
-    CU(minres_poll(P->st, P->poll, s));
-    CU(cudaMemcpyAsync(P->hpoll_pinned + 2 * c.slot, P->poll, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(minres_poll(P->st, P->dpoll + 2 * c.slot, s));
     CU(cudaEventRecord(P->pev[c.slot], s));
     next_slot ^= 1;
     inq[nq++] = c;
@@ -2191,10 +2210,13 @@ rs_status rs_create_problem(const rs_problem_desc* desc, const double* d_dev, vo
   Carver cv{(char*)workspace_dev};
   carve(P, cv);
   const long n = P->z.n;
-  if (cudaHostAlloc(&P->hpoll_pinned, 4 * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+  if (cudaHostAlloc(&P->hpoll_pinned, 4 * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&P->dpoll), P->hpoll_pinned, 0) != cudaSuccess ||
+      cudaHostAlloc(reinterpret_cast<void**>(&P->hstage), kStageBytes, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&P->dstage), P->hstage, 0) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->pev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->pev[1], cudaEventDisableTiming) != cudaSuccess) {
-    snprintf(g_err, sizeof g_err, "could not create the poll buffer / events");
+    snprintf(g_err, sizeof g_err, "could not create the poll / staging buffers or events");
     delete P;
     return RS_ECUDA;
   }

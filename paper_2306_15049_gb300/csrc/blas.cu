@@ -712,10 +712,47 @@ __global__ void k_split_d2f(const double* __restrict__ X, long ldx, int ncols, l
   }
 }
 
+// Device bytes into host-mapped pinned memory with plain stores (4-byte words
+// where both ends and the size allow): the library's synchronous reads of
+// scalars and small arrays then use no copy engine, so they never queue behind a
+// caller's bulk device-to-host copies on another stream.
+__global__ void k_stage_copy(const unsigned char* __restrict__ src, unsigned char* __restrict__ dst,
+                             long bytes, int words) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x, st = (long)gridDim.x * blockDim.x;
+  if (words) {
+    const unsigned int* s4 = reinterpret_cast<const unsigned int*>(src);
+    unsigned int* d4 = reinterpret_cast<unsigned int*>(dst);
+    for (long i = t; i < bytes / 4; i += st) d4[i] = s4[i];
+  } else {
+    for (long i = t; i < bytes; i += st) dst[i] = src[i];
+  }
+  __threadfence_system();
+}
+
 template <typename TX, typename TY>
 __global__ void k_axpby(const TX* __restrict__ x, double a, TY* __restrict__ y, double b, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     y[i] = TY(a * (double)x[i] + (b == 0.0 ? 0.0 : b * (double)y[i]));
+}
+
+// y = a x + b y on FP32 data in FP32 arithmetic, 16 bytes per access (the FP64
+// form of k_axpby is bound by GB300's FP64 rate on FP32 blocks of several columns)
+__global__ void __launch_bounds__(kThreads)
+k_axpby_f4(const float4* __restrict__ x, float a, float4* __restrict__ y, float b, long nv) {
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < nv; i += (long)gridDim.x * kThreads) {
+    const float4 u = x[i];
+    float4 v;
+    if (b == 0.f) {
+      v = make_float4(a * u.x, a * u.y, a * u.z, a * u.w);
+    } else {
+      v = y[i];
+      v.x = fmaf(a, u.x, b * v.x);
+      v.y = fmaf(a, u.y, b * v.y);
+      v.z = fmaf(a, u.z, b * v.z);
+      v.w = fmaf(a, u.w, b * v.w);
+    }
+    y[i] = v;
+  }
 }
 
 template <typename T>
@@ -1001,8 +1038,27 @@ cudaError_t split_d2f_cols(const double* X, long ldx, int ncols, long n, float* 
   return launched();
 }
 
+cudaError_t stage_copy(void* dst_mapped, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  const auto a4 = [](const void* p) { return (reinterpret_cast<unsigned long long>(p) & 3ull) == 0; };
+  const int words = (bytes % 4 == 0 && a4(src) && a4(dst_mapped)) ? 1 : 0;
+  const long units = words ? (long)bytes / 4 : (long)bytes;
+  const int blocks = (int)std::min<long>(8, (units + kThreads - 1) / kThreads);
+  k_stage_copy<<<blocks, kThreads, 0, s>>>(static_cast<const unsigned char*>(src),
+                                           static_cast<unsigned char*>(dst_mapped), (long)bytes, words);
+  return launched();
+}
+
 template <typename TX, typename TY>
 cudaError_t axpby(const TX* x, double a, TY* y, double b, long n, cudaStream_t s) {
+  if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4) {
+    auto al = [](const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; };
+    if (n % 4 == 0 && al(x) && al(y)) {
+      k_axpby_f4<<<ew_grid(n / 4), kThreads, 0, s>>>(reinterpret_cast<const float4*>(x), (float)a,
+                                                     reinterpret_cast<float4*>(y), (float)b, n / 4);
+      return launched();
+    }
+  }
   k_axpby<TX, TY><<<ew_grid(n), kThreads, 0, s>>>(x, a, y, b, n);
   return launched();
 }
@@ -1085,12 +1141,58 @@ k_gather_axpy(PtrList cand, const int* __restrict__ kept_idx, const int* __restr
     y[i] = v;
   }
 }
+
+// The same with 16-byte accesses and the loads of four columns issued before
+// their FMAs (every candidate column and y 16-byte aligned, n a multiple of the
+// vector width); each element adds its terms in the same order as k_gather_axpy.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gather_axpy_v(PtrList cand, const int* __restrict__ kept_idx, const int* __restrict__ cnt_dev,
+                const double* __restrict__ coef, T* __restrict__ y, long n) {
+  using V = typename V16<T>::type;
+  constexpr int VW = V16<T>::n;
+  __shared__ const V* cols[kMaxLocal];
+  __shared__ T sc[kMaxLocal];
+  const int cnt = *cnt_dev;
+  if (threadIdx.x < cnt) {
+    cols[threadIdx.x] = reinterpret_cast<const V*>(cand.p[kept_idx[threadIdx.x]]);
+    sc[threadIdx.x] = T(coef[threadIdx.x]);
+  }
+  __syncthreads();
+  const long nv = n / VW;
+  V* yv = reinterpret_cast<V*>(y);
+  for (long i = blockIdx.x * (long)kThreads + threadIdx.x; i < nv; i += (long)gridDim.x * kThreads) {
+    V v = yv[i];
+    T* va = reinterpret_cast<T*>(&v);
+    for (int k0 = 0; k0 < cnt; k0 += 4) {
+      V a[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (k0 + q < cnt) a[q] = cols[k0 + q][i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (k0 + q < cnt) {
+          const T* aa = reinterpret_cast<const T*>(&a[q]);
+#pragma unroll
+          for (int e = 0; e < VW; ++e) va[e] = fma(sc[k0 + q], aa[e], va[e]);
+        }
+    }
+    yv[i] = v;
+  }
+}
 }  // namespace
 
 template <typename T>
 cudaError_t gather_axpy(const PtrList& cand, const int* kept_idx, const int* cnt_dev,
                         const double* coef, T* y, long n, cudaStream_t s) {
-  k_gather_axpy<T><<<red_grid(n), kThreads, 0, s>>>(cand, kept_idx, cnt_dev, coef, y, n);
+  constexpr int VW = V16<T>::n;
+  bool vec = n % VW == 0 && (reinterpret_cast<unsigned long long>(y) & 15ull) == 0;
+  for (int k = 0; k < kMaxLocal && vec; ++k)
+    if (cand.p[k] && (reinterpret_cast<unsigned long long>(cand.p[k]) & 15ull) != 0) vec = false;
+  if (vec)
+    k_gather_axpy_v<T><<<red_grid(n), kThreads, 0, s>>>(cand, kept_idx, cnt_dev, coef, y, n);
+  else
+    k_gather_axpy<T><<<red_grid(n), kThreads, 0, s>>>(cand, kept_idx, cnt_dev, coef, y, n);
   return launched();
 }
 template cudaError_t gather_axpy<float>(const PtrList&, const int*, const int*, const double*,

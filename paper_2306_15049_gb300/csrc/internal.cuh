@@ -61,6 +61,9 @@ Taps make_taps(double sigma, int r);
 // Every kernel launch of the library goes through launched(): it returns the
 // launch status and counts the launch (process-wide, for the benchmark).
 cudaError_t launched();
+// bytes from device memory into host-mapped pinned memory (its device address)
+// with plain stores on the stream: no copy engine involved.
+cudaError_t stage_copy(void* dst_mapped, const void* src, size_t bytes, cudaStream_t s);
 long long launch_count();
 void add_launches(long long k);   // kernels replayed from a CUDA graph
 // Message returned by rs_last_error(NULL) (failures of calls without a problem).
@@ -315,6 +318,8 @@ cudaError_t lanczos_update(const MinresState* st, const T* K, long ldk, const do
 template <typename T>
 cudaError_t minres_direction(const MinresState* st, const T* u, T* vnext, const T* v,
                              const T* d1, const T* d2, T* d, T* xm, long n, cudaStream_t s);
+// (stop, iters) into out_dev2: two ints at a device address (the library passes
+// host-mapped pinned memory, read by the host after an event)
 cudaError_t minres_poll(const MinresState* st, int* out_dev2, cudaStream_t s);
 
 // ---------------------------------------------------------------- mrfused.cu

@@ -210,9 +210,11 @@ k_minres_direction(const MinresState* __restrict__ st, const T* __restrict__ u,
   }
 }
 
+// out: two ints of host-mapped pinned memory (the host reads them after an event)
 __global__ void k_poll(const MinresState* st, int* out) {
   out[0] = st->stop;
   out[1] = st->iters;
+  __threadfence_system();
 }
 
 }  // namespace
