@@ -13,7 +13,9 @@
 // A = H^T H is applied as the two 1-D passes of the autocorrelation taps with
 // the edge corrections (the form of op_tile2), E = L^T diag(w) L as the 5-point
 // difference stencil. x and w are split into float pairs by k_split_df first
-// (one FP64 subtraction per value instead of one per staged halo value).
+// (one FP64 subtraction per value instead of one per staged halo value). The
+// blur H x alone, for the misfit ||H x - d|| of the L-curve (Section 2.2), takes
+// the same arithmetic (k_blur_df).
 #include "internal.cuh"
 #include "optile.cuh"
 
@@ -237,9 +239,10 @@ cudaError_t launch_df(const float* xh, const float* xl, const float* wh, const f
   return launched();
 }
 
-// The blur y = H x (FP64 out) in the same two-float arithmetic: H = T_h (x) T_w as
-// two 1-D passes of the taps g (2R + 1) over the tile and a halo of R (the
-// misfit ||H x - d|| of the L-curve).
+// The blur y = H x (FP64 out) in the same two-float arithmetic: H = T_h (x) T_w,
+// the Kronecker product of the zero-boundary 1-D blurs, as two 1-D passes of the
+// 2R + 1 taps g over the 32 x 32 tile and a halo of R (pass 1 over the rows of
+// the staged tile, pass 2 down the columns at the owned pixels).
 template <int R>
 struct TapsG {
   float gh[2 * R + 1], gl[2 * R + 1];
