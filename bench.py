@@ -59,7 +59,6 @@ TRAFFIC = {
     "k_mr_tma<float,12>": {"dram_per_alg": 1.085, "src": "1c2c3fff45f90c26"},
 }
 
-E2E_BLOCK = 16   # shifts per device-to-host copy of solutions in the end-to-end timing
 
 OUTER_KEYS = ("init_solves", "update_vnew", "principal_setup", "shift_setup", "shift_minres",
               "fp64_residuals")
@@ -380,7 +379,6 @@ class Job:
         self.d_host = self.d.cpu().pin_memory()
         self.w_host = torch.ones(2 * wl.n, dtype=torch.float64).pin_memory()
         self.X_host = None
-        self.copy_stream = None
         self.plain = plain
         self.P = None
         self.k = 0
@@ -422,11 +420,10 @@ class Job:
         self.k = 0
 
     def prepare_e2e(self):
-        """The pinned host buffer for the solutions and the copy stream: allocated once,
-        outside any timed region (a caller keeps its host buffers across steps)."""
+        """The pinned host buffer for the solutions: allocated once, outside any timed
+        region (a caller keeps its host buffers across steps)."""
         if self.X_host is None:
             self.X_host = self.torch.empty(self.wl.M, self.wl.n, dtype=self.torch.float64).pin_memory()
-            self.copy_stream = self.torch.cuda.Stream(self.dev)
 
     def step(self, e2e=False):
         torch, recyc, wl = self.torch, self.recyc, self.wl
@@ -455,27 +452,18 @@ class Job:
         else:
             P.rs_update_recycle(recyc.RS_INIT if k == 0 else recyc.RS_UPDATE)
             if e2e:
-                # the solutions of each block of 16 shifts go back to the host on a copy
-                # stream while the next block solves (sub-range calls equal one call bit for bit)
-                stats = []
-                for l0 in range(0, wl.M, E2E_BLOCK):
-                    cnt = min(E2E_BLOCK, wl.M - l0)
-                    stats += P.rs_solve_shifts(self.X[l0:l0 + cnt], l0=l0, count=cnt)
-                    done = torch.cuda.Event()
-                    done.record(self.stream)
-                    self.copy_stream.wait_event(done)
-                    with torch.cuda.stream(self.copy_stream):
-                        self.X_host[l0:l0 + cnt].copy_(self.X[l0:l0 + cnt], non_blocking=True)
+                # every solution lands in the pinned host buffer as soon as it is final
+                # (the library's copy stream), while the next shifts solve; the call
+                # returns once the last one has landed
+                stats = P.rs_solve_shifts_host(self.X, self.X_host)
             else:
                 stats = P.rs_solve_shifts(self.X)
         _, _, ls = P.rs_lcurve(self.X, wl.M)
         P.rs_irn_weights(self.X[ls], wl.beta, self.w_next)
         self.w, self.w_next = self.w_next, self.w
         if e2e:
+            # on the job's stream: the step's closing event follows the copy
             self.w_host.copy_(self.w, non_blocking=True)
-            # the step ends when its copies have landed (and the next step must not
-            # overwrite X before they have read it)
-            self.stream.wait_stream(self.copy_stream)
             self.d2h += (self.X.numel() + self.w.numel()) * 8
         info = P.rs_get_info()
         self.k += 1
@@ -945,8 +933,8 @@ def main():
                        "h2d_bytes_per_step": job.h2d // args.steps, "d2h_bytes_per_step": job.d2h // args.steps,
                        "what": "data image (at k = 0) and weights w_k copied in from pinned host memory, all "
                                "solutions x^(k,.) and w_{k+1} copied back into pinned host memory, every step; "
-                               "the solutions of each block of 16 shifts on a copy stream while the next block "
-                               "solves, the step ending when every copy has landed",
+                               "each solution copied by rs_solve_shifts_host as soon as it is final while the "
+                               "next shifts solve, the step ending when every copy has landed",
                        "ms_per_outer_step_by_k": per_k(e_step_ms, e_res),
                        "matvecs_per_solve": sum(r["matvecs"] for r in e_res) /
                        max(1, sum(r["solves"] for r in e_res))}

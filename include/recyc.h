@@ -228,6 +228,19 @@ rs_status rs_set_recycle_basis(rs_problem* prob, const double* U_dev, int ncols)
 rs_status rs_solve_shifts(rs_problem* prob, int l0, int count, double* X_dev,
                           rs_solve_stats* stats_host, const int* iters_override_host);
 
+/* rs_solve_shifts that also delivers the solutions to host memory: X_host
+ * (count x n doubles, host memory; the caller owns it) receives what X_dev
+ * receives, each row copied on a stream of the problem's own as soon as that
+ * shift's solution is final, while the next shifts solve (all rows at once
+ * after a batched_local launch). Page-locked X_host lets the copies overlap the
+ * solves; pageable memory also works, each copy then holding the host thread
+ * until it lands. The call returns once every copy has landed (also on
+ * failure). The copy stream and its event are created on the first call and
+ * kept with the problem. Errors: those of rs_solve_shifts, RS_EINVAL for a NULL
+ * X_host, RS_ECUDA if the stream cannot be created. */
+rs_status rs_solve_shifts_host(rs_problem* prob, int l0, int count, double* X_dev, double* X_host,
+                               rs_solve_stats* stats_host, const int* iters_override_host);
+
 /* The comparison solver of the paper's experiments (Section 8): each shifted
  * system (A + gamma_l E_k) x = b of the current weights solved from x0 = 0 by
  * the inner solver of `inner` with no recycling at all (no principal space, no

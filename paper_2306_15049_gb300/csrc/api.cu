@@ -322,6 +322,12 @@ struct rs_problem {
   // host, dstage its device address): kernel stores, no copy engine
   unsigned char* hstage = nullptr;
   unsigned char* dstage = nullptr;
+  // rs_solve_shifts_host: the caller's host rows for the solutions of the call in
+  // progress (NULL otherwise), and the stream and event of their copies (created
+  // on first use)
+  double* x_host = nullptr;
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t cev = nullptr;
   cudaEvent_t pev[2] = {nullptr, nullptr};
   double* gcur = nullptr;
   double* partials_a = nullptr;
@@ -353,6 +359,8 @@ struct rs_problem {
       if (e) cudaEventDestroy(e);
     if (hpoll_pinned) cudaFreeHost(hpoll_pinned);
     if (hstage) cudaFreeHost(hstage);
+    if (cev) cudaEventDestroy(cev);
+    if (cstream) cudaStreamDestroy(cstream);
     if (cap) cudaStreamDestroy(cap);
   }
 
@@ -1406,6 +1414,16 @@ int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats
   // (a sub-range continues it); adjoint solves chain only within the call
   std::vector<char> gnz_adj(z.M, 0);
   std::vector<char>& gnz = adj ? gnz_adj : P->gcur_nz;
+  // rs_solve_shifts_host: row i goes to host memory on the copy stream once it is
+  // final (no later shift of the call writes it), while the next shifts solve
+  const auto hand_out = [&](int i) -> int {
+    if (!P->x_host) return RS_OK;
+    CU(cudaEventRecord(P->cev, s));
+    CU(cudaStreamWaitEvent(P->cstream, P->cev, 0));
+    CU(cudaMemcpyAsync(P->x_host + (long)i * n, X + (long)i * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                       P->cstream));
+    return RS_OK;
+  };
   for (int l = l0; l < l0 + count; ++l) {
     const int i = l - l0;           // position in the caller's X, stats, overrides
     const double gl = P->gammas[l];
@@ -1434,6 +1452,7 @@ int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats
       CU(cudaMemsetAsync(gl_buf, 0, n * sizeof(T), s));
       phase_end(P, 3, ph0);
       if (stats) stats[i] = sl;
+      RS(hand_out(i));
       continue;
     }
     CU(cudaMemcpyAsync(P->r64, P->R0blk + (long)(i % kGuessBatch) * ld, n * sizeof(double),
@@ -1461,6 +1480,7 @@ int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats
         sl.relres_est = sl.relres0;
         sl.sweeps = 0;
         if (stats) stats[i] = sl;
+        RS(hand_out(i));
         continue;
       }
       sl.relres0 = sl.relres_true;
@@ -1561,6 +1581,7 @@ int solve_all(rs_problem* P, int l0, int count, double* X, rs_solve_stats* stats
                     ? RS_ENOCONV : RS_OK;
     if (sl.status == RS_ENOCONV) any_noconv = 1;
     if (stats) stats[i] = sl;
+    RS(hand_out(i));
   }
   if (adj) return any_noconv ? P->set_err(RS_ENOCONV, "an adjoint shift reached maxit") : RS_OK;
   // x^(k,l) and g^(k,l) of the solved shifts are in Xcur and Gcur; rs_set_weights
@@ -2313,24 +2334,71 @@ rs_status rs_set_recycle_basis(rs_problem* P, const double* U_dev, int ncols) {
   return (rs_status)finish_principal<double>(P, ncols);
 }
 
-rs_status rs_solve_shifts(rs_problem* P, int l0, int count, double* X_dev, rs_solve_stats* stats_host,
-                          const int* iters_override_host) {
-  if (!P) return RS_EINVAL;
-  if (!P->have_recycle) return (rs_status)P->set_err(RS_ENOTREADY, "call rs_update_recycle first");
-  if (l0 < 0 || count < 1 || l0 > P->z.M - count)
-    return (rs_status)P->set_err(RS_EINVAL, "need 0 <= l0 and 1 <= count <= M - l0 (M = %d)", P->z.M);
-  if (!X_dev) return (rs_status)P->set_err(RS_EINVAL, "X_dev is NULL");
+namespace {
+// the shifted solves behind rs_solve_shifts and rs_solve_shifts_host (arguments checked)
+int solve_shifts(rs_problem* P, int l0, int count, double* X_dev, rs_solve_stats* stats_host,
+                 const int* iters_override_host) {
   // batched local spaces: every shift in one cooperative launch where it fits
   if (P->d.batched_local && P->use_batch && !iters_override_host && P->tp.radon.nang == 0 && l0 == 0 &&
       count == P->z.M) {
     const int cap = mr_batch_capacity(P->d.radius, P->mixed ? 4 : 8);
     if (cap >= P->z.M) {
-      if (P->mixed) return (rs_status)solve_batched<float>(P, X_dev, stats_host, cap);
-      return (rs_status)solve_batched<double>(P, X_dev, stats_host, cap);
+      const int rc = P->mixed ? solve_batched<float>(P, X_dev, stats_host, cap)
+                              : solve_batched<double>(P, X_dev, stats_host, cap);
+      // the shifts finish together: their rows go to the host in one copy
+      if (rc != RS_OK && rc != RS_ENOCONV) return rc;
+      if (P->x_host)
+        CU(cudaMemcpyAsync(P->x_host, X_dev, (size_t)count * P->z.n * sizeof(double), cudaMemcpyDeviceToHost,
+                           P->s));
+      return rc;
     }
   }
-  if (P->mixed) return (rs_status)solve_all<float>(P, l0, count, X_dev, stats_host, iters_override_host);
-  return (rs_status)solve_all<double>(P, l0, count, X_dev, stats_host, iters_override_host);
+  if (P->mixed) return solve_all<float>(P, l0, count, X_dev, stats_host, iters_override_host);
+  return solve_all<double>(P, l0, count, X_dev, stats_host, iters_override_host);
+}
+
+int check_solve_args(rs_problem* P, int l0, int count, const double* X_dev) {
+  if (!P->have_recycle) return P->set_err(RS_ENOTREADY, "call rs_update_recycle first");
+  if (l0 < 0 || count < 1 || l0 > P->z.M - count)
+    return P->set_err(RS_EINVAL, "need 0 <= l0 and 1 <= count <= M - l0 (M = %d)", P->z.M);
+  if (!X_dev) return P->set_err(RS_EINVAL, "X_dev is NULL");
+  return RS_OK;
+}
+}  // namespace
+
+rs_status rs_solve_shifts(rs_problem* P, int l0, int count, double* X_dev, rs_solve_stats* stats_host,
+                          const int* iters_override_host) {
+  if (!P) return RS_EINVAL;
+  if (const int r = check_solve_args(P, l0, count, X_dev)) return (rs_status)r;
+  return (rs_status)solve_shifts(P, l0, count, X_dev, stats_host, iters_override_host);
+}
+
+rs_status rs_solve_shifts_host(rs_problem* P, int l0, int count, double* X_dev, double* X_host,
+                               rs_solve_stats* stats_host, const int* iters_override_host) {
+  if (!P) return RS_EINVAL;
+  if (const int r = check_solve_args(P, l0, count, X_dev)) return (rs_status)r;
+  if (!X_host) return (rs_status)P->set_err(RS_EINVAL, "X_host is NULL");
+  if (!P->cstream) {
+    if (cudaStreamCreateWithFlags(&P->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+      P->cstream = nullptr;
+      return (rs_status)P->set_err(RS_ECUDA, "could not create the copy stream");
+    }
+    if (cudaEventCreateWithFlags(&P->cev, cudaEventDisableTiming) != cudaSuccess) {
+      P->cev = nullptr;
+      return (rs_status)P->set_err(RS_ECUDA, "could not create the copy event");
+    }
+  }
+  P->x_host = X_host;
+  const int rc = solve_shifts(P, l0, count, X_dev, stats_host, iters_override_host);
+  P->x_host = nullptr;
+  // every copy queued so far has landed (or the call failed) before the caller reads X_host
+  const cudaError_t e1 = cudaStreamSynchronize(P->cstream);
+  const cudaError_t e2 = cudaStreamSynchronize(P->s);
+  if (rc != RS_OK) return (rs_status)rc;
+  if (e1 != cudaSuccess || e2 != cudaSuccess)
+    return (rs_status)P->set_err(RS_ECUDA, "CUDA error %s after the solves",
+                                 cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+  return RS_OK;
 }
 
 size_t rs_batch_scratch_bytes(int count, int total_shifts) {

@@ -77,6 +77,7 @@ _SIGS = {
     "rs_update_recycle": (_I, [_P, _I]),
     "rs_set_recycle_basis": (_I, [_P, _P, _I]),
     "rs_solve_shifts": (_I, [_P, _I, _I, _P, ctypes.POINTER(rs_solve_stats), ctypes.POINTER(_I)]),
+    "rs_solve_shifts_host": (_I, [_P, _I, _I, _P, _P, ctypes.POINTER(rs_solve_stats), ctypes.POINTER(_I)]),
     "rs_initial_guesses": (_I, [_P, _P, _P]),
     "rs_solve_plain": (_I, [_P, _P, ctypes.POINTER(rs_solve_stats)]),
     "rs_solve_adjoint": (_I, [_P, _P, _P, ctypes.POINTER(rs_solve_stats)]),
@@ -258,6 +259,19 @@ class Problem:
         if iters_override is not None:
             ov = (ctypes.c_int * len(iters_override))(*[int(v) for v in iters_override])
         st = self.lib.rs_solve_shifts(self.h, int(l0), count, _ptr(X_dev), stats, ov)
+        self._check(st, (RS_OK, RS_ENOCONV) if allow_noconv else (RS_OK,))
+        return [dict((f, getattr(s, f)) for f, _ in rs_solve_stats._fields_) for s in stats[:count]]
+
+    def rs_solve_shifts_host(self, X_dev, X_host, iters_override: Optional[List[int]] = None,
+                             allow_noconv=False, l0: int = 0, count: Optional[int] = None):
+        """rs_solve_shifts, each solution also copied into the host tensor X_host
+        (count rows; page-locked for overlap) as soon as it is final."""
+        count = self.M - l0 if count is None else int(count)
+        stats = (rs_solve_stats * max(count, 1))()
+        ov = None
+        if iters_override is not None:
+            ov = (ctypes.c_int * len(iters_override))(*[int(v) for v in iters_override])
+        st = self.lib.rs_solve_shifts_host(self.h, int(l0), count, _ptr(X_dev), _ptr(X_host), stats, ov)
         self._check(st, (RS_OK, RS_ENOCONV) if allow_noconv else (RS_OK,))
         return [dict((f, getattr(s, f)) for f, _ in rs_solve_stats._fields_) for s in stats[:count]]
 

@@ -75,3 +75,38 @@ def test_incomplete_step_does_not_hand_over_and_bad_ranges_are_rejected():
     pr.P.rs_update_recycle(0)                             # a fresh principal space still works
     st = pr.P.rs_solve_shifts(X)
     assert all(s["relres_true"] <= wl.tol * (1 + 1e-6) for s in st)
+
+
+@pytest.mark.parametrize("precision,batched,pinned", [(0, 0, True), (1, 0, True), (1, 0, False), (0, 1, True)])
+def test_solutions_delivered_to_host_equal_the_device_solve(precision, batched, pinned):
+    """rs_solve_shifts_host: the host rows (copied as each shift finishes, or after
+    the one batched launch) equal the device rows bit for bit, and both equal an
+    rs_solve_shifts call on an identical problem; sub-ranges work the same way."""
+    from paper_2306_15049_gb300 import recyc
+    wl = synth.tiny(40, 36, sigma=1.5, radius=4, M=7, p=8, n_ritz_local=3, seed=33, tol=1e-9)
+    ref = Pair(wl, precision=precision, batched_local=batched)
+    hst = Pair(wl, precision=precision, batched_local=batched)
+    torch = ref.torch
+    for k, w in enumerate([np.ones(2 * wl.n), synth.random_weights(wl.n, 9, lo=1.0, hi=1000.0)]):
+        for pr in (ref, hst):
+            pr.P.rs_set_weights(pr.t(w))
+            pr.P.rs_update_recycle(0 if k == 0 else 1)
+        X1 = torch.empty(wl.M, wl.n, dtype=torch.float64, device=ref.dev)
+        st1 = ref.P.rs_solve_shifts(X1)
+        X2 = torch.empty_like(X1)
+        H2 = torch.full((wl.M, wl.n), np.nan, dtype=torch.float64)
+        if pinned:
+            H2 = H2.pin_memory()
+        if k == 0:
+            st2 = hst.P.rs_solve_shifts_host(X2, H2)
+        else:
+            st2 = (hst.P.rs_solve_shifts_host(X2[:3], H2[:3], l0=0, count=3) +
+                   hst.P.rs_solve_shifts_host(X2[3:], H2[3:], l0=3, count=4))
+        np.testing.assert_array_equal(H2.numpy(), hst.n(X2))
+        if not (batched and k == 1):      # batched: the sub-ranges run shift by shift
+            np.testing.assert_array_equal(hst.n(X2), ref.n(X1))
+            assert [s["iters"] for s in st2] == [s["iters"] for s in st1]
+        assert all(s["relres_true"] <= wl.tol * (1 + 1e-6) for s in st2)
+    with pytest.raises(recyc.RecycError) as e:
+        hst.P.rs_solve_shifts_host(X2, None)
+    assert e.value.status == recyc.RS_EINVAL
